@@ -1,0 +1,231 @@
+/*
+ * ising.h -- C ABI of the GB300 Ising max-cut annealer.
+ *
+ * The library anneals the Ising form of a max-cut problem on a general sparse
+ * weighted graph, following Cook, Zhao, Sato, Hiromoto and Tan, "GPU Ising
+ * Computing for Combinatorial Optimization Problems in VLSI Physical Design":
+ *
+ *   max-cut objective (Eq. 4):  cut(s) = 1/2 sum_{i<j} w_ij (1 - s_i s_j)
+ *   Ising energy (Eq. 3 and 5, with J = -w so that low energy = large cut):
+ *                               H(s) = sum_{(i,j) in E} w_ij s_i s_j,
+ *                               cut(s) = (W - H(s)) / 2,  W = sum_{(i,j)} w_ij
+ *   local field and update (Eq. 2):  f_i = sum_j w_ij s_j;
+ *                               s_i <- -1 if f_i > 0, +1 if f_i < 0,
+ *                               unchanged if f_i = 0
+ *   annealing (Algorithm 2):    every sweep updates every spin, and right after
+ *                               its own update each spin flips with probability
+ *                               F_p; F_p decreases from sweep to sweep.
+ *
+ * Spins, weights, fields, energies and cuts are exact integers. Nothing here
+ * uses floating point inside a sweep.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Every function returns an int status (ISING_OK or a negative ISING_E*
+ *    code); ising_strerror() names it. No C++ exception crosses this ABI.
+ *  - A handle owns all device memory it uses. Input arrays passed to a call are
+ *    only read during that call (the caller keeps ownership).
+ *  - Device work runs on the handle's CUDA stream: the stream given to
+ *    ising_create(), replaced by the stream given to each ising_anneal() call.
+ *    NULL means the legacy default stream. Calls that return a value to the
+ *    host (ising_cut, ising_energy, ising_get_spins to host memory) synchronise
+ *    that stream.
+ *  - A handle is not thread-safe: calls on one handle must be serialised.
+ *    Different handles are independent.
+ *  - After a CUDA error the handle latches ISING_ECUDA and every later call on
+ *    it returns ISING_ECUDA; destroy it.
+ *  - Vertex ids in every array that crosses this ABI are the caller's original
+ *    ids 0..n-1; the internal reordering is invisible.
+ */
+#ifndef ISING_H
+#define ISING_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ising_graph ising_graph; /* opaque */
+
+/* Status codes. */
+enum {
+  ISING_OK = 0,
+  ISING_EINVAL = -1,   /* invalid argument (null pointer, bad id, self-loop, bad spin value ...) */
+  ISING_ENOMEM = -2,   /* host or device allocation failed */
+  ISING_ECUDA = -3,    /* a CUDA call failed; latched in the handle */
+  ISING_ETIMEOUT = -4, /* a bounded device-side wait gave up; the result is invalid */
+  ISING_ESTATE = -5,   /* call not valid in the handle's current state */
+  ISING_ERANGE = -6    /* sizes or weights beyond the supported range */
+};
+
+/* Annealing modes. */
+enum {
+  /* Colour classes are swept one after another in increasing colour order (the
+   * checkerboard scheme of Sec. IV-B generalised to a greedy colouring); no two
+   * vertices of a class are adjacent, so the result is a deterministic function
+   * of (graph, initial spins, schedule, seed) and matches the CPU oracle bit
+   * for bit. */
+  ISING_MODE_DET = 0,
+  /* The paper's asynchronous update (Sec. IV-B): one pass over all spins per
+   * sweep with no ordering inside the sweep; each update reads whatever
+   * neighbour values are in memory at that moment. Results depend on hardware
+   * scheduling and are judged by cut value only. */
+  ISING_MODE_RACY = 1
+};
+
+/* Schedules. */
+enum {
+  /* Flip probability F_p decays linearly from p0 at sweep 0 to 0 at sweep
+   * t_total - 1 (Sec. V-A: linear decay; Algorithm 2: "reduce F_p"). It is
+   * applied as a 32-bit integer threshold:
+   *   T0     = floor(p0 * 2^32 + 0.5) clamped to [0, 2^32 - 1]
+   *   thr[t] = t_total <= 1 ? 0 : floor(T0 * (t_total - 1 - t) / (t_total - 1))
+   * and spin i flips in sweep t iff x < thr[t], where x is word 0 of
+   * Philox4x32-10 (Salmon et al., SC'11) with
+   *   key     = (lo32(seed), hi32(seed))
+   *   counter = (original id of i, t, replica, 0).                        */
+  ISING_SCHED_LINEAR = 0
+};
+
+/* Which kernel engine runs a deterministic anneal (all give identical spins). */
+enum {
+  ISING_ENGINE_AUTO = 0,       /* the library picks */
+  ISING_ENGINE_PHASE = 1,      /* one kernel launch per colour class */
+  ISING_ENGINE_PERSISTENT = 2  /* one cooperative launch per anneal call, bounded grid barrier */
+};
+
+/* ising_create flags. */
+enum {
+  /* Keep 32-bit weights on the device even when every merged weight fits in
+   * 8 bits (by default such graphs store int8 weights). */
+  ISING_CREATE_WEIGHTS_I32 = 1u << 0
+};
+
+typedef struct ising_schedule {
+  uint32_t kind;    /* ISING_SCHED_LINEAR */
+  uint32_t replica; /* counter word 2 of every Philox draw (independent replicas) */
+  double p0;        /* initial flip probability, 0 <= p0 <= 1 */
+  uint64_t t_begin; /* index of the first sweep this call runs, within the schedule */
+  uint64_t t_total; /* length T of the whole schedule; t_begin + sweeps <= T < 2^32 */
+} ising_schedule;
+
+/*
+ * ising_create -- build the device-resident problem from an undirected edge list
+ * (the max-cut instance of Sec. III, Eq. 4).
+ *
+ *   n        number of vertices, 1 <= n < 2^31.
+ *   m        number of listed edges, 0 <= m < 2^30.
+ *   src,dst  host int32[m]: edge endpoints, ids in [0, n), src[e] != dst[e].
+ *            Each undirected edge may be listed in either orientation; edges
+ *            listed more than once are merged by summing their weights, and a
+ *            merged weight of 0 removes the edge.
+ *   w        host int32[m]: edge weights (J_ij = w_ij). For every vertex the sum
+ *            of |merged weight| over its edges must be < 2^31 (so every local
+ *            field fits in int32).
+ *   flags    ISING_CREATE_* bits.
+ *   cuda_stream  cudaStream_t used for the upload and later calls (NULL: default).
+ *   out      receives the handle.
+ *
+ * The host colours the graph greedily (largest degree first, ties by smaller
+ * id; first fit), orders vertices by colour, and uploads a CSR adjacency
+ * (int32 column indices, int8 or int32 weights). Spins start at +1; call
+ * ising_init_random() or ising_set_spins() to choose them.
+ * Errors: ISING_EINVAL (null pointer, id out of range, self-loop, n <= 0, m < 0),
+ * ISING_ERANGE (n, m or a field bound too large), ISING_ENOMEM, ISING_ECUDA.
+ * On error *out is set to NULL and nothing is leaked.
+ */
+int ising_create(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, const int32_t* w,
+                 uint32_t flags, void* cuda_stream, ising_graph** out);
+
+/*
+ * ising_anneal -- run `sweeps` sweeps t = t_begin .. t_begin+sweeps-1 of the
+ * schedule (Algorithm 2), updating the handle's spins in place.
+ *
+ *   sched        schedule (see ising_schedule); copied.
+ *   sweeps       number of sweeps this call runs (0 is a no-op).
+ *   seed         64-bit Philox key.
+ *   mode         ISING_MODE_DET or ISING_MODE_RACY.
+ *   cuda_stream  becomes the handle's stream.
+ *
+ * Because the random numbers are counter-based, running t = 0..k-1 and then
+ * t = k..T-1 gives exactly the spins of one call over 0..T-1 (resume).
+ * Asynchronous: returns once the work is enqueued (no host synchronisation).
+ * Errors: ISING_EINVAL (null handle/schedule, p0 outside [0,1], unknown kind or
+ * mode, t_begin + sweeps > t_total, t_total >= 2^32), ISING_ECUDA,
+ * ISING_ETIMEOUT (persistent engine only; reported by a later synchronising call).
+ */
+int ising_anneal(ising_graph* g, const ising_schedule* sched, uint32_t sweeps, uint64_t seed,
+                 int mode, void* cuda_stream);
+
+/*
+ * ising_energy -- H(s) = sum over merged undirected edges of w_ij s_i s_j
+ * (Eq. 3/5 with J = -w), computed from scratch in int64. Synchronises the stream.
+ */
+int ising_energy(ising_graph* g, int64_t* out_energy);
+
+/*
+ * ising_cut -- cut(s) = (W - H(s)) / 2, the Eq. 4 objective of the current
+ * spins, exact int64. Synchronises the stream.
+ */
+int ising_cut(ising_graph* g, int64_t* out_cut);
+
+/* ising_total_weight -- W, the sum of the merged edge weights (host value). */
+int ising_total_weight(ising_graph* g, int64_t* out_w);
+
+/*
+ * ising_get_spins / ising_set_spins -- copy the spins out / in, int8[n] in the
+ * caller's vertex order, values +1 / -1. `on_device` = 1 if the pointer is a
+ * device pointer (e.g. a torch tensor's data_ptr()), 0 for host memory.
+ * ising_get_spins to host synchronises the stream. ising_set_spins rejects any
+ * value other than +1/-1 with ISING_EINVAL (device input: reported by the call
+ * itself, which then synchronises the stream), leaving the spins unchanged.
+ */
+int ising_get_spins(ising_graph* g, int8_t* out, int on_device);
+int ising_set_spins(ising_graph* g, const int8_t* in, int on_device);
+
+/*
+ * ising_init_random -- initial spins (Algorithm 2, "initialize all sigma_i"):
+ * s_i = -1 if bit 31 of Philox word 0 with counter (i, 0, replica, 1) and key
+ * (lo32(seed), hi32(seed)) is set, else +1.
+ */
+int ising_init_random(ising_graph* g, uint64_t seed, uint32_t replica);
+
+/* ising_num_colours / ising_colouring -- the greedy colouring the deterministic
+ * mode sweeps in (int32[n] colour per original vertex id; host memory). */
+int ising_num_colours(ising_graph* g, int32_t* out);
+int ising_colouring(ising_graph* g, int32_t* out_colour);
+
+/*
+ * ising_plan_colouring -- host-only (no GPU, no handle): the colouring that
+ * ising_create would build for this edge list, with the same validation and
+ * merging rules. out_colour: host int32[n]; out_num_colours: host int32.
+ * Errors as ising_create (except ISING_ECUDA / ISING_ENOMEM on the device).
+ */
+int ising_plan_colouring(int32_t n, int64_t m, const int32_t* src, const int32_t* dst,
+                         const int32_t* w, int32_t* out_colour, int32_t* out_num_colours);
+
+/* ising_num_edges -- number of merged undirected edges (after removing zero
+ * weights). */
+int ising_num_edges(ising_graph* g, int64_t* out_m);
+
+/* ising_set_engine -- choose the deterministic-mode kernel engine
+ * (ISING_ENGINE_*). Default ISING_ENGINE_AUTO. */
+int ising_set_engine(ising_graph* g, int engine);
+
+/* ising_launch_count -- number of CUDA kernels this handle has launched since
+ * ising_create (a diagnostic for benchmarks). */
+int ising_launch_count(ising_graph* g, uint64_t* out);
+
+/* ising_destroy -- free the handle and its device memory (NULL is ignored).
+ * Waits for the handle's outstanding work first. */
+void ising_destroy(ising_graph* g);
+
+/* ising_strerror -- static description of a status code. */
+const char* ising_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ISING_H */

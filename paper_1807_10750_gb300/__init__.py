@@ -1,0 +1,265 @@
+"""GB300 Ising max-cut annealer: thin Python binding of ``include/ising.h``.
+
+Every function here marshals arguments and calls the C ABI of
+``libising_gb300.so`` (built in-tree by ``paper_1807_10750_gb300._build``);
+all compute runs in the library's CUDA kernels. There is no CPU fallback: if
+the library is missing, :func:`lib` raises.
+
+Device buffers may be torch CUDA tensors (their ``data_ptr()`` is passed with
+``on_device=1``); streams may be ``torch.cuda.Stream`` objects or raw
+``cudaStream_t`` integers.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libising_gb300.so")
+
+ISING_OK = 0
+ISING_EINVAL = -1
+ISING_ENOMEM = -2
+ISING_ECUDA = -3
+ISING_ETIMEOUT = -4
+ISING_ESTATE = -5
+ISING_ERANGE = -6
+
+ISING_MODE_DET = 0
+ISING_MODE_RACY = 1
+ISING_SCHED_LINEAR = 0
+ISING_ENGINE_AUTO = 0
+ISING_ENGINE_PHASE = 1
+ISING_ENGINE_PERSISTENT = 2
+ISING_CREATE_WEIGHTS_I32 = 1
+
+# Every entry point declared in include/ising.h.
+EXPORTS = (
+    "ising_create", "ising_anneal", "ising_energy", "ising_cut", "ising_total_weight",
+    "ising_get_spins", "ising_set_spins", "ising_init_random", "ising_num_colours",
+    "ising_colouring", "ising_num_edges", "ising_set_engine", "ising_destroy",
+    "ising_strerror", "ising_plan_colouring", "ising_launch_count",
+)
+
+
+class IsingError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {strerror(code)} ({code})")
+
+
+class ising_schedule(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_uint32), ("replica", ctypes.c_uint32), ("p0", ctypes.c_double),
+                ("t_begin", ctypes.c_uint64), ("t_total", ctypes.c_uint64)]
+
+
+_lib = None
+
+
+def lib():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with "
+                              "`python -m paper_1807_10750_gb300._build` (needs nvcc)")
+        L = ctypes.CDLL(LIB_PATH)
+        vp = ctypes.c_void_p
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        L.ising_create.argtypes = [ctypes.c_int32, ctypes.c_int64, vp, vp, vp, ctypes.c_uint32, vp,
+                                   ctypes.POINTER(vp)]
+        L.ising_anneal.argtypes = [vp, ctypes.POINTER(ising_schedule), ctypes.c_uint32,
+                                   ctypes.c_uint64, ctypes.c_int, vp]
+        L.ising_energy.argtypes = [vp, i64p]
+        L.ising_cut.argtypes = [vp, i64p]
+        L.ising_total_weight.argtypes = [vp, i64p]
+        L.ising_get_spins.argtypes = [vp, vp, ctypes.c_int]
+        L.ising_set_spins.argtypes = [vp, vp, ctypes.c_int]
+        L.ising_init_random.argtypes = [vp, ctypes.c_uint64, ctypes.c_uint32]
+        L.ising_num_colours.argtypes = [vp, i32p]
+        L.ising_colouring.argtypes = [vp, i32p]
+        L.ising_num_edges.argtypes = [vp, i64p]
+        L.ising_set_engine.argtypes = [vp, ctypes.c_int]
+        L.ising_destroy.argtypes = [vp]
+        L.ising_destroy.restype = None
+        L.ising_plan_colouring.argtypes = [ctypes.c_int32, ctypes.c_int64, vp, vp, vp, i32p, i32p]
+        L.ising_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
+        L.ising_strerror.argtypes = [ctypes.c_int]
+        L.ising_strerror.restype = ctypes.c_char_p
+        for name in EXPORTS:
+            if name not in ("ising_destroy", "ising_strerror"):
+                getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def strerror(code: int) -> str:
+    return lib().ising_strerror(code).decode()
+
+
+def _check(code: int, what: str):
+    if code != ISING_OK:
+        raise IsingError(code, what)
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return int(stream.cuda_stream)
+    return int(stream)
+
+
+def _buffer(x, dtype, n: int | None, writable: bool):
+    """(pointer, on_device, keepalive) for a numpy array or torch tensor."""
+    if hasattr(x, "data_ptr") and hasattr(x, "is_cuda"):
+        import torch  # only when a tensor is passed
+        want = {np.int8: torch.int8, np.int32: torch.int32}[dtype]
+        if x.dtype != want:
+            raise TypeError(f"expected a {want} tensor")
+        if not x.is_contiguous() or (n is not None and x.numel() != n):
+            raise ValueError("tensor must be contiguous with the expected length")
+        return ctypes.c_void_p(x.data_ptr()), int(x.is_cuda), x
+    a = np.asarray(x)
+    if a.dtype != dtype or not a.flags.c_contiguous or (writable and not a.flags.writeable):
+        if writable:
+            raise TypeError(f"expected a writable contiguous {np.dtype(dtype).name} array")
+        a = np.ascontiguousarray(a, dtype=dtype)
+    if n is not None and a.size != n:
+        raise ValueError(f"expected {n} elements, got {a.size}")
+    return ctypes.c_void_p(a.ctypes.data), 0, a
+
+
+class IsingGraph:
+    """Owning wrapper of an ``ising_graph*`` handle (``ising_destroy`` on close)."""
+
+    def __init__(self, ptr: int, n: int):
+        self.ptr = ctypes.c_void_p(ptr)
+        self.n = n
+
+    def close(self):
+        if self.ptr and self.ptr.value:
+            lib().ising_destroy(self.ptr)
+            self.ptr = ctypes.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def ising_create(n: int, src, dst, w, flags: int = 0, stream=None) -> IsingGraph:
+    ps, _, ks = _buffer(src, np.int32, None, False)
+    m = ks.size if hasattr(ks, "size") else ks.numel()
+    pd, _, kd = _buffer(dst, np.int32, m, False)
+    pw, _, kw = _buffer(w, np.int32, m, False)
+    out = ctypes.c_void_p()
+    _check(lib().ising_create(n, m, ps, pd, pw, flags, _stream(stream), ctypes.byref(out)),
+           "ising_create")
+    return IsingGraph(out.value, n)
+
+
+def ising_anneal(g: IsingGraph, *, p0: float, t_total: int, sweeps: int | None = None,
+                 seed: int, mode: int = ISING_MODE_DET, t_begin: int = 0, replica: int = 0,
+                 stream=None, kind: int = ISING_SCHED_LINEAR) -> None:
+    if sweeps is None:
+        sweeps = t_total - t_begin
+    sched = ising_schedule(kind, replica, p0, t_begin, t_total)
+    _check(lib().ising_anneal(g.ptr, ctypes.byref(sched), sweeps, seed & (2 ** 64 - 1), mode,
+                              _stream(stream)), "ising_anneal")
+
+
+def ising_energy(g: IsingGraph) -> int:
+    v = ctypes.c_int64()
+    _check(lib().ising_energy(g.ptr, ctypes.byref(v)), "ising_energy")
+    return v.value
+
+
+def ising_cut(g: IsingGraph) -> int:
+    v = ctypes.c_int64()
+    _check(lib().ising_cut(g.ptr, ctypes.byref(v)), "ising_cut")
+    return v.value
+
+
+def ising_total_weight(g: IsingGraph) -> int:
+    v = ctypes.c_int64()
+    _check(lib().ising_total_weight(g.ptr, ctypes.byref(v)), "ising_total_weight")
+    return v.value
+
+
+def ising_num_edges(g: IsingGraph) -> int:
+    v = ctypes.c_int64()
+    _check(lib().ising_num_edges(g.ptr, ctypes.byref(v)), "ising_num_edges")
+    return v.value
+
+
+def ising_get_spins(g: IsingGraph, out=None):
+    """Spins in caller order; into ``out`` (numpy int8 or torch int8 tensor) if
+    given, else a new numpy array."""
+    if out is None:
+        out = np.empty(g.n, dtype=np.int8)
+    p, on_dev, keep = _buffer(out, np.int8, g.n, True)
+    _check(lib().ising_get_spins(g.ptr, p, on_dev), "ising_get_spins")
+    return out
+
+
+def ising_set_spins(g: IsingGraph, spins) -> None:
+    p, on_dev, keep = _buffer(spins, np.int8, g.n, False)
+    _check(lib().ising_set_spins(g.ptr, p, on_dev), "ising_set_spins")
+
+
+def ising_init_random(g: IsingGraph, seed: int, replica: int = 0) -> None:
+    _check(lib().ising_init_random(g.ptr, seed & (2 ** 64 - 1), replica), "ising_init_random")
+
+
+def ising_num_colours(g: IsingGraph) -> int:
+    v = ctypes.c_int32()
+    _check(lib().ising_num_colours(g.ptr, ctypes.byref(v)), "ising_num_colours")
+    return v.value
+
+
+def ising_colouring(g: IsingGraph) -> np.ndarray:
+    out = np.empty(g.n, dtype=np.int32)
+    _check(lib().ising_colouring(g.ptr, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))),
+           "ising_colouring")
+    return out
+
+
+def ising_plan_colouring(n: int, src, dst, w):
+    """Host-only: (number of colours, colour per vertex) that ising_create would
+    use for this edge list. Needs no GPU."""
+    ps, _, ks = _buffer(src, np.int32, None, False)
+    m = ks.size
+    pd, _, kd = _buffer(dst, np.int32, m, False)
+    pw, _, kw = _buffer(w, np.int32, m, False)
+    out = np.empty(max(n, 0), dtype=np.int32)
+    C = ctypes.c_int32()
+    _check(lib().ising_plan_colouring(n, m, ps, pd, pw,
+                                      out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                      ctypes.byref(C)), "ising_plan_colouring")
+    return C.value, out
+
+
+def ising_set_engine(g: IsingGraph, engine: int) -> None:
+    _check(lib().ising_set_engine(g.ptr, engine), "ising_set_engine")
+
+
+def ising_launch_count(g: IsingGraph) -> int:
+    v = ctypes.c_uint64()
+    _check(lib().ising_launch_count(g.ptr, ctypes.byref(v)), "ising_launch_count")
+    return v.value
+
+
+def ising_destroy(g: IsingGraph) -> None:
+    g.close()

@@ -1,0 +1,882 @@
+// Sweep kernels and the C ABI of include/ising.h.
+//
+// Layout in device memory (all owned by the handle):
+//   row_ptr  int32[n+1]   CSR offsets, vertices ordered by colour class
+//   col      int32[nnz]   neighbour positions (rows sorted ascending)
+//   w        int8[nnz] or int32[nnz]   merged edge weights J_ij = w_ij
+//   spins    int8[n]      +1 / -1 by position
+//   orig     int32[n]     position -> caller's vertex id (Philox counter word 0)
+//   pos      int32[n]     caller's vertex id -> position
+//   items    WorkItem[]   per-class warp work (see host_graph.h)
+//   split_*  int32[slots] partial-field combine for rows sliced across warps
+//
+// One warp processes one work item: the local fields f_i = sum_j w_ij s_j of
+// its rows (Eq. 2), gathered by sub-warp lane groups sized to the rows'
+// degree, then one lane per row applies the update rule and the random flip
+// of Algorithm 2.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/ising.h"
+#include "host_graph.h"
+#include "philox.cuh"
+
+using isingx::HostGraph;
+using isingx::PhiloxKey;
+using isingx::WorkItem;
+using isingx::WorkPlan;
+
+namespace {
+
+constexpr unsigned kFullMask = 0xffffffffu;
+constexpr int kBlock = 256;
+constexpr int kWarpsPerBlock = kBlock / 32;
+
+enum ItemPass { kPassDet = 0, kPassRacy = 1, kPassEnergy = 2 };
+
+struct DevGraph {
+  const int32_t* row_ptr;
+  const int32_t* col;
+  const void* w;
+  int8_t* spins;
+  const int32_t* orig;
+  const WorkItem* items;
+  int32_t* split_acc;
+  int32_t* split_cnt;
+  const int32_t* split_parts;
+};
+
+struct SweepArgs {
+  uint32_t thr;      // flip iff word < thr
+  uint32_t t;        // sweep index (counter word 1)
+  uint32_t replica;  // counter word 2
+  PhiloxKey key;
+};
+
+// Racy mode: neighbour reads and own writes race by design (Sec. IV-B); they
+// are relaxed atomics at GPU scope so the races are defined behaviour.
+__device__ __forceinline__ int ld_relaxed_s8(const int8_t* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.s8 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_s8(int8_t* p, int v) {
+  asm volatile("st.relaxed.gpu.global.s8 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+template <int PASS>
+__device__ __forceinline__ int spin_at(const DevGraph& d, int j) {
+  return (PASS == kPassRacy) ? ld_relaxed_s8(d.spins + j) : static_cast<int>(d.spins[j]);
+}
+
+// sum of w_e * s_col[e] over e = e0, e0 + step, ... < e1, four edges per round
+// so that each lane keeps several loads in flight.
+template <typename WT, int PASS>
+__device__ __forceinline__ int strided_field(const DevGraph& d, int e0, int e1, int step) {
+  int f = 0;
+  for (int e = e0; e < e1; e += 4 * step) {
+    int cj[4], wj[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int x = e + u * step;
+      const bool ok = x < e1;
+      cj[u] = ok ? __ldg(d.col + x) : -1;
+      wj[u] = ok ? static_cast<int>(__ldg(static_cast<const WT*>(d.w) + x)) : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (cj[u] >= 0) f += wj[u] * spin_at<PASS>(d, cj[u]);
+  }
+  return f;
+}
+
+// Eq. 2 under the max-cut sign (s <- -sign f, tie keeps), then Algorithm 2's
+// flip with probability thr / 2^32 keyed by the caller's vertex id.
+template <int PASS>
+__device__ __forceinline__ void update_spin(const DevGraph& d, int v, int f, const SweepArgs& a) {
+  int s = (PASS == kPassRacy) ? ld_relaxed_s8(d.spins + v) : static_cast<int>(d.spins[v]);
+  if (f > 0)
+    s = -1;
+  else if (f < 0)
+    s = 1;
+  if (a.thr != 0u) {
+    const uint32_t o = static_cast<uint32_t>(__ldg(d.orig + v));
+    if (isingx::philox4x32_10_word0(o, a.t, a.replica, 0u, a.key) < a.thr) s = -s;
+  }
+  if (PASS == kPassRacy)
+    st_relaxed_s8(d.spins + v, s);
+  else
+    d.spins[v] = static_cast<int8_t>(s);
+}
+
+constexpr int kRowsPerLane = 4;  // work items hold at most 32 * kRowsPerLane rows
+constexpr int kLightMeanDegree = 16;
+
+// Light rows (mean degree <= kLightMeanDegree): one lane per row, up to
+// kRowsPerLane rows per lane, all row offsets, then all column/weight loads,
+// then all neighbour-spin gathers issued together (three memory round trips
+// for rows of degree <= 4).
+template <typename WT, int PASS>
+__device__ __forceinline__ void run_light_rows(const DevGraph& d, const WorkItem& it,
+                                               const SweepArgs& a, int lane, long long& energy) {
+  int rp[kRowsPerLane], re[kRowsPerLane], f[kRowsPerLane];
+#pragma unroll
+  for (int r = 0; r < kRowsPerLane; ++r) {
+    const int v = it.v_begin + lane + 32 * r;
+    rp[r] = 0;
+    re[r] = 0;
+    f[r] = 0;
+    if (v < it.v_end) {
+      rp[r] = __ldg(d.row_ptr + v);
+      re[r] = __ldg(d.row_ptr + v + 1);
+    }
+  }
+  int kmax = 0;
+#pragma unroll
+  for (int r = 0; r < kRowsPerLane; ++r) kmax = max(kmax, re[r] - rp[r]);
+  for (int k = 0; k < kmax; k += 4) {
+    int cj[kRowsPerLane][4], wj[kRowsPerLane][4];
+#pragma unroll
+    for (int r = 0; r < kRowsPerLane; ++r)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = rp[r] + k + u;
+        const bool ok = e < re[r];
+        cj[r][u] = ok ? __ldg(d.col + e) : -1;
+        wj[r][u] = ok ? static_cast<int>(__ldg(static_cast<const WT*>(d.w) + e)) : 0;
+      }
+#pragma unroll
+    for (int r = 0; r < kRowsPerLane; ++r)
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (cj[r][u] >= 0) f[r] += wj[r][u] * spin_at<PASS>(d, cj[r][u]);
+  }
+#pragma unroll
+  for (int r = 0; r < kRowsPerLane; ++r) {
+    const int v = it.v_begin + lane + 32 * r;
+    if (v < it.v_end) {
+      if (PASS == kPassEnergy)
+        energy += static_cast<long long>(d.spins[v]) * f[r];
+      else
+        update_spin<PASS>(d, v, f[r], a);
+    }
+  }
+}
+
+template <typename WT, int PASS>
+__device__ __forceinline__ void run_item(const DevGraph& d, const WorkItem it, const SweepArgs& a,
+                                         int lane, long long& energy) {
+  if (it.v_end < 0) {
+    // A slice of one heavy row: partial field, combined across slices by the
+    // last slice to finish (integer sums, so the order does not matter).
+    const int v = it.v_begin;
+    int f = strided_field<WT, PASS>(d, it.e_begin + lane, it.e_end, 32);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(kFullMask, f, o);
+    if (PASS == kPassEnergy) {
+      if (lane == 0) energy += static_cast<long long>(d.spins[v]) * f;
+      return;
+    }
+    if (lane == 0) {
+      const int slot = -it.v_end - 1;
+      atomicAdd(d.split_acc + slot, f);
+      __threadfence();
+      const int ticket = atomicAdd(d.split_cnt + slot, 1);
+      if (ticket == d.split_parts[slot] - 1) {
+        __threadfence();
+        const int total = atomicExch(d.split_acc + slot, 0);
+        d.split_cnt[slot] = 0;
+        update_spin<PASS>(d, v, total, a);
+      }
+    }
+    return;
+  }
+  const int nv = it.v_end - it.v_begin;
+  if (it.e_end - it.e_begin <= kLightMeanDegree * nv) {
+    run_light_rows<WT, PASS>(d, it, a, lane, energy);
+    return;
+  }
+  // Heavier rows: lane groups of g lanes (power of two >= a quarter of the
+  // mean degree) each gather one row per pass; 32 / g rows per pass.
+  const int mean = (it.e_end - it.e_begin + nv - 1) / nv;
+  int lg = 0;
+  while ((4 << lg) < mean && lg < 5) ++lg;
+  const int g = 1 << lg;
+  const int rows_per_pass = 32 >> lg;
+  const int sub = lane & (g - 1);
+  const int grp = lane >> lg;
+  for (int base = it.v_begin; base < it.v_end; base += 32) {
+    const int rows = min(32, it.v_end - base);
+    const int passes = (rows + rows_per_pass - 1) / rows_per_pass;
+    int my_f = 0;
+    for (int p = 0; p < passes; ++p) {
+      const int v = base + p * rows_per_pass + grp;
+      int f = 0;
+      if (v < it.v_end)
+        f = strided_field<WT, PASS>(d, __ldg(d.row_ptr + v) + sub, __ldg(d.row_ptr + v + 1), g);
+      for (int o = g >> 1; o > 0; o >>= 1) f += __shfl_xor_sync(kFullMask, f, o);
+      const int got = __shfl_sync(kFullMask, f, (lane % rows_per_pass) << lg);
+      if (lane / rows_per_pass == p) my_f = got;
+    }
+    const int v = base + lane;
+    if (v < it.v_end) {
+      if (PASS == kPassEnergy)
+        energy += static_cast<long long>(d.spins[v]) * my_f;
+      else
+        update_spin<PASS>(d, v, my_f, a);
+    }
+  }
+}
+
+// Item kernel of the per-launch engine. Deterministic sweeps launch it once
+// per colour class (phase_begin + 1 == phase_end); the racy mode launches it
+// once per sweep over every class, each warp walking the classes in order with
+// no wait between them; the energy pass covers all items.
+template <typename WT, int PASS>
+__global__ void __launch_bounds__(kBlock, 4)
+    items_kernel(DevGraph d, const int32_t* __restrict__ phase_items, int phase_begin,
+                 int phase_end, SweepArgs a, unsigned long long* energy_out) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * kBlock + threadIdx.x) >> 5;
+  const int nwarps = gridDim.x * kWarpsPerBlock;
+  long long energy = 0;
+  for (int c = phase_begin; c < phase_end; ++c) {
+    const int ie = __ldg(phase_items + c + 1);
+    for (int i = __ldg(phase_items + c) + warp; i < ie; i += nwarps) {
+      const WorkItem it = d.items[i];
+      run_item<WT, PASS>(d, it, a, lane, energy);
+    }
+  }
+  if (PASS == kPassEnergy) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) energy += __shfl_xor_sync(kFullMask, energy, o);
+    __shared__ long long part[kWarpsPerBlock];
+    if (lane == 0) part[threadIdx.x >> 5] = energy;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      long long s = 0;
+      for (int k = 0; k < kWarpsPerBlock; ++k) s += part[k];
+      atomicAdd(energy_out, static_cast<unsigned long long>(s));
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Persistent engine: one cooperative launch runs every sweep of an anneal
+// call; colour phases are separated by a grid-wide barrier. Every wait in the
+// barrier is bounded: after kBarrierBudgetNs the waiting block records a
+// timeout in the barrier state and the whole grid returns (the host reports
+// ISING_ETIMEOUT). Blocks also leave as soon as another block has failed.
+// ---------------------------------------------------------------------------
+constexpr int kPersistBlock = 512;
+constexpr long long kBarrierBudgetNs = 2000000000LL;  // 2 s
+
+struct BarrierState {
+  unsigned int count;
+  unsigned int generation;
+  int error;  // 0 ok, 1 a barrier wait timed out
+  int pad;
+};
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ int ld_relaxed_s32(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ long long global_ns() {
+  long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Returns false if this block (or another) gave up waiting.
+__device__ bool grid_barrier(BarrierState* bs, unsigned& gen_seen) {
+  __shared__ int ok_shared;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned gen = gen_seen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(&bs->count, 1u);
+    if (arrived == gridDim.x - 1) {
+      atomicExch(&bs->count, 0u);
+      __threadfence();
+      atomicAdd(&bs->generation, 1u);
+    } else {
+      const long long t0 = global_ns();
+      while (ld_acquire_u32(&bs->generation) == gen) {
+        if (ld_relaxed_s32(&bs->error) != 0) {
+          ok = 0;
+          break;
+        }
+        if (global_ns() - t0 > kBarrierBudgetNs) {
+          atomicExch(&bs->error, 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(20);
+      }
+    }
+    __threadfence();
+    gen_seen = gen + 1;
+    ok_shared = ok;
+  }
+  __syncthreads();
+  return ok_shared != 0;
+}
+
+template <typename WT, int PASS>
+__global__ void __launch_bounds__(kPersistBlock, 2)
+    persistent_kernel(DevGraph d, const int32_t* __restrict__ phase_items, int num_phases,
+                      uint64_t t_begin, uint32_t sweeps, uint64_t T, uint64_t T0, uint32_t replica,
+                      PhiloxKey key, BarrierState* bs) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * kPersistBlock + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * kPersistBlock) >> 5;
+  unsigned gen_seen = 0;
+  long long unused = 0;
+  for (uint32_t k = 0; k < sweeps; ++k) {
+    const uint64_t t = t_begin + k;
+    SweepArgs a;
+    a.t = static_cast<uint32_t>(t);
+    a.replica = replica;
+    a.key = key;
+    a.thr = (T <= 1) ? 0u : static_cast<uint32_t>((T0 * (T - 1 - t)) / (T - 1));
+    for (int c = 0; c < num_phases; ++c) {
+      const int ie = __ldg(phase_items + c + 1);
+      for (int i = __ldg(phase_items + c) + warp; i < ie; i += nwarps)
+        run_item<WT, PASS>(d, d.items[i], a, lane, unused);
+      // Deterministic: every class waits for the previous one. Racy: only the
+      // sweeps are synchronised (Sec. IV-B).
+      if (PASS == kPassRacy && c + 1 < num_phases) continue;
+      if (k + 1 == sweeps && c + 1 == num_phases) break;  // kernel end is the last barrier
+      if (!grid_barrier(bs, gen_seen)) return;
+    }
+  }
+}
+
+__global__ void init_random_kernel(int8_t* spins, const int32_t* orig, int n, PhiloxKey key,
+                                   uint32_t replica) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    const uint32_t x = isingx::philox4x32_10_word0(static_cast<uint32_t>(orig[p]), 0u, replica, 1u, key);
+    spins[p] = (x >> 31) ? int8_t(-1) : int8_t(1);
+  }
+}
+
+__global__ void gather_spins_kernel(int8_t* out, const int8_t* spins, const int32_t* pos, int n) {
+  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < n; o += gridDim.x * blockDim.x)
+    out[o] = spins[pos[o]];
+}
+
+__global__ void check_spins_kernel(const int8_t* in, int n, int32_t* bad) {
+  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < n; o += gridDim.x * blockDim.x)
+    if (in[o] != 1 && in[o] != -1) atomicExch(bad, 1);
+}
+
+__global__ void scatter_spins_kernel(int8_t* spins, const int8_t* in, const int32_t* pos, int n) {
+  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < n; o += gridDim.x * blockDim.x)
+    spins[pos[o]] = in[o];
+}
+
+__global__ void fill_spins_kernel(int8_t* spins, int n, int8_t value) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x)
+    spins[p] = value;
+}
+
+// T0 = round(p0 * 2^32) clamped to [0, 2^32 - 1] (ISING_SCHED_LINEAR, ising.h).
+uint64_t linear_t0(double p0) {
+  const double scaled = std::floor(p0 * 4294967296.0 + 0.5);
+  if (scaled >= 4294967295.0) return 4294967295ull;
+  if (scaled > 0.0) return static_cast<uint64_t>(scaled);
+  return 0;
+}
+
+// Flip threshold of sweep t.
+uint32_t linear_threshold(double p0, uint64_t T, uint64_t t) {
+  const uint64_t t0 = linear_t0(p0);
+  if (T <= 1 || t >= T) return 0u;
+  return static_cast<uint32_t>(t0 * (T - 1 - t) / (T - 1));
+}
+
+int grid_for(int64_t work, int per_block, int cap) {
+  int64_t b = (work + per_block - 1) / per_block;
+  if (b < 1) b = 1;
+  if (b > cap) b = cap;
+  return static_cast<int>(b);
+}
+
+}  // namespace
+
+struct ising_graph {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int status = ISING_OK;
+  int engine = ISING_ENGINE_AUTO;
+  int num_sms = 1;
+  uint64_t launches = 0;
+
+  int32_t n = 0;
+  int64_t num_edges = 0;
+  int64_t nnz = 0;
+  int64_t total_weight = 0;
+  int32_t num_colours = 0;
+  bool w8 = true;
+  std::vector<int32_t> colour;  // by caller id
+  std::vector<int32_t> class_item_begin;
+  int32_t num_items = 0;
+  int32_t num_slots = 0;
+
+  int32_t* d_row_ptr = nullptr;
+  int32_t* d_col = nullptr;
+  void* d_w = nullptr;
+  int8_t* d_spins = nullptr;
+  int32_t* d_orig = nullptr;
+  int32_t* d_pos = nullptr;
+  WorkItem* d_items = nullptr;
+  int32_t* d_split_acc = nullptr;
+  int32_t* d_split_cnt = nullptr;
+  int32_t* d_split_parts = nullptr;
+  unsigned long long* d_energy = nullptr;
+  int32_t* d_flag = nullptr;
+  int8_t* d_tmp = nullptr;
+  int32_t* d_class_items = nullptr;  // num_colours + 1 item offsets
+  int32_t* d_all_items = nullptr;    // {0, num_items}: one phase over every item (energy)
+  BarrierState* d_barrier = nullptr;
+  int persist_grid = 0;              // co-resident blocks of the persistent kernel
+
+  DevGraph dev() const {
+    DevGraph d;
+    d.row_ptr = d_row_ptr;
+    d.col = d_col;
+    d.w = d_w;
+    d.spins = d_spins;
+    d.orig = d_orig;
+    d.items = d_items;
+    d.split_acc = d_split_acc;
+    d.split_cnt = d_split_cnt;
+    d.split_parts = d_split_parts;
+    return d;
+  }
+};
+
+namespace {
+
+void free_device(ising_graph* g) {
+  void* ptrs[] = {g->d_row_ptr, g->d_col,         g->d_w,           g->d_spins,
+                  g->d_orig,    g->d_pos,         g->d_items,       g->d_split_acc,
+                  g->d_split_cnt, g->d_split_parts, g->d_energy,    g->d_flag,
+                  g->d_tmp,     g->d_class_items, g->d_all_items, g->d_barrier};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+}
+
+// Latch a CUDA failure in the handle.
+int cuda_fail(ising_graph* g, cudaError_t e) {
+  (void)e;
+  cudaGetLastError();
+  if (g) g->status = ISING_ECUDA;
+  return ISING_ECUDA;
+}
+
+#define ISING_CUDA(g, call)                      \
+  do {                                           \
+    cudaError_t e_ = (call);                     \
+    if (e_ != cudaSuccess) return cuda_fail((g), e_); \
+  } while (0)
+
+int enter(ising_graph* g) {
+  if (g == nullptr) return ISING_EINVAL;
+  if (g->status != ISING_OK) return g->status;
+  if (cudaSetDevice(g->device) != cudaSuccess) return cuda_fail(g, cudaErrorInvalidDevice);
+  return ISING_OK;
+}
+
+template <typename T>
+cudaError_t alloc_copy(T** dst, const T* src, size_t count, cudaStream_t s) {
+  const size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(dst), bytes);
+  if (e != cudaSuccess) return e;
+  if (src && count) return cudaMemcpyAsync(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice, s);
+  return cudaMemsetAsync(*dst, 0, bytes, s);
+}
+
+// Launch the item kernel over phases [pb, pe) of `phase_items` (device) whose
+// host copy is `host_items`.
+template <int PASS>
+cudaError_t launch_items(ising_graph* g, const int32_t* phase_items, const int32_t* host_items,
+                         int pb, int pe, const SweepArgs& a, unsigned long long* energy_out) {
+  int widest = 0;
+  for (int c = pb; c < pe; ++c) widest = std::max(widest, host_items[c + 1] - host_items[c]);
+  if (widest == 0) return cudaSuccess;
+  const int grid = grid_for(widest, kWarpsPerBlock, g->num_sms * 64);
+  const DevGraph d = g->dev();
+  g->launches++;
+  if (g->w8)
+    items_kernel<int8_t, PASS><<<grid, kBlock, 0, g->stream>>>(d, phase_items, pb, pe, a, energy_out);
+  else
+    items_kernel<int32_t, PASS><<<grid, kBlock, 0, g->stream>>>(d, phase_items, pb, pe, a, energy_out);
+  return cudaGetLastError();
+}
+
+// A persistent launch that timed out leaves error != 0 in the barrier state;
+// synchronising calls report it (and latch it).
+int check_device_error(ising_graph* g) {
+  int err = 0;
+  ISING_CUDA(g, cudaMemcpyAsync(&err, &g->d_barrier->error, sizeof(err), cudaMemcpyDeviceToHost, g->stream));
+  ISING_CUDA(g, cudaStreamSynchronize(g->stream));
+  if (err != 0) {
+    g->status = ISING_ETIMEOUT;
+    return ISING_ETIMEOUT;
+  }
+  return ISING_OK;
+}
+
+template <typename WT, int PASS>
+cudaError_t launch_persistent_t(ising_graph* g, const int32_t* phase_items, int num_phases,
+                                uint64_t t_begin, uint32_t sweeps, uint64_t T, uint64_t T0,
+                                uint32_t replica, PhiloxKey key) {
+  auto kernel = persistent_kernel<WT, PASS>;
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kPersistBlock, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+  per_sm = std::min(per_sm, 2);
+  const int grid = per_sm * g->num_sms;
+  g->persist_grid = grid;
+  e = cudaMemsetAsync(g->d_barrier, 0, sizeof(BarrierState), g->stream);
+  if (e != cudaSuccess) return e;
+  DevGraph d = g->dev();
+  BarrierState* bs = g->d_barrier;
+  void* args[] = {&d, &phase_items, &num_phases, &t_begin, &sweeps, &T, &T0, &replica, &key, &bs};
+  g->launches++;
+  return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(kernel), dim3(grid),
+                                     dim3(kPersistBlock), args, 0, g->stream);
+}
+
+template <int PASS>
+cudaError_t launch_persistent(ising_graph* g, const int32_t* phase_items, int num_phases,
+                              uint64_t t_begin, uint32_t sweeps, uint64_t T, uint64_t T0,
+                              uint32_t replica, PhiloxKey key) {
+  if (g->w8)
+    return launch_persistent_t<int8_t, PASS>(g, phase_items, num_phases, t_begin, sweeps, T, T0,
+                                             replica, key);
+  return launch_persistent_t<int32_t, PASS>(g, phase_items, num_phases, t_begin, sweeps, T, T0,
+                                            replica, key);
+}
+
+int compute_energy(ising_graph* g, int64_t* out) {
+  ISING_CUDA(g, cudaMemsetAsync(g->d_energy, 0, sizeof(unsigned long long), g->stream));
+  SweepArgs a{};
+  const int32_t all_items[2] = {0, g->num_items};
+  ISING_CUDA(g, launch_items<kPassEnergy>(g, g->d_all_items, all_items, 0, 1, a, g->d_energy));
+  unsigned long long twice = 0;
+  ISING_CUDA(g, cudaMemcpyAsync(&twice, g->d_energy, sizeof(twice), cudaMemcpyDeviceToHost, g->stream));
+  ISING_CUDA(g, cudaStreamSynchronize(g->stream));
+  const int rc = check_device_error(g);
+  if (rc != ISING_OK) return rc;
+  *out = static_cast<long long>(twice) / 2;
+  return ISING_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ising_strerror(int status) {
+  switch (status) {
+    case ISING_OK: return "ok";
+    case ISING_EINVAL: return "invalid argument";
+    case ISING_ENOMEM: return "out of memory";
+    case ISING_ECUDA: return "CUDA error (latched in the handle)";
+    case ISING_ETIMEOUT: return "a bounded device-side wait timed out";
+    case ISING_ESTATE: return "call not valid in the current state";
+    case ISING_ERANGE: return "size or weight out of the supported range";
+    default: return "unknown status";
+  }
+}
+
+int ising_create(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, const int32_t* w,
+                 uint32_t flags, void* cuda_stream, ising_graph** out) {
+  if (out == nullptr) return ISING_EINVAL;
+  *out = nullptr;
+  if ((flags & ~uint32_t(ISING_CREATE_WEIGHTS_I32)) != 0) return ISING_EINVAL;
+  HostGraph hg;
+  int rc;
+  try {
+    rc = isingx::build_host_graph(n, m, src, dst, w, &hg);
+  } catch (const std::bad_alloc&) {
+    return ISING_ENOMEM;
+  }
+  if (rc != ISING_OK) return rc;
+
+  ising_graph* g = new (std::nothrow) ising_graph();
+  if (g == nullptr) return ISING_ENOMEM;
+  g->stream = static_cast<cudaStream_t>(cuda_stream);
+  if (cudaGetDevice(&g->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete g;
+    return ISING_ECUDA;
+  }
+  cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
+  if (g->num_sms < 1) g->num_sms = 1;
+  g->n = hg.n;
+  g->num_edges = hg.num_edges;
+  g->nnz = hg.nnz;
+  g->total_weight = hg.total_weight;
+  g->num_colours = hg.num_colours;
+  g->w8 = hg.fits_int8 && !(flags & ISING_CREATE_WEIGHTS_I32);
+
+  WorkPlan plan;
+  try {
+    // ~32 resident warps per SM share a class; rows longer than a share are sliced.
+    isingx::build_work_plan(hg, g->num_sms * 32, 64, 32 * kRowsPerLane, &plan);
+    g->colour = hg.colour;
+    g->class_item_begin = plan.class_item_begin;
+  } catch (const std::bad_alloc&) {
+    delete g;
+    return ISING_ENOMEM;
+  }
+  g->num_items = static_cast<int32_t>(plan.items.size());
+  g->num_slots = static_cast<int32_t>(plan.split_parts.size());
+
+  std::vector<int8_t> w8;
+  cudaError_t e = cudaSuccess;
+  const size_t N = static_cast<size_t>(hg.n);
+  const size_t NNZ = static_cast<size_t>(hg.nnz);
+  do {
+    if ((e = alloc_copy(&g->d_row_ptr, hg.row_ptr.data(), N + 1, g->stream)) != cudaSuccess) break;
+    if ((e = alloc_copy(&g->d_col, hg.col.data(), NNZ, g->stream)) != cudaSuccess) break;
+    if (g->w8) {
+      w8.resize(NNZ);
+      for (size_t k = 0; k < NNZ; ++k) w8[k] = static_cast<int8_t>(hg.w[k]);
+      int8_t* p = nullptr;
+      e = alloc_copy(&p, w8.data(), NNZ, g->stream);
+      g->d_w = p;
+    } else {
+      int32_t* p = nullptr;
+      e = alloc_copy(&p, hg.w.data(), NNZ, g->stream);
+      g->d_w = p;
+    }
+    if (e != cudaSuccess) break;
+    if ((e = alloc_copy<int8_t>(&g->d_spins, nullptr, N, g->stream)) != cudaSuccess) break;
+    if ((e = alloc_copy(&g->d_orig, hg.perm.data(), N, g->stream)) != cudaSuccess) break;
+    if ((e = alloc_copy(&g->d_pos, hg.pos.data(), N, g->stream)) != cudaSuccess) break;
+    if ((e = alloc_copy(&g->d_items, plan.items.data(), plan.items.size(), g->stream)) != cudaSuccess) break;
+    const size_t slots = plan.split_parts.size();
+    if ((e = alloc_copy<int32_t>(&g->d_split_acc, nullptr, slots, g->stream)) != cudaSuccess) break;
+    if ((e = alloc_copy<int32_t>(&g->d_split_cnt, nullptr, slots, g->stream)) != cudaSuccess) break;
+    if ((e = alloc_copy(&g->d_split_parts, plan.split_parts.data(), slots, g->stream)) != cudaSuccess) break;
+    if ((e = alloc_copy<unsigned long long>(&g->d_energy, nullptr, 1, g->stream)) != cudaSuccess) break;
+    if ((e = alloc_copy<int32_t>(&g->d_flag, nullptr, 1, g->stream)) != cudaSuccess) break;
+    if ((e = alloc_copy<int8_t>(&g->d_tmp, nullptr, N, g->stream)) != cudaSuccess) break;
+    if ((e = alloc_copy(&g->d_class_items, plan.class_item_begin.data(),
+                        plan.class_item_begin.size(), g->stream)) != cudaSuccess) break;
+    const int32_t all_items[2] = {0, g->num_items};
+    if ((e = alloc_copy(&g->d_all_items, all_items, 2, g->stream)) != cudaSuccess) break;
+    if ((e = alloc_copy<BarrierState>(&g->d_barrier, nullptr, 1, g->stream)) != cudaSuccess) break;
+    fill_spins_kernel<<<grid_for(hg.n, 256, g->num_sms * 8), 256, 0, g->stream>>>(g->d_spins, hg.n, 1);
+    if ((e = cudaGetLastError()) != cudaSuccess) break;
+    e = cudaStreamSynchronize(g->stream);
+  } while (false);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    free_device(g);
+    delete g;
+    return e == cudaErrorMemoryAllocation ? ISING_ENOMEM : ISING_ECUDA;
+  }
+  *out = g;
+  return ISING_OK;
+}
+
+void ising_destroy(ising_graph* g) {
+  if (g == nullptr) return;
+  cudaSetDevice(g->device);
+  cudaStreamSynchronize(g->stream);
+  cudaGetLastError();
+  free_device(g);
+  delete g;
+}
+
+int ising_anneal(ising_graph* g, const ising_schedule* sched, uint32_t sweeps, uint64_t seed,
+                 int mode, void* cuda_stream) {
+  int rc = enter(g);
+  if (rc != ISING_OK) return rc;
+  if (sched == nullptr) return ISING_EINVAL;
+  if (sched->kind != ISING_SCHED_LINEAR) return ISING_EINVAL;
+  if (!(sched->p0 >= 0.0 && sched->p0 <= 1.0)) return ISING_EINVAL;
+  if (mode != ISING_MODE_DET && mode != ISING_MODE_RACY) return ISING_EINVAL;
+  if (sched->t_total >= (1ull << 32)) return ISING_EINVAL;
+  if (sched->t_begin > sched->t_total || sweeps > sched->t_total - sched->t_begin) return ISING_EINVAL;
+  g->stream = static_cast<cudaStream_t>(cuda_stream);
+  if (sweeps == 0) return ISING_OK;
+  const PhiloxKey key = isingx::philox_key(seed, 0u);
+  const int engine = g->engine == ISING_ENGINE_AUTO ? ISING_ENGINE_PHASE : g->engine;
+  if (engine == ISING_ENGINE_PERSISTENT) {
+    const uint64_t T0 = linear_t0(sched->p0);
+    if (mode == ISING_MODE_RACY)
+      ISING_CUDA(g, launch_persistent<kPassRacy>(g, g->d_class_items, g->num_colours,
+                                                 sched->t_begin, sweeps, sched->t_total, T0,
+                                                 sched->replica, key));
+    else
+      ISING_CUDA(g, launch_persistent<kPassDet>(g, g->d_class_items, g->num_colours,
+                                                sched->t_begin, sweeps, sched->t_total, T0,
+                                                sched->replica, key));
+    return ISING_OK;
+  }
+  SweepArgs a;
+  a.replica = sched->replica;
+  a.key = key;
+  for (uint32_t k = 0; k < sweeps; ++k) {
+    const uint64_t t = sched->t_begin + k;
+    a.t = static_cast<uint32_t>(t);
+    a.thr = linear_threshold(sched->p0, sched->t_total, t);
+    const int32_t* hi = g->class_item_begin.data();
+    if (mode == ISING_MODE_RACY) {
+      ISING_CUDA(g, launch_items<kPassRacy>(g, g->d_class_items, hi, 0, g->num_colours, a, nullptr));
+    } else {
+      for (int32_t c = 0; c < g->num_colours; ++c)
+        ISING_CUDA(g, launch_items<kPassDet>(g, g->d_class_items, hi, c, c + 1, a, nullptr));
+    }
+  }
+  return ISING_OK;
+}
+
+int ising_energy(ising_graph* g, int64_t* out_energy) {
+  int rc = enter(g);
+  if (rc != ISING_OK) return rc;
+  if (out_energy == nullptr) return ISING_EINVAL;
+  return compute_energy(g, out_energy);
+}
+
+int ising_cut(ising_graph* g, int64_t* out_cut) {
+  int rc = enter(g);
+  if (rc != ISING_OK) return rc;
+  if (out_cut == nullptr) return ISING_EINVAL;
+  int64_t H = 0;
+  rc = compute_energy(g, &H);
+  if (rc != ISING_OK) return rc;
+  *out_cut = (g->total_weight - H) / 2;
+  return ISING_OK;
+}
+
+int ising_total_weight(ising_graph* g, int64_t* out_w) {
+  if (g == nullptr || out_w == nullptr) return ISING_EINVAL;
+  *out_w = g->total_weight;
+  return ISING_OK;
+}
+
+int ising_get_spins(ising_graph* g, int8_t* out, int on_device) {
+  int rc = enter(g);
+  if (rc != ISING_OK) return rc;
+  if (out == nullptr) return ISING_EINVAL;
+  const int grid = grid_for(g->n, 256, g->num_sms * 8);
+  int8_t* target = on_device ? out : g->d_tmp;
+  g->launches++;
+  gather_spins_kernel<<<grid, 256, 0, g->stream>>>(target, g->d_spins, g->d_pos, g->n);
+  ISING_CUDA(g, cudaGetLastError());
+  if (!on_device) {
+    ISING_CUDA(g, cudaMemcpyAsync(out, g->d_tmp, static_cast<size_t>(g->n), cudaMemcpyDeviceToHost, g->stream));
+    ISING_CUDA(g, cudaStreamSynchronize(g->stream));
+    return check_device_error(g);
+  }
+  return ISING_OK;
+}
+
+int ising_set_spins(ising_graph* g, const int8_t* in, int on_device) {
+  int rc = enter(g);
+  if (rc != ISING_OK) return rc;
+  if (in == nullptr) return ISING_EINVAL;
+  const int grid = grid_for(g->n, 256, g->num_sms * 8);
+  const int8_t* source = in;
+  if (on_device) {
+    ISING_CUDA(g, cudaMemsetAsync(g->d_flag, 0, sizeof(int32_t), g->stream));
+    g->launches++;
+  check_spins_kernel<<<grid, 256, 0, g->stream>>>(in, g->n, g->d_flag);
+    ISING_CUDA(g, cudaGetLastError());
+    int32_t bad = 0;
+    ISING_CUDA(g, cudaMemcpyAsync(&bad, g->d_flag, sizeof(bad), cudaMemcpyDeviceToHost, g->stream));
+    ISING_CUDA(g, cudaStreamSynchronize(g->stream));
+    if (bad) return ISING_EINVAL;
+  } else {
+    for (int32_t o = 0; o < g->n; ++o)
+      if (in[o] != 1 && in[o] != -1) return ISING_EINVAL;
+    ISING_CUDA(g, cudaMemcpyAsync(g->d_tmp, in, static_cast<size_t>(g->n), cudaMemcpyHostToDevice, g->stream));
+    source = g->d_tmp;
+  }
+  g->launches++;
+  scatter_spins_kernel<<<grid, 256, 0, g->stream>>>(g->d_spins, source, g->d_pos, g->n);
+  ISING_CUDA(g, cudaGetLastError());
+  if (!on_device) ISING_CUDA(g, cudaStreamSynchronize(g->stream));
+  return ISING_OK;
+}
+
+int ising_init_random(ising_graph* g, uint64_t seed, uint32_t replica) {
+  int rc = enter(g);
+  if (rc != ISING_OK) return rc;
+  const int grid = grid_for(g->n, 256, g->num_sms * 8);
+  g->launches++;
+  init_random_kernel<<<grid, 256, 0, g->stream>>>(g->d_spins, g->d_orig, g->n,
+                                                  isingx::philox_key(seed, 0u), replica);
+  ISING_CUDA(g, cudaGetLastError());
+  return ISING_OK;
+}
+
+int ising_num_colours(ising_graph* g, int32_t* out) {
+  if (g == nullptr || out == nullptr) return ISING_EINVAL;
+  *out = g->num_colours;
+  return ISING_OK;
+}
+
+int ising_colouring(ising_graph* g, int32_t* out_colour) {
+  if (g == nullptr || out_colour == nullptr) return ISING_EINVAL;
+  std::memcpy(out_colour, g->colour.data(), g->colour.size() * sizeof(int32_t));
+  return ISING_OK;
+}
+
+int ising_num_edges(ising_graph* g, int64_t* out_m) {
+  if (g == nullptr || out_m == nullptr) return ISING_EINVAL;
+  *out_m = g->num_edges;
+  return ISING_OK;
+}
+
+int ising_plan_colouring(int32_t n, int64_t m, const int32_t* src, const int32_t* dst,
+                         const int32_t* w, int32_t* out_colour, int32_t* out_num_colours) {
+  if (out_colour == nullptr || out_num_colours == nullptr) return ISING_EINVAL;
+  HostGraph hg;
+  try {
+    const int rc = isingx::build_host_graph(n, m, src, dst, w, &hg);
+    if (rc != ISING_OK) return rc;
+  } catch (const std::bad_alloc&) {
+    return ISING_ENOMEM;
+  }
+  std::memcpy(out_colour, hg.colour.data(), hg.colour.size() * sizeof(int32_t));
+  *out_num_colours = hg.num_colours;
+  return ISING_OK;
+}
+
+int ising_launch_count(ising_graph* g, uint64_t* out) {
+  if (g == nullptr || out == nullptr) return ISING_EINVAL;
+  *out = g->launches;
+  return ISING_OK;
+}
+
+int ising_set_engine(ising_graph* g, int engine) {
+  if (g == nullptr) return ISING_EINVAL;
+  if (engine != ISING_ENGINE_AUTO && engine != ISING_ENGINE_PHASE && engine != ISING_ENGINE_PERSISTENT)
+    return ISING_EINVAL;
+  g->engine = engine;
+  return ISING_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,55 @@
+// Host-side construction of the device layout: validation, duplicate merging,
+// greedy colouring, colour-ordered CSR and the per-class work items the sweep
+// kernels consume.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+namespace isingx {
+
+// A unit of sweep work for one warp. Two kinds:
+//  * whole rows: vertices [v_begin, v_end) of one colour class, all of their
+//    edges [e_begin, e_end) (v_end > v_begin);
+//  * a slice of one heavy row: vertex v_begin, edges [e_begin, e_end), and
+//    v_end = -(slot + 1) names the partial-sum slot that combines the slices.
+struct WorkItem {
+  int32_t v_begin, v_end, e_begin, e_end;
+};
+
+struct HostGraph {
+  int32_t n = 0;
+  int64_t num_edges = 0;      // merged undirected edges
+  int64_t nnz = 0;            // directed CSR entries (2 * num_edges)
+  int64_t total_weight = 0;   // W
+  int32_t num_colours = 0;
+  int32_t max_degree = 0;
+  bool fits_int8 = true;      // every merged |w| <= 127
+
+  std::vector<int32_t> colour;       // per original id
+  std::vector<int32_t> perm;         // position -> original id
+  std::vector<int32_t> pos;          // original id -> position
+  std::vector<int32_t> class_begin;  // num_colours + 1 positions
+  std::vector<int32_t> row_ptr;      // n + 1, by position
+  std::vector<int32_t> col;          // nnz, neighbour positions
+  std::vector<int32_t> w;            // nnz
+};
+
+struct WorkPlan {
+  std::vector<WorkItem> items;
+  std::vector<int32_t> class_item_begin;  // num_colours + 1
+  std::vector<int32_t> split_parts;       // per slot: number of slices
+  int32_t max_class_items = 0;
+};
+
+// Returns 0, or a negative ISING_* status.
+int build_host_graph(int32_t n, int64_t m, const int32_t* src, const int32_t* dst,
+                     const int32_t* w, HostGraph* out);
+
+// Splits each colour class into work items of at most ~ceil(class edges /
+// target_warps) edges (never fewer than min_edges), at most max_rows rows each;
+// rows longer than that are sliced.
+void build_work_plan(const HostGraph& g, int32_t target_warps, int32_t min_edges,
+                     int32_t max_rows, WorkPlan* plan);
+
+}  // namespace isingx

@@ -1,0 +1,99 @@
+"""The C-ABI library without a GPU: it builds, loads, exports every entry point
+declared in include/ising.h, and its host-side logic (validation, merging,
+colouring) behaves as documented. No compute call touches a device here."""
+
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_1807_10750_gb300 import _build
+    _build.build()
+    import paper_1807_10750_gb300 as P
+    return P
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(ising_\w+)\s*\(", text))
+    return names
+
+
+def test_library_exports_every_declared_symbol(P):
+    import ctypes
+    declared = declared_functions()
+    assert "ising_create" in declared and "ising_anneal" in declared
+    L = ctypes.CDLL(P.LIB_PATH)
+    for name in declared:
+        assert hasattr(L, name), name
+    assert declared == set(P.EXPORTS)
+
+
+def test_strerror_names_every_status(P):
+    for code in (0, -1, -2, -3, -4, -5, -6):
+        assert P.strerror(code) != "unknown status"
+    assert P.strerror(-99) == "unknown status"
+
+
+@pytest.mark.parametrize("n,src,dst,w,code", [
+    (3, [0], [0], [1], -1),            # self-loop
+    (3, [0], [3], [1], -1),            # id out of range
+    (3, [-2], [1], [1], -1),           # negative id
+    (0, [], [], [], -1),               # no vertices
+    (-5, [], [], [], -1),
+    (2, [0, 0], [1, 1], [2 ** 31 - 1, 1], -6),  # merged field exceeds int32
+])
+def test_create_rejects_invalid_input_before_touching_the_device(P, n, src, dst, w, code):
+    with pytest.raises(P.IsingError) as e:
+        P.ising_create(n, np.array(src, np.int32), np.array(dst, np.int32), np.array(w, np.int32))
+    assert e.value.code == code
+
+
+def test_plan_colouring_rejects_the_same_inputs(P):
+    with pytest.raises(P.IsingError):
+        P.ising_plan_colouring(3, [0], [0], [1])
+
+
+@pytest.mark.parametrize("make", [
+    lambda: synth.torus_graph(16, 0),
+    lambda: synth.torus_graph(10, 1, weights="int8"),
+    lambda: synth.random_small_graph(400, 0.03, 3, duplicates=80),
+    lambda: synth.random_small_graph(50, 0.5, 4, weights="pm1", duplicates=200),
+    lambda: synth.zipf_config_graph(5000, 2.1, 2, 400, 5),
+    lambda: synth.complete_graph(9),
+])
+def test_host_colouring_equals_oracle(P, make):
+    g = make()
+    C, col = P.ising_plan_colouring(g.n, g.src, g.dst, g.w)
+    C2, col2 = oracle.colouring(g.n, g.src, g.dst, g.w)
+    assert C == C2
+    assert np.array_equal(col, col2)
+
+
+def test_host_colouring_edgeless_and_single_vertex(P):
+    e = np.zeros(0, np.int32)
+    C, col = P.ising_plan_colouring(5, e, e, e)
+    assert C == 1 and np.all(col == 0)
+    C, col = P.ising_plan_colouring(1, e, e, e)
+    assert C == 1 and col[0] == 0
+
+
+def test_zero_weight_merge_changes_colouring(P):
+    src = np.array([0, 1, 1, 2, 0], np.int32)
+    dst = np.array([1, 0, 2, 1, 2], np.int32)
+    w = np.array([2, 3, 4, -4, 1], np.int32)
+    C, col = P.ising_plan_colouring(3, src, dst, w)
+    assert C == 2 and list(col) == [0, 1, 1]

@@ -1,0 +1,233 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Deterministic mode must match the oracle bit for bit in spins, energy and cut.
+The racy mode is judged by cut value only.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+ENGINES = ["phase", "persistent"]
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1807_10750_gb300 import _build
+    _build.build()
+    import paper_1807_10750_gb300 as P
+    return P
+
+
+def engine_id(P, name):
+    return {"phase": P.ISING_ENGINE_PHASE, "persistent": P.ISING_ENGINE_PERSISTENT,
+            "auto": P.ISING_ENGINE_AUTO}[name]
+
+
+def gpu_anneal(P, g, s0, *, seed, p0, T, t_begin=0, sweeps=None, flags=0, engine="auto",
+               mode=None, replica=0):
+    with P.ising_create(g.n, g.src, g.dst, g.w, flags=flags) as h:
+        P.ising_set_engine(h, engine_id(P, engine))
+        P.ising_set_spins(h, s0)
+        P.ising_anneal(h, p0=p0, t_total=T, t_begin=t_begin, sweeps=sweeps, seed=seed,
+                       mode=P.ISING_MODE_DET if mode is None else mode, replica=replica)
+        s = P.ising_get_spins(h)
+        return s, P.ising_energy(h), P.ising_cut(h)
+
+
+def check_det(P, g, *, seed, p0, T, t_begin=0, sweeps=None, s0=None, flags=0, engine="auto",
+              replica=0):
+    if s0 is None:
+        s0 = oracle.init_spins(g.n, seed + 1000)
+    want = oracle.anneal(g.n, g.src, g.dst, g.w, s0, seed=seed, p0=p0, T=T, t_begin=t_begin,
+                         sweeps=sweeps, replica=replica)
+    got, H, cut = gpu_anneal(P, g, s0, seed=seed, p0=p0, T=T, t_begin=t_begin, sweeps=sweeps,
+                             flags=flags, engine=engine, replica=replica)
+    mism = np.nonzero(got != want)[0]
+    assert mism.size == 0, f"{mism.size} spins differ, first at {mism[:8]}"
+    Hw, W, cutw = oracle.energy_cut(g.n, g.src, g.dst, g.w, want)
+    assert (H, cut) == (Hw, cutw)
+    return got
+
+
+SMALL_GRAPHS = {
+    "er_dup_int8": lambda: synth.random_small_graph(300, 0.04, 1, weights="int8", duplicates=60),
+    "er_dense_pm1": lambda: synth.random_small_graph(120, 0.5, 2, weights="pm1"),
+    "torus_pm1": lambda: synth.torus_graph(16, 3, weights="pm1"),
+    "torus_odd": lambda: synth.torus_graph(15, 4, weights="int8", Ly=9),
+    "grid_one": lambda: synth.grid_graph(13, 7),
+    "complete": lambda: synth.complete_graph(40, 5, weights="int8"),
+    "zipf_small": lambda: synth.zipf_config_graph(20000, 2.1, 2, 3000, 6),
+    "cycle_odd": lambda: synth.cycle_graph(33),
+}
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+@pytest.mark.parametrize("name", sorted(SMALL_GRAPHS))
+def test_det_bit_exact_small(P, name, engine):
+    g = SMALL_GRAPHS[name]()
+    check_det(P, g, seed=17, p0=0.15, T=60, engine=engine)
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_det_bit_exact_int32_weights(P, engine):
+    g = synth.random_small_graph(500, 0.02, 8, weights="int8")
+    g.w = (g.w * 97).astype(np.int32)  # beyond int8
+    check_det(P, g, seed=3, p0=0.1, T=40, engine=engine)
+    g2 = synth.random_small_graph(500, 0.02, 8, weights="int8")
+    check_det(P, g2, seed=3, p0=0.1, T=40, flags=P.ISING_CREATE_WEIGHTS_I32, engine=engine)
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_det_hub_rows_sliced_across_warps(P, engine):
+    # A star-heavy graph: two hubs of degree ~n plus sparse noise, so the hubs'
+    # rows are split into many slices combined through the partial-sum slots.
+    rng = np.random.default_rng(0)
+    n = 60000
+    hub_a = np.full(n - 2, 0, np.int32); leaf = np.arange(2, n, dtype=np.int32)
+    hub_b = np.full(n // 2, 1, np.int32); leaf_b = rng.choice(np.arange(2, n), n // 2, replace=False).astype(np.int32)
+    noise = synth.er_graph(n, 3.0 / n, 1, weights="int8")
+    src = np.concatenate([hub_a, hub_b, noise.src]); dst = np.concatenate([leaf, leaf_b, noise.dst])
+    w = synth.draw_weights("int8", src.size, rng)
+    g = synth.Graph(n, src.astype(np.int32), dst.astype(np.int32), w)
+    check_det(P, g, seed=5, p0=0.2, T=30, engine=engine)
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_det_edge_cases(P, engine):
+    e = np.zeros(0, np.int32)
+    for n in (1, 2, 37, 100000):
+        g = synth.Graph(n, e, e, e)
+        check_det(P, g, seed=n, p0=0.4, T=7, engine=engine)
+    # merged-zero edges vanish
+    g = synth.Graph(3, np.array([0, 1, 1, 2], np.int32), np.array([1, 0, 2, 1], np.int32),
+                    np.array([2, 3, 4, -4], np.int32))
+    check_det(P, g, seed=2, p0=0.3, T=9, engine=engine)
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_er800_full_schedule_bit_exact(P, engine):
+    # G(800, 0.06), unit weights, 1000 sweeps, p0 = 0.1, seed 1.
+    g, sch = synth.workload("er800")
+    s0 = oracle.init_spins(g.n, sch["seed"])
+    check_det(P, g, seed=sch["seed"], p0=sch["p0"], T=sch["sweeps"], s0=s0, engine=engine)
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_torus1024_full_size_segments_bit_exact(P, engine):
+    # The 1024 x 1024 torus of the benchmark: first and last sweeps of the
+    # 2000-sweep schedule, each from a shared state.
+    g, sch = synth.workload("torus1024")
+    T = sch["sweeps"]
+    s0 = oracle.init_spins(g.n, sch["seed"])
+    s1 = check_det(P, g, seed=sch["seed"], p0=sch["p0"], T=T, sweeps=12, s0=s0, engine=engine)
+    check_det(P, g, seed=sch["seed"], p0=sch["p0"], T=T, t_begin=T - 12, s0=s1, engine=engine)
+
+
+def test_zipf1m_full_size_segment_bit_exact(P):
+    g, sch = synth.workload("zipf1m")
+    s0 = oracle.init_spins(g.n, sch["seed"])
+    for engine in ENGINES:
+        check_det(P, g, seed=sch["seed"], p0=sch["p0"], T=sch["sweeps"], sweeps=3, s0=s0,
+                  engine=engine)
+
+
+def test_init_random_matches_oracle(P):
+    g = synth.random_small_graph(3000, 0.002, 9)
+    with P.ising_create(g.n, g.src, g.dst, g.w) as h:
+        for seed, rep in [(0, 0), (1, 0), (2 ** 40 + 7, 3)]:
+            P.ising_init_random(h, seed, rep)
+            assert np.array_equal(P.ising_get_spins(h), oracle.init_spins(g.n, seed, replica=rep))
+
+
+def test_energy_and_cut_match_oracle(P):
+    g = synth.random_small_graph(2000, 0.01, 10, weights="int8", duplicates=300)
+    rng = np.random.default_rng(1)
+    with P.ising_create(g.n, g.src, g.dst, g.w) as h:
+        assert P.ising_num_edges(h) == oracle.num_edges(g.n, g.src, g.dst, g.w)
+        for _ in range(4):
+            s = (rng.integers(0, 2, g.n) * 2 - 1).astype(np.int8)
+            P.ising_set_spins(h, s)
+            H, W, cut = oracle.energy_cut(g.n, g.src, g.dst, g.w, s)
+            assert P.ising_energy(h) == H
+            assert P.ising_cut(h) == cut
+            assert P.ising_total_weight(h) == W
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_split_anneal_equals_whole(P, engine):
+    g = synth.random_small_graph(5000, 0.002, 11, weights="int8")
+    s0 = oracle.init_spins(g.n, 4)
+    whole, _, _ = gpu_anneal(P, g, s0, seed=9, p0=0.2, T=50, engine=engine)
+    with P.ising_create(g.n, g.src, g.dst, g.w) as h:
+        P.ising_set_engine(h, engine_id(P, engine))
+        P.ising_set_spins(h, s0)
+        P.ising_anneal(h, p0=0.2, t_total=50, sweeps=17, seed=9)
+        P.ising_anneal(h, p0=0.2, t_total=50, t_begin=17, sweeps=0, seed=9)
+        P.ising_anneal(h, p0=0.2, t_total=50, t_begin=17, seed=9)
+        assert np.array_equal(P.ising_get_spins(h), whole)
+
+
+def test_spins_roundtrip_host_and_device(P):
+    import torch
+    g = synth.random_small_graph(1000, 0.01, 12)
+    rng = np.random.default_rng(2)
+    s = (rng.integers(0, 2, g.n) * 2 - 1).astype(np.int8)
+    with P.ising_create(g.n, g.src, g.dst, g.w) as h:
+        P.ising_set_spins(h, s)
+        assert np.array_equal(P.ising_get_spins(h), s)
+        dev = torch.from_numpy(-s).cuda()
+        P.ising_set_spins(h, dev)
+        out = torch.zeros(g.n, dtype=torch.int8, device="cuda")
+        P.ising_get_spins(h, out)
+        torch.cuda.synchronize()
+        assert np.array_equal(out.cpu().numpy(), -s)
+        bad = s.copy(); bad[5] = 0
+        with pytest.raises(P.IsingError):
+            P.ising_set_spins(h, bad)
+        bad_dev = torch.from_numpy(bad).cuda()
+        with pytest.raises(P.IsingError):
+            P.ising_set_spins(h, bad_dev)
+        assert np.array_equal(P.ising_get_spins(h), -s)  # unchanged by rejected calls
+
+
+def test_anneal_argument_errors(P):
+    g = synth.cycle_graph(10)
+    with P.ising_create(g.n, g.src, g.dst, g.w) as h:
+        for kw in (dict(p0=1.5, t_total=10), dict(p0=-0.1, t_total=10),
+                   dict(p0=0.1, t_total=10, t_begin=8, sweeps=3), dict(p0=0.1, t_total=2 ** 32)):
+            with pytest.raises(P.IsingError) as e:
+                P.ising_anneal(h, seed=1, **kw)
+            assert e.value.code == P.ISING_EINVAL
+        with pytest.raises(P.IsingError):
+            P.ising_anneal(h, seed=1, p0=0.1, t_total=10, mode=7)
+        with pytest.raises(P.IsingError):
+            P.ising_set_engine(h, 9)
+        # the handle still works after rejected calls
+        P.ising_anneal(h, seed=1, p0=0.1, t_total=10)
+        assert P.ising_cut(h) >= 0
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+@pytest.mark.parametrize("name", ["torus256", "er800"])
+def test_racy_mode_cut_quality(P, name, engine):
+    if name == "torus256":
+        g, T = synth.torus_graph(256, 7, weights="pm1"), 400
+    else:
+        g, T = synth.workload("er800")[0], 1000
+    det, racy = [], []
+    for seed in range(6):
+        s0 = oracle.init_spins(g.n, seed)
+        det.append(gpu_anneal(P, g, s0, seed=seed, p0=0.1, T=T)[2])
+        s, H, cut = gpu_anneal(P, g, s0, seed=seed, p0=0.1, T=T, mode=P.ISING_MODE_RACY,
+                               engine=engine)
+        assert set(np.unique(s)) <= {-1, 1}
+        assert (H, cut) == oracle.energy_cut(g.n, g.src, g.dst, g.w, s)[::2]
+        racy.append(cut)
+    assert np.mean(racy) >= 0.98 * np.mean(det), (racy, det)
