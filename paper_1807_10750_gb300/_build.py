@@ -21,7 +21,7 @@ BUILD_DIR = os.path.join(HERE, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["anneal.cu", "host_graph.cpp"]
-HEADERS = ["host_graph.h", "philox.cuh"]
+HEADERS = ["host_graph.h", "philox.cuh", "sweep.cuh"]
 
 
 def nvcc() -> str:

@@ -8,12 +8,11 @@
 //   orig     int32[n]     position -> caller's vertex id (Philox counter word 0)
 //   pos      int32[n]     caller's vertex id -> position
 //   items    WorkItem[]   per-class warp work (see host_graph.h)
-//   split_*  int32[slots] partial-field combine for rows sliced across warps
+//   slice_*  partial-field combine for rows sliced across warps (scratch)
 //
-// One warp processes one work item: the local fields f_i = sum_j w_ij s_j of
-// its rows (Eq. 2), gathered by sub-warp lane groups sized to the rows'
-// degree, then one lane per row applies the update rule and the random flip
-// of Algorithm 2.
+// One warp processes one work item (sweep.cuh): the local fields
+// f_i = sum_j w_ij s_j of its rows (Eq. 2), then the update rule and the
+// random flip of Algorithm 2.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -26,6 +25,7 @@
 #include "../../include/ising.h"
 #include "host_graph.h"
 #include "philox.cuh"
+#include "sweep.cuh"
 
 using isingx::HostGraph;
 using isingx::PhiloxKey;
@@ -34,211 +34,22 @@ using isingx::WorkPlan;
 
 namespace {
 
-constexpr unsigned kFullMask = 0xffffffffu;
+using isingx::BarrierState;
+using isingx::DevGraph;
+using isingx::SweepArgs;
+using isingx::kPassDet;
+using isingx::kPassEnergy;
+using isingx::kPassRacy;
+
 constexpr int kBlock = 256;
 constexpr int kWarpsPerBlock = kBlock / 32;
-
-enum ItemPass { kPassDet = 0, kPassRacy = 1, kPassEnergy = 2 };
-
-struct DevGraph {
-  const int32_t* row_ptr;
-  const int32_t* col;
-  const void* w;
-  int8_t* spins;
-  const int32_t* orig;
-  const WorkItem* items;
-  int32_t* split_acc;
-  int32_t* split_cnt;
-  const int32_t* split_parts;
-};
-
-struct SweepArgs {
-  uint32_t thr;      // flip iff word < thr
-  uint32_t t;        // sweep index (counter word 1)
-  uint32_t replica;  // counter word 2
-  PhiloxKey key;
-};
-
-// Racy mode: neighbour reads and own writes race by design (Sec. IV-B); they
-// are relaxed atomics at GPU scope so the races are defined behaviour.
-__device__ __forceinline__ int ld_relaxed_s8(const int8_t* p) {
-  int v;
-  asm volatile("ld.relaxed.gpu.global.s8 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_relaxed_s8(int8_t* p, int v) {
-  asm volatile("st.relaxed.gpu.global.s8 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-template <int PASS>
-__device__ __forceinline__ int spin_at(const DevGraph& d, int j) {
-  return (PASS == kPassRacy) ? ld_relaxed_s8(d.spins + j) : static_cast<int>(d.spins[j]);
-}
-
-// sum of w_e * s_col[e] over e = e0, e0 + step, ... < e1, four edges per round
-// so that each lane keeps several loads in flight.
-template <typename WT, int PASS>
-__device__ __forceinline__ int strided_field(const DevGraph& d, int e0, int e1, int step) {
-  int f = 0;
-  for (int e = e0; e < e1; e += 4 * step) {
-    int cj[4], wj[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int x = e + u * step;
-      const bool ok = x < e1;
-      cj[u] = ok ? __ldg(d.col + x) : -1;
-      wj[u] = ok ? static_cast<int>(__ldg(static_cast<const WT*>(d.w) + x)) : 0;
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-      if (cj[u] >= 0) f += wj[u] * spin_at<PASS>(d, cj[u]);
-  }
-  return f;
-}
-
-// Eq. 2 under the max-cut sign (s <- -sign f, tie keeps), then Algorithm 2's
-// flip with probability thr / 2^32 keyed by the caller's vertex id.
-template <int PASS>
-__device__ __forceinline__ void update_spin(const DevGraph& d, int v, int f, const SweepArgs& a) {
-  int s = (PASS == kPassRacy) ? ld_relaxed_s8(d.spins + v) : static_cast<int>(d.spins[v]);
-  if (f > 0)
-    s = -1;
-  else if (f < 0)
-    s = 1;
-  if (a.thr != 0u) {
-    const uint32_t o = static_cast<uint32_t>(__ldg(d.orig + v));
-    if (isingx::philox4x32_10_word0(o, a.t, a.replica, 0u, a.key) < a.thr) s = -s;
-  }
-  if (PASS == kPassRacy)
-    st_relaxed_s8(d.spins + v, s);
-  else
-    d.spins[v] = static_cast<int8_t>(s);
-}
-
-constexpr int kRowsPerLane = 4;  // work items hold at most 32 * kRowsPerLane rows
-constexpr int kLightMeanDegree = 16;
-
-// Light rows (mean degree <= kLightMeanDegree): one lane per row, up to
-// kRowsPerLane rows per lane, all row offsets, then all column/weight loads,
-// then all neighbour-spin gathers issued together (three memory round trips
-// for rows of degree <= 4).
-template <typename WT, int PASS>
-__device__ __forceinline__ void run_light_rows(const DevGraph& d, const WorkItem& it,
-                                               const SweepArgs& a, int lane, long long& energy) {
-  int rp[kRowsPerLane], re[kRowsPerLane], f[kRowsPerLane];
-#pragma unroll
-  for (int r = 0; r < kRowsPerLane; ++r) {
-    const int v = it.v_begin + lane + 32 * r;
-    rp[r] = 0;
-    re[r] = 0;
-    f[r] = 0;
-    if (v < it.v_end) {
-      rp[r] = __ldg(d.row_ptr + v);
-      re[r] = __ldg(d.row_ptr + v + 1);
-    }
-  }
-  int kmax = 0;
-#pragma unroll
-  for (int r = 0; r < kRowsPerLane; ++r) kmax = max(kmax, re[r] - rp[r]);
-  for (int k = 0; k < kmax; k += 4) {
-    int cj[kRowsPerLane][4], wj[kRowsPerLane][4];
-#pragma unroll
-    for (int r = 0; r < kRowsPerLane; ++r)
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int e = rp[r] + k + u;
-        const bool ok = e < re[r];
-        cj[r][u] = ok ? __ldg(d.col + e) : -1;
-        wj[r][u] = ok ? static_cast<int>(__ldg(static_cast<const WT*>(d.w) + e)) : 0;
-      }
-#pragma unroll
-    for (int r = 0; r < kRowsPerLane; ++r)
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (cj[r][u] >= 0) f[r] += wj[r][u] * spin_at<PASS>(d, cj[r][u]);
-  }
-#pragma unroll
-  for (int r = 0; r < kRowsPerLane; ++r) {
-    const int v = it.v_begin + lane + 32 * r;
-    if (v < it.v_end) {
-      if (PASS == kPassEnergy)
-        energy += static_cast<long long>(d.spins[v]) * f[r];
-      else
-        update_spin<PASS>(d, v, f[r], a);
-    }
-  }
-}
-
-template <typename WT, int PASS>
-__device__ __forceinline__ void run_item(const DevGraph& d, const WorkItem it, const SweepArgs& a,
-                                         int lane, long long& energy) {
-  if (it.v_end < 0) {
-    // A slice of one heavy row: partial field, combined across slices by the
-    // last slice to finish (integer sums, so the order does not matter).
-    const int v = it.v_begin;
-    int f = strided_field<WT, PASS>(d, it.e_begin + lane, it.e_end, 32);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(kFullMask, f, o);
-    if (PASS == kPassEnergy) {
-      if (lane == 0) energy += static_cast<long long>(d.spins[v]) * f;
-      return;
-    }
-    if (lane == 0) {
-      const int slot = -it.v_end - 1;
-      atomicAdd(d.split_acc + slot, f);
-      __threadfence();
-      const int ticket = atomicAdd(d.split_cnt + slot, 1);
-      if (ticket == d.split_parts[slot] - 1) {
-        __threadfence();
-        const int total = atomicExch(d.split_acc + slot, 0);
-        d.split_cnt[slot] = 0;
-        update_spin<PASS>(d, v, total, a);
-      }
-    }
-    return;
-  }
-  const int nv = it.v_end - it.v_begin;
-  if (it.e_end - it.e_begin <= kLightMeanDegree * nv) {
-    run_light_rows<WT, PASS>(d, it, a, lane, energy);
-    return;
-  }
-  // Heavier rows: lane groups of g lanes (power of two >= a quarter of the
-  // mean degree) each gather one row per pass; 32 / g rows per pass.
-  const int mean = (it.e_end - it.e_begin + nv - 1) / nv;
-  int lg = 0;
-  while ((4 << lg) < mean && lg < 5) ++lg;
-  const int g = 1 << lg;
-  const int rows_per_pass = 32 >> lg;
-  const int sub = lane & (g - 1);
-  const int grp = lane >> lg;
-  for (int base = it.v_begin; base < it.v_end; base += 32) {
-    const int rows = min(32, it.v_end - base);
-    const int passes = (rows + rows_per_pass - 1) / rows_per_pass;
-    int my_f = 0;
-    for (int p = 0; p < passes; ++p) {
-      const int v = base + p * rows_per_pass + grp;
-      int f = 0;
-      if (v < it.v_end)
-        f = strided_field<WT, PASS>(d, __ldg(d.row_ptr + v) + sub, __ldg(d.row_ptr + v + 1), g);
-      for (int o = g >> 1; o > 0; o >>= 1) f += __shfl_xor_sync(kFullMask, f, o);
-      const int got = __shfl_sync(kFullMask, f, (lane % rows_per_pass) << lg);
-      if (lane / rows_per_pass == p) my_f = got;
-    }
-    const int v = base + lane;
-    if (v < it.v_end) {
-      if (PASS == kPassEnergy)
-        energy += static_cast<long long>(d.spins[v]) * my_f;
-      else
-        update_spin<PASS>(d, v, my_f, a);
-    }
-  }
-}
+constexpr int kPersistBlock = 512;
 
 // Item kernel of the per-launch engine. Deterministic sweeps launch it once
 // per colour class (phase_begin + 1 == phase_end); the racy mode launches it
 // once per sweep over every class, each warp walking the classes in order with
 // no wait between them; the energy pass covers all items.
-template <typename WT, int PASS>
+template <bool PACKED, int PASS>
 __global__ void __launch_bounds__(kBlock, 4)
     items_kernel(DevGraph d, const int32_t* __restrict__ phase_items, int phase_begin,
                  int phase_end, SweepArgs a, unsigned long long* energy_out) {
@@ -249,119 +60,82 @@ __global__ void __launch_bounds__(kBlock, 4)
   for (int c = phase_begin; c < phase_end; ++c) {
     const int ie = __ldg(phase_items + c + 1);
     for (int i = __ldg(phase_items + c) + warp; i < ie; i += nwarps) {
-      const WorkItem it = d.items[i];
-      run_item<WT, PASS>(d, it, a, lane, energy);
+      isingx::Staged<PACKED> st;
+      isingx::stage_item<PACKED>(d, i, a, lane, st);
+      isingx::finish_item<PACKED, PASS>(d, st, a, lane, energy);
     }
   }
   if (PASS == kPassEnergy) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) energy += __shfl_xor_sync(kFullMask, energy, o);
+    for (int o = 16; o > 0; o >>= 1) energy += __shfl_xor_sync(isingx::kFullMask, energy, o);
     __shared__ long long part[kWarpsPerBlock];
     if (lane == 0) part[threadIdx.x >> 5] = energy;
     __syncthreads();
     if (threadIdx.x == 0) {
-      long long s = 0;
-      for (int k = 0; k < kWarpsPerBlock; ++k) s += part[k];
-      atomicAdd(energy_out, static_cast<unsigned long long>(s));
+      long long sum = 0;
+      for (int k = 0; k < kWarpsPerBlock; ++k) sum += part[k];
+      atomicAdd(energy_out, static_cast<unsigned long long>(sum));
     }
   }
 }
 
-// ---------------------------------------------------------------------------
 // Persistent engine: one cooperative launch runs every sweep of an anneal
-// call; colour phases are separated by a grid-wide barrier. Every wait in the
-// barrier is bounded: after kBarrierBudgetNs the waiting block records a
-// timeout in the barrier state and the whole grid returns (the host reports
-// ISING_ETIMEOUT). Blocks also leave as soon as another block has failed.
-// ---------------------------------------------------------------------------
-constexpr int kPersistBlock = 512;
-constexpr long long kBarrierBudgetNs = 2000000000LL;  // 2 s
-
-struct BarrierState {
-  unsigned int count;
-  unsigned int generation;
-  int error;  // 0 ok, 1 a barrier wait timed out
-  int pad;
-};
-
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ int ld_relaxed_s32(const int* p) {
-  int v;
-  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ long long global_ns() {
-  long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Returns false if this block (or another) gave up waiting.
-__device__ bool grid_barrier(BarrierState* bs, unsigned& gen_seen) {
-  __shared__ int ok_shared;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    const unsigned gen = gen_seen;
-    __threadfence();
-    const unsigned arrived = atomicAdd(&bs->count, 1u);
-    if (arrived == gridDim.x - 1) {
-      atomicExch(&bs->count, 0u);
-      __threadfence();
-      atomicAdd(&bs->generation, 1u);
-    } else {
-      const long long t0 = global_ns();
-      while (ld_acquire_u32(&bs->generation) == gen) {
-        if (ld_relaxed_s32(&bs->error) != 0) {
-          ok = 0;
-          break;
-        }
-        if (global_ns() - t0 > kBarrierBudgetNs) {
-          atomicExch(&bs->error, 1);
-          ok = 0;
-          break;
-        }
-        __nanosleep(20);
-      }
-    }
-    __threadfence();
-    gen_seen = gen + 1;
-    ok_shared = ok;
-  }
-  __syncthreads();
-  return ok_shared != 0;
-}
-
-template <typename WT, int PASS>
+// call. Warp w takes items w, w + nwarps, ... of each colour class. Between
+// arriving at the grid barrier and waiting on it, the warp stages its first
+// item of the next class (loads and random flips need no spins), so after the
+// barrier only the neighbour gathers and the update remain. Deterministic:
+// a barrier after every class. Racy: only after every sweep (Sec. IV-B).
+template <bool PACKED, int PASS>
 __global__ void __launch_bounds__(kPersistBlock, 2)
     persistent_kernel(DevGraph d, const int32_t* __restrict__ phase_items, int num_phases,
                       uint64_t t_begin, uint32_t sweeps, uint64_t T, uint64_t T0, uint32_t replica,
-                      PhiloxKey key, BarrierState* bs) {
+                      isingx::PhiloxKey key, BarrierState* bs) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * kPersistBlock + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * kPersistBlock) >> 5;
-  unsigned gen_seen = 0;
-  long long unused = 0;
-  for (uint32_t k = 0; k < sweeps; ++k) {
+  auto sweep_args = [&](uint32_t k) {
+    SweepArgs sa;
     const uint64_t t = t_begin + k;
-    SweepArgs a;
-    a.t = static_cast<uint32_t>(t);
-    a.replica = replica;
-    a.key = key;
-    a.thr = (T <= 1) ? 0u : static_cast<uint32_t>((T0 * (T - 1 - t)) / (T - 1));
-    for (int c = 0; c < num_phases; ++c) {
-      const int ie = __ldg(phase_items + c + 1);
-      for (int i = __ldg(phase_items + c) + warp; i < ie; i += nwarps)
-        run_item<WT, PASS>(d, d.items[i], a, lane, unused);
-      // Deterministic: every class waits for the previous one. Racy: only the
-      // sweeps are synchronised (Sec. IV-B).
-      if (PASS == kPassRacy && c + 1 < num_phases) continue;
-      if (k + 1 == sweeps && c + 1 == num_phases) break;  // kernel end is the last barrier
-      if (!grid_barrier(bs, gen_seen)) return;
+    sa.t = static_cast<uint32_t>(t);
+    sa.replica = replica;
+    sa.key = key;
+    sa.thr = (T <= 1) ? 0u : static_cast<uint32_t>((T0 * (T - 1 - t)) / (T - 1));
+    return sa;
+  };
+  long long unused = 0;
+  unsigned target = 0;
+  uint32_t k = 0;
+  int c = 0;
+  SweepArgs a = sweep_args(0);
+  int ib = __ldg(phase_items), ie = __ldg(phase_items + 1);
+  isingx::Staged<PACKED> st;
+  bool have = ib + warp < ie;
+  if (have) isingx::stage_item<PACKED>(d, ib + warp, a, lane, st);
+  for (;;) {
+    if (have) {
+      isingx::finish_item<PACKED, PASS>(d, st, a, lane, unused);
+      for (int i = ib + warp + nwarps; i < ie; i += nwarps) {
+        isingx::stage_item<PACKED>(d, i, a, lane, st);
+        isingx::finish_item<PACKED, PASS>(d, st, a, lane, unused);
+      }
+    }
+    const bool sweep_end = (c + 1 == num_phases);
+    if (sweep_end && k + 1 == sweeps) break;
+    const bool sync = (PASS != kPassRacy) || sweep_end;
+    if (sync) isingx::barrier_arrive(bs);
+    if (sweep_end) {
+      c = 0;
+      a = sweep_args(++k);
+    } else {
+      ++c;
+    }
+    ib = __ldg(phase_items + c);
+    ie = __ldg(phase_items + c + 1);
+    have = ib + warp < ie;
+    if (have) isingx::stage_item<PACKED>(d, ib + warp, a, lane, st);
+    if (sync) {
+      target += gridDim.x;
+      if (!isingx::barrier_wait(bs, target)) return;
     }
   }
 }
@@ -431,22 +205,22 @@ struct ising_graph {
   int64_t nnz = 0;
   int64_t total_weight = 0;
   int32_t num_colours = 0;
-  bool w8 = true;
+  bool packed = true;  // packed (col << 8 | w) edges, else split int32 col / w
   std::vector<int32_t> colour;  // by caller id
   std::vector<int32_t> class_item_begin;
   int32_t num_items = 0;
   int32_t num_slots = 0;
 
   int32_t* d_row_ptr = nullptr;
-  int32_t* d_col = nullptr;
-  void* d_w = nullptr;
+  int32_t* d_adj = nullptr;  // packed format
+  int32_t* d_col = nullptr;  // split format
+  int32_t* d_w = nullptr;    // split format
   int8_t* d_spins = nullptr;
   int32_t* d_orig = nullptr;
   int32_t* d_pos = nullptr;
   WorkItem* d_items = nullptr;
-  int32_t* d_split_acc = nullptr;
-  int32_t* d_split_cnt = nullptr;
-  int32_t* d_split_parts = nullptr;
+  unsigned long long* d_slice_acc = nullptr;
+  int32_t* d_slice_parts = nullptr;
   unsigned long long* d_energy = nullptr;
   int32_t* d_flag = nullptr;
   int8_t* d_tmp = nullptr;
@@ -458,14 +232,14 @@ struct ising_graph {
   DevGraph dev() const {
     DevGraph d;
     d.row_ptr = d_row_ptr;
+    d.adj = d_adj;
     d.col = d_col;
     d.w = d_w;
     d.spins = d_spins;
     d.orig = d_orig;
     d.items = d_items;
-    d.split_acc = d_split_acc;
-    d.split_cnt = d_split_cnt;
-    d.split_parts = d_split_parts;
+    d.slice_acc = d_slice_acc;
+    d.slice_parts = d_slice_parts;
     return d;
   }
 };
@@ -473,9 +247,9 @@ struct ising_graph {
 namespace {
 
 void free_device(ising_graph* g) {
-  void* ptrs[] = {g->d_row_ptr, g->d_col,         g->d_w,           g->d_spins,
-                  g->d_orig,    g->d_pos,         g->d_items,       g->d_split_acc,
-                  g->d_split_cnt, g->d_split_parts, g->d_energy,    g->d_flag,
+  void* ptrs[] = {g->d_row_ptr, g->d_adj, g->d_col,  g->d_w,           g->d_spins,
+                  g->d_orig,    g->d_pos,         g->d_items,       g->d_slice_acc,
+                  g->d_slice_parts, g->d_energy,  g->d_flag,
                   g->d_tmp,     g->d_class_items, g->d_all_items, g->d_barrier};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -522,10 +296,10 @@ cudaError_t launch_items(ising_graph* g, const int32_t* phase_items, const int32
   const int grid = grid_for(widest, kWarpsPerBlock, g->num_sms * 64);
   const DevGraph d = g->dev();
   g->launches++;
-  if (g->w8)
-    items_kernel<int8_t, PASS><<<grid, kBlock, 0, g->stream>>>(d, phase_items, pb, pe, a, energy_out);
+  if (g->packed)
+    items_kernel<true, PASS><<<grid, kBlock, 0, g->stream>>>(d, phase_items, pb, pe, a, energy_out);
   else
-    items_kernel<int32_t, PASS><<<grid, kBlock, 0, g->stream>>>(d, phase_items, pb, pe, a, energy_out);
+    items_kernel<false, PASS><<<grid, kBlock, 0, g->stream>>>(d, phase_items, pb, pe, a, energy_out);
   return cudaGetLastError();
 }
 
@@ -542,11 +316,11 @@ int check_device_error(ising_graph* g) {
   return ISING_OK;
 }
 
-template <typename WT, int PASS>
+template <bool PACKED, int PASS>
 cudaError_t launch_persistent_t(ising_graph* g, const int32_t* phase_items, int num_phases,
                                 uint64_t t_begin, uint32_t sweeps, uint64_t T, uint64_t T0,
                                 uint32_t replica, PhiloxKey key) {
-  auto kernel = persistent_kernel<WT, PASS>;
+  auto kernel = persistent_kernel<PACKED, PASS>;
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kPersistBlock, 0);
   if (e != cudaSuccess) return e;
@@ -568,11 +342,11 @@ template <int PASS>
 cudaError_t launch_persistent(ising_graph* g, const int32_t* phase_items, int num_phases,
                               uint64_t t_begin, uint32_t sweeps, uint64_t T, uint64_t T0,
                               uint32_t replica, PhiloxKey key) {
-  if (g->w8)
-    return launch_persistent_t<int8_t, PASS>(g, phase_items, num_phases, t_begin, sweeps, T, T0,
-                                             replica, key);
-  return launch_persistent_t<int32_t, PASS>(g, phase_items, num_phases, t_begin, sweeps, T, T0,
-                                            replica, key);
+  if (g->packed)
+    return launch_persistent_t<true, PASS>(g, phase_items, num_phases, t_begin, sweeps, T, T0,
+                                           replica, key);
+  return launch_persistent_t<false, PASS>(g, phase_items, num_phases, t_begin, sweeps, T, T0,
+                                          replica, key);
 }
 
 int compute_energy(ising_graph* g, int64_t* out) {
@@ -635,12 +409,13 @@ int ising_create(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, c
   g->nnz = hg.nnz;
   g->total_weight = hg.total_weight;
   g->num_colours = hg.num_colours;
-  g->w8 = hg.fits_int8 && !(flags & ISING_CREATE_WEIGHTS_I32);
+  // Packed entries need int8 weights and column indices below 2^24 - 1.
+  g->packed = hg.fits_int8 && hg.n < (1 << 24) - 1 && !(flags & ISING_CREATE_WEIGHTS_I32);
 
   WorkPlan plan;
   try {
     // ~32 resident warps per SM share a class; rows longer than a share are sliced.
-    isingx::build_work_plan(hg, g->num_sms * 32, 64, 32 * kRowsPerLane, &plan);
+    isingx::build_work_plan(hg, g->num_sms * 32, 64, 32 * isingx::kRowsPerLane, &plan);
     g->colour = hg.colour;
     g->class_item_begin = plan.class_item_begin;
   } catch (const std::bad_alloc&) {
@@ -650,33 +425,28 @@ int ising_create(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, c
   g->num_items = static_cast<int32_t>(plan.items.size());
   g->num_slots = static_cast<int32_t>(plan.split_parts.size());
 
-  std::vector<int8_t> w8;
   cudaError_t e = cudaSuccess;
   const size_t N = static_cast<size_t>(hg.n);
   const size_t NNZ = static_cast<size_t>(hg.nnz);
   do {
     if ((e = alloc_copy(&g->d_row_ptr, hg.row_ptr.data(), N + 1, g->stream)) != cudaSuccess) break;
-    if ((e = alloc_copy(&g->d_col, hg.col.data(), NNZ, g->stream)) != cudaSuccess) break;
-    if (g->w8) {
-      w8.resize(NNZ);
-      for (size_t k = 0; k < NNZ; ++k) w8[k] = static_cast<int8_t>(hg.w[k]);
-      int8_t* p = nullptr;
-      e = alloc_copy(&p, w8.data(), NNZ, g->stream);
-      g->d_w = p;
+    if (g->packed) {
+      // reuse the host column array for the packed words
+      for (size_t k = 0; k < NNZ; ++k)
+        hg.col[k] = static_cast<int32_t>((static_cast<uint32_t>(hg.col[k]) << 8) |
+                                         (static_cast<uint32_t>(hg.w[k]) & 0xffu));
+      if ((e = alloc_copy(&g->d_adj, hg.col.data(), NNZ, g->stream)) != cudaSuccess) break;
     } else {
-      int32_t* p = nullptr;
-      e = alloc_copy(&p, hg.w.data(), NNZ, g->stream);
-      g->d_w = p;
+      if ((e = alloc_copy(&g->d_col, hg.col.data(), NNZ, g->stream)) != cudaSuccess) break;
+      if ((e = alloc_copy(&g->d_w, hg.w.data(), NNZ, g->stream)) != cudaSuccess) break;
     }
-    if (e != cudaSuccess) break;
     if ((e = alloc_copy<int8_t>(&g->d_spins, nullptr, N, g->stream)) != cudaSuccess) break;
     if ((e = alloc_copy(&g->d_orig, hg.perm.data(), N, g->stream)) != cudaSuccess) break;
     if ((e = alloc_copy(&g->d_pos, hg.pos.data(), N, g->stream)) != cudaSuccess) break;
     if ((e = alloc_copy(&g->d_items, plan.items.data(), plan.items.size(), g->stream)) != cudaSuccess) break;
     const size_t slots = plan.split_parts.size();
-    if ((e = alloc_copy<int32_t>(&g->d_split_acc, nullptr, slots, g->stream)) != cudaSuccess) break;
-    if ((e = alloc_copy<int32_t>(&g->d_split_cnt, nullptr, slots, g->stream)) != cudaSuccess) break;
-    if ((e = alloc_copy(&g->d_split_parts, plan.split_parts.data(), slots, g->stream)) != cudaSuccess) break;
+    if ((e = alloc_copy<unsigned long long>(&g->d_slice_acc, nullptr, slots, g->stream)) != cudaSuccess) break;
+    if ((e = alloc_copy(&g->d_slice_parts, plan.split_parts.data(), slots, g->stream)) != cudaSuccess) break;
     if ((e = alloc_copy<unsigned long long>(&g->d_energy, nullptr, 1, g->stream)) != cudaSuccess) break;
     if ((e = alloc_copy<int32_t>(&g->d_flag, nullptr, 1, g->stream)) != cudaSuccess) break;
     if ((e = alloc_copy<int8_t>(&g->d_tmp, nullptr, N, g->stream)) != cudaSuccess) break;

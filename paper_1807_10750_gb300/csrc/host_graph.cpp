@@ -202,7 +202,8 @@ void build_work_plan(const HostGraph& g, int32_t target_warps, int32_t min_edges
       const int64_t d = (int64_t)g.row_ptr[(size_t)v + 1] - g.row_ptr[(size_t)v];
       if (d > L) {
         flush(v);
-        const int64_t parts = (d + L - 1) / L;
+        // at most 65535 slices per row (the packed combine counts them in 16 bits)
+        const int64_t parts = std::min<int64_t>((d + L - 1) / L, 65535);
         const int64_t chunk = (d + parts - 1) / parts;
         const int32_t slot = (int32_t)plan->split_parts.size();
         plan->split_parts.push_back((int32_t)parts);
