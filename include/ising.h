@@ -213,6 +213,41 @@ int ising_num_edges(ising_graph* g, int64_t* out_m);
  * (ISING_ENGINE_*). Default ISING_ENGINE_AUTO. */
 int ising_set_engine(ising_graph* g, int engine);
 
+/* Largest vertex count ising_energy_csr_static accepts. */
+#define ISING_STATIC_MAX_VERTICES (1 << 24)
+
+/*
+ * ising_energy_csr_static -- energy H and cut of a spin vector on a CSR graph
+ * that the caller owns, computed without allocating any memory. The paper has
+ * no counterpart to this call. It exists for callers that cannot call
+ * cudaMalloc: code whose device memory all belongs to a pool it does not
+ * control, code held to a fixed memory budget, and loops where cudaMalloc's
+ * host blocking and implicit device synchronisation are not acceptable.
+ *
+ *   n        number of vertices, 1 <= n <= ISING_STATIC_MAX_VERTICES; a larger
+ *            n returns ISING_ERANGE before any device work.
+ *   row_ptr  device int32[n+1]; col, w: device int32[row_ptr[n]]. A symmetric
+ *            CSR adjacency: every undirected edge in both rows, no self-loops,
+ *            col entries in [0, n). Repeated entries simply add. Not validated.
+ *   spins    device int8[n], values +1 / -1.
+ *   out      device int64[2]; receives {H, cut}: H = sum over undirected edges
+ *            of w_ij s_i s_j and cut = (W - H) / 2, W = sum of the weights.
+ *   cuda_stream  stream for the two kernels (asynchronous; NULL = default).
+ *
+ * Scratch: one file-scope device array of ISING_STATIC_MAX_VERTICES / 1024
+ * pairs of int64 (256 KiB). Every GPU that loads the library holds it until
+ * the process exits. The first call on a device looks up the array's address;
+ * make that first call before any stream capture. All calls on a device share
+ * the array (each call rewrites what it reads, so nothing needs clearing);
+ * calls whose kernels overlap on the GPU race and return wrong results, so
+ * order them. The call never allocates or frees device or host memory.
+ * Errors: ISING_EINVAL (n <= 0 or a null row_ptr/spins/out), ISING_ERANGE,
+ * ISING_ECUDA.
+ */
+int ising_energy_csr_static(int32_t n, const int32_t* row_ptr, const int32_t* col,
+                            const int32_t* w, const int8_t* spins, int64_t* out,
+                            void* cuda_stream);
+
 /* ising_launch_count -- number of CUDA kernels this handle has launched since
  * ising_create (a diagnostic for benchmarks). */
 int ising_launch_count(ising_graph* g, uint64_t* out);

@@ -35,13 +35,14 @@ ISING_ENGINE_AUTO = 0
 ISING_ENGINE_PHASE = 1
 ISING_ENGINE_PERSISTENT = 2
 ISING_CREATE_WEIGHTS_I32 = 1
+ISING_STATIC_MAX_VERTICES = 1 << 24
 
 # Every entry point declared in include/ising.h.
 EXPORTS = (
     "ising_create", "ising_anneal", "ising_energy", "ising_cut", "ising_total_weight",
     "ising_get_spins", "ising_set_spins", "ising_init_random", "ising_num_colours",
     "ising_colouring", "ising_num_edges", "ising_set_engine", "ising_destroy",
-    "ising_strerror", "ising_plan_colouring", "ising_launch_count",
+    "ising_strerror", "ising_plan_colouring", "ising_launch_count", "ising_energy_csr_static",
 )
 
 
@@ -88,6 +89,7 @@ def lib():
         L.ising_destroy.restype = None
         L.ising_plan_colouring.argtypes = [ctypes.c_int32, ctypes.c_int64, vp, vp, vp, i32p, i32p]
         L.ising_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
+        L.ising_energy_csr_static.argtypes = [ctypes.c_int32, vp, vp, vp, vp, vp, vp]
         L.ising_strerror.argtypes = [ctypes.c_int]
         L.ising_strerror.restype = ctypes.c_char_p
         for name in EXPORTS:
@@ -118,7 +120,7 @@ def _buffer(x, dtype, n: int | None, writable: bool):
     """(pointer, on_device, keepalive) for a numpy array or torch tensor."""
     if hasattr(x, "data_ptr") and hasattr(x, "is_cuda"):
         import torch  # only when a tensor is passed
-        want = {np.int8: torch.int8, np.int32: torch.int32}[dtype]
+        want = {np.int8: torch.int8, np.int32: torch.int32, np.int64: torch.int64}[dtype]
         if x.dtype != want:
             raise TypeError(f"expected a {want} tensor")
         if not x.is_contiguous() or (n is not None and x.numel() != n):
@@ -253,6 +255,21 @@ def ising_plan_colouring(n: int, src, dst, w):
 
 def ising_set_engine(g: IsingGraph, engine: int) -> None:
     _check(lib().ising_set_engine(g.ptr, engine), "ising_set_engine")
+
+
+def ising_energy_csr_static(n: int, row_ptr, col, w, spins, out, stream=None) -> None:
+    """Energy and cut of ``spins`` on a caller-owned device CSR graph into the
+    device int64[2] ``out``, allocating nothing (see include/ising.h). All
+    arguments are torch CUDA tensors: row_ptr/col/w int32, spins int8."""
+    def ptr(t, dtype):
+        p, on_dev, _ = _buffer(t, dtype, None, False)
+        if not on_dev:
+            raise TypeError("ising_energy_csr_static takes device tensors")
+        return p
+    _check(lib().ising_energy_csr_static(n, ptr(row_ptr, np.int32), ptr(col, np.int32),
+                                         ptr(w, np.int32), ptr(spins, np.int8),
+                                         ptr(out, np.int64), _stream(stream)),
+           "ising_energy_csr_static")
 
 
 def ising_launch_count(g: IsingGraph) -> int:
