@@ -44,6 +44,8 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweeps", type=int, default=None,
+                    help="override the workload's schedule length (profiling runs only)")
     return ap.parse_args()
 
 
@@ -124,9 +126,11 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def build_workload(name):
+def build_workload(name, sweeps=None):
     import synth
     g, sch = synth.workload(name)
+    if sweeps is not None:
+        sch = dict(sch, sweeps=sweeps)
     return g, sch
 
 
@@ -217,7 +221,7 @@ def main():
         dist.barrier()
     import paper_1807_10750_gb300 as P
 
-    g, sch = build_workload(args.workload)
+    g, sch = build_workload(args.workload, args.sweeps)
     T, p0, seed = sch["sweeps"], sch["p0"], sch["seed"] + 7919 * rank
     stream = torch.cuda.Stream()
     engine = {"auto": P.ISING_ENGINE_AUTO, "phase": P.ISING_ENGINE_PHASE,

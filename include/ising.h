@@ -90,7 +90,7 @@ enum {
 
 /* Which kernel engine runs a deterministic anneal (all give identical spins). */
 enum {
-  ISING_ENGINE_AUTO = 0,       /* the library picks */
+  ISING_ENGINE_AUTO = 0,       /* persistent if the device supports cooperative launches */
   ISING_ENGINE_PHASE = 1,      /* one kernel launch per colour class */
   ISING_ENGINE_PERSISTENT = 2  /* one cooperative launch per anneal call, bounded grid barrier */
 };

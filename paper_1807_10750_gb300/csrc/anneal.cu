@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(kBlock, 4)
     const int ie = __ldg(phase_items + c + 1);
     for (int i = __ldg(phase_items + c) + warp; i < ie; i += nwarps) {
       isingx::Staged<PACKED> st;
-      isingx::stage_item<PACKED>(d, i, a, lane, st);
+      isingx::stage_item<PACKED>(d, d.items[i], a, lane, st);
       isingx::finish_item<PACKED, PASS>(d, st, a, lane, energy);
     }
   }
@@ -79,6 +79,27 @@ __global__ void __launch_bounds__(kBlock, 4)
   }
 }
 
+// Arguments of sweep t of a linear schedule of T sweeps starting at threshold
+// T0 (ISING_SCHED_LINEAR in ising.h).
+__device__ __forceinline__ SweepArgs sweep_args(uint64_t t, uint64_t T, uint64_t T0,
+                                                uint32_t replica, isingx::PhiloxKey key) {
+  SweepArgs sa;
+  sa.t = static_cast<uint32_t>(t);
+  sa.replica = replica;
+  sa.key = key;
+  sa.thr = (T <= 1) ? 0u : static_cast<uint32_t>((T0 * (T - 1 - t)) / (T - 1));
+  return sa;
+}
+
+// Item `warp` of colour class cls, or an empty item if the class has fewer.
+__device__ __forceinline__ WorkItem first_item(const DevGraph& d, const int32_t* phase_items,
+                                               int cls, int warp) {
+  const int i = __ldg(phase_items + cls) + warp;
+  WorkItem it = {0, 0, 0, 0};
+  if (i < __ldg(phase_items + cls + 1)) it = d.items[i];
+  return it;
+}
+
 // Persistent engine: one cooperative launch runs every sweep of an anneal
 // call. Warp w takes items w, w + nwarps, ... of each colour class. Between
 // arriving at the grid barrier and waiting on it, the warp stages its first
@@ -93,29 +114,22 @@ __global__ void __launch_bounds__(kPersistBlock, 2)
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * kPersistBlock + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * kPersistBlock) >> 5;
-  auto sweep_args = [&](uint32_t k) {
-    SweepArgs sa;
-    const uint64_t t = t_begin + k;
-    sa.t = static_cast<uint32_t>(t);
-    sa.replica = replica;
-    sa.key = key;
-    sa.thr = (T <= 1) ? 0u : static_cast<uint32_t>((T0 * (T - 1 - t)) / (T - 1));
-    return sa;
-  };
   long long unused = 0;
   unsigned target = 0;
   uint32_t k = 0;
   int c = 0;
-  SweepArgs a = sweep_args(0);
+  SweepArgs a = sweep_args(t_begin + 0, T, T0, replica, key);
   int ib = __ldg(phase_items), ie = __ldg(phase_items + 1);
   isingx::Staged<PACKED> st;
   bool have = ib + warp < ie;
-  if (have) isingx::stage_item<PACKED>(d, ib + warp, a, lane, st);
+  if (have) isingx::stage_item<PACKED>(d, d.items[ib + warp], a, lane, st);
+  // the warp's first item of the following class, loaded one class ahead
+  WorkItem next = first_item(d, phase_items, num_phases > 1 ? 1 : 0, warp);
   for (;;) {
     if (have) {
       isingx::finish_item<PACKED, PASS>(d, st, a, lane, unused);
       for (int i = ib + warp + nwarps; i < ie; i += nwarps) {
-        isingx::stage_item<PACKED>(d, i, a, lane, st);
+        isingx::stage_item<PACKED>(d, d.items[i], a, lane, st);
         isingx::finish_item<PACKED, PASS>(d, st, a, lane, unused);
       }
     }
@@ -125,14 +139,16 @@ __global__ void __launch_bounds__(kPersistBlock, 2)
     if (sync) isingx::barrier_arrive(bs);
     if (sweep_end) {
       c = 0;
-      a = sweep_args(++k);
+      ++k;
+      a = sweep_args(t_begin + k, T, T0, replica, key);
     } else {
       ++c;
     }
     ib = __ldg(phase_items + c);
     ie = __ldg(phase_items + c + 1);
     have = ib + warp < ie;
-    if (have) isingx::stage_item<PACKED>(d, ib + warp, a, lane, st);
+    if (have) isingx::stage_item<PACKED>(d, next, a, lane, st);
+    next = first_item(d, phase_items, c + 1 < num_phases ? c + 1 : 0, warp);
     if (sync) {
       target += gridDim.x;
       if (!isingx::barrier_wait(bs, target)) return;
@@ -215,6 +231,9 @@ struct ising_graph {
   int32_t* d_adj = nullptr;  // packed format
   int32_t* d_col = nullptr;  // split format
   int32_t* d_w = nullptr;    // split format
+  int32_t* d_ell = nullptr;      // sliced ELL, packed format
+  int32_t* d_ell_col = nullptr;  // sliced ELL, split format
+  int32_t* d_ell_w = nullptr;    // sliced ELL, split format
   int8_t* d_spins = nullptr;
   int32_t* d_orig = nullptr;
   int32_t* d_pos = nullptr;
@@ -235,6 +254,9 @@ struct ising_graph {
     d.adj = d_adj;
     d.col = d_col;
     d.w = d_w;
+    d.ell = d_ell;
+    d.ell_col = d_ell_col;
+    d.ell_w = d_ell_w;
     d.spins = d_spins;
     d.orig = d_orig;
     d.items = d_items;
@@ -247,7 +269,7 @@ struct ising_graph {
 namespace {
 
 void free_device(ising_graph* g) {
-  void* ptrs[] = {g->d_row_ptr, g->d_adj, g->d_col,  g->d_w,           g->d_spins,
+  void* ptrs[] = {g->d_row_ptr, g->d_adj, g->d_col,  g->d_w,  g->d_ell, g->d_ell_col, g->d_ell_w, g->d_spins,
                   g->d_orig,    g->d_pos,         g->d_items,       g->d_slice_acc,
                   g->d_slice_parts, g->d_energy,  g->d_flag,
                   g->d_tmp,     g->d_class_items, g->d_all_items, g->d_barrier};
@@ -415,7 +437,8 @@ int ising_create(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, c
   WorkPlan plan;
   try {
     // ~32 resident warps per SM share a class; rows longer than a share are sliced.
-    isingx::build_work_plan(hg, g->num_sms * 32, 64, 32 * isingx::kRowsPerLane, &plan);
+    isingx::build_work_plan(hg, g->num_sms * 32, 64, 32 * isingx::kRowsPerLane,
+                            isingx::light_slots(g->packed), &plan);
     g->colour = hg.colour;
     g->class_item_begin = plan.class_item_begin;
   } catch (const std::bad_alloc&) {
@@ -439,6 +462,18 @@ int ising_create(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, c
     } else {
       if ((e = alloc_copy(&g->d_col, hg.col.data(), NNZ, g->stream)) != cudaSuccess) break;
       if ((e = alloc_copy(&g->d_w, hg.w.data(), NNZ, g->stream)) != cudaSuccess) break;
+    }
+    const size_t NELL = plan.ell_col.size();
+    if (g->packed) {
+      for (size_t k = 0; k < NELL; ++k)
+        plan.ell_col[k] = plan.ell_col[k] < 0
+                              ? -1
+                              : static_cast<int32_t>((static_cast<uint32_t>(plan.ell_col[k]) << 8) |
+                                                     (static_cast<uint32_t>(plan.ell_w[k]) & 0xffu));
+      if ((e = alloc_copy(&g->d_ell, plan.ell_col.data(), NELL, g->stream)) != cudaSuccess) break;
+    } else {
+      if ((e = alloc_copy(&g->d_ell_col, plan.ell_col.data(), NELL, g->stream)) != cudaSuccess) break;
+      if ((e = alloc_copy(&g->d_ell_w, plan.ell_w.data(), NELL, g->stream)) != cudaSuccess) break;
     }
     if ((e = alloc_copy<int8_t>(&g->d_spins, nullptr, N, g->stream)) != cudaSuccess) break;
     if ((e = alloc_copy(&g->d_orig, hg.perm.data(), N, g->stream)) != cudaSuccess) break;
@@ -491,7 +526,13 @@ int ising_anneal(ising_graph* g, const ising_schedule* sched, uint32_t sweeps, u
   g->stream = static_cast<cudaStream_t>(cuda_stream);
   if (sweeps == 0) return ISING_OK;
   const PhiloxKey key = isingx::philox_key(seed, 0u);
-  const int engine = g->engine == ISING_ENGINE_AUTO ? ISING_ENGINE_PHASE : g->engine;
+  // AUTO: the persistent engine when the device supports cooperative launches.
+  int engine = g->engine;
+  if (engine == ISING_ENGINE_AUTO) {
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, g->device);
+    engine = coop ? ISING_ENGINE_PERSISTENT : ISING_ENGINE_PHASE;
+  }
   if (engine == ISING_ENGINE_PERSISTENT) {
     const uint64_t T0 = linear_t0(sched->p0);
     if (mode == ISING_MODE_RACY)

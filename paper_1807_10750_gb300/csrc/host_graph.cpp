@@ -178,30 +178,25 @@ int build_host_graph(int32_t n, int64_t m, const int32_t* src, const int32_t* ds
 }
 
 void build_work_plan(const HostGraph& g, int32_t target_warps, int32_t min_edges,
-                     int32_t max_rows, WorkPlan* plan) {
+                     int32_t max_rows, int32_t light_slots, WorkPlan* plan) {
   plan->items.clear();
   plan->split_parts.clear();
+  plan->ell_col.clear();
+  plan->ell_w.clear();
   plan->class_item_begin.assign((size_t)g.num_colours + 1, 0);
   plan->max_class_items = 0;
   if (target_warps < 1) target_warps = 1;
-  if (min_edges < 1) min_edges = 1;
+  if (min_edges < light_slots) min_edges = light_slots;
   if (max_rows < 1) max_rows = 1;
+  auto degree = [&](int32_t v) { return (int64_t)g.row_ptr[(size_t)v + 1] - g.row_ptr[(size_t)v]; };
   for (int32_t c = 0; c < g.num_colours; ++c) {
     const int32_t vb = g.class_begin[(size_t)c], ve = g.class_begin[(size_t)c + 1];
     const int64_t E = (int64_t)g.row_ptr[(size_t)ve] - g.row_ptr[(size_t)vb];
     const int64_t L = std::max<int64_t>(min_edges, (E + target_warps - 1) / target_warps);
-    int32_t cur_v = -1, cur_rows = 0;
-    int64_t cur_edges = 0;
-    auto flush = [&](int32_t v_end) {
-      if (cur_rows > 0)
-        plan->items.push_back({cur_v, v_end, g.row_ptr[(size_t)cur_v], g.row_ptr[(size_t)v_end]});
-      cur_rows = 0;
-      cur_edges = 0;
-    };
-    for (int32_t v = vb; v < ve; ++v) {
-      const int64_t d = (int64_t)g.row_ptr[(size_t)v + 1] - g.row_ptr[(size_t)v];
+    int32_t v = vb;
+    while (v < ve) {
+      const int64_t d = degree(v);
       if (d > L) {
-        flush(v);
         // at most 65535 slices per row (the packed combine counts them in 16 bits)
         const int64_t parts = std::min<int64_t>((d + L - 1) / L, 65535);
         const int64_t chunk = (d + parts - 1) / parts;
@@ -209,18 +204,51 @@ void build_work_plan(const HostGraph& g, int32_t target_warps, int32_t min_edges
         plan->split_parts.push_back((int32_t)parts);
         const int64_t e0 = g.row_ptr[(size_t)v];
         for (int64_t k = 0; k < parts; ++k) {
-          const int64_t a = e0 + k * chunk;
-          const int64_t b = std::min<int64_t>(e0 + d, a + chunk);
-          plan->items.push_back({v, -(slot + 1), (int32_t)a, (int32_t)b});
+          const int64_t a0 = e0 + k * chunk;
+          const int64_t b0 = std::min<int64_t>(e0 + d, a0 + chunk);
+          plan->items.push_back({v, -(slot + 1), (int32_t)a0, (int32_t)b0});
         }
+        ++v;
         continue;
       }
-      if (cur_rows > 0 && (cur_rows == max_rows || cur_edges + d > L)) flush(v);
-      if (cur_rows == 0) cur_v = v;
-      cur_rows++;
-      cur_edges += d;
+      if (d > light_slots) {
+        // group item: CSR rows until the edge budget, the row cap, or the
+        // first light row
+        int32_t end = v;
+        int64_t edges = 0;
+        while (end < ve && end - v < max_rows && degree(end) > light_slots &&
+               (end == v || edges + degree(end) <= L)) {
+          edges += degree(end);
+          ++end;
+        }
+        plan->items.push_back({v, end, g.row_ptr[(size_t)v], g.row_ptr[(size_t)end]});
+        v = end;
+        continue;
+      }
+      // light item: the widest row is the first (degree order)
+      const int32_t D = (int32_t)d;
+      const int32_t R = D <= light_slots / 4 ? 4 : (D <= light_slots / 2 ? 2 : 1);
+      int32_t end = v;
+      int64_t edges = 0;
+      while (end < ve && end - v < 32 * R && (end == v || edges + degree(end) <= L)) {
+        edges += degree(end);
+        ++end;
+      }
+      const int32_t nv = end - v;
+      const int64_t off = (int64_t)plan->ell_col.size();
+      plan->ell_col.resize((size_t)(off + (int64_t)D * nv), -1);
+      plan->ell_w.resize((size_t)(off + (int64_t)D * nv), 0);
+      for (int32_t r = 0; r < nv; ++r) {
+        const int64_t rb = g.row_ptr[(size_t)(v + r)];
+        const int64_t deg = degree(v + r);
+        for (int64_t k = 0; k < deg; ++k) {
+          plan->ell_col[(size_t)(off + k * nv + r)] = g.col[(size_t)(rb + k)];
+          plan->ell_w[(size_t)(off + k * nv + r)] = g.w[(size_t)(rb + k)];
+        }
+      }
+      plan->items.push_back({v, end, (int32_t)off, -(D + 1)});
+      v = end;
     }
-    flush(ve);
     plan->class_item_begin[(size_t)c + 1] = (int32_t)plan->items.size();
     plan->max_class_items = std::max<int32_t>(
         plan->max_class_items,

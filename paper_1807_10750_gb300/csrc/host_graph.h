@@ -8,11 +8,14 @@
 
 namespace isingx {
 
-// A unit of sweep work for one warp. Two kinds:
-//  * whole rows: vertices [v_begin, v_end) of one colour class, all of their
-//    edges [e_begin, e_end) (v_end > v_begin);
-//  * a slice of one heavy row: vertex v_begin, edges [e_begin, e_end), and
-//    v_end = -(slot + 1) names the partial-sum slot that combines the slices.
+// A unit of sweep work for one warp. Three kinds:
+//  * light rows (every row of degree <= the light slot count): vertices
+//    [v_begin, v_end) of one colour class stored in sliced-ELL form starting
+//    at ELL word e_begin, with e_end = -(D + 1) for D slots per row;
+//  * group rows: vertices [v_begin, v_end) with all of their CSR entries
+//    [e_begin, e_end) (e_end >= 0);
+//  * a slice of one heavy row: vertex v_begin, CSR entries [e_begin, e_end),
+//    and v_end = -(slot + 1) names the partial-sum slot that combines slices.
 struct WorkItem {
   int32_t v_begin, v_end, e_begin, e_end;
 };
@@ -39,6 +42,8 @@ struct WorkPlan {
   std::vector<WorkItem> items;
   std::vector<int32_t> class_item_begin;  // num_colours + 1
   std::vector<int32_t> split_parts;       // per slot: number of slices
+  std::vector<int32_t> ell_col;           // sliced-ELL columns of light items (-1: none)
+  std::vector<int32_t> ell_w;             // sliced-ELL weights (0 where the column is -1)
   int32_t max_class_items = 0;
 };
 
@@ -46,10 +51,12 @@ struct WorkPlan {
 int build_host_graph(int32_t n, int64_t m, const int32_t* src, const int32_t* dst,
                      const int32_t* w, HostGraph* out);
 
-// Splits each colour class into work items of at most ~ceil(class edges /
-// target_warps) edges (never fewer than min_edges), at most max_rows rows each;
-// rows longer than that are sliced.
+// Splits each colour class into work items of at most L = max(min_edges,
+// ceil(class edges / target_warps)) edges. Within a class rows are ordered by
+// degree, so a class is: rows longer than L (sliced), then rows longer than
+// light_slots (group items of up to max_rows rows), then light rows (items of
+// up to 32 * rows_per_lane(D) rows, D = the item's widest row).
 void build_work_plan(const HostGraph& g, int32_t target_warps, int32_t min_edges,
-                     int32_t max_rows, WorkPlan* plan);
+                     int32_t max_rows, int32_t light_slots, WorkPlan* plan);
 
 }  // namespace isingx

@@ -3,12 +3,13 @@
 // engine.
 //
 // A warp processes one work item (see host_graph.h) in two steps:
-//  * stage_item: everything that does not depend on the spins -- the item,
-//    its row offsets, the first round of (column, weight) pairs and the
-//    random-flip decisions (Philox words compared with the sweep's threshold);
+//  * stage_item: everything that does not depend on the spins -- for light
+//    rows the sliced-ELL words of the item and the random-flip decisions of
+//    Algorithm 2 (Philox words against the sweep's threshold), for a slice of
+//    a heavy row its first round of CSR words;
 //  * finish_item: the neighbour-spin gathers, the local fields
-//    f_i = sum_j w_ij s_j (Eq. 2), the update s_i <- -sign(f_i) (tie keeps) and
-//    the flip of Algorithm 2, then the spin stores.
+//    f_i = sum_j w_ij s_j (Eq. 2), the update s_i <- -sign(f_i) (f_i = 0 keeps
+//    s_i), the flip and the spin store.
 // The persistent engine stages the next colour class's item while it waits at
 // the grid barrier, so only the gathers and the update follow the barrier.
 #pragma once
@@ -21,25 +22,34 @@
 namespace isingx {
 
 constexpr unsigned kFullMask = 0xffffffffu;
-constexpr int kRowsPerLane = 4;      // work items hold at most 32 * kRowsPerLane rows
-// Edges per row (light rows) or per lane (slices) loaded per round: 4 packed
-// words, or 2 split (column, weight) pairs, to stay within 64 registers.
-template <bool PACKED>
-__host__ __device__ constexpr int edge_slots() {
-  return PACKED ? 4 : 2;
+constexpr int kRowsPerLane = 4;  // light items hold at most 32 * kRowsPerLane rows
+
+// Words a lane stages for a light item: 16 packed words or 8 split
+// (column, weight) pairs, shaped as rows-per-lane x slots-per-row =
+// 4 x 4, 2 x 8 or 1 x 16 (packed) and 4 x 2, 2 x 4 or 1 x 8 (split).
+__host__ __device__ constexpr int light_slots(bool packed) { return packed ? 16 : 8; }
+
+// Rows per lane of a light item whose widest row has D slots.
+__host__ __device__ constexpr int light_rows_per_lane(int D, bool packed) {
+  return D <= light_slots(packed) / 4 ? 4 : (D <= light_slots(packed) / 2 ? 2 : 1);
 }
-constexpr int kLightMeanDegree = 16;  // items up to this mean degree use one lane per row
 
 enum ItemPass { kPassDet = 0, kPassRacy = 1, kPassEnergy = 2 };
 
-// Edge formats. Packed: one int32 per CSR entry, (col << 8) | (w & 0xff),
-// used when every weight fits in int8 and n < 2^24 - 1 (so no valid word is
-// -1). Split: an int32 column array and an int32 weight array.
+// Edge formats. Packed: one int32 per entry, (col << 8) | (w & 0xff), used
+// when every weight fits in int8 and n < 2^24 - 1 (so no valid word is -1).
+// Split: an int32 column array and an int32 weight array (column -1 = none).
+// CSR arrays hold every row; the sliced-ELL arrays hold the light items' rows
+// (item-major, then slot-major, then row: slot k of row r of an item with nv
+// rows starting at word b is word b + k * nv + r; missing slots are -1).
 struct DevGraph {
   const int32_t* row_ptr;
-  const int32_t* adj;  // packed entries (packed format)
-  const int32_t* col;  // split format
-  const int32_t* w;    // split format
+  const int32_t* adj;      // CSR packed
+  const int32_t* col;      // CSR split
+  const int32_t* w;        // CSR split
+  const int32_t* ell;      // sliced ELL packed
+  const int32_t* ell_col;  // sliced ELL split
+  const int32_t* ell_w;    // sliced ELL split
   int8_t* spins;
   const int32_t* orig;
   const WorkItem* items;
@@ -79,7 +89,7 @@ __device__ __forceinline__ int spin_at(const DevGraph& d, int j) {
   return (PASS == kPassRacy) ? ld_relaxed_s8(d.spins + j) : static_cast<int>(d.spins[j]);
 }
 
-// One loaded CSR entry (or none) in either format.
+// One loaded entry (or none) in either format.
 template <bool PACKED>
 struct Edge;
 
@@ -88,6 +98,9 @@ struct Edge<true> {
   int word;
   __device__ __forceinline__ void load(const DevGraph& d, int e, bool ok) {
     word = ok ? __ldg(d.adj + e) : -1;
+  }
+  __device__ __forceinline__ void load_ell(const DevGraph& d, int e, bool ok) {
+    word = ok ? __ldg(d.ell + e) : -1;
   }
   __device__ __forceinline__ bool valid() const { return word != -1; }
   __device__ __forceinline__ int col() const { return static_cast<int>(static_cast<unsigned>(word) >> 8); }
@@ -101,6 +114,10 @@ struct Edge<false> {
     c = ok ? __ldg(d.col + e) : -1;
     w = ok ? __ldg(d.w + e) : 0;
   }
+  __device__ __forceinline__ void load_ell(const DevGraph& d, int e, bool ok) {
+    c = ok ? __ldg(d.ell_col + e) : -1;
+    w = ok ? __ldg(d.ell_w + e) : 0;
+  }
   __device__ __forceinline__ bool valid() const { return c >= 0; }
   __device__ __forceinline__ int col() const { return c; }
   __device__ __forceinline__ int weight() const { return w; }
@@ -111,27 +128,24 @@ __device__ __forceinline__ int edge_term(const DevGraph& d, const Edge<PACKED>& 
   return x.valid() ? x.weight() * spin_at<PASS>(d, x.col()) : 0;
 }
 
-// sum of w_e * s_col[e] over e = e0, e0 + step, ... < e1, several edges per
+// sum of w_e * s_col[e] over CSR entries e = e0, e0 + step, ... < e1, four per
 // round so that each lane keeps several loads in flight.
 template <bool PACKED, int PASS>
 __device__ __forceinline__ int strided_field(const DevGraph& d, int e0, int e1, int step) {
-  constexpr int S = edge_slots<PACKED>();
   int f = 0;
-  for (int e = e0; e < e1; e += S * step) {
-    Edge<PACKED> x[S];
+  for (int e = e0; e < e1; e += 4 * step) {
+    Edge<PACKED> x[4];
 #pragma unroll
-    for (int u = 0; u < S; ++u) x[u].load(d, e + u * step, e + u * step < e1);
+    for (int u = 0; u < 4; ++u) x[u].load(d, e + u * step, e + u * step < e1);
 #pragma unroll
-    for (int u = 0; u < S; ++u) f += edge_term<PACKED, PASS>(d, x[u]);
+    for (int u = 0; u < 4; ++u) f += edge_term<PACKED, PASS>(d, x[u]);
   }
   return f;
 }
 
-// Algorithm 2's random flip for position v (caller's id orig[v]) in sweep a.t.
-__device__ __forceinline__ bool flip_drawn(const DevGraph& d, int v, const SweepArgs& a) {
-  if (a.thr == 0u) return false;
-  const uint32_t o = static_cast<uint32_t>(__ldg(d.orig + v));
-  return philox4x32_10_word0(o, a.t, a.replica, 0u, a.key) < a.thr;
+// Algorithm 2's random flip of the vertex whose caller id is o, in sweep a.t.
+__device__ __forceinline__ bool flip_drawn(uint32_t o, const SweepArgs& a) {
+  return a.thr != 0u && philox4x32_10_word0(o, a.t, a.replica, 0u, a.key) < a.thr;
 }
 
 // Eq. 2 under the max-cut sign (s <- -sign f, f = 0 keeps s), then the flip.
@@ -155,56 +169,81 @@ template <bool PACKED>
 struct Staged {
   WorkItem it;
   int kind;
-  int rp[kRowsPerLane];  // light: row begin
-  int re[kRowsPerLane];  // light: row end
-  Edge<PACKED> x[kRowsPerLane][edge_slots<PACKED>()];
-  unsigned flips;  // light: bit r for row lane + 32 r; slice: bit 0 (lane 0)
+  unsigned flips;                       // light: bit r = row lane + 32 r flips
+  Edge<PACKED> x[light_slots(PACKED)];  // light: rows x slots; slice: first round
 };
 
-template <bool PACKED>
-__device__ __forceinline__ void stage_item(const DevGraph& d, int index, const SweepArgs& a,
-                                           int lane, Staged<PACKED>& s) {
-  constexpr int S = edge_slots<PACKED>();
-  s.it = d.items[index];
-  s.flips = 0;
-  if (s.it.v_end < 0) {
-    s.kind = kStageSlice;
-    const int e0 = s.it.e_begin + lane;
-#pragma unroll
-    for (int u = 0; u < S; ++u) s.x[0][u].load(d, e0 + 32 * u, e0 + 32 * u < s.it.e_end);
-    if (lane == 0 && flip_drawn(d, s.it.v_begin, a)) s.flips = 1;
-    return;
-  }
+__device__ __forceinline__ int item_kind(const WorkItem& it) {
+  if (it.v_end < 0) return kStageSlice;
+  return it.e_end < 0 ? kStageLight : kStageGroup;
+}
+
+template <bool PACKED, int R>
+__device__ __forceinline__ void stage_light_shape(const DevGraph& d, Staged<PACKED>& s,
+                                                  const SweepArgs& a, int lane) {
+  constexpr int DM = light_slots(PACKED) / R;
   const int nv = s.it.v_end - s.it.v_begin;
-  if (s.it.e_end - s.it.e_begin > kLightMeanDegree * nv) {
-    s.kind = kStageGroup;
+  const int D = -s.it.e_end - 1;
+  const int base = s.it.e_begin;
+  int orig[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int row = lane + 32 * r;
+    const bool valid = row < nv;
+    orig[r] = valid ? __ldg(d.orig + s.it.v_begin + row) : -1;
+#pragma unroll
+    for (int k = 0; k < DM; ++k) s.x[r * DM + k].load_ell(d, base + k * nv + row, valid && k < D);
+  }
+  s.flips = 0;
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+    if (orig[r] >= 0 && flip_drawn(static_cast<uint32_t>(orig[r]), a)) s.flips |= 1u << r;
+}
+
+template <bool PACKED>
+__device__ __forceinline__ void stage_item(const DevGraph& d, const WorkItem& it,
+                                           const SweepArgs& a, int lane, Staged<PACKED>& s) {
+  s.it = it;
+  s.kind = item_kind(it);
+  if (s.kind == kStageSlice) {
+    const int e0 = it.e_begin + lane;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) s.x[u].load(d, e0 + 32 * u, e0 + 32 * u < it.e_end);
     return;
   }
-  s.kind = kStageLight;
+  if (s.kind == kStageGroup) return;
+  const int R = light_rows_per_lane(-it.e_end - 1, PACKED);
+  if (R == 4)
+    stage_light_shape<PACKED, 4>(d, s, a, lane);
+  else if (R == 2)
+    stage_light_shape<PACKED, 2>(d, s, a, lane);
+  else
+    stage_light_shape<PACKED, 1>(d, s, a, lane);
+}
+
+template <bool PACKED, int PASS, int R>
+__device__ __forceinline__ void finish_light_shape(const DevGraph& d, const Staged<PACKED>& s,
+                                                   int lane, long long& energy) {
+  constexpr int DM = light_slots(PACKED) / R;
+  const int nv = s.it.v_end - s.it.v_begin;
 #pragma unroll
-  for (int r = 0; r < kRowsPerLane; ++r) {
-    const int v = s.it.v_begin + lane + 32 * r;
-    s.rp[r] = 0;
-    s.re[r] = 0;
-    if (v < s.it.v_end) {
-      s.rp[r] = __ldg(d.row_ptr + v);
-      s.re[r] = __ldg(d.row_ptr + v + 1);
+  for (int r = 0; r < R; ++r) {
+    int f = 0;
+#pragma unroll
+    for (int k = 0; k < DM; ++k) f += edge_term<PACKED, PASS>(d, s.x[r * DM + k]);
+    if (lane + 32 * r < nv) {
+      const int v = s.it.v_begin + lane + 32 * r;
+      if (PASS == kPassEnergy)
+        energy += static_cast<long long>(d.spins[v]) * f;
+      else
+        apply_update<PASS>(d, v, f, (s.flips >> r) & 1u);
     }
-  }
-#pragma unroll
-  for (int r = 0; r < kRowsPerLane; ++r)
-#pragma unroll
-    for (int u = 0; u < S; ++u) s.x[r][u].load(d, s.rp[r] + u, s.rp[r] + u < s.re[r]);
-#pragma unroll
-  for (int r = 0; r < kRowsPerLane; ++r) {
-    const int v = s.it.v_begin + lane + 32 * r;
-    if (v < s.it.v_end && flip_drawn(d, v, a)) s.flips |= 1u << r;
   }
 }
 
-// Rows of mean degree above kLightMeanDegree: lane groups of g lanes (power of
-// two >= a quarter of the mean degree) gather one row per pass, 32 / g rows per
-// pass; the 32 fields of a chunk are then moved to one lane each.
+// Rows too heavy for a light item but not sliced: lane groups of g lanes
+// (power of two >= a quarter of the mean degree) gather one CSR row per pass,
+// 32 / g rows per pass; the 32 fields of a chunk are then moved to one lane each.
 template <bool PACKED, int PASS>
 __device__ __forceinline__ void finish_group_rows(const DevGraph& d, const WorkItem& it,
                                                   const SweepArgs& a, int lane,
@@ -235,75 +274,53 @@ __device__ __forceinline__ void finish_group_rows(const DevGraph& d, const WorkI
       if (PASS == kPassEnergy)
         energy += static_cast<long long>(d.spins[v]) * my_f;
       else
-        apply_update<PASS>(d, v, my_f, flip_drawn(d, v, a));
+        apply_update<PASS>(d, v, my_f, flip_drawn(static_cast<uint32_t>(__ldg(d.orig + v)), a));
     }
   }
 }
 
 template <bool PACKED, int PASS>
-__device__ __forceinline__ void finish_item(const DevGraph& d, Staged<PACKED>& s,
+__device__ __forceinline__ void finish_item(const DevGraph& d, const Staged<PACKED>& s,
                                             const SweepArgs& a, int lane, long long& energy) {
-  constexpr int S = edge_slots<PACKED>();
+  if (s.kind == kStageLight) {
+    const int R = light_rows_per_lane(-s.it.e_end - 1, PACKED);
+    if (R == 4)
+      finish_light_shape<PACKED, PASS, 4>(d, s, lane, energy);
+    else if (R == 2)
+      finish_light_shape<PACKED, PASS, 2>(d, s, lane, energy);
+    else
+      finish_light_shape<PACKED, PASS, 1>(d, s, lane, energy);
+    return;
+  }
   if (s.kind == kStageGroup) {
     finish_group_rows<PACKED, PASS>(d, s.it, a, lane, energy);
     return;
   }
-  if (s.kind == kStageSlice) {
-    int f = 0;
+  // a slice of one heavy row
+  int f = 0;
 #pragma unroll
-    for (int u = 0; u < S; ++u) f += edge_term<PACKED, PASS>(d, s.x[0][u]);
-    f += strided_field<PACKED, PASS>(d, s.it.e_begin + lane + 32 * S, s.it.e_end, 32);
+  for (int u = 0; u < 4; ++u) f += edge_term<PACKED, PASS>(d, s.x[u]);
+  f += strided_field<PACKED, PASS>(d, s.it.e_begin + lane + 128, s.it.e_end, 32);
+  const int v = s.it.v_begin;
+  const bool flip = (PASS != kPassEnergy && lane == 0) &&
+                    flip_drawn(static_cast<uint32_t>(__ldg(d.orig + v)), a);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(kFullMask, f, o);
-    const int v = s.it.v_begin;
-    if (PASS == kPassEnergy) {
-      if (lane == 0) energy += static_cast<long long>(d.spins[v]) * f;
-      return;
-    }
-    if (lane == 0) {
-      const int slot = -s.it.v_end - 1;
-      const int parts = __ldg(d.slice_parts + slot);
-      const unsigned long long mine =
-          kSliceUnit + static_cast<unsigned long long>(static_cast<long long>(f) + kSliceBias);
-      const unsigned long long old = atomicAdd(d.slice_acc + slot, mine);
-      if (static_cast<int>(old >> 48) == parts - 1) {
-        const long long low = static_cast<long long>((old & kSliceLowMask) + (mine & kSliceLowMask));
-        const int total = static_cast<int>(low - static_cast<long long>(parts) * kSliceBias);
-        d.slice_acc[slot] = 0ull;
-        apply_update<PASS>(d, v, total, s.flips & 1u);
-      }
-    }
+  for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(kFullMask, f, o);
+  if (PASS == kPassEnergy) {
+    if (lane == 0) energy += static_cast<long long>(d.spins[v]) * f;
     return;
   }
-  // light rows: the staged round, then further rounds (reusing the staged
-  // registers) for rows longer than S
-  int f[kRowsPerLane];
-  int kmax = 0;
-#pragma unroll
-  for (int r = 0; r < kRowsPerLane; ++r) {
-    f[r] = 0;
-#pragma unroll
-    for (int u = 0; u < S; ++u) f[r] += edge_term<PACKED, PASS>(d, s.x[r][u]);
-    kmax = max(kmax, s.re[r] - s.rp[r]);
-  }
-  for (int k = S; k < kmax; k += S) {
-#pragma unroll
-    for (int r = 0; r < kRowsPerLane; ++r)
-#pragma unroll
-      for (int u = 0; u < S; ++u) s.x[r][u].load(d, s.rp[r] + k + u, s.rp[r] + k + u < s.re[r]);
-#pragma unroll
-    for (int r = 0; r < kRowsPerLane; ++r)
-#pragma unroll
-      for (int u = 0; u < S; ++u) f[r] += edge_term<PACKED, PASS>(d, s.x[r][u]);
-  }
-#pragma unroll
-  for (int r = 0; r < kRowsPerLane; ++r) {
-    const int v = s.it.v_begin + lane + 32 * r;
-    if (v < s.it.v_end) {
-      if (PASS == kPassEnergy)
-        energy += static_cast<long long>(d.spins[v]) * f[r];
-      else
-        apply_update<PASS>(d, v, f[r], (s.flips >> r) & 1u);
+  if (lane == 0) {
+    const int slot = -s.it.v_end - 1;
+    const int parts = __ldg(d.slice_parts + slot);
+    const unsigned long long mine =
+        kSliceUnit + static_cast<unsigned long long>(static_cast<long long>(f) + kSliceBias);
+    const unsigned long long old = atomicAdd(d.slice_acc + slot, mine);
+    if (static_cast<int>(old >> 48) == parts - 1) {
+      const long long low = static_cast<long long>((old & kSliceLowMask) + (mine & kSliceLowMask));
+      const int total = static_cast<int>(low - static_cast<long long>(parts) * kSliceBias);
+      d.slice_acc[slot] = 0ull;
+      apply_update<PASS>(d, v, total, flip);
     }
   }
 }
