@@ -52,7 +52,8 @@ constexpr int kPersistBlock = 512;
 template <bool PACKED, int PASS>
 __global__ void __launch_bounds__(kBlock, 4)
     items_kernel(DevGraph d, const int32_t* __restrict__ phase_items, int phase_begin,
-                 int phase_end, SweepArgs a, unsigned long long* energy_out) {
+                 int phase_end, SweepArgs a, isingx::PhiloxRounds rk,
+                 unsigned long long* energy_out) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * kBlock + threadIdx.x) >> 5;
   const int nwarps = gridDim.x * kWarpsPerBlock;
@@ -61,8 +62,8 @@ __global__ void __launch_bounds__(kBlock, 4)
     const int ie = __ldg(phase_items + c + 1);
     for (int i = __ldg(phase_items + c) + warp; i < ie; i += nwarps) {
       isingx::Staged<PACKED> st;
-      isingx::stage_item<PACKED>(d, d.items[i], a, lane, st);
-      isingx::finish_item<PACKED, PASS>(d, st, a, lane, energy);
+      isingx::stage_item<PACKED>(d, d.items[i], a, rk, lane, st);
+      isingx::finish_item<PACKED, PASS>(d, st, a, rk, lane, energy);
     }
   }
   if (PASS == kPassEnergy) {
@@ -82,11 +83,10 @@ __global__ void __launch_bounds__(kBlock, 4)
 // Arguments of sweep t of a linear schedule of T sweeps starting at threshold
 // T0 (ISING_SCHED_LINEAR in ising.h).
 __device__ __forceinline__ SweepArgs sweep_args(uint64_t t, uint64_t T, uint64_t T0,
-                                                uint32_t replica, isingx::PhiloxKey key) {
+                                                uint32_t replica) {
   SweepArgs sa;
   sa.t = static_cast<uint32_t>(t);
   sa.replica = replica;
-  sa.key = key;
   sa.thr = (T <= 1) ? 0u : static_cast<uint32_t>((T0 * (T - 1 - t)) / (T - 1));
   return sa;
 }
@@ -110,7 +110,7 @@ template <bool PACKED, int PASS>
 __global__ void __launch_bounds__(kPersistBlock, 2)
     persistent_kernel(DevGraph d, const int32_t* __restrict__ phase_items, int num_phases,
                       uint64_t t_begin, uint32_t sweeps, uint64_t T, uint64_t T0, uint32_t replica,
-                      isingx::PhiloxKey key, BarrierState* bs) {
+                      isingx::PhiloxRounds rk, BarrierState* bs) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * kPersistBlock + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * kPersistBlock) >> 5;
@@ -118,19 +118,19 @@ __global__ void __launch_bounds__(kPersistBlock, 2)
   unsigned target = 0;
   uint32_t k = 0;
   int c = 0;
-  SweepArgs a = sweep_args(t_begin + 0, T, T0, replica, key);
+  SweepArgs a = sweep_args(t_begin + 0, T, T0, replica);
   int ib = __ldg(phase_items), ie = __ldg(phase_items + 1);
   isingx::Staged<PACKED> st;
   bool have = ib + warp < ie;
-  if (have) isingx::stage_item<PACKED>(d, d.items[ib + warp], a, lane, st);
+  if (have) isingx::stage_item<PACKED>(d, d.items[ib + warp], a, rk, lane, st);
   // the warp's first item of the following class, loaded one class ahead
   WorkItem next = first_item(d, phase_items, num_phases > 1 ? 1 : 0, warp);
   for (;;) {
     if (have) {
-      isingx::finish_item<PACKED, PASS>(d, st, a, lane, unused);
+      isingx::finish_item<PACKED, PASS>(d, st, a, rk, lane, unused);
       for (int i = ib + warp + nwarps; i < ie; i += nwarps) {
-        isingx::stage_item<PACKED>(d, d.items[i], a, lane, st);
-        isingx::finish_item<PACKED, PASS>(d, st, a, lane, unused);
+        isingx::stage_item<PACKED>(d, d.items[i], a, rk, lane, st);
+        isingx::finish_item<PACKED, PASS>(d, st, a, rk, lane, unused);
       }
     }
     const bool sweep_end = (c + 1 == num_phases);
@@ -140,14 +140,14 @@ __global__ void __launch_bounds__(kPersistBlock, 2)
     if (sweep_end) {
       c = 0;
       ++k;
-      a = sweep_args(t_begin + k, T, T0, replica, key);
+      a = sweep_args(t_begin + k, T, T0, replica);
     } else {
       ++c;
     }
     ib = __ldg(phase_items + c);
     ie = __ldg(phase_items + c + 1);
     have = ib + warp < ie;
-    if (have) isingx::stage_item<PACKED>(d, next, a, lane, st);
+    if (have) isingx::stage_item<PACKED>(d, next, a, rk, lane, st);
     next = first_item(d, phase_items, c + 1 < num_phases ? c + 1 : 0, warp);
     if (sync) {
       target += gridDim.x;
@@ -156,10 +156,10 @@ __global__ void __launch_bounds__(kPersistBlock, 2)
   }
 }
 
-__global__ void init_random_kernel(int8_t* spins, const int32_t* orig, int n, PhiloxKey key,
-                                   uint32_t replica) {
+__global__ void init_random_kernel(int8_t* spins, const int32_t* orig, int n,
+                                   isingx::PhiloxRounds rk, uint32_t replica) {
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-    const uint32_t x = isingx::philox4x32_10_word0(static_cast<uint32_t>(orig[p]), 0u, replica, 1u, key);
+    const uint32_t x = isingx::philox4x32_10_word0(static_cast<uint32_t>(orig[p]), 0u, replica, 1u, rk);
     spins[p] = (x >> 31) ? int8_t(-1) : int8_t(1);
   }
 }
@@ -250,6 +250,7 @@ struct ising_graph {
 
   DevGraph dev() const {
     DevGraph d;
+    d.pad_col = n;
     d.row_ptr = d_row_ptr;
     d.adj = d_adj;
     d.col = d_col;
@@ -311,7 +312,8 @@ cudaError_t alloc_copy(T** dst, const T* src, size_t count, cudaStream_t s) {
 // host copy is `host_items`.
 template <int PASS>
 cudaError_t launch_items(ising_graph* g, const int32_t* phase_items, const int32_t* host_items,
-                         int pb, int pe, const SweepArgs& a, unsigned long long* energy_out) {
+                         int pb, int pe, const SweepArgs& a, const isingx::PhiloxRounds& rk,
+                         unsigned long long* energy_out) {
   int widest = 0;
   for (int c = pb; c < pe; ++c) widest = std::max(widest, host_items[c + 1] - host_items[c]);
   if (widest == 0) return cudaSuccess;
@@ -319,9 +321,9 @@ cudaError_t launch_items(ising_graph* g, const int32_t* phase_items, const int32
   const DevGraph d = g->dev();
   g->launches++;
   if (g->packed)
-    items_kernel<true, PASS><<<grid, kBlock, 0, g->stream>>>(d, phase_items, pb, pe, a, energy_out);
+    items_kernel<true, PASS><<<grid, kBlock, 0, g->stream>>>(d, phase_items, pb, pe, a, rk, energy_out);
   else
-    items_kernel<false, PASS><<<grid, kBlock, 0, g->stream>>>(d, phase_items, pb, pe, a, energy_out);
+    items_kernel<false, PASS><<<grid, kBlock, 0, g->stream>>>(d, phase_items, pb, pe, a, rk, energy_out);
   return cudaGetLastError();
 }
 
@@ -341,7 +343,7 @@ int check_device_error(ising_graph* g) {
 template <bool PACKED, int PASS>
 cudaError_t launch_persistent_t(ising_graph* g, const int32_t* phase_items, int num_phases,
                                 uint64_t t_begin, uint32_t sweeps, uint64_t T, uint64_t T0,
-                                uint32_t replica, PhiloxKey key) {
+                                uint32_t replica, isingx::PhiloxRounds rk) {
   auto kernel = persistent_kernel<PACKED, PASS>;
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kPersistBlock, 0);
@@ -354,7 +356,7 @@ cudaError_t launch_persistent_t(ising_graph* g, const int32_t* phase_items, int 
   if (e != cudaSuccess) return e;
   DevGraph d = g->dev();
   BarrierState* bs = g->d_barrier;
-  void* args[] = {&d, &phase_items, &num_phases, &t_begin, &sweeps, &T, &T0, &replica, &key, &bs};
+  void* args[] = {&d, &phase_items, &num_phases, &t_begin, &sweeps, &T, &T0, &replica, &rk, &bs};
   g->launches++;
   return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(kernel), dim3(grid),
                                      dim3(kPersistBlock), args, 0, g->stream);
@@ -363,19 +365,20 @@ cudaError_t launch_persistent_t(ising_graph* g, const int32_t* phase_items, int 
 template <int PASS>
 cudaError_t launch_persistent(ising_graph* g, const int32_t* phase_items, int num_phases,
                               uint64_t t_begin, uint32_t sweeps, uint64_t T, uint64_t T0,
-                              uint32_t replica, PhiloxKey key) {
+                              uint32_t replica, const isingx::PhiloxRounds& rk) {
   if (g->packed)
     return launch_persistent_t<true, PASS>(g, phase_items, num_phases, t_begin, sweeps, T, T0,
-                                           replica, key);
+                                           replica, rk);
   return launch_persistent_t<false, PASS>(g, phase_items, num_phases, t_begin, sweeps, T, T0,
-                                          replica, key);
+                                          replica, rk);
 }
 
 int compute_energy(ising_graph* g, int64_t* out) {
   ISING_CUDA(g, cudaMemsetAsync(g->d_energy, 0, sizeof(unsigned long long), g->stream));
   SweepArgs a{};
+  const isingx::PhiloxRounds rk{};
   const int32_t all_items[2] = {0, g->num_items};
-  ISING_CUDA(g, launch_items<kPassEnergy>(g, g->d_all_items, all_items, 0, 1, a, g->d_energy));
+  ISING_CUDA(g, launch_items<kPassEnergy>(g, g->d_all_items, all_items, 0, 1, a, rk, g->d_energy));
   unsigned long long twice = 0;
   ISING_CUDA(g, cudaMemcpyAsync(&twice, g->d_energy, sizeof(twice), cudaMemcpyDeviceToHost, g->stream));
   ISING_CUDA(g, cudaStreamSynchronize(g->stream));
@@ -467,15 +470,18 @@ int ising_create(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, c
     if (g->packed) {
       for (size_t k = 0; k < NELL; ++k)
         plan.ell_col[k] = plan.ell_col[k] < 0
-                              ? -1
+                              ? static_cast<int32_t>(static_cast<uint32_t>(hg.n) << 8)
                               : static_cast<int32_t>((static_cast<uint32_t>(plan.ell_col[k]) << 8) |
                                                      (static_cast<uint32_t>(plan.ell_w[k]) & 0xffu));
       if ((e = alloc_copy(&g->d_ell, plan.ell_col.data(), NELL, g->stream)) != cudaSuccess) break;
     } else {
+      for (size_t k = 0; k < NELL; ++k)
+        if (plan.ell_col[k] < 0) plan.ell_col[k] = hg.n;  // pad entry, weight 0
       if ((e = alloc_copy(&g->d_ell_col, plan.ell_col.data(), NELL, g->stream)) != cudaSuccess) break;
       if ((e = alloc_copy(&g->d_ell_w, plan.ell_w.data(), NELL, g->stream)) != cudaSuccess) break;
     }
-    if ((e = alloc_copy<int8_t>(&g->d_spins, nullptr, N, g->stream)) != cudaSuccess) break;
+    // spins[n] is the pad entry's spin and stays 0
+    if ((e = alloc_copy<int8_t>(&g->d_spins, nullptr, N + 1, g->stream)) != cudaSuccess) break;
     if ((e = alloc_copy(&g->d_orig, hg.perm.data(), N, g->stream)) != cudaSuccess) break;
     if ((e = alloc_copy(&g->d_pos, hg.pos.data(), N, g->stream)) != cudaSuccess) break;
     if ((e = alloc_copy(&g->d_items, plan.items.data(), plan.items.size(), g->stream)) != cudaSuccess) break;
@@ -525,7 +531,7 @@ int ising_anneal(ising_graph* g, const ising_schedule* sched, uint32_t sweeps, u
   if (sched->t_begin > sched->t_total || sweeps > sched->t_total - sched->t_begin) return ISING_EINVAL;
   g->stream = static_cast<cudaStream_t>(cuda_stream);
   if (sweeps == 0) return ISING_OK;
-  const PhiloxKey key = isingx::philox_key(seed, 0u);
+  const isingx::PhiloxRounds rk = isingx::philox_rounds(isingx::philox_key(seed, 0u));
   // AUTO: the persistent engine when the device supports cooperative launches.
   int engine = g->engine;
   if (engine == ISING_ENGINE_AUTO) {
@@ -538,26 +544,25 @@ int ising_anneal(ising_graph* g, const ising_schedule* sched, uint32_t sweeps, u
     if (mode == ISING_MODE_RACY)
       ISING_CUDA(g, launch_persistent<kPassRacy>(g, g->d_class_items, g->num_colours,
                                                  sched->t_begin, sweeps, sched->t_total, T0,
-                                                 sched->replica, key));
+                                                 sched->replica, rk));
     else
       ISING_CUDA(g, launch_persistent<kPassDet>(g, g->d_class_items, g->num_colours,
                                                 sched->t_begin, sweeps, sched->t_total, T0,
-                                                sched->replica, key));
+                                                sched->replica, rk));
     return ISING_OK;
   }
   SweepArgs a;
   a.replica = sched->replica;
-  a.key = key;
   for (uint32_t k = 0; k < sweeps; ++k) {
     const uint64_t t = sched->t_begin + k;
     a.t = static_cast<uint32_t>(t);
     a.thr = linear_threshold(sched->p0, sched->t_total, t);
     const int32_t* hi = g->class_item_begin.data();
     if (mode == ISING_MODE_RACY) {
-      ISING_CUDA(g, launch_items<kPassRacy>(g, g->d_class_items, hi, 0, g->num_colours, a, nullptr));
+      ISING_CUDA(g, launch_items<kPassRacy>(g, g->d_class_items, hi, 0, g->num_colours, a, rk, nullptr));
     } else {
       for (int32_t c = 0; c < g->num_colours; ++c)
-        ISING_CUDA(g, launch_items<kPassDet>(g, g->d_class_items, hi, c, c + 1, a, nullptr));
+        ISING_CUDA(g, launch_items<kPassDet>(g, g->d_class_items, hi, c, c + 1, a, rk, nullptr));
     }
   }
   return ISING_OK;
@@ -638,7 +643,8 @@ int ising_init_random(ising_graph* g, uint64_t seed, uint32_t replica) {
   const int grid = grid_for(g->n, 256, g->num_sms * 8);
   g->launches++;
   init_random_kernel<<<grid, 256, 0, g->stream>>>(g->d_spins, g->d_orig, g->n,
-                                                  isingx::philox_key(seed, 0u), replica);
+                                                  isingx::philox_rounds(isingx::philox_key(seed, 0u)),
+                                                  replica);
   ISING_CUDA(g, cudaGetLastError());
   return ISING_OK;
 }

@@ -24,21 +24,38 @@ __host__ __device__ inline PhiloxKey philox_key(uint64_t seed, uint32_t instance
   return k;
 }
 
+// The ten round keys of a key, computed once per launch and passed as kernel
+// parameters so that the per-draw rounds read them as constants.
+struct PhiloxRounds {
+  uint32_t lo[10], hi[10];
+};
+
+__host__ __device__ inline PhiloxRounds philox_rounds(PhiloxKey k) {
+  PhiloxRounds r;
+  uint32_t a = k.lo, b = k.hi;
+  for (int i = 0; i < 10; ++i) {
+    r.lo[i] = a;
+    r.hi[i] = b;
+    a += 0x9E3779B9u;
+    b += 0xBB67AE85u;
+  }
+  return r;
+}
+
+// Word 0 of Philox4x32-10 for counter (x0, x1, x2, x3). Each round is two
+// 32x32 -> 64 products and two three-way xors.
 __device__ __forceinline__ uint32_t philox4x32_10_word0(uint32_t x0, uint32_t x1, uint32_t x2,
-                                                         uint32_t x3, PhiloxKey key) {
-  uint32_t ka = key.lo, kb = key.hi;
+                                                         uint32_t x3, const PhiloxRounds& rk) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-    const uint32_t a_lo = 0xD2511F53u * x0;
-    const uint32_t a_hi = __umulhi(0xD2511F53u, x0);
-    const uint32_t b_lo = 0xCD9E8D57u * x2;
-    const uint32_t b_hi = __umulhi(0xCD9E8D57u, x2);
-    x0 = b_hi ^ x1 ^ ka;
-    x1 = b_lo;
-    x2 = a_hi ^ x3 ^ kb;
-    x3 = a_lo;
-    ka += 0x9E3779B9u;
-    kb += 0xBB67AE85u;
+    const uint64_t pa = static_cast<uint64_t>(0xD2511F53u) * x0;
+    const uint64_t pb = static_cast<uint64_t>(0xCD9E8D57u) * x2;
+    const uint32_t n0 = static_cast<uint32_t>(pb >> 32) ^ x1 ^ rk.lo[r];
+    const uint32_t n2 = static_cast<uint32_t>(pa >> 32) ^ x3 ^ rk.hi[r];
+    x1 = static_cast<uint32_t>(pb);
+    x3 = static_cast<uint32_t>(pa);
+    x0 = n0;
+    x2 = n2;
   }
   return x0;
 }

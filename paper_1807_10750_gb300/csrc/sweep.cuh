@@ -41,8 +41,13 @@ enum ItemPass { kPassDet = 0, kPassRacy = 1, kPassEnergy = 2 };
 // Split: an int32 column array and an int32 weight array (column -1 = none).
 // CSR arrays hold every row; the sliced-ELL arrays hold the light items' rows
 // (item-major, then slot-major, then row: slot k of row r of an item with nv
-// rows starting at word b is word b + k * nv + r; missing slots are -1).
+// rows starting at word b is word b + k * nv + r; padding slots hold the pad
+// entry).
+// Missing entries (ELL padding, slots past a row's degree, loads past a range)
+// read as the pad entry: column n, weight 0. spins[n] exists and is 0, so every
+// slot contributes w * s without a validity test.
 struct DevGraph {
+  int32_t pad_col;  // n
   const int32_t* row_ptr;
   const int32_t* adj;      // CSR packed
   const int32_t* col;      // CSR split
@@ -61,7 +66,6 @@ struct SweepArgs {
   uint32_t thr;      // flip iff Philox word 0 < thr
   uint32_t t;        // sweep index (counter word 1)
   uint32_t replica;  // counter word 2
-  PhiloxKey key;
 };
 
 // Sliced rows: each slice adds (1 << 48) + (partial + 2^31) to one 64-bit
@@ -97,12 +101,11 @@ template <>
 struct Edge<true> {
   int word;
   __device__ __forceinline__ void load(const DevGraph& d, int e, bool ok) {
-    word = ok ? __ldg(d.adj + e) : -1;
+    word = ok ? __ldg(d.adj + e) : (d.pad_col << 8);
   }
   __device__ __forceinline__ void load_ell(const DevGraph& d, int e, bool ok) {
-    word = ok ? __ldg(d.ell + e) : -1;
+    word = ok ? __ldg(d.ell + e) : (d.pad_col << 8);
   }
-  __device__ __forceinline__ bool valid() const { return word != -1; }
   __device__ __forceinline__ int col() const { return static_cast<int>(static_cast<unsigned>(word) >> 8); }
   __device__ __forceinline__ int weight() const { return (word << 24) >> 24; }
 };
@@ -111,21 +114,20 @@ template <>
 struct Edge<false> {
   int c, w;
   __device__ __forceinline__ void load(const DevGraph& d, int e, bool ok) {
-    c = ok ? __ldg(d.col + e) : -1;
+    c = ok ? __ldg(d.col + e) : d.pad_col;
     w = ok ? __ldg(d.w + e) : 0;
   }
   __device__ __forceinline__ void load_ell(const DevGraph& d, int e, bool ok) {
-    c = ok ? __ldg(d.ell_col + e) : -1;
+    c = ok ? __ldg(d.ell_col + e) : d.pad_col;
     w = ok ? __ldg(d.ell_w + e) : 0;
   }
-  __device__ __forceinline__ bool valid() const { return c >= 0; }
   __device__ __forceinline__ int col() const { return c; }
   __device__ __forceinline__ int weight() const { return w; }
 };
 
 template <bool PACKED, int PASS>
 __device__ __forceinline__ int edge_term(const DevGraph& d, const Edge<PACKED>& x) {
-  return x.valid() ? x.weight() * spin_at<PASS>(d, x.col()) : 0;
+  return x.weight() * spin_at<PASS>(d, x.col());
 }
 
 // sum of w_e * s_col[e] over CSR entries e = e0, e0 + step, ... < e1, four per
@@ -144,8 +146,8 @@ __device__ __forceinline__ int strided_field(const DevGraph& d, int e0, int e1, 
 }
 
 // Algorithm 2's random flip of the vertex whose caller id is o, in sweep a.t.
-__device__ __forceinline__ bool flip_drawn(uint32_t o, const SweepArgs& a) {
-  return a.thr != 0u && philox4x32_10_word0(o, a.t, a.replica, 0u, a.key) < a.thr;
+__device__ __forceinline__ bool flip_drawn(uint32_t o, const SweepArgs& a, const PhiloxRounds& rk) {
+  return a.thr != 0u && philox4x32_10_word0(o, a.t, a.replica, 0u, rk) < a.thr;
 }
 
 // Eq. 2 under the max-cut sign (s <- -sign f, f = 0 keeps s), then the flip.
@@ -180,7 +182,8 @@ __device__ __forceinline__ int item_kind(const WorkItem& it) {
 
 template <bool PACKED, int R>
 __device__ __forceinline__ void stage_light_shape(const DevGraph& d, Staged<PACKED>& s,
-                                                  const SweepArgs& a, int lane) {
+                                                  const SweepArgs& a, const PhiloxRounds& rk,
+                                                  int lane) {
   constexpr int DM = light_slots(PACKED) / R;
   const int nv = s.it.v_end - s.it.v_begin;
   const int D = -s.it.e_end - 1;
@@ -197,12 +200,13 @@ __device__ __forceinline__ void stage_light_shape(const DevGraph& d, Staged<PACK
   s.flips = 0;
 #pragma unroll
   for (int r = 0; r < R; ++r)
-    if (orig[r] >= 0 && flip_drawn(static_cast<uint32_t>(orig[r]), a)) s.flips |= 1u << r;
+    if (orig[r] >= 0 && flip_drawn(static_cast<uint32_t>(orig[r]), a, rk)) s.flips |= 1u << r;
 }
 
 template <bool PACKED>
 __device__ __forceinline__ void stage_item(const DevGraph& d, const WorkItem& it,
-                                           const SweepArgs& a, int lane, Staged<PACKED>& s) {
+                                           const SweepArgs& a, const PhiloxRounds& rk, int lane,
+                                           Staged<PACKED>& s) {
   s.it = it;
   s.kind = item_kind(it);
   if (s.kind == kStageSlice) {
@@ -214,11 +218,11 @@ __device__ __forceinline__ void stage_item(const DevGraph& d, const WorkItem& it
   if (s.kind == kStageGroup) return;
   const int R = light_rows_per_lane(-it.e_end - 1, PACKED);
   if (R == 4)
-    stage_light_shape<PACKED, 4>(d, s, a, lane);
+    stage_light_shape<PACKED, 4>(d, s, a, rk, lane);
   else if (R == 2)
-    stage_light_shape<PACKED, 2>(d, s, a, lane);
+    stage_light_shape<PACKED, 2>(d, s, a, rk, lane);
   else
-    stage_light_shape<PACKED, 1>(d, s, a, lane);
+    stage_light_shape<PACKED, 1>(d, s, a, rk, lane);
 }
 
 template <bool PACKED, int PASS, int R>
@@ -246,8 +250,8 @@ __device__ __forceinline__ void finish_light_shape(const DevGraph& d, const Stag
 // 32 / g rows per pass; the 32 fields of a chunk are then moved to one lane each.
 template <bool PACKED, int PASS>
 __device__ __forceinline__ void finish_group_rows(const DevGraph& d, const WorkItem& it,
-                                                  const SweepArgs& a, int lane,
-                                                  long long& energy) {
+                                                  const SweepArgs& a, const PhiloxRounds& rk,
+                                                  int lane, long long& energy) {
   const int nv = it.v_end - it.v_begin;
   const int mean = (it.e_end - it.e_begin + nv - 1) / nv;
   int lg = 0;
@@ -274,14 +278,15 @@ __device__ __forceinline__ void finish_group_rows(const DevGraph& d, const WorkI
       if (PASS == kPassEnergy)
         energy += static_cast<long long>(d.spins[v]) * my_f;
       else
-        apply_update<PASS>(d, v, my_f, flip_drawn(static_cast<uint32_t>(__ldg(d.orig + v)), a));
+        apply_update<PASS>(d, v, my_f, flip_drawn(static_cast<uint32_t>(__ldg(d.orig + v)), a, rk));
     }
   }
 }
 
 template <bool PACKED, int PASS>
 __device__ __forceinline__ void finish_item(const DevGraph& d, const Staged<PACKED>& s,
-                                            const SweepArgs& a, int lane, long long& energy) {
+                                            const SweepArgs& a, const PhiloxRounds& rk, int lane,
+                                            long long& energy) {
   if (s.kind == kStageLight) {
     const int R = light_rows_per_lane(-s.it.e_end - 1, PACKED);
     if (R == 4)
@@ -293,7 +298,7 @@ __device__ __forceinline__ void finish_item(const DevGraph& d, const Staged<PACK
     return;
   }
   if (s.kind == kStageGroup) {
-    finish_group_rows<PACKED, PASS>(d, s.it, a, lane, energy);
+    finish_group_rows<PACKED, PASS>(d, s.it, a, rk, lane, energy);
     return;
   }
   // a slice of one heavy row
@@ -303,7 +308,7 @@ __device__ __forceinline__ void finish_item(const DevGraph& d, const Staged<PACK
   f += strided_field<PACKED, PASS>(d, s.it.e_begin + lane + 128, s.it.e_end, 32);
   const int v = s.it.v_begin;
   const bool flip = (PASS != kPassEnergy && lane == 0) &&
-                    flip_drawn(static_cast<uint32_t>(__ldg(d.orig + v)), a);
+                    flip_drawn(static_cast<uint32_t>(__ldg(d.orig + v)), a, rk);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(kFullMask, f, o);
   if (PASS == kPassEnergy) {
