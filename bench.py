@@ -39,7 +39,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="torus1024", choices=["torus1024", "zipf1m", "er800"])
-    ap.add_argument("--engine", default="auto", choices=["auto", "phase", "persistent"])
+    ap.add_argument("--engine", default="auto", choices=["auto", "phase", "persistent", "dataflow"])
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
@@ -225,7 +225,8 @@ def main():
     T, p0, seed = sch["sweeps"], sch["p0"], sch["seed"] + 7919 * rank
     stream = torch.cuda.Stream()
     engine = {"auto": P.ISING_ENGINE_AUTO, "phase": P.ISING_ENGINE_PHASE,
-              "persistent": P.ISING_ENGINE_PERSISTENT}[args.engine]
+              "persistent": P.ISING_ENGINE_PERSISTENT,
+              "dataflow": P.ISING_ENGINE_DATAFLOW}[args.engine]
 
     h = P.ising_create(g.n, g.src, g.dst, g.w, stream=stream)
     P.ising_set_engine(h, engine)

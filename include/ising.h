@@ -92,7 +92,10 @@ enum {
 enum {
   ISING_ENGINE_AUTO = 0,       /* persistent if the device supports cooperative launches */
   ISING_ENGINE_PHASE = 1,      /* one kernel launch per colour class */
-  ISING_ENGINE_PERSISTENT = 2  /* one cooperative launch per anneal call, bounded grid barrier */
+  ISING_ENGINE_PERSISTENT = 2, /* one cooperative launch per anneal call, bounded grid barrier */
+  ISING_ENGINE_DATAFLOW = 3    /* one cooperative launch per anneal call without barriers: each
+                                  neighbour read waits (bounded) until the neighbour carries the
+                                  update the colour order requires; racy mode runs as PERSISTENT */
 };
 
 /* ising_create flags. */

@@ -39,6 +39,7 @@ using isingx::DevGraph;
 using isingx::SweepArgs;
 using isingx::kPassDet;
 using isingx::kPassEnergy;
+using isingx::kPassFlow;
 using isingx::kPassRacy;
 
 constexpr int kBlock = 256;
@@ -85,6 +86,8 @@ __global__ void __launch_bounds__(kBlock, 4)
 __device__ __forceinline__ SweepArgs sweep_args(uint64_t t, uint64_t T, uint64_t T0,
                                                 uint32_t replica) {
   SweepArgs sa;
+  sa.class_lo = 0;
+  sa.par_cur = 0;
   sa.t = static_cast<uint32_t>(t);
   sa.replica = replica;
   sa.thr = (T <= 1) ? 0u : static_cast<uint32_t>((T0 * (T - 1 - t)) / (T - 1));
@@ -156,17 +159,49 @@ __global__ void __launch_bounds__(kPersistBlock, 2)
   }
 }
 
+// Dataflow engine: one cooperative launch runs every sweep with no grid
+// barrier. Warp w takes items w, w + nwarps, ... of each colour class in
+// (sweep, class) order; every neighbour gather waits until the neighbour's
+// state byte shows the update the colour order requires (sweep.cuh,
+// kPassFlow). All warps are resident and each follows that order, so the
+// earliest unfinished item can always proceed. A wait that gives up stops
+// the kernel; the host reports ISING_ETIMEOUT.
+template <bool PACKED>
+__global__ void __launch_bounds__(kPersistBlock, 2)
+    flow_kernel(DevGraph d, const int32_t* __restrict__ phase_items,
+                const int32_t* __restrict__ class_begin, int num_phases, uint64_t t_begin,
+                uint32_t sweeps, uint64_t T, uint64_t T0, uint32_t replica, int par0,
+                isingx::PhiloxRounds rk) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * kPersistBlock + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * kPersistBlock) >> 5;
+  long long unused = 0;
+  isingx::Staged<PACKED> st;
+  for (uint32_t k = 0; k < sweeps; ++k) {
+    SweepArgs a = sweep_args(t_begin + k, T, T0, replica);
+    a.par_cur = par0 ^ static_cast<int>(k & 1u);
+    for (int c = 0; c < num_phases; ++c) {
+      a.class_lo = __ldg(class_begin + c);
+      const int ie = __ldg(phase_items + c + 1);
+      for (int i = __ldg(phase_items + c) + warp; i < ie; i += nwarps) {
+        isingx::stage_item<PACKED>(d, d.items[i], a, rk, lane, st);
+        isingx::finish_item<PACKED, kPassFlow>(d, st, a, rk, lane, unused);
+      }
+    }
+  }
+}
+
 __global__ void init_random_kernel(int8_t* spins, const int32_t* orig, int n,
                                    isingx::PhiloxRounds rk, uint32_t replica) {
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
     const uint32_t x = isingx::philox4x32_10_word0(static_cast<uint32_t>(orig[p]), 0u, replica, 1u, rk);
-    spins[p] = (x >> 31) ? int8_t(-1) : int8_t(1);
+    spins[p] = static_cast<int8_t>(isingx::state_byte((x >> 31) ? -1 : 1, 0));
   }
 }
 
 __global__ void gather_spins_kernel(int8_t* out, const int8_t* spins, const int32_t* pos, int n) {
   for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < n; o += gridDim.x * blockDim.x)
-    out[o] = spins[pos[o]];
+    out[o] = static_cast<int8_t>(isingx::spin_of(spins[pos[o]]));
 }
 
 __global__ void check_spins_kernel(const int8_t* in, int n, int32_t* bad) {
@@ -176,7 +211,7 @@ __global__ void check_spins_kernel(const int8_t* in, int n, int32_t* bad) {
 
 __global__ void scatter_spins_kernel(int8_t* spins, const int8_t* in, const int32_t* pos, int n) {
   for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < n; o += gridDim.x * blockDim.x)
-    spins[pos[o]] = in[o];
+    spins[pos[o]] = static_cast<int8_t>(isingx::state_byte(in[o], 0));
 }
 
 __global__ void fill_spins_kernel(int8_t* spins, int n, int8_t value) {
@@ -217,6 +252,7 @@ struct ising_graph {
   uint64_t launches = 0;
 
   int32_t n = 0;
+  int parity = 0;  // update parity of every state byte (bit 1) between calls
   int64_t num_edges = 0;
   int64_t nnz = 0;
   int64_t total_weight = 0;
@@ -244,6 +280,7 @@ struct ising_graph {
   int32_t* d_flag = nullptr;
   int8_t* d_tmp = nullptr;
   int32_t* d_class_items = nullptr;  // num_colours + 1 item offsets
+  int32_t* d_class_begin = nullptr;  // num_colours + 1 first positions
   int32_t* d_all_items = nullptr;    // {0, num_items}: one phase over every item (energy)
   BarrierState* d_barrier = nullptr;
   int persist_grid = 0;              // co-resident blocks of the persistent kernel
@@ -262,6 +299,7 @@ struct ising_graph {
     d.orig = d_orig;
     d.items = d_items;
     d.slice_acc = d_slice_acc;
+    d.error = d_barrier ? &d_barrier->error : nullptr;
     d.slice_parts = d_slice_parts;
     return d;
   }
@@ -273,7 +311,8 @@ void free_device(ising_graph* g) {
   void* ptrs[] = {g->d_row_ptr, g->d_adj, g->d_col,  g->d_w,  g->d_ell, g->d_ell_col, g->d_ell_w, g->d_spins,
                   g->d_orig,    g->d_pos,         g->d_items,       g->d_slice_acc,
                   g->d_slice_parts, g->d_energy,  g->d_flag,
-                  g->d_tmp,     g->d_class_items, g->d_all_items, g->d_barrier};
+                  g->d_tmp,     g->d_class_items, g->d_all_items, g->d_barrier,
+                  g->d_class_begin};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -371,6 +410,37 @@ cudaError_t launch_persistent(ising_graph* g, const int32_t* phase_items, int nu
                                            replica, rk);
   return launch_persistent_t<false, PASS>(g, phase_items, num_phases, t_begin, sweeps, T, T0,
                                           replica, rk);
+}
+
+template <bool PACKED>
+cudaError_t launch_flow_t(ising_graph* g, uint64_t t_begin, uint32_t sweeps, uint64_t T,
+                          uint64_t T0, uint32_t replica, int par0,
+                          const isingx::PhiloxRounds& rk_in) {
+  auto kernel = flow_kernel<PACKED>;
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kPersistBlock, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+  per_sm = std::min(per_sm, 2);
+  const int grid = per_sm * g->num_sms;
+  e = cudaMemsetAsync(g->d_barrier, 0, sizeof(BarrierState), g->stream);
+  if (e != cudaSuccess) return e;
+  DevGraph d = g->dev();
+  const int32_t* phase_items = g->d_class_items;
+  const int32_t* class_begin = g->d_class_begin;
+  int num_phases = g->num_colours;
+  isingx::PhiloxRounds rk = rk_in;
+  void* args[] = {&d, &phase_items, &class_begin, &num_phases, &t_begin, &sweeps, &T, &T0,
+                  &replica, &par0, &rk};
+  g->launches++;
+  return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(kernel), dim3(grid),
+                                     dim3(kPersistBlock), args, 0, g->stream);
+}
+
+cudaError_t launch_flow(ising_graph* g, uint64_t t_begin, uint32_t sweeps, uint64_t T, uint64_t T0,
+                        uint32_t replica, int par0, const isingx::PhiloxRounds& rk) {
+  if (g->packed) return launch_flow_t<true>(g, t_begin, sweeps, T, T0, replica, par0, rk);
+  return launch_flow_t<false>(g, t_begin, sweeps, T, T0, replica, par0, rk);
 }
 
 int compute_energy(ising_graph* g, int64_t* out) {
@@ -486,7 +556,7 @@ int ising_create(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, c
     if ((e = alloc_copy(&g->d_pos, hg.pos.data(), N, g->stream)) != cudaSuccess) break;
     if ((e = alloc_copy(&g->d_items, plan.items.data(), plan.items.size(), g->stream)) != cudaSuccess) break;
     const size_t slots = plan.split_parts.size();
-    if ((e = alloc_copy<unsigned long long>(&g->d_slice_acc, nullptr, slots, g->stream)) != cudaSuccess) break;
+    if ((e = alloc_copy<unsigned long long>(&g->d_slice_acc, nullptr, 2 * slots, g->stream)) != cudaSuccess) break;
     if ((e = alloc_copy(&g->d_slice_parts, plan.split_parts.data(), slots, g->stream)) != cudaSuccess) break;
     if ((e = alloc_copy<unsigned long long>(&g->d_energy, nullptr, 1, g->stream)) != cudaSuccess) break;
     if ((e = alloc_copy<int32_t>(&g->d_flag, nullptr, 1, g->stream)) != cudaSuccess) break;
@@ -495,8 +565,11 @@ int ising_create(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, c
                         plan.class_item_begin.size(), g->stream)) != cudaSuccess) break;
     const int32_t all_items[2] = {0, g->num_items};
     if ((e = alloc_copy(&g->d_all_items, all_items, 2, g->stream)) != cudaSuccess) break;
+    if ((e = alloc_copy(&g->d_class_begin, hg.class_begin.data(), hg.class_begin.size(),
+                        g->stream)) != cudaSuccess) break;
     if ((e = alloc_copy<BarrierState>(&g->d_barrier, nullptr, 1, g->stream)) != cudaSuccess) break;
-    fill_spins_kernel<<<grid_for(hg.n, 256, g->num_sms * 8), 256, 0, g->stream>>>(g->d_spins, hg.n, 1);
+    fill_spins_kernel<<<grid_for(hg.n, 256, g->num_sms * 8), 256, 0, g->stream>>>(
+        g->d_spins, hg.n, static_cast<int8_t>(isingx::state_byte(1, 0)));
     if ((e = cudaGetLastError()) != cudaSuccess) break;
     e = cudaStreamSynchronize(g->stream);
   } while (false);
@@ -539,7 +612,15 @@ int ising_anneal(ising_graph* g, const ising_schedule* sched, uint32_t sweeps, u
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, g->device);
     engine = coop ? ISING_ENGINE_PERSISTENT : ISING_ENGINE_PHASE;
   }
-  if (engine == ISING_ENGINE_PERSISTENT) {
+  // every sweep updates every vertex once, flipping its update parity
+  const int par0 = g->parity;
+  g->parity ^= static_cast<int>(sweeps & 1u);
+  if (engine == ISING_ENGINE_DATAFLOW && mode == ISING_MODE_DET) {
+    const uint64_t T0 = linear_t0(sched->p0);
+    ISING_CUDA(g, launch_flow(g, sched->t_begin, sweeps, sched->t_total, T0, sched->replica, par0, rk));
+    return ISING_OK;
+  }
+  if (engine == ISING_ENGINE_PERSISTENT || engine == ISING_ENGINE_DATAFLOW) {
     const uint64_t T0 = linear_t0(sched->p0);
     if (mode == ISING_MODE_RACY)
       ISING_CUDA(g, launch_persistent<kPassRacy>(g, g->d_class_items, g->num_colours,
@@ -551,7 +632,7 @@ int ising_anneal(ising_graph* g, const ising_schedule* sched, uint32_t sweeps, u
                                                 sched->replica, rk));
     return ISING_OK;
   }
-  SweepArgs a;
+  SweepArgs a{};
   a.replica = sched->replica;
   for (uint32_t k = 0; k < sweeps; ++k) {
     const uint64_t t = sched->t_begin + k;
@@ -632,6 +713,7 @@ int ising_set_spins(ising_graph* g, const int8_t* in, int on_device) {
   }
   g->launches++;
   scatter_spins_kernel<<<grid, 256, 0, g->stream>>>(g->d_spins, source, g->d_pos, g->n);
+  g->parity = 0;
   ISING_CUDA(g, cudaGetLastError());
   if (!on_device) ISING_CUDA(g, cudaStreamSynchronize(g->stream));
   return ISING_OK;
@@ -642,6 +724,7 @@ int ising_init_random(ising_graph* g, uint64_t seed, uint32_t replica) {
   if (rc != ISING_OK) return rc;
   const int grid = grid_for(g->n, 256, g->num_sms * 8);
   g->launches++;
+  g->parity = 0;
   init_random_kernel<<<grid, 256, 0, g->stream>>>(g->d_spins, g->d_orig, g->n,
                                                   isingx::philox_rounds(isingx::philox_key(seed, 0u)),
                                                   replica);
@@ -690,7 +773,8 @@ int ising_launch_count(ising_graph* g, uint64_t* out) {
 
 int ising_set_engine(ising_graph* g, int engine) {
   if (g == nullptr) return ISING_EINVAL;
-  if (engine != ISING_ENGINE_AUTO && engine != ISING_ENGINE_PHASE && engine != ISING_ENGINE_PERSISTENT)
+  if (engine != ISING_ENGINE_AUTO && engine != ISING_ENGINE_PHASE &&
+      engine != ISING_ENGINE_PERSISTENT && engine != ISING_ENGINE_DATAFLOW)
     return ISING_EINVAL;
   g->engine = engine;
   return ISING_OK;

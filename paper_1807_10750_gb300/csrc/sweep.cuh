@@ -34,7 +34,19 @@ __host__ __device__ constexpr int light_rows_per_lane(int D, bool packed) {
   return D <= light_slots(packed) / 4 ? 4 : (D <= light_slots(packed) / 2 ? 2 : 1);
 }
 
-enum ItemPass { kPassDet = 0, kPassRacy = 1, kPassEnergy = 2 };
+// kPassDet: deterministic colour-class sweep behind grid barriers or launch
+// boundaries; kPassRacy: the asynchronous mode; kPassEnergy: energy reduction;
+// kPassFlow: the deterministic sweep without barriers, each gather waiting
+// until its neighbour's state byte shows the update the colour order requires.
+enum ItemPass { kPassDet = 0, kPassRacy = 1, kPassEnergy = 2, kPassFlow = 3 };
+
+// Spin storage: one state byte per vertex. Bit 0 is 1 for spin -1; bit 1 is
+// the parity of the number of updates the vertex has had since the spins were
+// last set. Every update flips bit 1.
+__host__ __device__ constexpr int spin_of(int b) { return 1 - 2 * (b & 1); }
+__host__ __device__ constexpr int state_byte(int s, int parity) {
+  return (s < 0 ? 1 : 0) | ((parity & 1) << 1);
+}
 
 // Edge formats. Packed: one int32 per entry, (col << 8) | (w & 0xff), used
 // when every weight fits in int8 and n < 2^24 - 1 (so no valid word is -1).
@@ -48,6 +60,7 @@ enum ItemPass { kPassDet = 0, kPassRacy = 1, kPassEnergy = 2 };
 // slot contributes w * s without a validity test.
 struct DevGraph {
   int32_t pad_col;  // n
+  int* error;       // bounded waits record a timeout here
   const int32_t* row_ptr;
   const int32_t* adj;      // CSR packed
   const int32_t* col;      // CSR split
@@ -66,6 +79,8 @@ struct SweepArgs {
   uint32_t thr;      // flip iff Philox word 0 < thr
   uint32_t t;        // sweep index (counter word 1)
   uint32_t replica;  // counter word 2
+  int class_lo;      // kPassFlow: first position of the current colour class
+  int par_cur;       // kPassFlow: update parity every vertex had at the sweep's start
 };
 
 // Sliced rows: each slice adds (1 << 48) + (partial + 2^31) to one 64-bit
@@ -77,20 +92,61 @@ constexpr unsigned long long kSliceUnit = 1ull << 48;
 constexpr unsigned long long kSliceLowMask = kSliceUnit - 1;
 constexpr long long kSliceBias = 1ll << 31;
 
-// Racy mode: neighbour reads and own writes race by design (Sec. IV-B); they
-// are relaxed atomics at GPU scope so the races are defined behaviour.
+// Racy and dataflow passes: spin bytes change while they are read, so reads
+// and writes are relaxed atomics at GPU scope (defined behaviour under the
+// memory model). They order nothing else, so the compiler may schedule other
+// memory operations around them freely (no "memory" clobber); volatile keeps
+// each re-read of a dataflow wait.
 __device__ __forceinline__ int ld_relaxed_s8(const int8_t* p) {
   int v;
-  asm volatile("ld.relaxed.gpu.global.s8 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  asm volatile("ld.relaxed.gpu.global.s8 %0, [%1];" : "=r"(v) : "l"(p));
   return v;
 }
 __device__ __forceinline__ void st_relaxed_s8(int8_t* p, int v) {
-  asm volatile("st.relaxed.gpu.global.s8 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+  asm volatile("st.relaxed.gpu.global.s8 [%0], %1;" ::"l"(p), "r"(v));
+}
+
+__device__ __forceinline__ long long flow_ns() {
+  long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// State byte of vertex j (relaxed for the racy and dataflow passes, whose
+// neighbours change during the pass).
+template <int PASS>
+__device__ __forceinline__ int load_state(const DevGraph& d, int j) {
+  return (PASS == kPassRacy || PASS == kPassFlow) ? (ld_relaxed_s8(d.spins + j) & 3)
+                                                  : static_cast<int>(d.spins[j]);
+}
+
+constexpr long long kFlowBudgetNs = 2000000000LL;  // 2 s per wait
+
+// kPassFlow: neighbour j of a vertex in the current class must have had the
+// update of this sweep if its class comes earlier (parity par_cur ^ 1), and not
+// yet if it comes later (parity par_cur); the pad entry never changes. Re-reads
+// until that holds; gives up (recording a timeout) after kFlowBudgetNs or once
+// any wait has failed.
+__device__ __noinline__ int flow_wait(const DevGraph& d, int j, int need) {
+  const long long t0 = flow_ns();
+  for (;;) {
+    const int b = ld_relaxed_s8(d.spins + j) & 3;
+    if (((b >> 1) & 1) == need) return b;
+    if (*reinterpret_cast<volatile int*>(d.error) != 0) return b;
+    if (flow_ns() - t0 > kFlowBudgetNs) {
+      atomicExch(d.error, 1);
+      return b;
+    }
+  }
 }
 
 template <int PASS>
-__device__ __forceinline__ int spin_at(const DevGraph& d, int j) {
-  return (PASS == kPassRacy) ? ld_relaxed_s8(d.spins + j) : static_cast<int>(d.spins[j]);
+__device__ __forceinline__ int ready_spin(const DevGraph& d, int j, int b, const SweepArgs& a) {
+  if (PASS == kPassFlow && j != d.pad_col) {
+    const int need = (j < a.class_lo) ? (a.par_cur ^ 1) : a.par_cur;
+    if (((b >> 1) & 1) != need) b = flow_wait(d, j, need);
+  }
+  return spin_of(b);
 }
 
 // One loaded entry (or none) in either format.
@@ -125,22 +181,21 @@ struct Edge<false> {
   __device__ __forceinline__ int weight() const { return w; }
 };
 
-template <bool PACKED, int PASS>
-__device__ __forceinline__ int edge_term(const DevGraph& d, const Edge<PACKED>& x) {
-  return x.weight() * spin_at<PASS>(d, x.col());
-}
-
 // sum of w_e * s_col[e] over CSR entries e = e0, e0 + step, ... < e1, four per
 // round so that each lane keeps several loads in flight.
 template <bool PACKED, int PASS>
-__device__ __forceinline__ int strided_field(const DevGraph& d, int e0, int e1, int step) {
+__device__ __forceinline__ int strided_field(const DevGraph& d, int e0, int e1, int step,
+                                             const SweepArgs& a) {
   int f = 0;
   for (int e = e0; e < e1; e += 4 * step) {
     Edge<PACKED> x[4];
+    int b[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) x[u].load(d, e + u * step, e + u * step < e1);
 #pragma unroll
-    for (int u = 0; u < 4; ++u) f += edge_term<PACKED, PASS>(d, x[u]);
+    for (int u = 0; u < 4; ++u) b[u] = load_state<PASS>(d, x[u].col());
+#pragma unroll
+    for (int u = 0; u < 4; ++u) f += x[u].weight() * ready_spin<PASS>(d, x[u].col(), b[u], a);
   }
   return f;
 }
@@ -150,19 +205,26 @@ __device__ __forceinline__ bool flip_drawn(uint32_t o, const SweepArgs& a, const
   return a.thr != 0u && philox4x32_10_word0(o, a.t, a.replica, 0u, rk) < a.thr;
 }
 
-// Eq. 2 under the max-cut sign (s <- -sign f, f = 0 keeps s), then the flip.
+// Eq. 2 under the max-cut sign (s <- -sign f, f = 0 keeps s), then the flip;
+// the state byte's update parity flips.
 template <int PASS>
-__device__ __forceinline__ void apply_update(const DevGraph& d, int v, int f, bool flip) {
-  int s = spin_at<PASS>(d, v);
+__device__ __forceinline__ void apply_update(const DevGraph& d, int v, int f, bool flip,
+                                             const SweepArgs& a) {
+  int b = load_state<PASS>(d, v);
+  // dataflow: a sliced row's previous update may come from another warp; wait
+  // until its state shows that update
+  if (PASS == kPassFlow && ((b >> 1) & 1) != a.par_cur) b = flow_wait(d, v, a.par_cur);
+  int s = spin_of(b);
   if (f > 0)
     s = -1;
   else if (f < 0)
     s = 1;
   if (flip) s = -s;
-  if (PASS == kPassRacy)
-    st_relaxed_s8(d.spins + v, s);
+  const int nb = state_byte(s, ((b >> 1) & 1) ^ 1);
+  if (PASS == kPassRacy || PASS == kPassFlow)
+    st_relaxed_s8(d.spins + v, nb);
   else
-    d.spins[v] = static_cast<int8_t>(s);
+    d.spins[v] = static_cast<int8_t>(nb);
 }
 
 enum StageKind { kStageLight = 0, kStageSlice = 1, kStageGroup = 2 };
@@ -227,20 +289,25 @@ __device__ __forceinline__ void stage_item(const DevGraph& d, const WorkItem& it
 
 template <bool PACKED, int PASS, int R>
 __device__ __forceinline__ void finish_light_shape(const DevGraph& d, const Staged<PACKED>& s,
-                                                   int lane, long long& energy) {
+                                                   const SweepArgs& a, int lane,
+                                                   long long& energy) {
   constexpr int DM = light_slots(PACKED) / R;
   const int nv = s.it.v_end - s.it.v_begin;
+  int b[R * DM];
+#pragma unroll
+  for (int j = 0; j < R * DM; ++j) b[j] = load_state<PASS>(d, s.x[j].col());
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     int f = 0;
 #pragma unroll
-    for (int k = 0; k < DM; ++k) f += edge_term<PACKED, PASS>(d, s.x[r * DM + k]);
+    for (int k = 0; k < DM; ++k)
+      f += s.x[r * DM + k].weight() * ready_spin<PASS>(d, s.x[r * DM + k].col(), b[r * DM + k], a);
     if (lane + 32 * r < nv) {
       const int v = s.it.v_begin + lane + 32 * r;
       if (PASS == kPassEnergy)
-        energy += static_cast<long long>(d.spins[v]) * f;
+        energy += static_cast<long long>(spin_of(d.spins[v])) * f;
       else
-        apply_update<PASS>(d, v, f, (s.flips >> r) & 1u);
+        apply_update<PASS>(d, v, f, (s.flips >> r) & 1u, a);
     }
   }
 }
@@ -268,7 +335,8 @@ __device__ __forceinline__ void finish_group_rows(const DevGraph& d, const WorkI
       const int v = base + p * rows_per_pass + grp;
       int f = 0;
       if (v < it.v_end)
-        f = strided_field<PACKED, PASS>(d, __ldg(d.row_ptr + v) + sub, __ldg(d.row_ptr + v + 1), g);
+        f = strided_field<PACKED, PASS>(d, __ldg(d.row_ptr + v) + sub, __ldg(d.row_ptr + v + 1), g,
+                                        a);
       for (int o = g >> 1; o > 0; o >>= 1) f += __shfl_xor_sync(kFullMask, f, o);
       const int got = __shfl_sync(kFullMask, f, (lane % rows_per_pass) << lg);
       if (lane / rows_per_pass == p) my_f = got;
@@ -276,9 +344,9 @@ __device__ __forceinline__ void finish_group_rows(const DevGraph& d, const WorkI
     const int v = base + lane;
     if (v < it.v_end) {
       if (PASS == kPassEnergy)
-        energy += static_cast<long long>(d.spins[v]) * my_f;
+        energy += static_cast<long long>(spin_of(d.spins[v])) * my_f;
       else
-        apply_update<PASS>(d, v, my_f, flip_drawn(static_cast<uint32_t>(__ldg(d.orig + v)), a, rk));
+        apply_update<PASS>(d, v, my_f, flip_drawn(static_cast<uint32_t>(__ldg(d.orig + v)), a, rk), a);
     }
   }
 }
@@ -290,11 +358,11 @@ __device__ __forceinline__ void finish_item(const DevGraph& d, const Staged<PACK
   if (s.kind == kStageLight) {
     const int R = light_rows_per_lane(-s.it.e_end - 1, PACKED);
     if (R == 4)
-      finish_light_shape<PACKED, PASS, 4>(d, s, lane, energy);
+      finish_light_shape<PACKED, PASS, 4>(d, s, a, lane, energy);
     else if (R == 2)
-      finish_light_shape<PACKED, PASS, 2>(d, s, lane, energy);
+      finish_light_shape<PACKED, PASS, 2>(d, s, a, lane, energy);
     else
-      finish_light_shape<PACKED, PASS, 1>(d, s, lane, energy);
+      finish_light_shape<PACKED, PASS, 1>(d, s, a, lane, energy);
     return;
   }
   if (s.kind == kStageGroup) {
@@ -303,21 +371,28 @@ __device__ __forceinline__ void finish_item(const DevGraph& d, const Staged<PACK
   }
   // a slice of one heavy row
   int f = 0;
+  {
+    int b[4];
 #pragma unroll
-  for (int u = 0; u < 4; ++u) f += edge_term<PACKED, PASS>(d, s.x[u]);
-  f += strided_field<PACKED, PASS>(d, s.it.e_begin + lane + 128, s.it.e_end, 32);
+    for (int u = 0; u < 4; ++u) b[u] = load_state<PASS>(d, s.x[u].col());
+#pragma unroll
+    for (int u = 0; u < 4; ++u) f += s.x[u].weight() * ready_spin<PASS>(d, s.x[u].col(), b[u], a);
+  }
+  f += strided_field<PACKED, PASS>(d, s.it.e_begin + lane + 128, s.it.e_end, 32, a);
   const int v = s.it.v_begin;
   const bool flip = (PASS != kPassEnergy && lane == 0) &&
                     flip_drawn(static_cast<uint32_t>(__ldg(d.orig + v)), a, rk);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(kFullMask, f, o);
   if (PASS == kPassEnergy) {
-    if (lane == 0) energy += static_cast<long long>(d.spins[v]) * f;
+    if (lane == 0) energy += static_cast<long long>(spin_of(d.spins[v])) * f;
     return;
   }
   if (lane == 0) {
-    const int slot = -s.it.v_end - 1;
-    const int parts = __ldg(d.slice_parts + slot);
+    // two accumulators per sliced row: the dataflow pass alternates them by
+    // sweep parity, so a later sweep's slices never meet this sweep's sum
+    const int slot = 2 * (-s.it.v_end - 1) + (PASS == kPassFlow ? a.par_cur : 0);
+    const int parts = __ldg(d.slice_parts + (-s.it.v_end - 1));
     const unsigned long long mine =
         kSliceUnit + static_cast<unsigned long long>(static_cast<long long>(f) + kSliceBias);
     const unsigned long long old = atomicAdd(d.slice_acc + slot, mine);
@@ -325,7 +400,7 @@ __device__ __forceinline__ void finish_item(const DevGraph& d, const Staged<PACK
       const long long low = static_cast<long long>((old & kSliceLowMask) + (mine & kSliceLowMask));
       const int total = static_cast<int>(low - static_cast<long long>(parts) * kSliceBias);
       d.slice_acc[slot] = 0ull;
-      apply_update<PASS>(d, v, total, flip);
+      apply_update<PASS>(d, v, total, flip, a);
     }
   }
 }

@@ -12,7 +12,7 @@ import synth
 
 pytestmark = pytest.mark.gpu
 
-ENGINES = ["phase", "persistent"]
+ENGINES = ["phase", "persistent", "dataflow"]
 
 
 @pytest.fixture(scope="module")
@@ -27,7 +27,7 @@ def P():
 
 def engine_id(P, name):
     return {"phase": P.ISING_ENGINE_PHASE, "persistent": P.ISING_ENGINE_PERSISTENT,
-            "auto": P.ISING_ENGINE_AUTO}[name]
+            "dataflow": P.ISING_ENGINE_DATAFLOW, "auto": P.ISING_ENGINE_AUTO}[name]
 
 
 def gpu_anneal(P, g, s0, *, seed, p0, T, t_begin=0, sweeps=None, flags=0, engine="auto",
