@@ -216,6 +216,58 @@ int ising_num_edges(ising_graph* g, int64_t* out_m);
  * (ISING_ENGINE_*). Default ISING_ENGINE_AUTO. */
 int ising_set_engine(ising_graph* g, int engine);
 
+/* ------------------------------------------------------------------------
+ * Batched annealing of many independent instances.
+ *
+ * Every instance (a max-cut graph as in ising_create) is annealed in
+ * `replicas` independent replicas by the deterministic colour-class schedule
+ * of ISING_MODE_DET, all in one persistent kernel launch (captured in a CUDA
+ * graph and replayed). The randomness of instance g, replica r is Philox4x32-10
+ * with key (lo32(seed), hi32(seed) ^ g * 0x9E3779B9) and counter
+ * (vertex id within g, sweep t, r, 0) for flips and (vertex id, 0, r, 1) for
+ * ising_batch_init_random -- so each instance/replica reproduces a single-graph
+ * anneal keyed by that instance and replica exactly.
+ * ------------------------------------------------------------------------ */
+typedef struct ising_batch ising_batch; /* opaque */
+
+/*
+ * ising_batch_create -- num_graphs instances. Instance g has n[g] vertices and
+ * m[g] listed edges; its edges are the m[g] consecutive entries of src/dst/w
+ * starting after those of instances 0..g-1 (host int32 arrays; ids local to the
+ * instance, same rules as ising_create). replicas: 1..8. Every merged weight
+ * must fit in int8, and every instance must have at most 204800 vertices
+ * (ISING_ERANGE otherwise). Spins start at +1.
+ */
+int ising_batch_create(int32_t num_graphs, const int32_t* n, const int64_t* m, const int32_t* src,
+                       const int32_t* dst, const int32_t* w, uint32_t replicas, void* cuda_stream,
+                       ising_batch** out);
+/* ising_batch_init_random -- initial spins of every instance and replica. */
+int ising_batch_init_random(ising_batch* b, uint64_t seed);
+/* ising_batch_anneal -- sweeps t_begin .. t_begin + sweeps - 1 of `sched`
+ * (ISING_SCHED_LINEAR; sched->replica is ignored, every replica runs) for every
+ * instance and replica. Asynchronous on cuda_stream. */
+int ising_batch_anneal(ising_batch* b, const ising_schedule* sched, uint32_t sweeps, uint64_t seed,
+                       void* cuda_stream);
+/* ising_batch_cuts -- host int64[num_graphs * replicas]: cut of instance g,
+ * replica r at index g * replicas + r. Synchronises the stream. */
+int ising_batch_cuts(ising_batch* b, int64_t* out_cuts);
+/* ising_batch_get_spins / ising_batch_set_spins -- host int8[n[graph]] of one
+ * instance and replica in the caller's vertex order (set: values +1 / -1,
+ * ISING_EINVAL otherwise). Synchronise the stream. */
+int ising_batch_get_spins(ising_batch* b, int32_t graph, uint32_t replica, int8_t* out);
+int ising_batch_set_spins(ising_batch* b, int32_t graph, uint32_t replica, const int8_t* in);
+/* ising_batch_autotune -- times `probe_sweeps` sweeps of the batch for each
+ * candidate block size (128, 256, 512 threads), keeps the fastest and restores
+ * the spins. out_block (may be NULL) receives the choice. */
+int ising_batch_autotune(ising_batch* b, uint32_t probe_sweeps, int32_t* out_block);
+/* ising_batch_set_block -- choose the block size directly (128, 256 or 512). */
+int ising_batch_set_block(ising_batch* b, int32_t block);
+/* ising_batch_info -- instances, total vertices, block size, kernel launches. */
+int ising_batch_info(ising_batch* b, int32_t* out_num_graphs, int64_t* out_vertices,
+                     int32_t* out_block, uint64_t* out_launches);
+/* ising_batch_destroy -- free the batch (NULL is ignored). */
+void ising_batch_destroy(ising_batch* b);
+
 /* Largest vertex count ising_energy_csr_static accepts. */
 #define ISING_STATIC_MAX_VERTICES (1 << 24)
 

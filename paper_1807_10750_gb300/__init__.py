@@ -44,6 +44,9 @@ EXPORTS = (
     "ising_get_spins", "ising_set_spins", "ising_init_random", "ising_num_colours",
     "ising_colouring", "ising_num_edges", "ising_set_engine", "ising_destroy",
     "ising_strerror", "ising_plan_colouring", "ising_launch_count", "ising_energy_csr_static",
+    "ising_batch_create", "ising_batch_init_random", "ising_batch_anneal", "ising_batch_cuts",
+    "ising_batch_get_spins", "ising_batch_set_spins", "ising_batch_autotune", "ising_batch_set_block",
+    "ising_batch_info", "ising_batch_destroy",
 )
 
 
@@ -91,10 +94,24 @@ def lib():
         L.ising_plan_colouring.argtypes = [ctypes.c_int32, ctypes.c_int64, vp, vp, vp, i32p, i32p]
         L.ising_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
         L.ising_energy_csr_static.argtypes = [ctypes.c_int32, vp, vp, vp, vp, vp, vp]
+        L.ising_batch_create.argtypes = [ctypes.c_int32, vp, vp, vp, vp, vp, ctypes.c_uint32, vp,
+                                         ctypes.POINTER(vp)]
+        L.ising_batch_init_random.argtypes = [vp, ctypes.c_uint64]
+        L.ising_batch_anneal.argtypes = [vp, ctypes.POINTER(ising_schedule), ctypes.c_uint32,
+                                         ctypes.c_uint64, vp]
+        L.ising_batch_cuts.argtypes = [vp, vp]
+        L.ising_batch_get_spins.argtypes = [vp, ctypes.c_int32, ctypes.c_uint32, vp]
+        L.ising_batch_set_spins.argtypes = [vp, ctypes.c_int32, ctypes.c_uint32, vp]
+        L.ising_batch_autotune.argtypes = [vp, ctypes.c_uint32, ctypes.POINTER(ctypes.c_int32)]
+        L.ising_batch_set_block.argtypes = [vp, ctypes.c_int32]
+        L.ising_batch_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), i64p,
+                                       ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_uint64)]
+        L.ising_batch_destroy.argtypes = [vp]
+        L.ising_batch_destroy.restype = None
         L.ising_strerror.argtypes = [ctypes.c_int]
         L.ising_strerror.restype = ctypes.c_char_p
         for name in EXPORTS:
-            if name not in ("ising_destroy", "ising_strerror"):
+            if name not in ("ising_destroy", "ising_strerror", "ising_batch_destroy"):
                 getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -281,3 +298,101 @@ def ising_launch_count(g: IsingGraph) -> int:
 
 def ising_destroy(g: IsingGraph) -> None:
     g.close()
+
+
+# ---------------------------------------------------------------------------
+# batched instances
+# ---------------------------------------------------------------------------
+class IsingBatch:
+    """Owning wrapper of an ``ising_batch*`` handle."""
+
+    def __init__(self, ptr: int, ns, replicas: int):
+        self.ptr = ctypes.c_void_p(ptr)
+        self.n = [int(x) for x in ns]
+        self.replicas = replicas
+
+    def close(self):
+        if self.ptr and self.ptr.value:
+            lib().ising_batch_destroy(self.ptr)
+            self.ptr = ctypes.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def ising_batch_create(graphs, replicas: int = 8, stream=None) -> IsingBatch:
+    """``graphs``: sequence of (n, src, dst, w) host arrays."""
+    ns = np.array([g[0] for g in graphs], dtype=np.int32)
+    srcs = [np.ascontiguousarray(g[1], dtype=np.int32) for g in graphs]
+    ms = np.array([s.size for s in srcs], dtype=np.int64)
+    src = np.ascontiguousarray(np.concatenate(srcs) if srcs else np.zeros(0), dtype=np.int32)
+    dst = np.ascontiguousarray(np.concatenate([np.asarray(g[2], dtype=np.int32) for g in graphs]), dtype=np.int32)
+    w = np.ascontiguousarray(np.concatenate([np.asarray(g[3], dtype=np.int32) for g in graphs]), dtype=np.int32)
+    out = ctypes.c_void_p()
+    _check(lib().ising_batch_create(len(graphs), ns.ctypes.data, ms.ctypes.data, src.ctypes.data,
+                                    dst.ctypes.data, w.ctypes.data, replicas, _stream(stream),
+                                    ctypes.byref(out)), "ising_batch_create")
+    return IsingBatch(out.value, ns, replicas)
+
+
+def ising_batch_init_random(b: IsingBatch, seed: int) -> None:
+    _check(lib().ising_batch_init_random(b.ptr, seed & (2 ** 64 - 1)), "ising_batch_init_random")
+
+
+def ising_batch_anneal(b: IsingBatch, *, p0: float, t_total: int, seed: int, sweeps: int | None = None,
+                       t_begin: int = 0, stream=None) -> None:
+    if sweeps is None:
+        sweeps = t_total - t_begin
+    sched = ising_schedule(ISING_SCHED_LINEAR, 0, p0, t_begin, t_total)
+    _check(lib().ising_batch_anneal(b.ptr, ctypes.byref(sched), sweeps, seed & (2 ** 64 - 1),
+                                    _stream(stream)), "ising_batch_anneal")
+
+
+def ising_batch_cuts(b: IsingBatch) -> np.ndarray:
+    """int64 array [num_graphs, replicas]."""
+    out = np.zeros((len(b.n), b.replicas), dtype=np.int64)
+    _check(lib().ising_batch_cuts(b.ptr, out.ctypes.data), "ising_batch_cuts")
+    return out
+
+
+def ising_batch_get_spins(b: IsingBatch, graph: int, replica: int) -> np.ndarray:
+    out = np.empty(b.n[graph], dtype=np.int8)
+    _check(lib().ising_batch_get_spins(b.ptr, graph, replica, out.ctypes.data), "ising_batch_get_spins")
+    return out
+
+
+def ising_batch_set_spins(b: IsingBatch, graph: int, replica: int, spins) -> None:
+    s = np.ascontiguousarray(spins, dtype=np.int8)
+    if s.size != b.n[graph]:
+        raise ValueError("wrong length")
+    _check(lib().ising_batch_set_spins(b.ptr, graph, replica, s.ctypes.data), "ising_batch_set_spins")
+
+
+def ising_batch_autotune(b: IsingBatch, probe_sweeps: int = 20) -> int:
+    v = ctypes.c_int32()
+    _check(lib().ising_batch_autotune(b.ptr, probe_sweeps, ctypes.byref(v)), "ising_batch_autotune")
+    return v.value
+
+
+def ising_batch_set_block(b: IsingBatch, block: int) -> None:
+    _check(lib().ising_batch_set_block(b.ptr, block), "ising_batch_set_block")
+
+
+def ising_batch_info(b: IsingBatch) -> dict:
+    g = ctypes.c_int32(); v = ctypes.c_int64(); blk = ctypes.c_int32(); la = ctypes.c_uint64()
+    _check(lib().ising_batch_info(b.ptr, ctypes.byref(g), ctypes.byref(v), ctypes.byref(blk),
+                                  ctypes.byref(la)), "ising_batch_info")
+    return {"num_graphs": g.value, "vertices": v.value, "block": blk.value, "launches": la.value}
+
+
+def ising_batch_destroy(b: IsingBatch) -> None:
+    b.close()

@@ -13,6 +13,8 @@ random graphs (the custom C1-C7 rows). G-set itself is not reproduced.
 from .graphs import (  # noqa: F401
     Graph,
     batched_er_graphs,
+    batched_workload,
+    BATCHED,
     complete_graph,
     cycle_graph,
     er_graph,

@@ -210,6 +210,20 @@ WORKLOADS = {
 }
 
 
+# The batched workload: 1024 Erdos-Renyi instances, n log-uniform in
+# [500, 20000], mean degree 10, +-1 weights; 8 replicas each, 1000 sweeps.
+BATCHED = dict(count=1024, nmin=500, nmax=20000, avg_degree=10.0, gen_seed=4, weights="pm1",
+               replicas=8, p0=0.1, sweeps=1000, seed=1)
+
+
+def batched_workload(**override) -> tuple[list[Graph], dict]:
+    spec = dict(BATCHED)
+    spec.update(override)
+    gs = batched_er_graphs(spec["count"], spec["nmin"], spec["nmax"], spec["avg_degree"],
+                           spec["gen_seed"], spec["weights"])
+    return gs, {k: spec[k] for k in ("replicas", "p0", "sweeps", "seed")}
+
+
 def workload(name: str, **override) -> tuple[Graph, dict]:
     """Build a named workload's graph; returns (graph, schedule parameters)."""
     spec = dict(WORKLOADS[name])
