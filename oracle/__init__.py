@@ -17,6 +17,8 @@ Computing for Combinatorial Optimization Problems in VLSI Physical Design"):
 * :func:`philox` -- Philox4x32-10 (Salmon et al., SC'11), the counter-based
   generator that stands in for the per-thread cuRAND streams of Sec. IV-B.
 * :func:`colouring` -- Welsh-Powell greedy colouring (reading R6).
+* :func:`anneal_nflip` -- Algorithm 1's schedule: update every spin, then flip
+  N_t distinct random spins, N decreasing linearly (reading R10).
 
 Parity of the full spin trajectory is unpinned by the paper (it prints no
 worked example); the pins are the properties checked in ``tests/``.
@@ -75,6 +77,11 @@ def lib():
                                     ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64,
                                     ctypes.c_uint64]
         L.oracle_anneal.restype = ctypes.c_int
+        L.oracle_anneal_nflip.argtypes = [ctypes.c_int32, ctypes.c_int64, i32p, i32p, i32p, i8p,
+                                          ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                          ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64,
+                                          ctypes.c_uint64]
+        L.oracle_anneal_nflip.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -162,4 +169,19 @@ def anneal(n, src, dst, w, s, *, seed: int, p0: float, T: int, t_begin: int = 0,
                             replica, p0, T, t_begin, sweeps)
     if r != 0:
         raise ValueError("invalid anneal arguments")
+    return out
+
+
+def anneal_nflip(n, src, dst, w, s, *, seed: int, n0: int, T: int, t_begin: int = 0,
+                 sweeps: int | None = None, instance: int = 0, replica: int = 0) -> np.ndarray:
+    """Algorithm 1's N-flip schedule; returns the new spins (input unchanged)."""
+    src, dst, w = _edges(src, dst, w)
+    out = np.array(s, dtype=np.int8, copy=True)
+    if sweeps is None:
+        sweeps = T - t_begin
+    r = lib().oracle_anneal_nflip(n, src.size, _p(src, ctypes.c_int32), _p(dst, ctypes.c_int32),
+                                  _p(w, ctypes.c_int32), _p(out, ctypes.c_int8), seed, instance,
+                                  replica, n0, T, t_begin, sweeps)
+    if r != 0:
+        raise ValueError("invalid N-flip anneal arguments")
     return out

@@ -324,4 +324,54 @@ int oracle_anneal(int32_t n, int64_t m, const int32_t* src, const int32_t* dst,
   return 0;
 }
 
+// Algorithm 1's schedule: a sweep updates every spin (colour classes as in
+// oracle_anneal, no per-spin random flip), then flips N_t distinct randomly
+// chosen spins, and N decreases: N_t = floor(N0 (T-1-t) / (T-1)) (R4's linear
+// decay applied to the count), N0 <= n. Reading R10 (the paper only says
+// "randomly choose and flip N spin glasses"): the candidates are
+// c_j = floor(x_j * n / 2^32), x_j = Philox word 0 with counter (j, t, replica,
+// 2), j = 0, 1, 2, ...; the first N_t distinct candidates are flipped.
+int oracle_anneal_nflip(int32_t n, int64_t m, const int32_t* src, const int32_t* dst,
+                        const int32_t* w, int8_t* s, uint64_t seed, uint32_t instance,
+                        uint32_t replica, uint32_t n0, uint64_t T, uint64_t t_begin,
+                        uint64_t sweeps) {
+  if (T >= 4294967296ull || t_begin + sweeps > T) return -1;
+  if ((int64_t)n0 > (int64_t)n) return -1;
+  Adjacency adj;
+  if (build_adjacency(n, m, src, dst, w, &adj) != 0) return -1;
+  for (int32_t i = 0; i < n; ++i)
+    if (s[i] != 1 && s[i] != -1) return -1;
+  std::vector<int32_t> colour;
+  int32_t C = colour_graph(adj, &colour);
+  std::vector<std::vector<int32_t>> members((size_t)C);
+  for (int32_t v = 0; v < n; ++v) members[(size_t)colour[(size_t)v]].push_back(v);
+  std::vector<char> chosen((size_t)n, 0);
+  std::vector<int32_t> picked;
+  for (uint64_t t = t_begin; t < t_begin + sweeps; ++t) {
+    for (int32_t c = 0; c < C; ++c)
+      for (int32_t v : members[(size_t)c]) {
+        int64_t f = local_field(adj, s, v);
+        if (f > 0)
+          s[v] = -1;
+        else if (f < 0)
+          s[v] = 1;
+      }
+    const uint64_t Nt = T <= 1 ? 0 : (uint64_t)n0 * (T - 1 - t) / (T - 1);
+    picked.clear();
+    for (uint32_t j = 0; picked.size() < Nt; ++j) {
+      uint32_t x = random_word(seed, instance, j, (uint32_t)t, replica, 2u);
+      int32_t v = (int32_t)(((uint64_t)x * (uint64_t)n) >> 32);
+      if (!chosen[(size_t)v]) {
+        chosen[(size_t)v] = 1;
+        picked.push_back(v);
+      }
+    }
+    for (int32_t v : picked) {
+      s[v] = (int8_t)(-s[v]);
+      chosen[(size_t)v] = 0;
+    }
+  }
+  return 0;
+}
+
 }  // extern "C"

@@ -343,3 +343,60 @@ def test_flip_needs_word_strictly_below_threshold():
     assert oracle.anneal(1, e, e, e, s0, seed=seed, p0=p_eq, T=2, sweeps=1)[0] == 1
     p_up = (x + 1) / 2.0 ** 32
     assert oracle.anneal(1, e, e, e, s0, seed=seed, p0=p_up, T=2, sweeps=1)[0] == -1
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 1's N-flip schedule
+# ---------------------------------------------------------------------------
+def test_nflip_flips_exactly_n_distinct_spins_on_an_edgeless_graph():
+    # No edges: Eq. 2 never changes a spin, so after sweep t exactly N_t spins
+    # differ from before, N_t = floor(N0 (T-1-t) / (T-1)).
+    n, T, N0 = 5000, 6, 1234
+    e = np.zeros(0, dtype=np.int32)
+    s = oracle.init_spins(n, 1)
+    for t in range(T):
+        s2 = oracle.anneal_nflip(n, e, e, e, s, seed=3, n0=N0, T=T, t_begin=t, sweeps=1)
+        assert int((s2 != s).sum()) == N0 * (T - 1 - t) // (T - 1)
+        s = s2
+
+
+def test_nflip_all_spins_when_n0_equals_n():
+    n = 300
+    e = np.zeros(0, dtype=np.int32)
+    s = oracle.init_spins(n, 2)
+    s2 = oracle.anneal_nflip(n, e, e, e, s, seed=5, n0=n, T=2, sweeps=1)
+    assert np.array_equal(s2, -s)
+
+
+def test_nflip_choice_is_uniform():
+    # over many sweeps every vertex is chosen about equally often
+    n, T, N0 = 64, 401, 16
+    e = np.zeros(0, dtype=np.int32)
+    counts = np.zeros(n)
+    s = np.ones(n, np.int8)
+    for t in range(T - 1):
+        s2 = oracle.anneal_nflip(n, e, e, e, s, seed=9, n0=N0, T=T, t_begin=t, sweeps=1)
+        counts += (s2 != s)
+        s = s2
+    exp = counts.sum() / n
+    chi2 = float(((counts - exp) ** 2 / exp).sum())
+    assert chi2 < (n - 1) + 6 * math.sqrt(2 * (n - 1))
+
+
+def test_nflip_zero_is_greedy_and_reaches_local_minimum():
+    g = synth.random_small_graph(150, 0.05, 8, weights="int8")
+    s = oracle.init_spins(g.n, 8)
+    a = oracle.anneal_nflip(g.n, g.src, g.dst, g.w, s, seed=1, n0=0, T=30)
+    b = oracle.anneal(g.n, g.src, g.dst, g.w, s, seed=1, p0=0.0, T=30)
+    assert np.array_equal(a, b)
+    assert np.all(a.astype(np.int64) * field(g, a) <= 0)
+
+
+def test_nflip_reaches_known_optimum_and_rejects_bad_n0():
+    g = synth.torus_graph(10, 0, weights="one")
+    best = max(oracle.energy_cut(g.n, g.src, g.dst, g.w,
+                                 oracle.anneal_nflip(g.n, g.src, g.dst, g.w, oracle.init_spins(g.n, k),
+                                                     seed=k, n0=8, T=300))[2] for k in range(6))
+    assert best == int(g.w.sum())
+    with pytest.raises(ValueError):
+        oracle.anneal_nflip(g.n, g.src, g.dst, g.w, np.ones(g.n, np.int8), seed=1, n0=g.n + 1, T=5)
