@@ -85,7 +85,14 @@ enum {
    * Philox4x32-10 (Salmon et al., SC'11) with
    *   key     = (lo32(seed), hi32(seed))
    *   counter = (original id of i, t, replica, 0).                        */
-  ISING_SCHED_LINEAR = 0
+  ISING_SCHED_LINEAR = 0,
+  /* Algorithm 1: a sweep updates every spin (no per-spin flips), then flips
+   * N_t distinct randomly chosen spins, N_t = floor(n0 (t_total-1-t) /
+   * (t_total-1)) (n0 <= n). The spins are the first N_t distinct candidates
+   * c_j = floor(x_j * n / 2^32), x_j = word 0 of Philox4x32-10 with the key
+   * above and counter (j, t, replica, 2), j = 0, 1, 2, ... p0 is ignored. The
+   * dataflow engine runs this schedule as ISING_ENGINE_PERSISTENT. */
+  ISING_SCHED_NFLIP = 1
 };
 
 /* Which kernel engine runs a deterministic anneal (all give identical spins). */
@@ -106,11 +113,13 @@ enum {
 };
 
 typedef struct ising_schedule {
-  uint32_t kind;    /* ISING_SCHED_LINEAR */
-  uint32_t replica; /* counter word 2 of every Philox draw (independent replicas) */
-  double p0;        /* initial flip probability, 0 <= p0 <= 1 */
-  uint64_t t_begin; /* index of the first sweep this call runs, within the schedule */
-  uint64_t t_total; /* length T of the whole schedule; t_begin + sweeps <= T < 2^32 */
+  uint32_t kind;     /* ISING_SCHED_LINEAR or ISING_SCHED_NFLIP */
+  uint32_t replica;  /* counter word 2 of every Philox draw (independent replicas) */
+  double p0;         /* LINEAR: initial flip probability, 0 <= p0 <= 1 */
+  uint64_t t_begin;  /* index of the first sweep this call runs, within the schedule */
+  uint64_t t_total;  /* length T of the whole schedule; t_begin + sweeps <= T < 2^32 */
+  uint32_t n0;       /* NFLIP: flips at sweep 0, n0 <= n */
+  uint32_t reserved; /* 0 */
 } ising_schedule;
 
 /*
@@ -160,6 +169,18 @@ int ising_create(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, c
  */
 int ising_anneal(ising_graph* g, const ising_schedule* sched, uint32_t sweeps, uint64_t seed,
                  int mode, void* cuda_stream);
+
+/*
+ * ising_anneal_trace -- as ising_anneal, recording the energy along the way:
+ * the sweeps run in chunks of `every` (the last chunk may be shorter) and
+ * out_energy[i] (host int64[ceil(sweeps / every)]) receives H after chunk i.
+ * Counter-based randomness makes the chunked run identical to one call. This
+ * is the energy-versus-sweep view of the paper's convergence study (Fig. 4).
+ * Synchronises the stream. Errors as ising_anneal, plus ISING_EINVAL for
+ * every == 0 or a null out_energy.
+ */
+int ising_anneal_trace(ising_graph* g, const ising_schedule* sched, uint32_t sweeps, uint64_t seed,
+                       int mode, uint32_t every, int64_t* out_energy, void* cuda_stream);
 
 /*
  * ising_energy -- H(s) = sum over merged undirected edges of w_ij s_i s_j
@@ -244,8 +265,8 @@ int ising_batch_create(int32_t num_graphs, const int32_t* n, const int64_t* m, c
 /* ising_batch_init_random -- initial spins of every instance and replica. */
 int ising_batch_init_random(ising_batch* b, uint64_t seed);
 /* ising_batch_anneal -- sweeps t_begin .. t_begin + sweeps - 1 of `sched`
- * (ISING_SCHED_LINEAR; sched->replica is ignored, every replica runs) for every
- * instance and replica. Asynchronous on cuda_stream. */
+ * (ISING_SCHED_LINEAR only; sched->replica is ignored, every replica runs) for
+ * every instance and replica. Asynchronous on cuda_stream. */
 int ising_batch_anneal(ising_batch* b, const ising_schedule* sched, uint32_t sweeps, uint64_t seed,
                        void* cuda_stream);
 /* ising_batch_cuts -- host int64[num_graphs * replicas]: cut of instance g,

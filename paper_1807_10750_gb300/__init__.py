@@ -31,6 +31,7 @@ ISING_ERANGE = -6
 ISING_MODE_DET = 0
 ISING_MODE_RACY = 1
 ISING_SCHED_LINEAR = 0
+ISING_SCHED_NFLIP = 1
 ISING_ENGINE_AUTO = 0
 ISING_ENGINE_PHASE = 1
 ISING_ENGINE_PERSISTENT = 2
@@ -46,7 +47,7 @@ EXPORTS = (
     "ising_strerror", "ising_plan_colouring", "ising_launch_count", "ising_energy_csr_static",
     "ising_batch_create", "ising_batch_init_random", "ising_batch_anneal", "ising_batch_cuts",
     "ising_batch_get_spins", "ising_batch_set_spins", "ising_batch_autotune", "ising_batch_set_block",
-    "ising_batch_info", "ising_batch_destroy",
+    "ising_batch_info", "ising_batch_destroy", "ising_anneal_trace",
 )
 
 
@@ -58,7 +59,8 @@ class IsingError(RuntimeError):
 
 class ising_schedule(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_uint32), ("replica", ctypes.c_uint32), ("p0", ctypes.c_double),
-                ("t_begin", ctypes.c_uint64), ("t_total", ctypes.c_uint64)]
+                ("t_begin", ctypes.c_uint64), ("t_total", ctypes.c_uint64), ("n0", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
 
 
 _lib = None
@@ -94,6 +96,8 @@ def lib():
         L.ising_plan_colouring.argtypes = [ctypes.c_int32, ctypes.c_int64, vp, vp, vp, i32p, i32p]
         L.ising_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
         L.ising_energy_csr_static.argtypes = [ctypes.c_int32, vp, vp, vp, vp, vp, vp]
+        L.ising_anneal_trace.argtypes = [vp, ctypes.POINTER(ising_schedule), ctypes.c_uint32,
+                                         ctypes.c_uint64, ctypes.c_int, ctypes.c_uint32, vp, vp]
         L.ising_batch_create.argtypes = [ctypes.c_int32, vp, vp, vp, vp, vp, ctypes.c_uint32, vp,
                                          ctypes.POINTER(vp)]
         L.ising_batch_init_random.argtypes = [vp, ctypes.c_uint64]
@@ -190,14 +194,45 @@ def ising_create(n: int, src, dst, w, flags: int = 0, stream=None) -> IsingGraph
     return IsingGraph(out.value, n)
 
 
-def ising_anneal(g: IsingGraph, *, p0: float, t_total: int, sweeps: int | None = None,
-                 seed: int, mode: int = ISING_MODE_DET, t_begin: int = 0, replica: int = 0,
-                 stream=None, kind: int = ISING_SCHED_LINEAR) -> None:
+def ising_anneal(g: IsingGraph, *, t_total: int, seed: int, p0: float = 0.0,
+                 sweeps: int | None = None, mode: int = ISING_MODE_DET, t_begin: int = 0,
+                 replica: int = 0, stream=None, kind: int = ISING_SCHED_LINEAR, n0: int = 0) -> None:
+    """Linear schedule (kind=ISING_SCHED_LINEAR, p0) or Algorithm 1's N-flip
+    schedule (kind=ISING_SCHED_NFLIP, n0)."""
     if sweeps is None:
         sweeps = t_total - t_begin
-    sched = ising_schedule(kind, replica, p0, t_begin, t_total)
+    sched = ising_schedule(kind, replica, p0, t_begin, t_total, n0, 0)
     _check(lib().ising_anneal(g.ptr, ctypes.byref(sched), sweeps, seed & (2 ** 64 - 1), mode,
                               _stream(stream)), "ising_anneal")
+
+
+def ising_anneal_trace(g: IsingGraph, *, t_total: int, seed: int, every: int, p0: float = 0.0,
+                       sweeps: int | None = None, mode: int = ISING_MODE_DET, t_begin: int = 0,
+                       replica: int = 0, stream=None, kind: int = ISING_SCHED_LINEAR,
+                       n0: int = 0) -> np.ndarray:
+    """Energies after every ``every`` sweeps (int64 array)."""
+    if sweeps is None:
+        sweeps = t_total - t_begin
+    sched = ising_schedule(kind, replica, p0, t_begin, t_total, n0, 0)
+    out = np.zeros(max(0, -(-sweeps // every)) if every > 0 else 0, dtype=np.int64)
+    _check(lib().ising_anneal_trace(g.ptr, ctypes.byref(sched), sweeps, seed & (2 ** 64 - 1), mode,
+                                    every, out.ctypes.data, _stream(stream)), "ising_anneal_trace")
+    return out
+
+
+def convergence_region(g: IsingGraph, *, seeds, p0: float, t_total: int, every: int,
+                       init_seed_offset: int = 1000, mode: int = ISING_MODE_DET, stream=None):
+    """Cut value versus sweep for several seeds (the paper's Fig. 4 view):
+    returns (sweep index after each chunk, cuts[seed, checkpoint])."""
+    W = ising_total_weight(g)
+    rows = []
+    for sd in seeds:
+        ising_init_random(g, sd + init_seed_offset)
+        H = ising_anneal_trace(g, p0=p0, t_total=t_total, seed=sd, every=every, mode=mode,
+                               stream=stream)
+        rows.append((W - H) // 2)
+    idx = np.minimum(np.arange(1, len(rows[0]) + 1) * every, t_total)
+    return idx, np.array(rows)
 
 
 def ising_energy(g: IsingGraph) -> int:
@@ -352,7 +387,7 @@ def ising_batch_anneal(b: IsingBatch, *, p0: float, t_total: int, seed: int, swe
                        t_begin: int = 0, stream=None) -> None:
     if sweeps is None:
         sweeps = t_total - t_begin
-    sched = ising_schedule(ISING_SCHED_LINEAR, 0, p0, t_begin, t_total)
+    sched = ising_schedule(ISING_SCHED_LINEAR, 0, p0, t_begin, t_total, 0, 0)
     _check(lib().ising_batch_anneal(b.ptr, ctypes.byref(sched), sweeps, seed & (2 ** 64 - 1),
                                     _stream(stream)), "ising_batch_anneal")
 

@@ -113,7 +113,8 @@ template <bool PACKED, int PASS>
 __global__ void __launch_bounds__(kPersistBlock, 2)
     persistent_kernel(DevGraph d, const int32_t* __restrict__ phase_items, int num_phases,
                       uint64_t t_begin, uint32_t sweeps, uint64_t T, uint64_t T0, uint32_t replica,
-                      isingx::PhiloxRounds rk, BarrierState* bs) {
+                      isingx::PhiloxRounds rk, BarrierState* bs, uint32_t nflip0,
+                      const int32_t* __restrict__ pos, unsigned* bitmap, int32_t* picked) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * kPersistBlock + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * kPersistBlock) >> 5;
@@ -137,6 +138,17 @@ __global__ void __launch_bounds__(kPersistBlock, 2)
       }
     }
     const bool sweep_end = (c + 1 == num_phases);
+    if (nflip0 != 0u && sweep_end) {
+      // Algorithm 1: once every update of the sweep is visible, one warp flips
+      // the sweep's N random spins; the barrier below publishes them.
+      isingx::barrier_arrive(bs);
+      target += gridDim.x;
+      if (!isingx::barrier_wait(bs, target)) return;
+      const uint32_t N = isingx::nflip_count(nflip0, T, t_begin + k);
+      if (blockIdx.x == 0 && threadIdx.x < 32 && N > 0u)
+        isingx::nflip_step(d, pos, bitmap, picked, N, static_cast<uint32_t>(t_begin + k), replica,
+                           rk, lane);
+    }
     if (sweep_end && k + 1 == sweeps) break;
     const bool sync = (PASS != kPassRacy) || sweep_end;
     if (sync) isingx::barrier_arrive(bs);
@@ -189,6 +201,12 @@ __global__ void __launch_bounds__(kPersistBlock, 2)
       }
     }
   }
+}
+
+// Algorithm 1's end-of-sweep flips for the per-launch engine (one warp).
+__global__ void nflip_kernel(DevGraph d, const int32_t* pos, unsigned* bitmap, int32_t* picked,
+                             uint32_t N, uint32_t t, uint32_t replica, isingx::PhiloxRounds rk) {
+  isingx::nflip_step(d, pos, bitmap, picked, N, t, replica, rk, threadIdx.x & 31);
 }
 
 __global__ void init_random_kernel(int8_t* spins, const int32_t* orig, int n,
@@ -281,6 +299,10 @@ struct ising_graph {
   int8_t* d_tmp = nullptr;
   int32_t* d_class_items = nullptr;  // num_colours + 1 item offsets
   int32_t* d_class_begin = nullptr;  // num_colours + 1 first positions
+  unsigned long long* d_trace = nullptr;  // energy trace (twice H per checkpoint)
+  unsigned* d_nflip_bits = nullptr;        // N-flip: chosen-vertex bitmap (kept zero)
+  int32_t* d_nflip_list = nullptr;         // N-flip: chosen vertices, n entries
+  size_t trace_cap = 0;
   int32_t* d_all_items = nullptr;    // {0, num_items}: one phase over every item (energy)
   BarrierState* d_barrier = nullptr;
   int persist_grid = 0;              // co-resident blocks of the persistent kernel
@@ -312,7 +334,7 @@ void free_device(ising_graph* g) {
                   g->d_orig,    g->d_pos,         g->d_items,       g->d_slice_acc,
                   g->d_slice_parts, g->d_energy,  g->d_flag,
                   g->d_tmp,     g->d_class_items, g->d_all_items, g->d_barrier,
-                  g->d_class_begin};
+                  g->d_class_begin, g->d_trace, g->d_nflip_bits, g->d_nflip_list};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -382,7 +404,7 @@ int check_device_error(ising_graph* g) {
 template <bool PACKED, int PASS>
 cudaError_t launch_persistent_t(ising_graph* g, const int32_t* phase_items, int num_phases,
                                 uint64_t t_begin, uint32_t sweeps, uint64_t T, uint64_t T0,
-                                uint32_t replica, isingx::PhiloxRounds rk) {
+                                uint32_t replica, isingx::PhiloxRounds rk, uint32_t nflip0) {
   auto kernel = persistent_kernel<PACKED, PASS>;
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kPersistBlock, 0);
@@ -395,7 +417,11 @@ cudaError_t launch_persistent_t(ising_graph* g, const int32_t* phase_items, int 
   if (e != cudaSuccess) return e;
   DevGraph d = g->dev();
   BarrierState* bs = g->d_barrier;
-  void* args[] = {&d, &phase_items, &num_phases, &t_begin, &sweeps, &T, &T0, &replica, &rk, &bs};
+  const int32_t* pos = g->d_pos;
+  unsigned* bitmap = g->d_nflip_bits;
+  int32_t* picked = g->d_nflip_list;
+  void* args[] = {&d,       &phase_items, &num_phases, &t_begin, &sweeps, &T,     &T0,
+                  &replica, &rk,          &bs,         &nflip0,  &pos,    &bitmap, &picked};
   g->launches++;
   return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(kernel), dim3(grid),
                                      dim3(kPersistBlock), args, 0, g->stream);
@@ -404,12 +430,12 @@ cudaError_t launch_persistent_t(ising_graph* g, const int32_t* phase_items, int 
 template <int PASS>
 cudaError_t launch_persistent(ising_graph* g, const int32_t* phase_items, int num_phases,
                               uint64_t t_begin, uint32_t sweeps, uint64_t T, uint64_t T0,
-                              uint32_t replica, const isingx::PhiloxRounds& rk) {
+                              uint32_t replica, const isingx::PhiloxRounds& rk, uint32_t nflip0) {
   if (g->packed)
     return launch_persistent_t<true, PASS>(g, phase_items, num_phases, t_begin, sweeps, T, T0,
-                                           replica, rk);
+                                           replica, rk, nflip0);
   return launch_persistent_t<false, PASS>(g, phase_items, num_phases, t_begin, sweeps, T, T0,
-                                          replica, rk);
+                                          replica, rk, nflip0);
 }
 
 template <bool PACKED>
@@ -441,6 +467,16 @@ cudaError_t launch_flow(ising_graph* g, uint64_t t_begin, uint32_t sweeps, uint6
                         uint32_t replica, int par0, const isingx::PhiloxRounds& rk) {
   if (g->packed) return launch_flow_t<true>(g, t_begin, sweeps, T, T0, replica, par0, rk);
   return launch_flow_t<false>(g, t_begin, sweeps, T, T0, replica, par0, rk);
+}
+
+// Enqueue twice the energy into *slot (device), no host synchronisation.
+int enqueue_energy(ising_graph* g, unsigned long long* slot) {
+  ISING_CUDA(g, cudaMemsetAsync(slot, 0, sizeof(unsigned long long), g->stream));
+  SweepArgs a{};
+  const isingx::PhiloxRounds rk{};
+  const int32_t all_items[2] = {0, g->num_items};
+  ISING_CUDA(g, launch_items<kPassEnergy>(g, g->d_all_items, all_items, 0, 1, a, rk, slot));
+  return ISING_OK;
 }
 
 int compute_energy(ising_graph* g, int64_t* out) {
@@ -567,6 +603,8 @@ int ising_create(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, c
     if ((e = alloc_copy(&g->d_all_items, all_items, 2, g->stream)) != cudaSuccess) break;
     if ((e = alloc_copy(&g->d_class_begin, hg.class_begin.data(), hg.class_begin.size(),
                         g->stream)) != cudaSuccess) break;
+    if ((e = alloc_copy<unsigned>(&g->d_nflip_bits, nullptr, (N + 31) / 32, g->stream)) != cudaSuccess) break;
+    if ((e = alloc_copy<int32_t>(&g->d_nflip_list, nullptr, N, g->stream)) != cudaSuccess) break;
     if ((e = alloc_copy<BarrierState>(&g->d_barrier, nullptr, 1, g->stream)) != cudaSuccess) break;
     fill_spins_kernel<<<grid_for(hg.n, 256, g->num_sms * 8), 256, 0, g->stream>>>(
         g->d_spins, hg.n, static_cast<int8_t>(isingx::state_byte(1, 0)));
@@ -592,17 +630,73 @@ void ising_destroy(ising_graph* g) {
   delete g;
 }
 
+static int check_anneal_args(const ising_graph* g, const ising_schedule* sched, uint32_t sweeps,
+                             int mode) {
+  if (sched == nullptr) return ISING_EINVAL;
+  if (sched->kind == ISING_SCHED_LINEAR) {
+    if (!(sched->p0 >= 0.0 && sched->p0 <= 1.0)) return ISING_EINVAL;
+  } else if (sched->kind == ISING_SCHED_NFLIP) {
+    if (static_cast<int64_t>(sched->n0) > static_cast<int64_t>(g->n)) return ISING_EINVAL;
+  } else {
+    return ISING_EINVAL;
+  }
+  if (mode != ISING_MODE_DET && mode != ISING_MODE_RACY) return ISING_EINVAL;
+  if (sched->t_total >= (1ull << 32)) return ISING_EINVAL;
+  if (sched->t_begin > sched->t_total || sweeps > sched->t_total - sched->t_begin) return ISING_EINVAL;
+  return ISING_OK;
+}
+
+static int anneal_impl(ising_graph* g, const ising_schedule* sched, uint32_t sweeps, uint64_t seed,
+                       int mode);
+
 int ising_anneal(ising_graph* g, const ising_schedule* sched, uint32_t sweeps, uint64_t seed,
                  int mode, void* cuda_stream) {
   int rc = enter(g);
   if (rc != ISING_OK) return rc;
-  if (sched == nullptr) return ISING_EINVAL;
-  if (sched->kind != ISING_SCHED_LINEAR) return ISING_EINVAL;
-  if (!(sched->p0 >= 0.0 && sched->p0 <= 1.0)) return ISING_EINVAL;
-  if (mode != ISING_MODE_DET && mode != ISING_MODE_RACY) return ISING_EINVAL;
-  if (sched->t_total >= (1ull << 32)) return ISING_EINVAL;
-  if (sched->t_begin > sched->t_total || sweeps > sched->t_total - sched->t_begin) return ISING_EINVAL;
+  rc = check_anneal_args(g, sched, sweeps, mode);
+  if (rc != ISING_OK) return rc;
   g->stream = static_cast<cudaStream_t>(cuda_stream);
+  return anneal_impl(g, sched, sweeps, seed, mode);
+}
+
+int ising_anneal_trace(ising_graph* g, const ising_schedule* sched, uint32_t sweeps, uint64_t seed,
+                       int mode, uint32_t every, int64_t* out_energy, void* cuda_stream) {
+  int rc = enter(g);
+  if (rc != ISING_OK) return rc;
+  rc = check_anneal_args(g, sched, sweeps, mode);
+  if (rc != ISING_OK) return rc;
+  if (every == 0 || out_energy == nullptr) return ISING_EINVAL;
+  g->stream = static_cast<cudaStream_t>(cuda_stream);
+  const size_t points = (static_cast<size_t>(sweeps) + every - 1) / every;
+  if (points == 0) return ISING_OK;
+  if (points > g->trace_cap) {
+    if (g->d_trace) cudaFree(g->d_trace);
+    g->d_trace = nullptr;
+    g->trace_cap = 0;
+    ISING_CUDA(g, cudaMalloc(reinterpret_cast<void**>(&g->d_trace), points * sizeof(unsigned long long)));
+    g->trace_cap = points;
+  }
+  ising_schedule chunk = *sched;
+  for (size_t i = 0; i < points; ++i) {
+    const uint32_t k = static_cast<uint32_t>(std::min<uint64_t>(every, sweeps - i * every));
+    chunk.t_begin = sched->t_begin + i * every;
+    rc = anneal_impl(g, &chunk, k, seed, mode);
+    if (rc != ISING_OK) return rc;
+    rc = enqueue_energy(g, g->d_trace + i);
+    if (rc != ISING_OK) return rc;
+  }
+  std::vector<unsigned long long> twice(points);
+  ISING_CUDA(g, cudaMemcpyAsync(twice.data(), g->d_trace, points * sizeof(unsigned long long),
+                                cudaMemcpyDeviceToHost, g->stream));
+  ISING_CUDA(g, cudaStreamSynchronize(g->stream));
+  rc = check_device_error(g);
+  if (rc != ISING_OK) return rc;
+  for (size_t i = 0; i < points; ++i) out_energy[i] = static_cast<long long>(twice[i]) / 2;
+  return ISING_OK;
+}
+
+static int anneal_impl(ising_graph* g, const ising_schedule* sched, uint32_t sweeps, uint64_t seed,
+                       int mode) {
   if (sweeps == 0) return ISING_OK;
   const isingx::PhiloxRounds rk = isingx::philox_rounds(isingx::philox_key(seed, 0u));
   // AUTO: the persistent engine when the device supports cooperative launches.
@@ -615,21 +709,24 @@ int ising_anneal(ising_graph* g, const ising_schedule* sched, uint32_t sweeps, u
   // every sweep updates every vertex once, flipping its update parity
   const int par0 = g->parity;
   g->parity ^= static_cast<int>(sweeps & 1u);
-  if (engine == ISING_ENGINE_DATAFLOW && mode == ISING_MODE_DET) {
-    const uint64_t T0 = linear_t0(sched->p0);
+  // Algorithm 1 (N-flip): no per-spin flips during the sweep, N_t random
+  // flips after it. Algorithm 2 (linear): per-spin flips with threshold thr[t].
+  const bool nflip = sched->kind == ISING_SCHED_NFLIP;
+  const uint32_t n0 = nflip ? sched->n0 : 0u;
+  const uint64_t T0 = nflip ? 0 : linear_t0(sched->p0);
+  if (engine == ISING_ENGINE_DATAFLOW && mode == ISING_MODE_DET && !nflip) {
     ISING_CUDA(g, launch_flow(g, sched->t_begin, sweeps, sched->t_total, T0, sched->replica, par0, rk));
     return ISING_OK;
   }
   if (engine == ISING_ENGINE_PERSISTENT || engine == ISING_ENGINE_DATAFLOW) {
-    const uint64_t T0 = linear_t0(sched->p0);
     if (mode == ISING_MODE_RACY)
       ISING_CUDA(g, launch_persistent<kPassRacy>(g, g->d_class_items, g->num_colours,
                                                  sched->t_begin, sweeps, sched->t_total, T0,
-                                                 sched->replica, rk));
+                                                 sched->replica, rk, n0));
     else
       ISING_CUDA(g, launch_persistent<kPassDet>(g, g->d_class_items, g->num_colours,
                                                 sched->t_begin, sweeps, sched->t_total, T0,
-                                                sched->replica, rk));
+                                                sched->replica, rk, n0));
     return ISING_OK;
   }
   SweepArgs a{};
@@ -637,13 +734,20 @@ int ising_anneal(ising_graph* g, const ising_schedule* sched, uint32_t sweeps, u
   for (uint32_t k = 0; k < sweeps; ++k) {
     const uint64_t t = sched->t_begin + k;
     a.t = static_cast<uint32_t>(t);
-    a.thr = linear_threshold(sched->p0, sched->t_total, t);
+    a.thr = nflip ? 0u : linear_threshold(sched->p0, sched->t_total, t);
     const int32_t* hi = g->class_item_begin.data();
     if (mode == ISING_MODE_RACY) {
       ISING_CUDA(g, launch_items<kPassRacy>(g, g->d_class_items, hi, 0, g->num_colours, a, rk, nullptr));
     } else {
       for (int32_t c = 0; c < g->num_colours; ++c)
         ISING_CUDA(g, launch_items<kPassDet>(g, g->d_class_items, hi, c, c + 1, a, rk, nullptr));
+    }
+    const uint32_t N = nflip ? isingx::nflip_count(n0, sched->t_total, t) : 0u;
+    if (N > 0u) {
+      g->launches++;
+      nflip_kernel<<<1, 32, 0, g->stream>>>(g->dev(), g->d_pos, g->d_nflip_bits, g->d_nflip_list, N,
+                                            static_cast<uint32_t>(t), sched->replica, rk);
+      ISING_CUDA(g, cudaGetLastError());
     }
   }
   return ISING_OK;

@@ -406,6 +406,59 @@ __device__ __forceinline__ void finish_item(const DevGraph& d, const Staged<PACK
 }
 
 // ---------------------------------------------------------------------------
+// Algorithm 1's end-of-sweep flips (ISING_SCHED_NFLIP), run by one warp after
+// every update of sweep t is visible: the first N distinct candidates
+// c_j = floor(x_j * n / 2^32), x_j = Philox word 0 with counter
+// (j, t, replica, 2), j = 0, 1, 2, ..., are flipped (spin bit only; the update
+// parity is unchanged). Candidates are drawn 32 at a time; inside a batch a
+// repeated candidate keeps its first occurrence, and a bitmap of the chosen
+// vertices (zero on entry, cleared again on exit) rejects candidates chosen in
+// earlier batches, so the chosen set is exactly the sequential definition.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned ld_relaxed_u32g(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+
+__device__ __forceinline__ void nflip_step(const DevGraph& d, const int32_t* pos, unsigned* bitmap,
+                                           int32_t* picked, uint32_t N, uint32_t t,
+                                           uint32_t replica, const PhiloxRounds& rk, int lane) {
+  const uint64_t n = static_cast<uint64_t>(d.pad_col);
+  uint32_t count = 0;
+  for (uint32_t j0 = 0; count < N; j0 += 32) {
+    const uint32_t x = philox4x32_10_word0(j0 + lane, t, replica, 2u, rk);
+    const uint32_t c = static_cast<uint32_t>((static_cast<uint64_t>(x) * n) >> 32);
+    const unsigned same = __match_any_sync(kFullMask, c);
+    const bool first = (__ffs(same) - 1) == lane;
+    const bool seen = (ld_relaxed_u32g(bitmap + (c >> 5)) >> (c & 31)) & 1u;
+    const bool fresh = first && !seen;
+    const unsigned fmask = __ballot_sync(kFullMask, fresh);
+    const uint32_t take = min(static_cast<uint32_t>(__popc(fmask)), N - count);
+    const uint32_t rank = static_cast<uint32_t>(__popc(fmask & ((1u << lane) - 1u)));
+    if (fresh && rank < take) {
+      atomicOr(bitmap + (c >> 5), 1u << (c & 31));
+      picked[count + rank] = static_cast<int32_t>(c);
+    }
+    count += take;
+    __syncwarp();
+  }
+  for (uint32_t k = lane; k < N; k += 32) {
+    const uint32_t c = static_cast<uint32_t>(picked[k]);
+    const int p = __ldg(pos + c);
+    d.spins[p] = static_cast<int8_t>(d.spins[p] ^ 1);
+    atomicAnd(bitmap + (c >> 5), ~(1u << (c & 31)));
+  }
+  __syncwarp();
+}
+
+// Flips of sweep t of an N-flip schedule: floor(N0 (T-1-t) / (T-1)).
+__host__ __device__ inline uint32_t nflip_count(uint32_t n0, uint64_t T, uint64_t t) {
+  if (T <= 1 || t >= T) return 0u;
+  return static_cast<uint32_t>(static_cast<uint64_t>(n0) * (T - 1 - t) / (T - 1));
+}
+
+// ---------------------------------------------------------------------------
 // Grid barrier of the persistent engine: a counter that only grows. A block
 // arrives with one release-add by thread 0 (after __syncthreads, so the whole
 // block's spin stores are ordered before it) and waits until the counter

@@ -231,3 +231,85 @@ def test_racy_mode_cut_quality(P, name, engine):
         assert (H, cut) == oracle.energy_cut(g.n, g.src, g.dst, g.w, s)[::2]
         racy.append(cut)
     assert np.mean(racy) >= 0.98 * np.mean(det), (racy, det)
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_energy_trace_matches_oracle_checkpoints(P, engine):
+    g = synth.random_small_graph(700, 0.01, 21, weights="int8", duplicates=30)
+    s0 = oracle.init_spins(g.n, 3)
+    T, every = 50, 7
+    with P.ising_create(g.n, g.src, g.dst, g.w) as h:
+        P.ising_set_engine(h, engine_id(P, engine))
+        P.ising_set_spins(h, s0)
+        trace = P.ising_anneal_trace(h, p0=0.2, t_total=T, seed=4, every=every)
+        final = P.ising_energy(h)
+    assert trace.size == -(-T // every) and trace[-1] == final
+    s = s0.copy()
+    for i in range(trace.size):
+        k = min(every, T - i * every)
+        s = oracle.anneal(g.n, g.src, g.dst, g.w, s, seed=4, p0=0.2, T=T, t_begin=i * every, sweeps=k)
+        assert trace[i] == oracle.energy_cut(g.n, g.src, g.dst, g.w, s)[0], i
+
+
+def test_convergence_region_shape(P):
+    g = synth.torus_graph(32, 5, weights="pm1")
+    with P.ising_create(g.n, g.src, g.dst, g.w) as h:
+        idx, cuts = P.convergence_region(h, seeds=range(4), p0=0.1, t_total=100, every=10)
+        W = P.ising_total_weight(h)
+    assert idx.tolist() == list(range(10, 101, 10))
+    assert cuts.shape == (4, 10) and np.all(np.abs(cuts) <= g.m)
+    # annealing improves the cut from early to late checkpoints on average
+    assert cuts[:, -1].mean() > cuts[:, 0].mean()
+
+
+def gpu_anneal_nflip(P, g, s0, *, seed, n0, T, t_begin=0, sweeps=None, engine="auto", mode=None):
+    with P.ising_create(g.n, g.src, g.dst, g.w) as h:
+        P.ising_set_engine(h, engine_id(P, engine))
+        P.ising_set_spins(h, s0)
+        P.ising_anneal(h, kind=P.ISING_SCHED_NFLIP, n0=n0, t_total=T, t_begin=t_begin,
+                       sweeps=sweeps, seed=seed, mode=P.ISING_MODE_DET if mode is None else mode)
+        return P.ising_get_spins(h), P.ising_cut(h)
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+@pytest.mark.parametrize("name", ["er_dup_int8", "torus_pm1", "zipf_small", "complete"])
+def test_nflip_schedule_bit_exact(P, name, engine):
+    g = SMALL_GRAPHS[name]()
+    s0 = oracle.init_spins(g.n, 12)
+    n0 = min(g.n, 37)
+    want = oracle.anneal_nflip(g.n, g.src, g.dst, g.w, s0, seed=6, n0=n0, T=40)
+    got, cut = gpu_anneal_nflip(P, g, s0, seed=6, n0=n0, T=40, engine=engine)
+    assert np.array_equal(got, want)
+    assert cut == oracle.energy_cut(g.n, g.src, g.dst, g.w, want)[2]
+
+
+@pytest.mark.parametrize("engine", ["phase", "persistent"])
+def test_nflip_paper_setting_er800(P, engine):
+    # the paper's accuracy runs: 1000 sweeps, 200 random flips decaying linearly
+    g, sch = synth.workload("er800")
+    s0 = oracle.init_spins(g.n, 1)
+    want = oracle.anneal_nflip(g.n, g.src, g.dst, g.w, s0, seed=1, n0=200, T=1000)
+    got, _ = gpu_anneal_nflip(P, g, s0, seed=1, n0=200, T=1000, engine=engine)
+    assert np.array_equal(got, want)
+
+
+def test_nflip_edge_cases(P):
+    e = np.zeros(0, np.int32)
+    g = synth.Graph(3000, e, e, e)
+    s0 = oracle.init_spins(g.n, 2)
+    for n0 in (g.n, 1, 0):
+        want = oracle.anneal_nflip(g.n, e, e, e, s0, seed=4, n0=n0, T=3)
+        for engine in ("phase", "persistent"):
+            got, _ = gpu_anneal_nflip(P, g, s0, seed=4, n0=n0, T=3, engine=engine)
+            assert np.array_equal(got, want), (n0, engine)
+    # split equals whole, and n0 > n is rejected
+    g = SMALL_GRAPHS["er_dup_int8"]()
+    s0 = oracle.init_spins(g.n, 3)
+    whole = oracle.anneal_nflip(g.n, g.src, g.dst, g.w, s0, seed=8, n0=50, T=30)
+    with P.ising_create(g.n, g.src, g.dst, g.w) as h:
+        P.ising_set_spins(h, s0)
+        P.ising_anneal(h, kind=P.ISING_SCHED_NFLIP, n0=50, t_total=30, sweeps=11, seed=8)
+        P.ising_anneal(h, kind=P.ISING_SCHED_NFLIP, n0=50, t_total=30, t_begin=11, seed=8)
+        assert np.array_equal(P.ising_get_spins(h), whole)
+        with pytest.raises(P.IsingError):
+            P.ising_anneal(h, kind=P.ISING_SCHED_NFLIP, n0=g.n + 1, t_total=30, seed=8)
