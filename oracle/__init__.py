@@ -17,6 +17,8 @@ Computing for Combinatorial Optimization Problems in VLSI Physical Design"):
 * :func:`philox` -- Philox4x32-10 (Salmon et al., SC'11), the counter-based
   generator that stands in for the per-thread cuRAND streams of Sec. IV-B.
 * :func:`colouring` -- Welsh-Powell greedy colouring (reading R6).
+* :func:`anneal` with ``bias`` -- a per-vertex flip bias (R11, a project
+  addition used by the learned warm start; not in the paper).
 * :func:`anneal_nflip` -- Algorithm 1's schedule: update every spin, then flip
   N_t distinct random spins, N decreasing linearly (reading R10).
 
@@ -77,6 +79,8 @@ def lib():
                                     ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64,
                                     ctypes.c_uint64]
         L.oracle_anneal.restype = ctypes.c_int
+        L.oracle_anneal_biased.argtypes = L.oracle_anneal.argtypes + [ctypes.POINTER(ctypes.c_uint8)]
+        L.oracle_anneal_biased.restype = ctypes.c_int
         L.oracle_anneal_nflip.argtypes = [ctypes.c_int32, ctypes.c_int64, i32p, i32p, i32p, i8p,
                                           ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                           ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64,
@@ -158,15 +162,25 @@ def energy_cut(n, src, dst, w, s):
 
 
 def anneal(n, src, dst, w, s, *, seed: int, p0: float, T: int, t_begin: int = 0,
-           sweeps: int | None = None, instance: int = 0, replica: int = 0) -> np.ndarray:
-    """Deterministic anneal; returns the new spin vector (input not modified)."""
+           sweeps: int | None = None, instance: int = 0, replica: int = 0,
+           bias=None) -> np.ndarray:
+    """Deterministic anneal; returns the new spin vector (input not modified).
+    ``bias``: optional uint8 per-vertex flip bias q (R11; 128 = unbiased)."""
     src, dst, w = _edges(src, dst, w)
     out = np.array(s, dtype=np.int8, copy=True)
     if sweeps is None:
         sweeps = T - t_begin
-    r = lib().oracle_anneal(n, src.size, _p(src, ctypes.c_int32), _p(dst, ctypes.c_int32),
-                            _p(w, ctypes.c_int32), _p(out, ctypes.c_int8), seed, instance,
-                            replica, p0, T, t_begin, sweeps)
+    if bias is None:
+        r = lib().oracle_anneal(n, src.size, _p(src, ctypes.c_int32), _p(dst, ctypes.c_int32),
+                                _p(w, ctypes.c_int32), _p(out, ctypes.c_int8), seed, instance,
+                                replica, p0, T, t_begin, sweeps)
+    else:
+        q = np.ascontiguousarray(bias, dtype=np.uint8)
+        assert q.shape == (n,)
+        r = lib().oracle_anneal_biased(n, src.size, _p(src, ctypes.c_int32),
+                                       _p(dst, ctypes.c_int32), _p(w, ctypes.c_int32),
+                                       _p(out, ctypes.c_int8), seed, instance, replica, p0, T,
+                                       t_begin, sweeps, _p(q, ctypes.c_uint8))
     if r != 0:
         raise ValueError("invalid anneal arguments")
     return out

@@ -38,6 +38,8 @@
 //      degree (ties: smaller id first), i.e. Welsh-Powell; classes are swept in
 //      increasing colour order, and inside a class the order is irrelevant
 //      because no two vertices of a class are adjacent.
+//   R11 flip bias (project addition, oracle_anneal_biased): a per-vertex
+//      factor q_v / 128 on the flip threshold, in integers.
 //   R7 edges: undirected; repeated pairs are merged by summing their weights;
 //      a merged weight of 0 is no edge; self-loops and ids outside [0, n) are
 //      rejected.
@@ -291,9 +293,15 @@ int oracle_energy_cut(int32_t n, int64_t m, const int32_t* src, const int32_t* d
 // Deterministic annealing (Algorithm 2 over colour classes): sweeps
 // t_begin .. t_begin + sweeps - 1 of a T-sweep schedule, updating s in place.
 // Returns 0, or -1 on invalid input.
-int oracle_anneal(int32_t n, int64_t m, const int32_t* src, const int32_t* dst,
-                  const int32_t* w, int8_t* s, uint64_t seed, uint32_t instance,
-                  uint32_t replica, double p0, uint64_t T, uint64_t t_begin, uint64_t sweeps) {
+//
+// bias (may be null): a per-vertex flip bias q_v in 0..255, a project addition
+// with no counterpart in the paper (R11): vertex v flips iff
+// x < min((thr[t] * q_v) >> 7, 2^32 - 1), computed in 64-bit integers, so
+// q_v = 128 is Algorithm 2 unchanged and q_v = 0 never flips.
+int oracle_anneal_biased(int32_t n, int64_t m, const int32_t* src, const int32_t* dst,
+                         const int32_t* w, int8_t* s, uint64_t seed, uint32_t instance,
+                         uint32_t replica, double p0, uint64_t T, uint64_t t_begin,
+                         uint64_t sweeps, const uint8_t* bias) {
   if (!(p0 >= 0.0 && p0 <= 1.0)) return -1;
   if (T >= 4294967296ull || t_begin + sweeps > T) return -1;
   Adjacency adj;
@@ -316,12 +324,24 @@ int oracle_anneal(int32_t n, int64_t m, const int32_t* src, const int32_t* dst,
         else if (f < 0)
           s[v] = 1;
         // Algorithm 2: flip right after the update with probability F_p.
+        uint64_t thr_v = thr;
+        if (bias != nullptr) {
+          thr_v = ((uint64_t)thr * (uint64_t)bias[v]) >> 7;
+          if (thr_v > 4294967295ull) thr_v = 4294967295ull;
+        }
         uint32_t x = random_word(seed, instance, (uint32_t)v, (uint32_t)t, replica, 0u);
-        if (x < thr) s[v] = (int8_t)(-s[v]);
+        if ((uint64_t)x < thr_v) s[v] = (int8_t)(-s[v]);
       }
     }
   }
   return 0;
+}
+
+int oracle_anneal(int32_t n, int64_t m, const int32_t* src, const int32_t* dst,
+                  const int32_t* w, int8_t* s, uint64_t seed, uint32_t instance,
+                  uint32_t replica, double p0, uint64_t T, uint64_t t_begin, uint64_t sweeps) {
+  return oracle_anneal_biased(n, m, src, dst, w, s, seed, instance, replica, p0, T, t_begin,
+                              sweeps, nullptr);
 }
 
 // Algorithm 1's schedule: a sweep updates every spin (colour classes as in

@@ -26,3 +26,4 @@ from .graphs import (  # noqa: F401
     workload,
     WORKLOADS,
 )
+from .gnn_init import GNN_NUM_PARAMS, gnn_init_params  # noqa: F401

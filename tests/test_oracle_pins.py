@@ -400,3 +400,46 @@ def test_nflip_reaches_known_optimum_and_rejects_bad_n0():
     assert best == int(g.w.sum())
     with pytest.raises(ValueError):
         oracle.anneal_nflip(g.n, g.src, g.dst, g.w, np.ones(g.n, np.int8), seed=1, n0=g.n + 1, T=5)
+
+
+# --- R11: per-vertex flip bias (project addition; q = 128 is Algorithm 2) ---
+
+def test_bias_128_is_algorithm_2_and_zero_is_greedy():
+    g = synth.random_small_graph(300, 0.05, 21, weights="int8")
+    s0 = oracle.init_spins(g.n, 5)
+    plain = oracle.anneal(g.n, g.src, g.dst, g.w, s0, seed=9, p0=0.2, T=40)
+    q128 = oracle.anneal(g.n, g.src, g.dst, g.w, s0, seed=9, p0=0.2, T=40,
+                         bias=np.full(g.n, 128, np.uint8))
+    assert np.array_equal(plain, q128)
+    greedy = oracle.anneal(g.n, g.src, g.dst, g.w, s0, seed=9, p0=0.0, T=40)
+    q0 = oracle.anneal(g.n, g.src, g.dst, g.w, s0, seed=9, p0=0.2, T=40,
+                       bias=np.zeros(g.n, np.uint8))
+    assert np.array_equal(greedy, q0)
+
+
+def test_bias_scales_the_flip_rate_per_vertex():
+    # Edgeless graph: only the flip acts. Four groups of vertices with
+    # q = 32, 64, 200, 255 must flip at rate thr[0] * q / 128 / 2^32.
+    n = 4 * 30000
+    e = np.zeros(0, dtype=np.int32)
+    qs = np.array([32, 64, 200, 255], np.uint8)
+    q = np.repeat(qs, n // 4)
+    s0 = oracle.init_spins(n, 3)
+    s = oracle.anneal(n, e, e, e, s0, seed=8, p0=0.25, T=2, sweeps=1, bias=q)
+    thr = oracle.threshold(0.25, 2, 0)
+    for k, qk in enumerate(qs):
+        part = slice(k * (n // 4), (k + 1) * (n // 4))
+        frac = float((s[part] != s0[part]).mean())
+        p = (thr * int(qk) >> 7) / 2 ** 32
+        assert abs(frac - p) < 5 * math.sqrt(p * (1 - p) / (n // 4)), (qk, frac, p)
+
+
+def test_bias_threshold_clamps_at_the_top():
+    # p0 = 1 and q = 255: thr * q / 128 exceeds 2^32 - 1 and clamps there, so
+    # sweep 0 flips every spin whose word is not 2^32 - 1 (all of them here).
+    n = 5000
+    e = np.zeros(0, dtype=np.int32)
+    s0 = oracle.init_spins(n, 2)
+    s = oracle.anneal(n, e, e, e, s0, seed=6, p0=1.0, T=2, sweeps=1,
+                      bias=np.full(n, 255, np.uint8))
+    assert np.array_equal(s, -s0)
