@@ -324,6 +324,76 @@ int ising_energy_csr_static(int32_t n, const int32_t* row_ptr, const int32_t* co
                             const int32_t* w, const int8_t* spins, int64_t* out,
                             void* cuda_stream);
 
+/* ------------------------------------------------------------------------
+ * Per-vertex flip bias and the learned warm start. Neither is in the paper:
+ * they are project additions built on its Algorithm 2 and Eq. 2.
+ *
+ * Flip bias (reading R11): with a bias q_v in 0..255 set on a graph, vertex v
+ * flips in sweep t of a linear schedule iff its Philox word is below
+ * min((thr[t] * q_v) >> 7, 2^32 - 1), computed in 64-bit integers -- q_v = 128
+ * is Algorithm 2 unchanged, q_v = 0 never flips. It applies to ISING_MODE_DET
+ * and ISING_MODE_RACY sweeps of every engine; the N-flip schedule and the
+ * batched engine ignore it.
+ *
+ * Warm-start network (readings G1-G6), evaluated on a graph's current spins:
+ *   G1  merged weights w (as in ising_create); d_i = sum_j |w_ij|,
+ *       c_i = (d_i + 1)^-1/2, A_hat = C W C.
+ *   G2  x_i = [s_i, f_i c_i^2, s_i f_i c_i^2, log(1 + deg_i) / 8,
+ *       (sum_j w_ij) c_i^2, 1, 0, 0], f_i = sum_j w_ij s_j (Eq. 2's field),
+ *       deg_i the number of merged neighbours.
+ *   G3  for l = 0, 1, 2: a = A_hat h, h <- relu([h, a] W_l + b_l), h = x at
+ *       first (widths 8 -> 64 -> 64 -> 64); logit z = h w_o + b_o.
+ *   G4  training loss against annealer spins y: mean_i softplus(-y_i z_i).
+ *   G5  warm start: s_i = +1 if z_i > 0, -1 if z_i < 0, else unchanged.
+ *   G6  flip bias: q_i = min(255, round_half_even(512 / (1 + exp(|z_i|)))).
+ * Parameters: ISING_GNN_NUM_PARAMS floats, row-major in this order:
+ * W_0 [16][64], b_0 [64], W_1 [128][64], b_1 [64], W_2 [128][64], b_2 [64],
+ * w_o [64], b_o [1]; row k of W_l multiplies feature k of [h, a].
+ * Arithmetic: W_0..W_2 are used rounded to bf16 and every activation h, a is
+ * stored in bf16 between kernels; sums and the head are fp32 (tensor-core
+ * mma with fp32 accumulation for the dense layers). Logits therefore agree
+ * with exact arithmetic to about 1e-2 relative, not bit for bit.
+ * A network handle may serve several graphs on the same device, one call at a
+ * time; its work runs on the graph's stream.
+ * ------------------------------------------------------------------------ */
+#define ISING_GNN_NUM_PARAMS 17665
+typedef struct ising_gnn ising_gnn; /* opaque */
+
+/* ising_set_flip_bias -- q: uint8[n] in the caller's vertex order (host, or
+ * device with on_device = 1), or NULL to remove the bias. */
+int ising_set_flip_bias(ising_graph* g, const uint8_t* q, int on_device);
+/* ising_get_flip_bias -- host uint8[n] in the caller's order; ISING_ESTATE if
+ * no bias is set. Synchronises the stream. */
+int ising_get_flip_bias(ising_graph* g, uint8_t* out);
+/* ising_gnn_create -- a network on the current device with the given host
+ * parameters (ISING_EINVAL if any is not finite); Adam moments start at 0. */
+int ising_gnn_create(const float* params, ising_gnn** out);
+/* ising_gnn_set_params / ising_gnn_get_params -- host float[ISING_GNN_NUM_PARAMS];
+ * set also resets the Adam state. */
+int ising_gnn_set_params(ising_gnn* net, const float* params);
+int ising_gnn_get_params(ising_gnn* net, float* out);
+/* ising_gnn_forward -- logits z (G3) of every vertex of g from g's current
+ * spins: float[n] in the caller's order, host (synchronises) or device. */
+int ising_gnn_forward(ising_gnn* net, ising_graph* g, float* out_logits, int on_device);
+/* ising_gnn_gradients -- loss G4 and its gradient for labels y (int8[n], +1 /
+ * -1, caller order; host values are checked, device values are read as
+ * y > 0 -> +1, else -1). out_loss and out_grad (host
+ * float[ISING_GNN_NUM_PARAMS]) may be NULL; a non-NULL one synchronises. */
+int ising_gnn_gradients(ising_gnn* net, ising_graph* g, const int8_t* labels, int labels_on_device,
+                        float* out_loss, float* out_grad);
+/* ising_gnn_train_step -- the same gradient, then one Adam step (beta1 0.9,
+ * beta2 0.999, eps 1e-8) with learning rate lr on the fp32 master weights. */
+int ising_gnn_train_step(ising_gnn* net, ising_graph* g, const int8_t* labels, int labels_on_device,
+                         float lr, float* out_loss);
+/* ising_gnn_warm_start -- forward pass, then G5 on g's spins (resets the
+ * update parity, like ising_set_spins) and, if set_bias, G6 as g's flip bias.
+ * Asynchronous on g's stream. */
+int ising_gnn_warm_start(ising_gnn* net, ising_graph* g, int set_bias);
+/* ising_gnn_launch_count -- kernels launched by this network handle. */
+int ising_gnn_launch_count(ising_gnn* net, uint64_t* out);
+/* ising_gnn_destroy -- free the network (NULL is ignored). */
+void ising_gnn_destroy(ising_gnn* net);
+
 /* ising_launch_count -- number of CUDA kernels this handle has launched since
  * ising_create (a diagnostic for benchmarks). */
 int ising_launch_count(ising_graph* g, uint64_t* out);

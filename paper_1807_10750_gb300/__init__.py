@@ -48,7 +48,11 @@ EXPORTS = (
     "ising_batch_create", "ising_batch_init_random", "ising_batch_anneal", "ising_batch_cuts",
     "ising_batch_get_spins", "ising_batch_set_spins", "ising_batch_autotune", "ising_batch_set_block",
     "ising_batch_info", "ising_batch_destroy", "ising_anneal_trace",
+    "ising_set_flip_bias", "ising_get_flip_bias", "ising_gnn_create", "ising_gnn_set_params",
+    "ising_gnn_get_params", "ising_gnn_forward", "ising_gnn_gradients", "ising_gnn_train_step",
+    "ising_gnn_warm_start", "ising_gnn_launch_count", "ising_gnn_destroy",
 )
+ISING_GNN_NUM_PARAMS = 17665
 
 
 class IsingError(RuntimeError):
@@ -112,6 +116,18 @@ def lib():
                                        ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_uint64)]
         L.ising_batch_destroy.argtypes = [vp]
         L.ising_batch_destroy.restype = None
+        L.ising_set_flip_bias.argtypes = [vp, vp, ctypes.c_int]
+        L.ising_get_flip_bias.argtypes = [vp, vp]
+        L.ising_gnn_create.argtypes = [vp, ctypes.POINTER(ctypes.c_void_p)]
+        L.ising_gnn_set_params.argtypes = [vp, vp]
+        L.ising_gnn_get_params.argtypes = [vp, vp]
+        L.ising_gnn_forward.argtypes = [vp, vp, vp, ctypes.c_int]
+        L.ising_gnn_gradients.argtypes = [vp, vp, vp, ctypes.c_int, vp, vp]
+        L.ising_gnn_train_step.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_float, vp]
+        L.ising_gnn_warm_start.argtypes = [vp, vp, ctypes.c_int]
+        L.ising_gnn_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
+        L.ising_gnn_destroy.argtypes = [vp]
+        L.ising_gnn_destroy.restype = None
         L.ising_strerror.argtypes = [ctypes.c_int]
         L.ising_strerror.restype = ctypes.c_char_p
         for name in EXPORTS:
@@ -142,7 +158,8 @@ def _buffer(x, dtype, n: int | None, writable: bool):
     """(pointer, on_device, keepalive) for a numpy array or torch tensor."""
     if hasattr(x, "data_ptr") and hasattr(x, "is_cuda"):
         import torch  # only when a tensor is passed
-        want = {np.int8: torch.int8, np.int32: torch.int32, np.int64: torch.int64}[dtype]
+        want = {np.int8: torch.int8, np.int32: torch.int32, np.int64: torch.int64,
+                np.uint8: torch.uint8, np.float32: torch.float32}[dtype]
         if x.dtype != want:
             raise TypeError(f"expected a {want} tensor")
         if not x.is_contiguous() or (n is not None and x.numel() != n):
@@ -431,3 +448,115 @@ def ising_batch_info(b: IsingBatch) -> dict:
 
 def ising_batch_destroy(b: IsingBatch) -> None:
     b.close()
+
+
+# ---------------------------------------------------------------------------
+# flip bias and the learned warm start
+# ---------------------------------------------------------------------------
+def ising_set_flip_bias(g: IsingGraph, q) -> None:
+    """Per-vertex flip bias q (uint8, caller order), or None to remove it."""
+    if q is None:
+        _check(lib().ising_set_flip_bias(g.ptr, None, 0), "ising_set_flip_bias")
+        return
+    p, on_dev, _keep = _buffer(q, np.uint8, g.n, False)
+    _check(lib().ising_set_flip_bias(g.ptr, p, on_dev), "ising_set_flip_bias")
+
+
+def ising_get_flip_bias(g: IsingGraph) -> np.ndarray:
+    out = np.zeros(g.n, dtype=np.uint8)
+    _check(lib().ising_get_flip_bias(g.ptr, out.ctypes.data), "ising_get_flip_bias")
+    return out
+
+
+class IsingGnn:
+    """Owning wrapper of an ``ising_gnn*`` handle."""
+
+    def __init__(self, ptr: int):
+        self.ptr = ctypes.c_void_p(ptr)
+
+    def close(self):
+        if self.ptr and self.ptr.value:
+            lib().ising_gnn_destroy(self.ptr)
+            self.ptr = ctypes.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def _params(params) -> np.ndarray:
+    a = np.ascontiguousarray(params, dtype=np.float32)
+    if a.shape != (ISING_GNN_NUM_PARAMS,):
+        raise ValueError(f"expected {ISING_GNN_NUM_PARAMS} parameters")
+    return a
+
+
+def ising_gnn_create(params) -> IsingGnn:
+    a = _params(params)
+    out = ctypes.c_void_p()
+    _check(lib().ising_gnn_create(a.ctypes.data, ctypes.byref(out)), "ising_gnn_create")
+    return IsingGnn(out.value)
+
+
+def ising_gnn_set_params(net: IsingGnn, params) -> None:
+    a = _params(params)
+    _check(lib().ising_gnn_set_params(net.ptr, a.ctypes.data), "ising_gnn_set_params")
+
+
+def ising_gnn_get_params(net: IsingGnn) -> np.ndarray:
+    out = np.zeros(ISING_GNN_NUM_PARAMS, dtype=np.float32)
+    _check(lib().ising_gnn_get_params(net.ptr, out.ctypes.data), "ising_gnn_get_params")
+    return out
+
+
+def ising_gnn_forward(net: IsingGnn, g: IsingGraph, out=None):
+    """Logits in the caller's vertex order (numpy float32, or into ``out``,
+    a float32 numpy array or CUDA tensor of n elements)."""
+    if out is None:
+        out = np.zeros(g.n, dtype=np.float32)
+    p, on_dev, _keep = _buffer(out, np.float32, g.n, True)
+    _check(lib().ising_gnn_forward(net.ptr, g.ptr, p, on_dev), "ising_gnn_forward")
+    return out
+
+
+def ising_gnn_gradients(net: IsingGnn, g: IsingGraph, labels):
+    """(loss, gradient) for int8 +-1 labels in the caller's order."""
+    p, on_dev, _keep = _buffer(labels, np.int8, g.n, False)
+    loss = ctypes.c_float()
+    grad = np.zeros(ISING_GNN_NUM_PARAMS, dtype=np.float32)
+    _check(lib().ising_gnn_gradients(net.ptr, g.ptr, p, on_dev, ctypes.byref(loss), grad.ctypes.data),
+           "ising_gnn_gradients")
+    return float(loss.value), grad
+
+
+def ising_gnn_train_step(net: IsingGnn, g: IsingGraph, labels, lr: float, want_loss: bool = False):
+    """One Adam step on the loss against ``labels``; returns the loss (before
+    the step) if ``want_loss``, else None without synchronising."""
+    p, on_dev, _keep = _buffer(labels, np.int8, g.n, False)
+    loss = ctypes.c_float()
+    _check(lib().ising_gnn_train_step(net.ptr, g.ptr, p, on_dev, float(lr),
+                                      ctypes.byref(loss) if want_loss else None),
+           "ising_gnn_train_step")
+    return float(loss.value) if want_loss else None
+
+
+def ising_gnn_warm_start(net: IsingGnn, g: IsingGraph, set_bias: bool = True) -> None:
+    _check(lib().ising_gnn_warm_start(net.ptr, g.ptr, int(bool(set_bias))), "ising_gnn_warm_start")
+
+
+def ising_gnn_launch_count(net: IsingGnn) -> int:
+    v = ctypes.c_uint64()
+    _check(lib().ising_gnn_launch_count(net.ptr, ctypes.byref(v)), "ising_gnn_launch_count")
+    return v.value
+
+
+def ising_gnn_destroy(net: IsingGnn) -> None:
+    net.close()

@@ -26,6 +26,7 @@
 #include "host_graph.h"
 #include "philox.cuh"
 #include "sweep.cuh"
+#include "graph_handle.h"
 
 using isingx::HostGraph;
 using isingx::PhiloxKey;
@@ -94,10 +95,27 @@ __device__ __forceinline__ SweepArgs sweep_args(uint64_t t, uint64_t T, uint64_t
   return sa;
 }
 
-// Item `warp` of colour class cls, or an empty item if the class has fewer.
+// First item of colour class cls for this warp. Deterministic passes: item
+// warp of every class (a barrier follows each class). The racy pass walks
+// all classes without a barrier, so there items are dealt round-robin over
+// the whole sweep -- item i, counted across classes, belongs to warp
+// i mod nwarps -- and a warp gets as many items as any other instead of one
+// in every class.
+template <int PASS>
+__device__ __forceinline__ int class_start(const int32_t* phase_items, int cls, int warp,
+                                           int nwarps) {
+  const int ib = __ldg(phase_items + cls);
+  if (PASS != kPassRacy) return ib + warp;
+  int r = (warp - ib) % nwarps;
+  if (r < 0) r += nwarps;
+  return ib + r;
+}
+
+// The warp's first item of colour class cls, or an empty item if it has none.
+template <int PASS>
 __device__ __forceinline__ WorkItem first_item(const DevGraph& d, const int32_t* phase_items,
-                                               int cls, int warp) {
-  const int i = __ldg(phase_items + cls) + warp;
+                                               int cls, int warp, int nwarps) {
+  const int i = class_start<PASS>(phase_items, cls, warp, nwarps);
   WorkItem it = {0, 0, 0, 0};
   if (i < __ldg(phase_items + cls + 1)) it = d.items[i];
   return it;
@@ -123,16 +141,16 @@ __global__ void __launch_bounds__(kPersistBlock, 2)
   uint32_t k = 0;
   int c = 0;
   SweepArgs a = sweep_args(t_begin + 0, T, T0, replica);
-  int ib = __ldg(phase_items), ie = __ldg(phase_items + 1);
+  int ib = class_start<PASS>(phase_items, 0, warp, nwarps), ie = __ldg(phase_items + 1);
   isingx::Staged<PACKED> st;
-  bool have = ib + warp < ie;
-  if (have) isingx::stage_item<PACKED>(d, d.items[ib + warp], a, rk, lane, st);
+  bool have = ib < ie;
+  if (have) isingx::stage_item<PACKED>(d, d.items[ib], a, rk, lane, st);
   // the warp's first item of the following class, loaded one class ahead
-  WorkItem next = first_item(d, phase_items, num_phases > 1 ? 1 : 0, warp);
+  WorkItem next = first_item<PASS>(d, phase_items, num_phases > 1 ? 1 : 0, warp, nwarps);
   for (;;) {
     if (have) {
       isingx::finish_item<PACKED, PASS>(d, st, a, rk, lane, unused);
-      for (int i = ib + warp + nwarps; i < ie; i += nwarps) {
+      for (int i = ib + nwarps; i < ie; i += nwarps) {
         isingx::stage_item<PACKED>(d, d.items[i], a, rk, lane, st);
         isingx::finish_item<PACKED, PASS>(d, st, a, rk, lane, unused);
       }
@@ -159,11 +177,11 @@ __global__ void __launch_bounds__(kPersistBlock, 2)
     } else {
       ++c;
     }
-    ib = __ldg(phase_items + c);
+    ib = class_start<PASS>(phase_items, c, warp, nwarps);
     ie = __ldg(phase_items + c + 1);
-    have = ib + warp < ie;
+    have = ib < ie;
     if (have) isingx::stage_item<PACKED>(d, next, a, rk, lane, st);
-    next = first_item(d, phase_items, c + 1 < num_phases ? c + 1 : 0, warp);
+    next = first_item<PASS>(d, phase_items, c + 1 < num_phases ? c + 1 : 0, warp, nwarps);
     if (sync) {
       target += gridDim.x;
       if (!isingx::barrier_wait(bs, target)) return;
@@ -261,71 +279,6 @@ int grid_for(int64_t work, int per_block, int cap) {
 
 }  // namespace
 
-struct ising_graph {
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  int status = ISING_OK;
-  int engine = ISING_ENGINE_AUTO;
-  int num_sms = 1;
-  uint64_t launches = 0;
-
-  int32_t n = 0;
-  int parity = 0;  // update parity of every state byte (bit 1) between calls
-  int64_t num_edges = 0;
-  int64_t nnz = 0;
-  int64_t total_weight = 0;
-  int32_t num_colours = 0;
-  bool packed = true;  // packed (col << 8 | w) edges, else split int32 col / w
-  std::vector<int32_t> colour;  // by caller id
-  std::vector<int32_t> class_item_begin;
-  int32_t num_items = 0;
-  int32_t num_slots = 0;
-
-  int32_t* d_row_ptr = nullptr;
-  int32_t* d_adj = nullptr;  // packed format
-  int32_t* d_col = nullptr;  // split format
-  int32_t* d_w = nullptr;    // split format
-  int32_t* d_ell = nullptr;      // sliced ELL, packed format
-  int32_t* d_ell_col = nullptr;  // sliced ELL, split format
-  int32_t* d_ell_w = nullptr;    // sliced ELL, split format
-  int8_t* d_spins = nullptr;
-  int32_t* d_orig = nullptr;
-  int32_t* d_pos = nullptr;
-  WorkItem* d_items = nullptr;
-  unsigned long long* d_slice_acc = nullptr;
-  int32_t* d_slice_parts = nullptr;
-  unsigned long long* d_energy = nullptr;
-  int32_t* d_flag = nullptr;
-  int8_t* d_tmp = nullptr;
-  int32_t* d_class_items = nullptr;  // num_colours + 1 item offsets
-  int32_t* d_class_begin = nullptr;  // num_colours + 1 first positions
-  unsigned long long* d_trace = nullptr;  // energy trace (twice H per checkpoint)
-  unsigned* d_nflip_bits = nullptr;        // N-flip: chosen-vertex bitmap (kept zero)
-  int32_t* d_nflip_list = nullptr;         // N-flip: chosen vertices, n entries
-  size_t trace_cap = 0;
-  int32_t* d_all_items = nullptr;    // {0, num_items}: one phase over every item (energy)
-  BarrierState* d_barrier = nullptr;
-  int persist_grid = 0;              // co-resident blocks of the persistent kernel
-
-  DevGraph dev() const {
-    DevGraph d;
-    d.pad_col = n;
-    d.row_ptr = d_row_ptr;
-    d.adj = d_adj;
-    d.col = d_col;
-    d.w = d_w;
-    d.ell = d_ell;
-    d.ell_col = d_ell_col;
-    d.ell_w = d_ell_w;
-    d.spins = d_spins;
-    d.orig = d_orig;
-    d.items = d_items;
-    d.slice_acc = d_slice_acc;
-    d.error = d_barrier ? &d_barrier->error : nullptr;
-    d.slice_parts = d_slice_parts;
-    return d;
-  }
-};
 
 namespace {
 
@@ -334,7 +287,8 @@ void free_device(ising_graph* g) {
                   g->d_orig,    g->d_pos,         g->d_items,       g->d_slice_acc,
                   g->d_slice_parts, g->d_energy,  g->d_flag,
                   g->d_tmp,     g->d_class_items, g->d_all_items, g->d_barrier,
-                  g->d_class_begin, g->d_trace, g->d_nflip_bits, g->d_nflip_list};
+                  g->d_class_begin, g->d_trace, g->d_nflip_bits, g->d_nflip_list,
+                  g->d_bias,    g->d_rowid};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -885,3 +839,8 @@ int ising_set_engine(ising_graph* g, int engine) {
 }
 
 }  // extern "C"
+
+namespace isingx {
+int graph_enter(ising_graph* g) { return enter(g); }
+int graph_cuda_fail(ising_graph* g, cudaError_t e) { return cuda_fail(g, e); }
+}  // namespace isingx

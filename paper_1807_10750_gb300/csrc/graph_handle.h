@@ -1,0 +1,92 @@
+// The graph handle of include/ising.h, shared by the sweep engine
+// (anneal.cu) and the warm-start network (gnn.cu). Internal to the library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "../../include/ising.h"
+#include "host_graph.h"
+#include "sweep.cuh"
+
+struct ising_graph {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int status = ISING_OK;
+  int engine = ISING_ENGINE_AUTO;
+  int num_sms = 1;
+  uint64_t launches = 0;
+
+  int32_t n = 0;
+  int parity = 0;  // update parity of every state byte (bit 1) between calls
+  int64_t num_edges = 0;
+  int64_t nnz = 0;
+  int64_t total_weight = 0;
+  int32_t num_colours = 0;
+  bool packed = true;  // packed (col << 8 | w) edges, else split int32 col / w
+  std::vector<int32_t> colour;  // by caller id
+  std::vector<int32_t> class_item_begin;
+  int32_t num_items = 0;
+  int32_t num_slots = 0;
+
+  int32_t* d_row_ptr = nullptr;
+  int32_t* d_adj = nullptr;  // packed format
+  int32_t* d_col = nullptr;  // split format
+  int32_t* d_w = nullptr;    // split format
+  int32_t* d_ell = nullptr;      // sliced ELL, packed format
+  int32_t* d_ell_col = nullptr;  // sliced ELL, split format
+  int32_t* d_ell_w = nullptr;    // sliced ELL, split format
+  int8_t* d_spins = nullptr;
+  int32_t* d_orig = nullptr;
+  int32_t* d_pos = nullptr;
+  isingx::WorkItem* d_items = nullptr;
+  unsigned long long* d_slice_acc = nullptr;
+  int32_t* d_slice_parts = nullptr;
+  unsigned long long* d_energy = nullptr;
+  int32_t* d_flag = nullptr;
+  int8_t* d_tmp = nullptr;
+  int32_t* d_class_items = nullptr;  // num_colours + 1 item offsets
+  int32_t* d_class_begin = nullptr;  // num_colours + 1 first positions
+  unsigned long long* d_trace = nullptr;  // energy trace (twice H per checkpoint)
+  unsigned* d_nflip_bits = nullptr;        // N-flip: chosen-vertex bitmap (kept zero)
+  int32_t* d_nflip_list = nullptr;         // N-flip: chosen vertices, n entries
+  size_t trace_cap = 0;
+  int32_t* d_all_items = nullptr;    // {0, num_items}: one phase over every item (energy)
+  uint8_t* d_bias = nullptr;         // per-position flip bias (null: none)
+  int32_t* d_rowid = nullptr;        // row of every CSR entry (built on first use)
+  isingx::BarrierState* d_barrier = nullptr;
+  int persist_grid = 0;              // co-resident blocks of the persistent kernel
+
+  isingx::DevGraph dev() const {
+    isingx::DevGraph d;
+    d.pad_col = n;
+    d.row_ptr = d_row_ptr;
+    d.adj = d_adj;
+    d.col = d_col;
+    d.w = d_w;
+    d.ell = d_ell;
+    d.ell_col = d_ell_col;
+    d.ell_w = d_ell_w;
+    d.spins = d_spins;
+    d.orig = d_orig;
+    d.items = d_items;
+    d.slice_acc = d_slice_acc;
+    d.error = d_barrier ? &d_barrier->error : nullptr;
+    d.slice_parts = d_slice_parts;
+    d.bias = d_bias;
+    return d;
+  }
+};
+
+namespace isingx {
+
+// Argument and state check at the top of every entry point: the handle is
+// valid, has no latched error, and its device is current.
+int graph_enter(ising_graph* g);
+
+// Latch a CUDA failure in the handle and return ISING_ECUDA.
+int graph_cuda_fail(ising_graph* g, cudaError_t e);
+
+}  // namespace isingx

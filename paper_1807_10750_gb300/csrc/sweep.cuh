@@ -73,6 +73,7 @@ struct DevGraph {
   const WorkItem* items;
   unsigned long long* slice_acc;  // packed partial fields of sliced rows
   const int32_t* slice_parts;
+  const uint8_t* bias;  // per-position flip bias q (threshold * q / 128), or null
 };
 
 struct SweepArgs {
@@ -127,7 +128,7 @@ constexpr long long kFlowBudgetNs = 2000000000LL;  // 2 s per wait
 // yet if it comes later (parity par_cur); the pad entry never changes. Re-reads
 // until that holds; gives up (recording a timeout) after kFlowBudgetNs or once
 // any wait has failed.
-__device__ __noinline__ int flow_wait(const DevGraph& d, int j, int need) {
+static __device__ __noinline__ int flow_wait(const DevGraph& d, int j, int need) {
   const long long t0 = flow_ns();
   for (;;) {
     const int b = ld_relaxed_s8(d.spins + j) & 3;
@@ -200,9 +201,19 @@ __device__ __forceinline__ int strided_field(const DevGraph& d, int e0, int e1, 
   return f;
 }
 
-// Algorithm 2's random flip of the vertex whose caller id is o, in sweep a.t.
-__device__ __forceinline__ bool flip_drawn(uint32_t o, const SweepArgs& a, const PhiloxRounds& rk) {
-  return a.thr != 0u && philox4x32_10_word0(o, a.t, a.replica, 0u, rk) < a.thr;
+// Algorithm 2's random flip of the vertex at position v whose caller id is
+// o, in sweep a.t. With a flip bias the threshold is min((thr * q_v) >> 7,
+// 2^32 - 1) in 64-bit integers (q_v = 128 leaves it unchanged).
+__device__ __forceinline__ bool flip_drawn(const DevGraph& d, int v, uint32_t o,
+                                           const SweepArgs& a, const PhiloxRounds& rk) {
+  if (a.thr == 0u) return false;
+  uint32_t thr = a.thr;
+  if (d.bias != nullptr) {
+    const unsigned long long t =
+        (static_cast<unsigned long long>(a.thr) * __ldg(d.bias + v)) >> 7;
+    thr = t > 0xffffffffull ? 0xffffffffu : static_cast<uint32_t>(t);
+  }
+  return philox4x32_10_word0(o, a.t, a.replica, 0u, rk) < thr;
 }
 
 // Eq. 2 under the max-cut sign (s <- -sign f, f = 0 keeps s), then the flip;
@@ -262,7 +273,9 @@ __device__ __forceinline__ void stage_light_shape(const DevGraph& d, Staged<PACK
   s.flips = 0;
 #pragma unroll
   for (int r = 0; r < R; ++r)
-    if (orig[r] >= 0 && flip_drawn(static_cast<uint32_t>(orig[r]), a, rk)) s.flips |= 1u << r;
+    if (orig[r] >= 0 &&
+        flip_drawn(d, s.it.v_begin + lane + 32 * r, static_cast<uint32_t>(orig[r]), a, rk))
+      s.flips |= 1u << r;
 }
 
 template <bool PACKED>
@@ -346,7 +359,7 @@ __device__ __forceinline__ void finish_group_rows(const DevGraph& d, const WorkI
       if (PASS == kPassEnergy)
         energy += static_cast<long long>(spin_of(d.spins[v])) * my_f;
       else
-        apply_update<PASS>(d, v, my_f, flip_drawn(static_cast<uint32_t>(__ldg(d.orig + v)), a, rk), a);
+        apply_update<PASS>(d, v, my_f, flip_drawn(d, v, static_cast<uint32_t>(__ldg(d.orig + v)), a, rk), a);
     }
   }
 }
@@ -381,7 +394,7 @@ __device__ __forceinline__ void finish_item(const DevGraph& d, const Staged<PACK
   f += strided_field<PACKED, PASS>(d, s.it.e_begin + lane + 128, s.it.e_end, 32, a);
   const int v = s.it.v_begin;
   const bool flip = (PASS != kPassEnergy && lane == 0) &&
-                    flip_drawn(static_cast<uint32_t>(__ldg(d.orig + v)), a, rk);
+                    flip_drawn(d, v, static_cast<uint32_t>(__ldg(d.orig + v)), a, rk);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(kFullMask, f, o);
   if (PASS == kPassEnergy) {

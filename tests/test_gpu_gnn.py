@@ -1,0 +1,224 @@
+"""GPU parity of the flip bias (bit-exact against the oracle) and of the
+warm-start network (logits and gradients against the FP64 oracle).
+
+Tolerances of the network. The GPU uses bf16-rounded weights W_0..W_2 (the
+oracle is given the same rounded values) and stores every activation in
+bf16 between kernels (relative rounding 2^-9 per value). Emulating exactly
+those roundings in float64 on these graphs gives logits within 0.6 % of the
+exact network in norm and within 2 % element-wise (relative to |z| plus the
+rms logit), so the bars are 1e-2 in norm (the stated tolerance) and 5e-2
+element-wise. Gradients are compared per parameter block, also at 1e-2 in
+norm, with labels that agree with the input spins on 80 % of the vertices
+(as annealer labels do): emulated errors are 2e-3 there. With labels
+independent of the input the gradient is a sum that almost cancels and its
+relative error is not bounded by the arithmetic, so that case is not used.
+"""
+
+import numpy as np
+import pytest
+
+import synth
+import oracle
+from oracle import gnn_oracle as go
+
+pytestmark = pytest.mark.gpu
+
+P = pytest.importorskip("paper_1807_10750_gb300")
+
+
+def bf16_round(x):
+    """Round float32 values to the nearest bf16 (ties to even)."""
+    u = np.asarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32)
+
+
+def effective_params(params):
+    """The parameters the GPU computes with: W_0..W_2 in bf16, the rest fp32."""
+    d = go.unpack(np.asarray(params, np.float32).astype(np.float64))
+    for l in range(3):
+        d[f"W{l}"] = bf16_round(d[f"W{l}"]).astype(np.float64)
+    return go.pack(d)
+
+
+GRAPHS = {
+    "er_int8": lambda: synth.random_small_graph(3000, 0.004, 3, weights="int8", duplicates=50),
+    "torus_pm1": lambda: synth.torus_graph(64, 1, weights="pm1"),
+    "zipf_hubs": lambda: synth.zipf_config_graph(20011, 2.1, 4, 3000, 5),
+    "int32_weights": lambda: synth.Graph(
+        *(lambda g: (g.n, g.src, g.dst, (g.w * 300).astype(np.int32)))(
+            synth.random_small_graph(1500, 0.01, 9, weights="int8"))),
+}
+
+
+def _spins(n, seed):
+    return np.random.default_rng(seed).choice(np.array([-1, 1], np.int8), size=n)
+
+
+def _norm_rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+@pytest.mark.parametrize("name", sorted(GRAPHS))
+@pytest.mark.parametrize("pseed", [1, 2])
+def test_logits_match_fp64_oracle(name, pseed):
+    g = GRAPHS[name]()
+    s = _spins(g.n, 7)
+    params = synth.gnn_init_params(pseed)
+    with P.ising_create(g.n, g.src, g.dst, g.w) as h, P.ising_gnn_create(params) as net:
+        P.ising_set_spins(h, s)
+        z = P.ising_gnn_forward(net, h)
+    G = go.Graph(g.n, g.src, g.dst, g.w)
+    z_or, _ = go.forward(G, go.features(G, s), effective_params(params))
+    assert _norm_rel(z, z_or) <= 1e-2
+    scale = np.abs(z_or) + np.sqrt(np.mean(z_or ** 2))
+    assert np.all(np.abs(z - z_or) <= 5e-2 * scale)
+
+
+def test_logits_of_edgeless_and_single_vertex_graphs():
+    params = synth.gnn_init_params(4)
+    e = np.zeros(0, np.int32)
+    for n in (1, 100):
+        s = _spins(n, 3)
+        with P.ising_create(n, e, e, e) as h, P.ising_gnn_create(params) as net:
+            P.ising_set_spins(h, s)
+            z = P.ising_gnn_forward(net, h)
+        G = go.Graph(n, e, e, e)
+        pe = effective_params(params)
+        z_or, cache = go.forward(G, go.features(G, s), pe)
+        # a logit is a dot product that may nearly cancel: bound its error by
+        # the magnitude of its terms
+        d = go.unpack(pe)
+        terms = np.abs(cache["h3"]) @ np.abs(d["wo"]) + abs(d["bo"][0])
+        assert np.all(np.abs(z - z_or) <= 1e-2 * terms)
+
+
+@pytest.mark.parametrize("name", ["er_int8", "zipf_hubs", "torus_pm1"])
+def test_gradients_match_fp64_oracle(name):
+    g = GRAPHS[name]()
+    s = _spins(g.n, 11)
+    rng = np.random.default_rng(12)
+    y = np.where(rng.random(g.n) < 0.8, s, -s).astype(np.int8)
+    params = synth.gnn_init_params(3)
+    with P.ising_create(g.n, g.src, g.dst, g.w) as h, P.ising_gnn_create(params) as net:
+        P.ising_set_spins(h, s)
+        loss, grad = P.ising_gnn_gradients(net, h, y)
+    G = go.Graph(g.n, g.src, g.dst, g.w)
+    pe = effective_params(params)
+    z_or, cache = go.forward(G, go.features(G, s), pe)
+    assert loss == pytest.approx(go.loss(z_or, y.astype(np.float64)), rel=1e-3)
+    g_or = go.backward(G, pe, cache, z_or, y.astype(np.float64))
+    k = 0
+    for blk, shape in go.SHAPES:
+        size = int(np.prod(shape))
+        assert _norm_rel(grad[k:k + size], g_or[k:k + size]) <= 1e-2, blk
+        k += size
+
+
+def test_warm_start_and_bias_follow_the_logits():
+    g = GRAPHS["zipf_hubs"]()
+    s = _spins(g.n, 5)
+    params = synth.gnn_init_params(6)
+    with P.ising_create(g.n, g.src, g.dst, g.w) as h, P.ising_gnn_create(params) as net:
+        P.ising_set_spins(h, s)
+        z = P.ising_gnn_forward(net, h)
+        P.ising_gnn_warm_start(net, h, set_bias=True)
+        s2 = P.ising_get_spins(h)
+        q = P.ising_get_flip_bias(h)
+    # the warm start ran its own forward pass; fp32 atomics may reorder sums,
+    # so decisions are compared away from z = 0
+    sure = np.abs(z) > 1e-4 * (np.abs(z).max() + 1e-30)
+    want = go.warm_start(z, s)
+    assert np.array_equal(s2[sure], want[sure])
+    qw = go.flip_bias(z.astype(np.float32))
+    assert np.max(np.abs(q.astype(int) - qw.astype(int))) <= 1
+
+
+@pytest.mark.parametrize("engine", ["phase", "persistent", "dataflow"])
+@pytest.mark.parametrize("mode", ["det", "racy"])
+def test_flip_bias_anneal_matches_oracle(engine, mode):
+    g = synth.random_small_graph(700, 0.02, 17, weights="int8")
+    q = np.random.default_rng(3).integers(0, 256, size=g.n).astype(np.uint8)
+    eng = {"phase": P.ISING_ENGINE_PHASE, "persistent": P.ISING_ENGINE_PERSISTENT,
+           "dataflow": P.ISING_ENGINE_DATAFLOW}[engine]
+    with P.ising_create(g.n, g.src, g.dst, g.w) as h:
+        P.ising_set_engine(h, eng)
+        P.ising_init_random(h, 4)
+        s0 = P.ising_get_spins(h)
+        P.ising_set_flip_bias(h, q)
+        assert np.array_equal(P.ising_get_flip_bias(h), q)
+        md = P.ISING_MODE_DET if mode == "det" else P.ISING_MODE_RACY
+        P.ising_anneal(h, p0=0.3, t_total=60, seed=8, mode=md)
+        s1 = P.ising_get_spins(h)
+        cut = P.ising_cut(h)
+    want = oracle.anneal(g.n, g.src, g.dst, g.w, s0, seed=8, p0=0.3, T=60, bias=q)
+    if mode == "det":
+        assert np.array_equal(s1, want)
+    else:
+        # racy: judged by cut only (a sanity bound against the biased
+        # deterministic run; the racy pass's quality is tested elsewhere)
+        _, _, cut_det = oracle.energy_cut(g.n, g.src, g.dst, g.w, want)
+        assert cut >= 0.9 * cut_det
+
+
+def test_bias_128_and_removal_reproduce_the_unbiased_anneal():
+    g = synth.random_small_graph(500, 0.03, 2, weights="int8")
+    out = []
+    for q in (None, np.full(g.n, 128, np.uint8), "removed"):
+        with P.ising_create(g.n, g.src, g.dst, g.w) as h:
+            P.ising_init_random(h, 1)
+            if q is not None:
+                P.ising_set_flip_bias(h, np.zeros(g.n, np.uint8) if isinstance(q, str) else q)
+            if isinstance(q, str):
+                P.ising_set_flip_bias(h, None)
+            P.ising_anneal(h, p0=0.2, t_total=50, seed=3)
+            out.append(P.ising_get_spins(h))
+    assert np.array_equal(out[0], out[1]) and np.array_equal(out[0], out[2])
+
+
+def test_gnn_argument_errors():
+    g = synth.random_small_graph(50, 0.1, 1)
+    params = synth.gnn_init_params(1)
+    with P.ising_create(g.n, g.src, g.dst, g.w) as h, P.ising_gnn_create(params) as net:
+        with pytest.raises(P.IsingError) as e:
+            P.ising_gnn_gradients(net, h, np.zeros(g.n, np.int8))
+        assert e.value.code == P.ISING_EINVAL
+        with pytest.raises(P.IsingError) as e:
+            P.ising_get_flip_bias(h)
+        assert e.value.code == P.ISING_ESTATE
+        bad = params.copy()
+        bad[5] = np.nan
+        with pytest.raises(P.IsingError):
+            P.ising_gnn_set_params(net, bad)
+        with pytest.raises(ValueError):
+            P.ising_gnn_create(params[:-1])
+        assert np.array_equal(P.ising_gnn_get_params(net), params)
+
+
+def test_training_on_annealer_labels_lowers_the_loss():
+    # a few generated graphs; the input spins are a short hot anneal, the
+    # labels the spins a longer cool anneal continues to from there
+    graphs = [synth.zipf_config_graph(4000, 2.1, 4, 400, 100 + k, weights="int8") for k in range(4)]
+    params = synth.gnn_init_params(5)
+    with P.ising_gnn_create(params) as net:
+        hs, snaps, labels = [], [], []
+        for k, g in enumerate(graphs):
+            h = P.ising_create(g.n, g.src, g.dst, g.w)
+            P.ising_init_random(h, k)
+            P.ising_anneal(h, p0=0.1, t_total=200, seed=k, sweeps=20)
+            snap = P.ising_get_spins(h)
+            P.ising_anneal(h, p0=0.02, t_total=400, seed=50 + k)
+            labels.append(P.ising_get_spins(h))
+            P.ising_set_spins(h, snap)
+            hs.append(h)
+            snaps.append(snap)
+        first = [P.ising_gnn_gradients(net, h, y)[0] for h, y in zip(hs, labels)]
+        for it in range(150):
+            k = it % len(hs)
+            P.ising_gnn_train_step(net, hs[k], labels[k], lr=3e-3)
+        last = [P.ising_gnn_gradients(net, h, y)[0] for h, y in zip(hs, labels)]
+        for h in hs:
+            h.close()
+    # the labels are only partly predictable from the snapshot; 150 steps
+    # took the loss from 0.694 to 0.631 when this test was written
+    assert np.mean(last) < np.mean(first) - 0.03
