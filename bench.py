@@ -41,6 +41,8 @@ def parse_args():
     ap.add_argument("--workload", default="torus1024",
                     choices=["torus1024", "zipf1m", "er800", "batched"])
     ap.add_argument("--engine", default="auto", choices=["auto", "phase", "persistent", "dataflow"])
+    ap.add_argument("--mode", default="det", choices=["det", "racy"],
+                    help="deterministic colour phases (bit-exact) or the racy pass")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
@@ -99,6 +101,27 @@ def kernel_traffic(workload: str, sweeps: int):
     if h.hexdigest()[:16] != e["sources"]:
         return None
     return e["fixed"] + e["per_sweep"] * sweeps
+
+
+def replica_seed(seed: int, rank: int) -> int:
+    """Each rank anneals its own replica: the Philox seed is offset by rank."""
+    return seed + 7919 * rank
+
+
+def max_over_ranks(x: float, world: int, dist, device) -> float:
+    """The slowest rank's time (the job's wall time); a no-op at world 1."""
+    if world <= 1:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput: every rank processes the same number of units
+    (weak scaling), divided by the max-over-ranks time."""
+    return units_per_rank * world / seconds
 
 
 def measured_peaks():
@@ -250,7 +273,7 @@ def run_batched(args, world, rank, P, torch, dist):
     if args.sweeps is not None:
         sch = dict(sch, sweeps=args.sweeps)
     T, p0, R = sch["sweeps"], sch["p0"], sch["replicas"]
-    seed = sch["seed"] + 7919 * rank
+    seed = replica_seed(sch["seed"], rank)
     stream = torch.cuda.Stream()
     arrays = [(g.n, g.src, g.dst, g.w) for g in gs]
     b = P.ising_batch_create(arrays, replicas=R, stream=stream)
@@ -291,11 +314,8 @@ def run_batched(args, world, rank, P, torch, dist):
             best.append(float(cuts.max(axis=1).sum()))
     launches = P.ising_batch_info(b)["launches"] - launches0
     total_ms = sum(s_.elapsed_time(e_) for s_, e_ in zip(starts, ends))
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = nvert * R * T * args.steps * world / (total_ms / 1e3)
+    total_ms = max_over_ranks(total_ms, world, dist, "cuda")
+    value = job_throughput(nvert * R * T * args.steps, world, total_ms / 1e3)
     # per sweep every instance's packed CSR words, row offsets and vertex ids
     # are read once; spins live in shared memory
     B = nnz * 4 + 4 * (nvert + len(gs)) + 4 * nvert
@@ -315,10 +335,7 @@ def run_batched(args, world, rank, P, torch, dist):
             if k > 0:
                 e2e_t.append(time.perf_counter() - t0)
         e2e_total = sum(e2e_t)
-        if world > 1:
-            t = torch.tensor([e2e_total], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_total = float(t.item())
+        e2e_total = max_over_ranks(e2e_total, world, dist, "cuda")
         e2e = {"value": nvert * R * T * len(e2e_t) * world / e2e_total, "unit": "spin-updates/s",
                "h2d_bytes_per_step": int(12 * sum(g.m for g in gs) + 4 * len(gs) + 8 * len(gs)),
                "d2h_bytes_per_step": int(8 * len(gs) * R),
@@ -377,7 +394,7 @@ def main():
         return
 
     g, sch = build_workload(args.workload, args.sweeps)
-    T, p0, seed = sch["sweeps"], sch["p0"], sch["seed"] + 7919 * rank
+    T, p0, seed = sch["sweeps"], sch["p0"], replica_seed(sch["seed"], rank)
     stream = torch.cuda.Stream()
     engine = {"auto": P.ISING_ENGINE_AUTO, "phase": P.ISING_ENGINE_PHASE,
               "persistent": P.ISING_ENGINE_PERSISTENT,
@@ -385,6 +402,7 @@ def main():
 
     h = P.ising_create(g.n, g.src, g.dst, g.w, stream=stream)
     P.ising_set_engine(h, engine)
+    mode = P.ISING_MODE_RACY if args.mode == "racy" else P.ISING_MODE_DET
     # AUTO resolves to the persistent engine on devices with cooperative launch
     engine_name = "persistent" if args.engine == "auto" else args.engine
     colours = P.ising_num_colours(h)
@@ -398,7 +416,7 @@ def main():
     def step(k):
         P.ising_init_random(h, seed + k)
         ev[0].record(stream)
-        P.ising_anneal(h, p0=p0, t_total=T, seed=seed + k, stream=stream)
+        P.ising_anneal(h, p0=p0, t_total=T, seed=seed + k, stream=stream, mode=mode)
         ev[1].record(stream)
         return P.ising_cut(h)
 
@@ -430,13 +448,10 @@ def main():
     launches = P.ising_launch_count(h) - launches0
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = sum(step_ms)
+    total_ms = max_over_ranks(total_ms, world, dist, "cuda")
     if world > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
         dist.barrier()
-    units = g.n * T * args.steps * world
-    value = units / (total_ms / 1e3)
+    value = job_throughput(g.n * T * args.steps, world, total_ms / 1e3)
 
     # roofline of the sweep kernels: algorithmic bytes per sweep / time per sweep
     B = algorithmic_bytes_per_sweep(g.n, nnz, entry_bytes)
@@ -458,17 +473,14 @@ def main():
             with P.ising_create(g.n, src_p, dst_p, w_p, stream=stream) as h2:
                 P.ising_set_engine(h2, engine)
                 P.ising_init_random(h2, seed + k)
-                P.ising_anneal(h2, p0=p0, t_total=T, seed=seed + k, stream=stream)
+                P.ising_anneal(h2, p0=p0, t_total=T, seed=seed + k, stream=stream, mode=mode)
                 P.ising_cut(h2)
                 P.ising_get_spins(h2, spins_out)
             dt = time.perf_counter() - t0
             if k > 0:
                 e2e_t.append(dt)
         e2e_total = sum(e2e_t)
-        if world > 1:
-            t = torch.tensor([e2e_total], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_total = float(t.item())
+        e2e_total = max_over_ranks(e2e_total, world, dist, "cuda")
         e2e = {"value": g.n * T * len(e2e_t) * world / e2e_total, "unit": "spin-updates/s",
                "h2d_bytes_per_step": int(3 * 4 * g.m), "d2h_bytes_per_step": int(g.n + 8),
                "ms_per_step": 1e3 * e2e_total / len(e2e_t)}
@@ -498,7 +510,8 @@ def main():
         "data": "synthetic",
         "config": {
             "workload": args.workload, "n": g.n, "m": m, "colours": colours,
-            "sweeps": T, "p0": p0, "schedule": "linear", "mode": "deterministic",
+            "sweeps": T, "p0": p0, "schedule": "linear",
+            "mode": "racy" if args.mode == "racy" else "deterministic",
             "engine": args.engine, "weights": "int8" if w_bytes == 1 else "int32",
             "csr_entry_bytes": entry_bytes,
             "replicas_per_gpu": 1, "parallelism": f"replicas{world}",
@@ -510,7 +523,8 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
                      "traffic": (kernel_traffic(args.workload, T)
-                                 if engine_name == "persistent" else None),
+                                 if engine_name == "persistent" and args.mode == "det"
+                                 else None),
                      "peak_kind": peak_kind, "bytes_per_sweep": B, "bytes_per_launch": B * T,
                      "kernel": f"{engine_name} sweep kernel(s) of one anneal call"},
         "cpu_baseline": cpu,
