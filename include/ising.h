@@ -99,10 +99,15 @@ enum {
 enum {
   ISING_ENGINE_AUTO = 0,       /* persistent if the device supports cooperative launches */
   ISING_ENGINE_PHASE = 1,      /* one kernel launch per colour class */
-  ISING_ENGINE_PERSISTENT = 2, /* one cooperative launch per anneal call, bounded grid barrier */
-  ISING_ENGINE_DATAFLOW = 3    /* one cooperative launch per anneal call without barriers: each
+  ISING_ENGINE_PERSISTENT = 2, /* one cooperative launch per anneal call, bounded grid barrier;
+                                  deterministic anneals of a graph with int8 weights and at most
+                                  4095 vertices (at most 1024 colours and 4M CSR entries) run in
+                                  one block instead: block barriers between classes, the packed
+                                  adjacency streamed by bulk copies */
+  ISING_ENGINE_DATAFLOW = 3,   /* one cooperative launch per anneal call without barriers: each
                                   neighbour read waits (bounded) until the neighbour carries the
                                   update the colour order requires; racy mode runs as PERSISTENT */
+  ISING_ENGINE_PERSISTENT_GRID = 4 /* PERSISTENT without the one-block form for small graphs */
 };
 
 /* ising_create flags. */

@@ -36,6 +36,7 @@ ISING_ENGINE_AUTO = 0
 ISING_ENGINE_PHASE = 1
 ISING_ENGINE_PERSISTENT = 2
 ISING_ENGINE_DATAFLOW = 3
+ISING_ENGINE_PERSISTENT_GRID = 4
 ISING_CREATE_WEIGHTS_I32 = 1
 ISING_STATIC_MAX_VERTICES = 1 << 24
 

@@ -26,6 +26,7 @@
 #include "host_graph.h"
 #include "philox.cuh"
 #include "sweep.cuh"
+#include "block.cuh"
 #include "graph_handle.h"
 
 using isingx::HostGraph;
@@ -189,6 +190,32 @@ __global__ void __launch_bounds__(kPersistBlock, 2)
   }
 }
 
+// Block engine (block.cuh): a graph of at most 4095 vertices, every sweep of
+// an anneal call in one block; deterministic pass, with Algorithm 1's flips
+// after each sweep when nflip0 > 0.
+__global__ void __launch_bounds__(isingx::kBlockThreads)
+    block_kernel(DevGraph d, isingx::BlockArgs ba, uint64_t t_begin, uint32_t sweeps, uint64_t T,
+                 uint64_t T0, uint32_t replica, isingx::PhiloxRounds rk, uint32_t nflip0,
+                 const int32_t* __restrict__ pos, unsigned* bitmap, int32_t* picked) {
+  extern __shared__ __align__(128) unsigned char block_mem[];
+  const isingx::BlockShared sh = isingx::block_shared(block_mem, ba);
+  isingx::block_setup(ba, sh);
+  __syncthreads();
+  unsigned seq = 0;
+  for (uint32_t k = 0; k < sweeps; ++k) {
+    const SweepArgs a = sweep_args(t_begin + k, T, T0, replica);
+    if (!isingx::block_sweep(d, ba, a, rk, sh, seq)) return;
+    if (nflip0 != 0u) {
+      // the sweep's updates are in global memory; warp 0 flips N_t spins
+      const uint32_t N = isingx::nflip_count(nflip0, T, t_begin + k);
+      if (threadIdx.x < 32 && N > 0u)
+        isingx::nflip_step(d, pos, bitmap, picked, N, static_cast<uint32_t>(t_begin + k), replica,
+                           rk, threadIdx.x & 31);
+      __syncthreads();
+    }
+  }
+}
+
 // Dataflow engine: one cooperative launch runs every sweep with no grid
 // barrier. Warp w takes items w, w + nwarps, ... of each colour class in
 // (sweep, class) order; every neighbour gather waits until the neighbour's
@@ -288,7 +315,8 @@ void free_device(ising_graph* g) {
                   g->d_slice_parts, g->d_energy,  g->d_flag,
                   g->d_tmp,     g->d_class_items, g->d_all_items, g->d_barrier,
                   g->d_class_begin, g->d_trace, g->d_nflip_bits, g->d_nflip_list,
-                  g->d_bias,    g->d_rowid};
+                  g->d_bias,    g->d_rowid, g->d_block_words, g->d_block_chunk_off,
+                  g->d_block_chunk_len, g->d_block_class_chunk};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -379,6 +407,30 @@ cudaError_t launch_persistent_t(ising_graph* g, const int32_t* phase_items, int 
   g->launches++;
   return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(kernel), dim3(grid),
                                      dim3(kPersistBlock), args, 0, g->stream);
+}
+
+cudaError_t launch_block(ising_graph* g, uint64_t t_begin, uint32_t sweeps, uint64_t T, uint64_t T0,
+                         uint32_t replica, const isingx::PhiloxRounds& rk, uint32_t nflip0) {
+  isingx::BlockArgs ba{};
+  ba.n = g->n;
+  ba.num_chunks = g->block_num_chunks;
+  ba.num_classes = g->num_colours;
+  ba.words = reinterpret_cast<const uint32_t*>(g->d_block_words);
+  ba.chunk_off = g->d_block_chunk_off;
+  ba.chunk_len = g->d_block_chunk_len;
+  ba.class_chunk = g->d_block_class_chunk;
+  ba.class_pos = g->d_class_begin;
+  const int smem = isingx::block_layout(ba.n, ba.num_chunks, ba.num_classes).total;
+  cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void*>(block_kernel),
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(g->d_barrier, 0, sizeof(BarrierState), g->stream);
+  if (e != cudaSuccess) return e;
+  g->launches++;
+  block_kernel<<<1, isingx::kBlockThreads, smem, g->stream>>>(
+      g->dev(), ba, t_begin, sweeps, T, T0, replica, rk, nflip0, g->d_pos, g->d_nflip_bits,
+      g->d_nflip_list);
+  return cudaGetLastError();
 }
 
 template <int PASS>
@@ -510,6 +562,15 @@ int ising_create(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, c
   }
   g->num_items = static_cast<int32_t>(plan.items.size());
   g->num_slots = static_cast<int32_t>(plan.split_parts.size());
+  isingx::BlockPlan block;
+  if (g->packed) {
+    try {
+      isingx::build_block_plan(hg, &block);
+    } catch (const std::bad_alloc&) {
+      delete g;
+      return ISING_ENOMEM;
+    }
+  }
 
   cudaError_t e = cudaSuccess;
   const size_t N = static_cast<size_t>(hg.n);
@@ -557,6 +618,17 @@ int ising_create(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, c
     if ((e = alloc_copy(&g->d_all_items, all_items, 2, g->stream)) != cudaSuccess) break;
     if ((e = alloc_copy(&g->d_class_begin, hg.class_begin.data(), hg.class_begin.size(),
                         g->stream)) != cudaSuccess) break;
+    if (block.ok) {
+      if ((e = alloc_copy(&g->d_block_words, block.words.data(), block.words.size(), g->stream)) != cudaSuccess) break;
+      if ((e = alloc_copy(&g->d_block_chunk_off, block.chunk_off.data(), block.chunk_off.size(),
+                          g->stream)) != cudaSuccess) break;
+      if ((e = alloc_copy(&g->d_block_chunk_len, block.chunk_len.data(), block.chunk_len.size(),
+                          g->stream)) != cudaSuccess) break;
+      if ((e = alloc_copy(&g->d_block_class_chunk, block.class_chunk.data(), block.class_chunk.size(),
+                          g->stream)) != cudaSuccess) break;
+      g->block_ok = true;
+      g->block_num_chunks = static_cast<int32_t>(block.chunk_off.size());
+    }
     if ((e = alloc_copy<unsigned>(&g->d_nflip_bits, nullptr, (N + 31) / 32, g->stream)) != cudaSuccess) break;
     if ((e = alloc_copy<int32_t>(&g->d_nflip_list, nullptr, N, g->stream)) != cudaSuccess) break;
     if ((e = alloc_copy<BarrierState>(&g->d_barrier, nullptr, 1, g->stream)) != cudaSuccess) break;
@@ -672,7 +744,12 @@ static int anneal_impl(ising_graph* g, const ising_schedule* sched, uint32_t swe
     ISING_CUDA(g, launch_flow(g, sched->t_begin, sweeps, sched->t_total, T0, sched->replica, par0, rk));
     return ISING_OK;
   }
-  if (engine == ISING_ENGINE_PERSISTENT || engine == ISING_ENGINE_DATAFLOW) {
+  if (engine == ISING_ENGINE_PERSISTENT && mode == ISING_MODE_DET && g->block_ok) {
+    ISING_CUDA(g, launch_block(g, sched->t_begin, sweeps, sched->t_total, T0, sched->replica, rk, n0));
+    return ISING_OK;
+  }
+  if (engine == ISING_ENGINE_PERSISTENT || engine == ISING_ENGINE_DATAFLOW ||
+      engine == ISING_ENGINE_PERSISTENT_GRID) {
     if (mode == ISING_MODE_RACY)
       ISING_CUDA(g, launch_persistent<kPassRacy>(g, g->d_class_items, g->num_colours,
                                                  sched->t_begin, sweeps, sched->t_total, T0,
@@ -832,7 +909,8 @@ int ising_launch_count(ising_graph* g, uint64_t* out) {
 int ising_set_engine(ising_graph* g, int engine) {
   if (g == nullptr) return ISING_EINVAL;
   if (engine != ISING_ENGINE_AUTO && engine != ISING_ENGINE_PHASE &&
-      engine != ISING_ENGINE_PERSISTENT && engine != ISING_ENGINE_DATAFLOW)
+      engine != ISING_ENGINE_PERSISTENT && engine != ISING_ENGINE_DATAFLOW &&
+      engine != ISING_ENGINE_PERSISTENT_GRID)
     return ISING_EINVAL;
   g->engine = engine;
   return ISING_OK;

@@ -54,6 +54,13 @@ struct ising_graph {
   int32_t* d_nflip_list = nullptr;         // N-flip: chosen vertices, n entries
   size_t trace_cap = 0;
   int32_t* d_all_items = nullptr;    // {0, num_items}: one phase over every item (energy)
+  // block engine of small graphs (host_graph.h, block.cuh)
+  bool block_ok = false;
+  int32_t block_num_chunks = 0;
+  int32_t* d_block_words = nullptr;
+  int32_t* d_block_chunk_off = nullptr;
+  int32_t* d_block_chunk_len = nullptr;
+  int32_t* d_block_class_chunk = nullptr;
   uint8_t* d_bias = nullptr;         // per-position flip bias (null: none)
   int32_t* d_rowid = nullptr;        // row of every CSR entry (built on first use)
   isingx::BarrierState* d_barrier = nullptr;

@@ -256,4 +256,30 @@ void build_work_plan(const HostGraph& g, int32_t target_warps, int32_t min_edges
   }
 }
 
+void build_block_plan(const HostGraph& g, BlockPlan* bp) {
+  *bp = BlockPlan();
+  const int32_t C = g.num_colours;
+  if (!g.fits_int8 || g.n > kBlockMaxVertices || C > kBlockMaxClasses) return;
+  bp->class_chunk.push_back(0);
+  for (int32_t c = 0; c < C; ++c) {
+    const int64_t start = (int64_t)bp->words.size();
+    for (int32_t v = g.class_begin[(size_t)c]; v < g.class_begin[(size_t)c + 1]; ++v)
+      for (int32_t k = g.row_ptr[(size_t)v]; k < g.row_ptr[(size_t)v + 1]; ++k)
+        bp->words.push_back((int32_t)(((uint32_t)v << 20) | ((uint32_t)g.col[(size_t)k] << 8) |
+                                      ((uint32_t)g.w[(size_t)k] & 0xffu)));
+    while (bp->words.size() % 4 != 0) bp->words.push_back((int32_t)((uint32_t)g.n << 20));
+    const int64_t end = (int64_t)bp->words.size();
+    for (int64_t a = start; a < end; a += kBlockChunkWords) {
+      bp->chunk_off.push_back((int32_t)a);
+      bp->chunk_len.push_back((int32_t)std::min<int64_t>(kBlockChunkWords, end - a));
+    }
+    bp->class_chunk.push_back((int32_t)bp->chunk_off.size());
+    if ((int32_t)bp->chunk_off.size() > kBlockMaxChunks) {
+      *bp = BlockPlan();
+      return;
+    }
+  }
+  bp->ok = true;
+}
+
 }  // namespace isingx

@@ -47,6 +47,31 @@ struct WorkPlan {
   int32_t max_class_items = 0;
 };
 
+// Small graphs are annealed by one block (block.cuh) with block barriers
+// between colour classes instead of grid barriers. Every CSR entry becomes a
+// word (row << 20) | (col << 8) | (w & 0xff) over 12-bit positions; the words
+// are grouped by the row's colour class, each class is padded to a multiple
+// of four words with (n << 20) (a zero term on a spare row), and the classes
+// are cut into chunks of at most kBlockChunkWords words that never cross a
+// class.
+constexpr int32_t kBlockMaxVertices = 4095;  // 12-bit positions
+constexpr int32_t kBlockChunkWords = 4096;
+constexpr int32_t kBlockMaxChunks = 1024;   // chunk table kept in shared memory
+constexpr int32_t kBlockMaxClasses = 1024;  // class tables kept in shared memory
+
+struct BlockPlan {
+  bool ok = false;
+  std::vector<int32_t> words;
+  std::vector<int32_t> chunk_off;    // per chunk: first word (multiple of 4)
+  std::vector<int32_t> chunk_len;    // per chunk: words (multiple of 4)
+  std::vector<int32_t> class_chunk;  // per class + 1: first chunk
+};
+
+// Fills bp (ok = true) for a graph with int8 weights, at most
+// kBlockMaxVertices vertices, kBlockMaxClasses classes and kBlockMaxChunks
+// chunks; otherwise leaves bp->ok = false.
+void build_block_plan(const HostGraph& g, BlockPlan* bp);
+
 // Returns 0, or a negative ISING_* status.
 int build_host_graph(int32_t n, int64_t m, const int32_t* src, const int32_t* dst,
                      const int32_t* w, HostGraph* out);

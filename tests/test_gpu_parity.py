@@ -12,7 +12,7 @@ import synth
 
 pytestmark = pytest.mark.gpu
 
-ENGINES = ["phase", "persistent", "dataflow"]
+ENGINES = ["phase", "persistent", "dataflow", "persistent_grid"]
 
 
 @pytest.fixture(scope="module")
@@ -27,7 +27,8 @@ def P():
 
 def engine_id(P, name):
     return {"phase": P.ISING_ENGINE_PHASE, "persistent": P.ISING_ENGINE_PERSISTENT,
-            "dataflow": P.ISING_ENGINE_DATAFLOW, "auto": P.ISING_ENGINE_AUTO}[name]
+            "dataflow": P.ISING_ENGINE_DATAFLOW, "auto": P.ISING_ENGINE_AUTO,
+            "persistent_grid": P.ISING_ENGINE_PERSISTENT_GRID}[name]
 
 
 def gpu_anneal(P, g, s0, *, seed, p0, T, t_begin=0, sweeps=None, flags=0, engine="auto",
@@ -313,3 +314,54 @@ def test_nflip_edge_cases(P):
         assert np.array_equal(P.ising_get_spins(h), whole)
         with pytest.raises(P.IsingError):
             P.ising_anneal(h, kind=P.ISING_SCHED_NFLIP, n0=g.n + 1, t_total=30, seed=8)
+
+
+# Graphs the persistent engine anneals in one block (int8 weights, at most
+# 4095 vertices): dense with repeated edges (29 classes), K_40 (40 classes of
+# one vertex), a torus (2 classes), a 4095-vertex random graph (the size
+# limit) and a single vertex. Deterministic sweeps, with and without a flip
+# bias and Algorithm 1's schedule, must match the grid-barrier form and the
+# oracle bit for bit.
+BLOCK_GRAPHS = {
+    "dense300": lambda: synth.random_small_graph(300, 0.3, 3, weights="int8", duplicates=100),
+    "complete40": lambda: synth.complete_graph(40, 1, weights="pm1"),
+    "torus32": lambda: synth.torus_graph(32, 1, weights="pm1"),
+    "n4095": lambda: synth.random_small_graph(4095, 0.01, 8, weights="int8"),
+    "single": lambda: synth.Graph(1, np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0, np.int32)),
+}
+
+
+@pytest.mark.parametrize("name", sorted(BLOCK_GRAPHS))
+@pytest.mark.parametrize("biased", [False, True])
+def test_block_engine_matches_grid_engine_and_oracle(P, name, biased):
+    g = BLOCK_GRAPHS[name]()
+    q = np.random.default_rng(9).integers(0, 256, size=g.n).astype(np.uint8) if biased else None
+    T = 40
+    out = {}
+    for engine in ("persistent", "persistent_grid"):
+        with P.ising_create(g.n, g.src, g.dst, g.w) as h:
+            P.ising_set_engine(h, engine_id(P, engine))
+            P.ising_init_random(h, 2)
+            s0 = P.ising_get_spins(h)
+            if biased:
+                P.ising_set_flip_bias(h, q)
+            P.ising_anneal(h, p0=0.2, t_total=T, seed=5, sweeps=17)
+            P.ising_anneal(h, p0=0.2, t_total=T, seed=5, t_begin=17)
+            out[engine] = (P.ising_get_spins(h), P.ising_cut(h))
+    assert np.array_equal(out["persistent"][0], out["persistent_grid"][0])
+    want = oracle.anneal(g.n, g.src, g.dst, g.w, s0, seed=5, p0=0.2, T=T, bias=q)
+    assert np.array_equal(out["persistent"][0], want)
+    assert out["persistent"][1] == oracle.energy_cut(g.n, g.src, g.dst, g.w, want)[2]
+
+
+@pytest.mark.parametrize("name", ["dense300", "n4095"])
+def test_block_engine_nflip_schedule(P, name):
+    g = BLOCK_GRAPHS[name]()
+    n0, T = min(200, g.n), 60
+    with P.ising_create(g.n, g.src, g.dst, g.w) as h:
+        P.ising_init_random(h, 6)
+        s0 = P.ising_get_spins(h)
+        P.ising_anneal(h, t_total=T, seed=7, kind=P.ISING_SCHED_NFLIP, n0=n0)
+        got = P.ising_get_spins(h)
+    want = oracle.anneal_nflip(g.n, g.src, g.dst, g.w, s0, seed=7, n0=n0, T=T)
+    assert np.array_equal(got, want)
