@@ -39,7 +39,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="torus1024",
-                    choices=["torus1024", "zipf1m", "er800", "batched"])
+                    choices=["torus1024", "zipf1m", "er800", "batched", "warmstart"])
     ap.add_argument("--engine", default="auto", choices=["auto", "phase", "persistent", "dataflow"])
     ap.add_argument("--mode", default="det", choices=["det", "racy"],
                     help="deterministic colour phases (bit-exact) or the racy pass")
@@ -362,6 +362,146 @@ def run_batched(args, world, rank, P, torch, dist):
     print(json.dumps(line), flush=True)
 
 
+def run_warmstart(args, world, rank, P, torch, dist):
+    """The learned warm start against the plain annealer on held-out graphs.
+
+    Untimed set-up: the network is trained on the GPU from annealer labels
+    (input: spins after a 100-sweep anneal; label: spins after a further
+    200-sweep anneal at p0 = 0.01), and the long-run best cut of every test
+    graph is the best of 4 replicas x 10000 sweeps. Timed (CUDA events on the
+    library's stream, from random spins): plain anneals of T sweeps, and the
+    learned form -- a short anneal, then rounds of network warm start
+    followed by 10 greedy sweeps. Reported: the least time at which each form
+    reaches 99 % of the best cut."""
+    import synth
+    train, test, spec = synth.warmstart_workload()
+    stream = torch.cuda.Stream()
+    seed0 = 1000 + 7919 * rank
+    t_setup = time.perf_counter()
+    # training data from the annealer itself
+    examples = []
+    for k, g in enumerate(train):
+        h = P.ising_create(g.n, g.src, g.dst, g.w, stream=stream)
+        P.ising_init_random(h, seed0 + k)
+        P.ising_anneal(h, p0=0.1, t_total=100, seed=seed0 + k, stream=stream)
+        snap = torch.empty(g.n, dtype=torch.int8, device="cuda")
+        P.ising_get_spins(h, snap)
+        P.ising_anneal(h, p0=0.01, t_total=200, seed=seed0 + 5000 + k, stream=stream)
+        lab = torch.empty(g.n, dtype=torch.int8, device="cuda")
+        P.ising_get_spins(h, lab)
+        examples.append((h, snap, lab))
+    net = P.ising_gnn_create(synth.gnn_init_params(spec["gen_seed"]))
+    steps = 4000
+    torch.cuda.synchronize()
+    t_train = time.perf_counter()
+    losses = []
+    for it in range(steps):
+        h, snap, lab = examples[it % len(examples)]
+        P.ising_set_spins(h, snap)
+        loss = P.ising_gnn_train_step(net, h, lab, lr=2e-3 if it < 3 * steps // 4 else 5e-4,
+                                      want_loss=(it % 500 == 0 or it == steps - 1))
+        if loss is not None:
+            losses.append(round(loss, 4))
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t_train
+    for h, _, _ in examples:
+        h.close()
+
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def timed(fn):
+        ev[0].record(stream)
+        fn()
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        return ev[0].elapsed_time(ev[1]) / 1e3
+
+    results = []
+    for gi, g in enumerate(test):
+        h = P.ising_create(g.n, g.src, g.dst, g.w, stream=stream)
+        best = -(1 << 62)
+        for r in range(4):
+            P.ising_init_random(h, 90000 + r)
+            P.ising_anneal(h, p0=0.1, t_total=10000, seed=90000 + r, stream=stream)
+            best = max(best, P.ising_cut(h))
+        best_plain = best
+        # untimed: the network's workspace for this size and the graph's row table
+        P.ising_gnn_forward(net, h, torch.empty(g.n, dtype=torch.float32, device="cuda"))
+        torch.cuda.synchronize()
+        plain = []
+        for T in (100, 200, 400, 800, 1600, 3200, 6400, 12800):
+            P.ising_init_random(h, 7 + gi)
+            sec = timed(lambda: P.ising_anneal(h, p0=0.1, t_total=T, seed=7 + gi, stream=stream))
+            plain.append({"sweeps": T, "s": sec, "cut": P.ising_cut(h)})
+        learned = []
+        for Ta in (25, 50, 100):
+            for rounds in (1, 2, 4, 8):
+                P.ising_init_random(h, 7 + gi)
+
+                def run():
+                    P.ising_anneal(h, p0=0.1, t_total=Ta, seed=7 + gi, stream=stream)
+                    for r in range(rounds):
+                        P.ising_gnn_warm_start(net, h, set_bias=False)
+                        P.ising_anneal(h, p0=0.0, t_total=10, seed=11 + r, stream=stream)
+                sec = timed(run)
+                learned.append({"prefix": Ta, "rounds": rounds, "s": sec, "cut": P.ising_cut(h)})
+        # one forward pass alone
+        fwd = timed(lambda: P.ising_gnn_forward(net, h, torch.empty(g.n, dtype=torch.float32,
+                                                                     device="cuda")))
+        h.close()
+        # 99 % of the best cut any run found (the learned form can beat the
+        # plain annealer's long-run best)
+        best = max([best_plain] + [c["cut"] for c in plain + learned])
+        target = 0.99 * best
+
+        def first(curve, tgt):
+            ok = [c["s"] for c in curve if c["cut"] >= tgt]
+            return min(ok) if ok else None
+        target_plain = 0.99 * best_plain
+        results.append({"n": g.n, "m": g.m, "best": best, "best_plain_long_run": best_plain,
+                        "plain": plain, "learned": learned,
+                        "plain_s_to_99": first(plain, target), "learned_s_to_99": first(learned, target),
+                        "plain_s_to_99_of_plain_best": first(plain, target_plain),
+                        "learned_s_to_99_of_plain_best": first(learned, target_plain),
+                        "plain_longest_s": max(c["s"] for c in plain),
+                        "forward_ms": fwd * 1e3})
+    if rank != 0:
+        return
+    def mean_or_none(key):
+        xs = [r[key] for r in results]
+        return None if any(x is None for x in xs) else sum(xs) / len(xs)
+    value = mean_or_none("learned_s_to_99")
+    plain_value = mean_or_none("plain_s_to_99")
+    # where the plain annealer never got there, its longest timed run bounds
+    # its time from below
+    plain_bound = sum(r["plain_s_to_99"] if r["plain_s_to_99"] is not None else r["plain_longest_s"]
+                      for r in results) / len(results)
+    line = {
+        "metric": "time_to_cut_99pct_of_best", "value": value, "unit": "s", "n_gpus": world,
+        "steps": len(test), "warmup": 0, "ms_per_step": None if value is None else value * 1e3,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "int8+bf16",
+        "data": "synthetic",
+        "config": {"workload": "warmstart", "train_graphs": len(train),
+                   "train_vertices": sum(g.n for g in train), "train_steps": steps,
+                   "test_graphs": len(test), "test_n": spec["test_n"],
+                   "best_of": "max(best of 4 plain replicas x 10000 sweeps at p0 0.1, "
+                              "every timed run)",
+                   "learned_form": "anneal(prefix sweeps, p0 0.1) + rounds x (network warm start "
+                                   "+ 10 greedy sweeps)",
+                   "parallelism": f"replicas{world}"},
+        "plain_value": plain_value,
+        "plain_value_lower_bound": plain_bound,
+        "speedup_vs_plain": (None if value is None or plain_value is None else plain_value / value),
+        "speedup_vs_plain_lower_bound": None if value is None else plain_bound / value,
+        "of_plain_long_run_best": {"learned_s": mean_or_none("learned_s_to_99_of_plain_best"),
+                                   "plain_s": mean_or_none("plain_s_to_99_of_plain_best")},
+        "train_s": train_s, "setup_s": time.perf_counter() - t_setup, "train_loss": losses,
+        "results": results, "roofline": None, "cpu_baseline": None, "e2e": None,
+        "gpu_launches": None, "clocks": None,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     world, rank, local = dist_env()
@@ -385,6 +525,13 @@ def main():
     if world > 1:
         dist.barrier()
     import paper_1807_10750_gb300 as P
+
+    if args.workload == "warmstart":
+        run_warmstart(args, world, rank, P, torch, dist)
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
 
     if args.workload == "batched":
         run_batched(args, world, rank, P, torch, dist)

@@ -15,6 +15,8 @@ from .graphs import (  # noqa: F401
     batched_er_graphs,
     batched_workload,
     BATCHED,
+    WARMSTART,
+    warmstart_workload,
     complete_graph,
     cycle_graph,
     er_graph,

@@ -240,3 +240,30 @@ def workload(name: str, **override) -> tuple[Graph, dict]:
         raise ValueError(gen)
     sched = {k: spec[k] for k in ("p0", "sweeps", "seed")}
     return g, sched
+
+
+# The learned warm-start workload: training graphs (Erdos-Renyi with mean
+# degree 10 and power-law graphs, alternating; n log-uniform in
+# [nmin, nmax]; weights uniform in [-8, 8] without 0) and held-out
+# 100k-vertex power-law test graphs.
+WARMSTART = dict(train_count=64, nmin=1000, nmax=30000, gen_seed=5, test_count=2, test_n=100000,
+                 test_seed=4242, alpha=2.1, dmin=4, dmax=10000)
+
+
+def warmstart_workload(**override):
+    spec = dict(WARMSTART)
+    spec.update(override)
+    rng = np.random.default_rng(spec["gen_seed"])
+    train = []
+    for k in range(spec["train_count"]):
+        n = int(np.clip(np.rint(np.exp(rng.uniform(math.log(spec["nmin"]), math.log(spec["nmax"])))),
+                        spec["nmin"], spec["nmax"]))
+        s = int(rng.integers(0, 2 ** 31 - 1))
+        if k % 2 == 0:
+            train.append(zipf_config_graph(n, spec["alpha"], spec["dmin"], min(spec["dmax"], n // 4), s,
+                                           weights="int8"))
+        else:
+            train.append(er_graph(n, min(1.0, 10.0 / (n - 1)), s, weights="int8"))
+    test = [zipf_config_graph(spec["test_n"], spec["alpha"], spec["dmin"], spec["dmax"],
+                              spec["test_seed"] + k, weights="int8") for k in range(spec["test_count"])]
+    return train, test, spec
