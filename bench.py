@@ -39,7 +39,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="torus1024",
-                    choices=["torus1024", "zipf1m", "er800", "batched", "warmstart"])
+                    choices=["torus1024", "zipf1m", "er800", "batched", "warmstart", "gnn"])
     ap.add_argument("--engine", default="auto", choices=["auto", "phase", "persistent", "dataflow"])
     ap.add_argument("--mode", default="det", choices=["det", "racy"],
                     help="deterministic colour phases (bit-exact) or the racy pass")
@@ -75,10 +75,10 @@ def algorithmic_bytes_per_sweep(n: int, nnz: int, entry_bytes: int) -> int:
 # the sweeps. The entry holds only while the kernel sources hash to `sources`:
 # once they change the counters are stale and traffic is reported as null.
 NCU_TRAFFIC = {
-    "torus1024": {"fixed": 22.3809e6, "per_sweep": 0.0, "kernel": "persistent_kernel",
+    "torus1024": {"fixed": 22.3642e6, "per_sweep": 0.0, "kernel": "persistent_kernel",
                   "files": ("sweep.cuh", "anneal.cu", "philox.cuh"),
-                  "sources": "aace815c91543ed2",
-                  "how": "ncu 20- and 60-sweep captures: 22.383 MB and 22.379 MB, so the "
+                  "sources": "cad09791196b872b",
+                  "how": "ncu 20- and 60-sweep captures: 22.361 MB and 22.367 MB, so the "
                          "working set is read once and then stays in L2"},
     "batched": {"fixed": 0.0, "per_sweep": 2.94971e9 / 20, "kernel": "batch_anneal_kernel",
                 "files": ("batch.cu", "philox.cuh"),
@@ -502,6 +502,88 @@ def run_warmstart(args, world, rank, P, torch, dist):
     print(json.dumps(line), flush=True)
 
 
+def gnn_forward_bytes(n: int, nnz: int) -> int:
+    """Compulsory bytes of one forward pass of the warm-start network, by
+    kernel: row sums (CSR word, row id, neighbour spin per entry; an int4 per
+    row), features (sums, spin in; 8 bf16 features and c out), three
+    aggregations (CSR word, row id, c_j and the neighbour's feature row per
+    entry; one fp32 row out per vertex), three dense layers ([h, a] in, h'
+    out) and the head (h3 in, z out)."""
+    rowsum = nnz * 9 + n * 16
+    feats = n * (16 + 1 + 16 + 4)
+    agg8 = nnz * (12 + 16) + n * 32
+    agg64 = nnz * (12 + 128) + n * 256
+    mlp8 = n * (16 + 32 + 128)
+    mlp64 = n * (128 + 256 + 128)
+    head = n * (128 + 4)
+    return rowsum + feats + agg8 + 2 * agg64 + mlp8 + 2 * mlp64 + head
+
+
+def run_gnn(args, world, rank, P, torch, dist):
+    """Throughput of the warm-start network's kernels on a held-out-sized
+    graph (100k-vertex power-law graph, random parameters): forward passes
+    and training steps (forward, backward, Adam) per second."""
+    import synth
+    _, test, spec = synth.warmstart_workload(train_count=0, test_count=1)
+    g = test[0]
+    stream = torch.cuda.Stream()
+    h = P.ising_create(g.n, g.src, g.dst, g.w, stream=stream)
+    P.ising_init_random(h, 1)
+    net = P.ising_gnn_create(synth.gnn_init_params(1))
+    z = torch.empty(g.n, dtype=torch.float32, device="cuda")
+    y = torch.from_numpy(np.where(np.random.default_rng(2).random(g.n) < 0.5, 1, -1).astype(np.int8)).cuda()
+    nnz = 2 * P.ising_num_edges(h)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    for _ in range(args.warmup):
+        P.ising_gnn_forward(net, h, z)
+        P.ising_gnn_train_step(net, h, y, lr=0.0)
+    torch.cuda.synchronize()
+    fwd, trn = [], []
+    l0 = P.ising_gnn_launch_count(net)
+    with ClockSampler(torch.cuda.current_device()) as clocks:
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            ev[0].record(stream)
+            P.ising_gnn_forward(net, h, z)
+            ev[1].record(stream)
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            ev[2].record(stream)
+            P.ising_gnn_train_step(net, h, y, lr=0.0)
+            ev[3].record(stream)
+            torch.cuda.synchronize()
+            fwd.append(ev[0].elapsed_time(ev[1]))
+            trn.append(ev[2].elapsed_time(ev[3]))
+    launches = P.ising_gnn_launch_count(net) - l0
+    fwd_ms = statistics.median(fwd)
+    trn_ms = statistics.median(trn)
+    B = gnn_forward_bytes(g.n, nnz)
+    achieved = B / (fwd_ms / 1e3) / 1e9
+    peak, peak_kind = measured_peaks()
+    if rank != 0:
+        return
+    line = {
+        "metric": "gnn_forward_vertices_per_s", "value": g.n / (fwd_ms / 1e3) * world,
+        "unit": "vertices/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": fwd_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": "gnn", "n": g.n, "nnz": nnz, "layers": 3, "hidden": 64,
+                   "parallelism": f"replicas{world}",
+                   "l2": "512 MiB buffer zeroed before every timed pass (outside the events)"},
+        "train_step_ms": trn_ms, "train_vertices_per_s": g.n / (trn_ms / 1e3) * world,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                     "bytes_per_forward": B, "kernel": "all kernels of one forward pass"},
+        "cpu_baseline": None, "e2e": None,
+        "gpu_launches": int(launches), "clocks": clocks.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    h.close()
+    net.close()
+
+
 def main():
     args = parse_args()
     world, rank, local = dist_env()
@@ -525,6 +607,13 @@ def main():
     if world > 1:
         dist.barrier()
     import paper_1807_10750_gb300 as P
+
+    if args.workload == "gnn":
+        run_gnn(args, world, rank, P, torch, dist)
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
 
     if args.workload == "warmstart":
         run_warmstart(args, world, rank, P, torch, dist)

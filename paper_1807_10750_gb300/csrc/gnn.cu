@@ -752,7 +752,8 @@ int run_forward(ising_gnn* net, ising_graph* g, bool with_labels) {
                                                              reinterpret_cast<uint4*>(net->d_x), net->d_c);
   net->launches++;
   GNN_CUDA(net, cudaGetLastError());
-  const int mlp_grid = grid_of((n + kTileRows - 1) / kTileRows, 1, sms * 4);
+  // about 36 KB of shared memory per block: six blocks fit on an SM
+  const int mlp_grid = grid_of((n + kTileRows - 1) / kTileRows, 1, sms * 6);
   // layer 0
   GNN_CUDA(net, cudaMemsetAsync(net->d_a0, 0, sizeof(float) * static_cast<size_t>(n) * kF, st));
   if (nnz > 0) {
