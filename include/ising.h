@@ -399,6 +399,20 @@ int ising_gnn_launch_count(ising_gnn* net, uint64_t* out);
 /* ising_gnn_destroy -- free the network (NULL is ignored). */
 void ising_gnn_destroy(ising_gnn* net);
 
+/* Failure-detection test hook. Every device-side wait of the anneal kernels
+ * is bounded (2 s by default); a wait that runs out records an error, the
+ * kernel returns, and the next synchronising call reports ISING_ETIMEOUT and
+ * latches it in the handle (create a new handle to continue; the CUDA
+ * context stays usable). Kinds:
+ *   ISING_FAULT_SKIP_ARRIVAL  persistent grid engine: block 0 skips its first
+ *                             grid-barrier arrival, so every block's wait runs out;
+ *   ISING_FAULT_SHORT_COPY    block engine: the first chunk's barrier expects 16
+ *                             bytes that never arrive, so its wait runs out.
+ * wait_budget_ns bounds every wait of later anneal calls (0: the default; at
+ * most 60 s). No fault is a GPU fault: nothing traps or hangs. */
+enum { ISING_FAULT_NONE = 0, ISING_FAULT_SKIP_ARRIVAL = 1, ISING_FAULT_SHORT_COPY = 2 };
+int ising_debug_fault(ising_graph* g, int kind, uint64_t wait_budget_ns);
+
 /* ising_launch_count -- number of CUDA kernels this handle has launched since
  * ising_create (a diagnostic for benchmarks). */
 int ising_launch_count(ising_graph* g, uint64_t* out);

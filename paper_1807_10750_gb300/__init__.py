@@ -51,8 +51,11 @@ EXPORTS = (
     "ising_batch_info", "ising_batch_destroy", "ising_anneal_trace",
     "ising_set_flip_bias", "ising_get_flip_bias", "ising_gnn_create", "ising_gnn_set_params",
     "ising_gnn_get_params", "ising_gnn_forward", "ising_gnn_gradients", "ising_gnn_train_step",
-    "ising_gnn_warm_start", "ising_gnn_launch_count", "ising_gnn_destroy",
+    "ising_gnn_warm_start", "ising_gnn_launch_count", "ising_gnn_destroy", "ising_debug_fault",
 )
+ISING_FAULT_NONE = 0
+ISING_FAULT_SKIP_ARRIVAL = 1
+ISING_FAULT_SHORT_COPY = 2
 ISING_GNN_NUM_PARAMS = 17665
 
 
@@ -129,6 +132,7 @@ def lib():
         L.ising_gnn_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
         L.ising_gnn_destroy.argtypes = [vp]
         L.ising_gnn_destroy.restype = None
+        L.ising_debug_fault.argtypes = [vp, ctypes.c_int, ctypes.c_uint64]
         L.ising_strerror.argtypes = [ctypes.c_int]
         L.ising_strerror.restype = ctypes.c_char_p
         for name in EXPORTS:
@@ -322,6 +326,11 @@ def ising_plan_colouring(n: int, src, dst, w):
                                       out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                                       ctypes.byref(C)), "ising_plan_colouring")
     return C.value, out
+
+
+def ising_debug_fault(g: IsingGraph, kind: int, wait_budget_ns: int = 0) -> None:
+    """Failure-detection test hook (see include/ising.h)."""
+    _check(lib().ising_debug_fault(g.ptr, kind, wait_budget_ns), "ising_debug_fault")
 
 
 def ising_set_engine(g: IsingGraph, engine: int) -> None:

@@ -148,6 +148,8 @@ __global__ void __launch_bounds__(kPersistBlock, 2)
   if (have) isingx::stage_item<PACKED>(d, d.items[ib], a, rk, lane, st);
   // the warp's first item of the following class, loaded one class ahead
   WorkItem next = first_item<PASS>(d, phase_items, num_phases > 1 ? 1 : 0, warp, nwarps);
+  // failure-detection tests: this block may skip its first barrier arrival
+  bool skip_arrival = bs->skip_block == static_cast<int>(blockIdx.x) + 1;
   for (;;) {
     if (have) {
       isingx::finish_item<PACKED, PASS>(d, st, a, rk, lane, unused);
@@ -160,7 +162,8 @@ __global__ void __launch_bounds__(kPersistBlock, 2)
     if (nflip0 != 0u && sweep_end) {
       // Algorithm 1: once every update of the sweep is visible, one warp flips
       // the sweep's N random spins; the barrier below publishes them.
-      isingx::barrier_arrive(bs);
+      isingx::barrier_arrive(bs, skip_arrival);
+      skip_arrival = false;
       target += gridDim.x;
       if (!isingx::barrier_wait(bs, target)) return;
       const uint32_t N = isingx::nflip_count(nflip0, T, t_begin + k);
@@ -170,7 +173,10 @@ __global__ void __launch_bounds__(kPersistBlock, 2)
     }
     if (sweep_end && k + 1 == sweeps) break;
     const bool sync = (PASS != kPassRacy) || sweep_end;
-    if (sync) isingx::barrier_arrive(bs);
+    if (sync) {
+      isingx::barrier_arrive(bs, skip_arrival);
+      skip_arrival = false;
+    }
     if (sweep_end) {
       c = 0;
       ++k;
@@ -370,6 +376,15 @@ cudaError_t launch_items(ising_graph* g, const int32_t* phase_items, const int32
   return cudaGetLastError();
 }
 
+// The barrier state at the start of a launch: zero counts and errors, the
+// wait bound and the injected fault of ising_debug_fault.
+cudaError_t barrier_init(ising_graph* g) {
+  BarrierState init{};
+  init.skip_block = g->fault_kind == ISING_FAULT_SKIP_ARRIVAL ? 1 : 0;
+  init.budget_ns = static_cast<long long>(g->wait_budget_ns);
+  return cudaMemcpyAsync(g->d_barrier, &init, sizeof(init), cudaMemcpyHostToDevice, g->stream);
+}
+
 // A persistent launch that timed out leaves error != 0 in the barrier state;
 // synchronising calls report it (and latch it).
 int check_device_error(ising_graph* g) {
@@ -395,7 +410,7 @@ cudaError_t launch_persistent_t(ising_graph* g, const int32_t* phase_items, int 
   per_sm = std::min(per_sm, 2);
   const int grid = per_sm * g->num_sms;
   g->persist_grid = grid;
-  e = cudaMemsetAsync(g->d_barrier, 0, sizeof(BarrierState), g->stream);
+  e = barrier_init(g);
   if (e != cudaSuccess) return e;
   DevGraph d = g->dev();
   BarrierState* bs = g->d_barrier;
@@ -420,11 +435,13 @@ cudaError_t launch_block(ising_graph* g, uint64_t t_begin, uint32_t sweeps, uint
   ba.chunk_len = g->d_block_chunk_len;
   ba.class_chunk = g->d_block_class_chunk;
   ba.class_pos = g->d_class_begin;
+  ba.wait_ns = static_cast<long long>(g->wait_budget_ns);
+  ba.short_copy = g->fault_kind == ISING_FAULT_SHORT_COPY ? 1 : 0;
   const int smem = isingx::block_layout(ba.n, ba.num_chunks, ba.num_classes).total;
   cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void*>(block_kernel),
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(g->d_barrier, 0, sizeof(BarrierState), g->stream);
+  e = barrier_init(g);
   if (e != cudaSuccess) return e;
   g->launches++;
   block_kernel<<<1, isingx::kBlockThreads, smem, g->stream>>>(
@@ -455,7 +472,7 @@ cudaError_t launch_flow_t(ising_graph* g, uint64_t t_begin, uint32_t sweeps, uin
   if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
   per_sm = std::min(per_sm, 2);
   const int grid = per_sm * g->num_sms;
-  e = cudaMemsetAsync(g->d_barrier, 0, sizeof(BarrierState), g->stream);
+  e = barrier_init(g);
   if (e != cudaSuccess) return e;
   DevGraph d = g->dev();
   const int32_t* phase_items = g->d_class_items;
@@ -903,6 +920,16 @@ int ising_plan_colouring(int32_t n, int64_t m, const int32_t* src, const int32_t
 int ising_launch_count(ising_graph* g, uint64_t* out) {
   if (g == nullptr || out == nullptr) return ISING_EINVAL;
   *out = g->launches;
+  return ISING_OK;
+}
+
+int ising_debug_fault(ising_graph* g, int kind, uint64_t wait_budget_ns) {
+  if (g == nullptr) return ISING_EINVAL;
+  if (kind != ISING_FAULT_NONE && kind != ISING_FAULT_SKIP_ARRIVAL && kind != ISING_FAULT_SHORT_COPY)
+    return ISING_EINVAL;
+  if (wait_budget_ns > 60000000000ull) return ISING_EINVAL;
+  g->fault_kind = kind;
+  g->wait_budget_ns = wait_budget_ns;
   return ISING_OK;
 }
 

@@ -30,6 +30,8 @@ struct BlockArgs {
   const int32_t* chunk_len;     // per chunk: words
   const int32_t* class_chunk;   // per class + 1
   const int32_t* class_pos;     // per class + 1: first position
+  long long wait_ns;            // bound of every wait (0: kBlockWaitNs)
+  int short_copy;               // failure-detection tests: the first chunk expects 16 more bytes
 };
 
 constexpr int kBlockThreads = 512;
@@ -84,9 +86,10 @@ __device__ __forceinline__ void fence_mbar_init() {
 // One thread: expect `bytes` on bar, then copy [src, src + bytes) to dst.
 // dst, src and bytes are multiples of 16.
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes,
-                                          unsigned long long* bar) {
+                                          unsigned long long* bar, unsigned extra = 0) {
+  // extra: bytes expected beyond the copy (failure-detection tests only)
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
+               "r"(bytes + extra)
                : "memory");
   asm volatile(
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -107,8 +110,10 @@ __device__ __forceinline__ bool mbar_test(unsigned long long* bar, unsigned pari
 
 constexpr long long kBlockWaitNs = 2000000000LL;  // 2 s
 
-// Waits until phase `parity` of bar completes; false after kBlockWaitNs.
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+// Waits until phase `parity` of bar completes; false after `budget` ns
+// (kBlockWaitNs if budget <= 0).
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, long long budget) {
+  if (budget <= 0) budget = kBlockWaitNs;
   long long t0 = 0;
   for (unsigned it = 0;; ++it) {
     if (mbar_test(bar, parity)) return true;
@@ -117,7 +122,7 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
       asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
       if (it == 0u)
         t0 = now;
-      else if (now - t0 > kBlockWaitNs)
+      else if (now - t0 > budget)
         return false;
     }
   }
@@ -172,7 +177,7 @@ __device__ __forceinline__ void block_issue(const BlockArgs& ba, const BlockShar
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   const int2 c = sh.chunk[q];
   bulk_load(sh.buf + b * kBlockChunkWords, ba.words + c.x, 4u * static_cast<unsigned>(c.y),
-            sh.bar + b);
+            sh.bar + b, (ba.short_copy && sq == 0u) ? 16u : 0u);
 }
 
 // One sweep a.t of every class. seq numbers chunks over the whole launch:
@@ -211,7 +216,7 @@ __device__ __forceinline__ bool block_sweep(const DevGraph& d, const BlockArgs& 
       const unsigned sq = seq0 + q;
       if (tid == 0) {
         if (q + kBlockRing - 1 < nch) block_issue(ba, sh, q + kBlockRing - 1, sq + kBlockRing - 1);
-        if (!mbar_wait(sh.bar + sq % kBlockRing, (sq / kBlockRing) & 1u)) {
+        if (!mbar_wait(sh.bar + sq % kBlockRing, (sq / kBlockRing) & 1u, ba.wait_ns)) {
           block_ok = 0;
           if (d.error) atomicExch(d.error, 1);
         }
@@ -291,7 +296,7 @@ __device__ __forceinline__ bool block_sweep(const DevGraph& d, const BlockArgs& 
     const int last = q + kBlockRing < nch ? q + kBlockRing : nch;
     for (int j = q; j < last; ++j) {
       const unsigned sj = seq0 + j;
-      mbar_wait(sh.bar + sj % kBlockRing, (sj / kBlockRing) & 1u);
+      mbar_wait(sh.bar + sj % kBlockRing, (sj / kBlockRing) & 1u, ba.wait_ns);
     }
   }
   __syncthreads();

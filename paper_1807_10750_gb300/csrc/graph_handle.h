@@ -16,6 +16,8 @@ struct ising_graph {
   cudaStream_t stream = nullptr;
   int status = ISING_OK;
   int engine = ISING_ENGINE_AUTO;
+  int fault_kind = ISING_FAULT_NONE;  // ising_debug_fault
+  uint64_t wait_budget_ns = 0;        // 0: the kernels' default bound
   int num_sms = 1;
   uint64_t launches = 0;
 

@@ -483,8 +483,10 @@ constexpr long long kBarrierBudgetNs = 2000000000LL;  // 2 s
 
 struct BarrierState {
   unsigned int count;
-  int error;  // 0 ok, 1 a wait timed out
-  int pad[2];
+  int error;            // 0 ok, 1 a wait timed out
+  int skip_block;       // failure-detection tests: block skip_block - 1 skips its first arrival
+  int pad;
+  long long budget_ns;  // bound of every wait (0: kBarrierBudgetNs)
 };
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
@@ -503,9 +505,9 @@ __device__ __forceinline__ long long global_ns() {
   return t;
 }
 
-__device__ __forceinline__ void barrier_arrive(BarrierState* bs) {
+__device__ __forceinline__ void barrier_arrive(BarrierState* bs, bool skip = false) {
   __syncthreads();
-  if (threadIdx.x == 0)
+  if (threadIdx.x == 0 && !skip)
     asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&bs->count) : "memory");
 }
 
@@ -514,6 +516,7 @@ __device__ __forceinline__ bool barrier_wait(BarrierState* bs, unsigned target) 
   if (threadIdx.x == 0) {
     int ok = 1;
     long long t0 = 0;
+    const long long budget = bs->budget_ns > 0 ? bs->budget_ns : kBarrierBudgetNs;
     for (unsigned it = 0; static_cast<int>(ld_acquire_u32(&bs->count) - target) < 0; ++it) {
       if ((it & 63u) == 0u) {
         if (it == 0u) t0 = global_ns();
@@ -521,7 +524,7 @@ __device__ __forceinline__ bool barrier_wait(BarrierState* bs, unsigned target) 
           ok = 0;
           break;
         }
-        if (global_ns() - t0 > kBarrierBudgetNs) {
+        if (global_ns() - t0 > budget) {
           atomicExch(&bs->error, 1);
           ok = 0;
           break;
