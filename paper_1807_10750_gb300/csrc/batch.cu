@@ -39,7 +39,7 @@ struct BatchGraph {
   int32_t vtx_base;    // first vertex in the concatenated vertex arrays
   int32_t row_base;    // first entry of this instance's row_ptr (n + 1 entries)
   int32_t class_base;  // first entry of this instance's class bounds (num_classes + 1)
-  int32_t pad;
+  int32_t byte_lanes;  // 1: every row's sum of |w| is at most 255 (byte-lane sums apply)
 };
 
 struct BatchDev {
@@ -100,13 +100,42 @@ __global__ void __launch_bounds__(BLOCK)
           const int e1 = __ldg(rp + v + 1);
           int wsum = 0;
           int acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-          for (int e = __ldg(rp + v); e < e1; ++e) {
-            const int word = __ldg(d.adj + e);
-            const int wgt = (word << 24) >> 24;
-            const int b = sp[static_cast<unsigned>(word) >> 8];
-            wsum += wgt;
+          if (G.byte_lanes) {
+            // the 8 replica bits of a neighbour spread into 8 byte lanes (4 per
+            // word: x * 0x00204081 puts bit k of a nibble at bit 8k), weighted
+            // by |w| into a positive and a negative accumulator; no lane can
+            // exceed 255 because the row's sum of |w| does not
+            uint32_t plo = 0, phi = 0, nlo = 0, nhi = 0;
+            for (int e = __ldg(rp + v); e < e1; ++e) {
+              const int word = __ldg(d.adj + e);
+              const int wgt = (word << 24) >> 24;
+              const uint32_t b = sp[static_cast<unsigned>(word) >> 8];
+              wsum += wgt;
+              const uint32_t lo = ((b & 0xfu) * 0x00204081u) & 0x01010101u;
+              const uint32_t hi = ((b >> 4) * 0x00204081u) & 0x01010101u;
+              const uint32_t mag = static_cast<uint32_t>(wgt < 0 ? -wgt : wgt);
+              if (wgt > 0) {
+                plo += lo * mag;
+                phi += hi * mag;
+              } else {
+                nlo += lo * mag;
+                nhi += hi * mag;
+              }
+            }
 #pragma unroll
-            for (int r = 0; r < 8; ++r) acc[r] += (b >> r) & 1 ? wgt : 0;
+            for (int r = 0; r < 4; ++r) {
+              acc[r] = static_cast<int>((plo >> (8 * r)) & 0xffu) - static_cast<int>((nlo >> (8 * r)) & 0xffu);
+              acc[r + 4] = static_cast<int>((phi >> (8 * r)) & 0xffu) - static_cast<int>((nhi >> (8 * r)) & 0xffu);
+            }
+          } else {
+            for (int e = __ldg(rp + v); e < e1; ++e) {
+              const int word = __ldg(d.adj + e);
+              const int wgt = (word << 24) >> 24;
+              const int b = sp[static_cast<unsigned>(word) >> 8];
+              wsum += wgt;
+#pragma unroll
+              for (int r = 0; r < 8; ++r) acc[r] += (b >> r) & 1 ? wgt : 0;
+            }
           }
           // f_r = sum_j w_j s_j = wsum - 2 * sum over neighbours with spin -1
           const int own = sp[v];
@@ -387,7 +416,14 @@ int ising_batch_create(int32_t num_graphs, const int32_t* n, const int64_t* m, c
       G.vtx_base = static_cast<int32_t>(vtx);
       G.row_base = static_cast<int32_t>(row_ptr.size());
       G.class_base = static_cast<int32_t>(class_pos.size());
-      G.pad = 0;
+      int64_t widest = 0;  // largest sum of |w| over a row
+      for (int32_t v = 0; v < hg.n; ++v) {
+        int64_t row = 0;
+        for (int32_t k = hg.row_ptr[(size_t)v]; k < hg.row_ptr[(size_t)v + 1]; ++k)
+          row += std::abs(static_cast<int64_t>(hg.w[(size_t)k]));
+        widest = std::max(widest, row);
+      }
+      G.byte_lanes = widest <= 255 ? 1 : 0;
       for (size_t v = 0; v <= (size_t)hg.n; ++v)
         row_ptr.push_back(static_cast<int32_t>(edge_off + hg.row_ptr[v]));
       for (size_t k = 0; k < (size_t)hg.nnz; ++k)

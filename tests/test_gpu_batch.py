@@ -30,6 +30,14 @@ def small_batch():
         gs.append(g)
     gs.append(synth.Graph(5, np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0, np.int32)))
     gs.append(synth.torus_graph(8, 3, weights="pm1"))
+    # a star whose hub row sums |w| to more than 255 (the instance takes the
+    # per-replica loop instead of byte-lane sums), plus a few extra edges
+    rng = np.random.default_rng(5)
+    leaves = np.arange(1, 61, dtype=np.int32)
+    src = np.concatenate([np.zeros(60, np.int32), leaves[:-1]])
+    dst = np.concatenate([leaves, leaves[1:]])
+    w = (rng.integers(5, 9, size=src.size) * rng.choice([-1, 1], size=src.size)).astype(np.int32)
+    gs.append(synth.Graph(61, src, dst, w))
     return gs
 
 
