@@ -40,7 +40,8 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="torus1024",
                     choices=["torus1024", "zipf1m", "er800", "batched", "warmstart", "gnn"])
-    ap.add_argument("--engine", default="auto", choices=["auto", "phase", "persistent", "dataflow"])
+    ap.add_argument("--engine", default="auto",
+                    choices=["auto", "phase", "persistent", "dataflow", "persistent_grid", "itemflow"])
     ap.add_argument("--mode", default="det", choices=["det", "racy"],
                     help="deterministic colour phases (bit-exact) or the racy pass")
     ap.add_argument("--e2e-steps", type=int, default=2)
@@ -75,24 +76,25 @@ def algorithmic_bytes_per_sweep(n: int, nnz: int, entry_bytes: int) -> int:
 # the sweeps. The entry holds only while the kernel sources hash to `sources`:
 # once they change the counters are stale and traffic is reported as null.
 NCU_TRAFFIC = {
-    "torus1024": {"fixed": 22.3642e6, "per_sweep": 0.0, "kernel": "persistent_kernel",
+    "torus1024": {"fixed": 23.9207e6, "per_sweep": 0.0, "kernel": "itemflow_kernel",
+                  "engine": "itemflow",
                   "files": ("sweep.cuh", "anneal.cu", "philox.cuh"),
-                  "sources": "cad09791196b872b",
-                  "how": "ncu 20- and 60-sweep captures: 22.361 MB and 22.367 MB, so the "
+                  "sources": "37d2a87d22e3c338",
+                  "how": "ncu 20- and 60-sweep captures: 23.949 MB and 23.920 MB, so the "
                          "working set is read once and then stays in L2"},
-    "batched": {"fixed": 0.0, "per_sweep": 2.94971e9 / 20, "kernel": "batch_anneal_kernel",
+    "batched": {"fixed": 0.2383e9, "per_sweep": 0.18541e9, "kernel": "batch_anneal_kernel",
                 "files": ("batch.cu", "philox.cuh"),
-                "sources": "b9cc8929057fad4f",
-                "how": "ncu 20-sweep capture (2.950 GB) scaled in proportion to sweeps"},
+                "sources": "d907bff657ba27b4",
+                "how": "ncu 20- and 60-sweep captures: 3.946 GB and 11.362 GB"},
 }
 
 
-def kernel_traffic(workload: str, sweeps: int):
+def kernel_traffic(workload: str, sweeps: int, engine: str = ""):
     """Per-launch DRAM bytes of the dominant kernel, or None when no capture
-    matches the current kernel sources."""
+    matches the workload, the engine that ran, or the current kernel sources."""
     import hashlib
     e = NCU_TRAFFIC.get(workload)
-    if e is None:
+    if e is None or (engine and e.get("engine", engine) != engine):
         return None
     h = hashlib.sha256()
     for f in e["files"]:
@@ -634,13 +636,13 @@ def main():
     stream = torch.cuda.Stream()
     engine = {"auto": P.ISING_ENGINE_AUTO, "phase": P.ISING_ENGINE_PHASE,
               "persistent": P.ISING_ENGINE_PERSISTENT,
-              "dataflow": P.ISING_ENGINE_DATAFLOW}[args.engine]
+              "dataflow": P.ISING_ENGINE_DATAFLOW,
+              "persistent_grid": P.ISING_ENGINE_PERSISTENT_GRID,
+              "itemflow": P.ISING_ENGINE_ITEMFLOW}[args.engine]
 
     h = P.ising_create(g.n, g.src, g.dst, g.w, stream=stream)
     P.ising_set_engine(h, engine)
     mode = P.ISING_MODE_RACY if args.mode == "racy" else P.ISING_MODE_DET
-    # AUTO resolves to the persistent engine on devices with cooperative launch
-    engine_name = "persistent" if args.engine == "auto" else args.engine
     colours = P.ising_num_colours(h)
     m = P.ising_num_edges(h)
     nnz = 2 * m
@@ -682,6 +684,9 @@ def main():
             anneal_ms.append(ev[0].elapsed_time(ev[1]))
     torch.cuda.synchronize()
     launches = P.ising_launch_count(h) - launches0
+    engine_name = {P.ISING_ENGINE_PHASE: "phase", P.ISING_ENGINE_PERSISTENT_GRID: "persistent",
+                   P.ISING_ENGINE_DATAFLOW: "dataflow", P.ISING_ENGINE_ITEMFLOW: "itemflow",
+                   P.ISING_ENGINE_USED_BLOCK: "block"}.get(P.ising_engine_used(h), "unknown")
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = sum(step_ms)
     total_ms = max_over_ranks(total_ms, world, dist, "cuda")
@@ -748,7 +753,8 @@ def main():
             "workload": args.workload, "n": g.n, "m": m, "colours": colours,
             "sweeps": T, "p0": p0, "schedule": "linear",
             "mode": "racy" if args.mode == "racy" else "deterministic",
-            "engine": args.engine, "weights": "int8" if w_bytes == 1 else "int32",
+            "engine": args.engine, "engine_used": engine_name,
+            "weights": "int8" if w_bytes == 1 else "int32",
             "csr_entry_bytes": entry_bytes,
             "replicas_per_gpu": 1, "parallelism": f"replicas{world}",
             "l2": "512 MiB buffer zeroed between timed steps (outside the events)",
@@ -758,9 +764,8 @@ def main():
         "final_cut_mean": float(np.mean(cuts)),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
-                     "traffic": (kernel_traffic(args.workload, T)
-                                 if engine_name == "persistent" and args.mode == "det"
-                                 else None),
+                     "traffic": (kernel_traffic(args.workload, T, engine_name)
+                                 if args.mode == "det" else None),
                      "peak_kind": peak_kind, "bytes_per_sweep": B, "bytes_per_launch": B * T,
                      "kernel": f"{engine_name} sweep kernel(s) of one anneal call"},
         "cpu_baseline": cpu,

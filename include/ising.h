@@ -97,7 +97,10 @@ enum {
 
 /* Which kernel engine runs a deterministic anneal (all give identical spins). */
 enum {
-  ISING_ENGINE_AUTO = 0,       /* persistent if the device supports cooperative launches */
+  ISING_ENGINE_AUTO = 0,       /* with cooperative launches: ITEMFLOW for deterministic linear
+                                  anneals of graphs without sliced rows (unless the graph is small
+                                  enough for PERSISTENT's one-block form), else PERSISTENT;
+                                  without: PHASE */
   ISING_ENGINE_PHASE = 1,      /* one kernel launch per colour class */
   ISING_ENGINE_PERSISTENT = 2, /* one cooperative launch per anneal call, bounded grid barrier;
                                   deterministic anneals of a graph with int8 weights and at most
@@ -107,7 +110,13 @@ enum {
   ISING_ENGINE_DATAFLOW = 3,   /* one cooperative launch per anneal call without barriers: each
                                   neighbour read waits (bounded) until the neighbour carries the
                                   update the colour order requires; racy mode runs as PERSISTENT */
-  ISING_ENGINE_PERSISTENT_GRID = 4 /* PERSISTENT without the one-block form for small graphs */
+  ISING_ENGINE_PERSISTENT_GRID = 4, /* PERSISTENT without the one-block form for small graphs */
+  ISING_ENGINE_ITEMFLOW = 5    /* one cooperative launch per anneal call without barriers: each
+                                  warp's work item waits (bounded) for the items holding its
+                                  rows' neighbours to finish the sweep the colour order requires
+                                  (per-item counters, release/acquire); for graphs whose rows
+                                  are not sliced across warps, deterministic linear schedule;
+                                  otherwise runs as PERSISTENT_GRID */
 };
 
 /* ising_create flags. */
@@ -398,6 +407,13 @@ int ising_gnn_warm_start(ising_gnn* net, ising_graph* g, int set_bias);
 int ising_gnn_launch_count(ising_gnn* net, uint64_t* out);
 /* ising_gnn_destroy -- free the network (NULL is ignored). */
 void ising_gnn_destroy(ising_gnn* net);
+
+/* ising_engine_used -- the engine the last anneal call ran: ISING_ENGINE_PHASE,
+ * ISING_ENGINE_PERSISTENT_GRID (the persistent grid-barrier kernel),
+ * ISING_ENGINE_DATAFLOW, ISING_ENGINE_ITEMFLOW or ISING_ENGINE_USED_BLOCK
+ * (PERSISTENT's one-block form); -1 before the first anneal. */
+#define ISING_ENGINE_USED_BLOCK 6
+int ising_engine_used(ising_graph* g, int32_t* out);
 
 /* Failure-detection test hook. Every device-side wait of the anneal kernels
  * is bounded (2 s by default); a wait that runs out records an error, the

@@ -37,6 +37,7 @@ ISING_ENGINE_PHASE = 1
 ISING_ENGINE_PERSISTENT = 2
 ISING_ENGINE_DATAFLOW = 3
 ISING_ENGINE_PERSISTENT_GRID = 4
+ISING_ENGINE_ITEMFLOW = 5
 ISING_CREATE_WEIGHTS_I32 = 1
 ISING_STATIC_MAX_VERTICES = 1 << 24
 
@@ -52,7 +53,9 @@ EXPORTS = (
     "ising_set_flip_bias", "ising_get_flip_bias", "ising_gnn_create", "ising_gnn_set_params",
     "ising_gnn_get_params", "ising_gnn_forward", "ising_gnn_gradients", "ising_gnn_train_step",
     "ising_gnn_warm_start", "ising_gnn_launch_count", "ising_gnn_destroy", "ising_debug_fault",
+    "ising_engine_used",
 )
+ISING_ENGINE_USED_BLOCK = 6
 ISING_FAULT_NONE = 0
 ISING_FAULT_SKIP_ARRIVAL = 1
 ISING_FAULT_SHORT_COPY = 2
@@ -133,6 +136,7 @@ def lib():
         L.ising_gnn_destroy.argtypes = [vp]
         L.ising_gnn_destroy.restype = None
         L.ising_debug_fault.argtypes = [vp, ctypes.c_int, ctypes.c_uint64]
+        L.ising_engine_used.argtypes = [vp, ctypes.POINTER(ctypes.c_int32)]
         L.ising_strerror.argtypes = [ctypes.c_int]
         L.ising_strerror.restype = ctypes.c_char_p
         for name in EXPORTS:
@@ -326,6 +330,13 @@ def ising_plan_colouring(n: int, src, dst, w):
                                       out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                                       ctypes.byref(C)), "ising_plan_colouring")
     return C.value, out
+
+
+def ising_engine_used(g: IsingGraph) -> int:
+    """The engine the last anneal call ran (ISING_ENGINE_*, or ISING_ENGINE_USED_BLOCK)."""
+    v = ctypes.c_int32()
+    _check(lib().ising_engine_used(g.ptr, ctypes.byref(v)), "ising_engine_used")
+    return v.value
 
 
 def ising_debug_fault(g: IsingGraph, kind: int, wait_budget_ns: int = 0) -> None:

@@ -222,6 +222,84 @@ __global__ void __launch_bounds__(isingx::kBlockThreads)
   }
 }
 
+// Item-dataflow engine: one cooperative launch runs every sweep with no grid
+// barrier and no per-vertex waits. Warp w takes items w, w + nwarps, ... of
+// each colour class in (sweep, class) order; before updating item i in the
+// launch's k-th sweep it waits (bounded) until done[j] >= k + 1 for every
+// dependency j of an earlier class and done[j] >= k for every j of a later
+// class (host_graph.h, build_item_deps), then gathers with ordinary loads and
+// publishes done[i] = k + 1 with a release store. The items' own loads and
+// Philox draws are staged before the wait. All warps are resident and each
+// follows the (sweep, class) order, so the earliest unfinished item can
+// always proceed.
+// Completion counters sit one per 128-byte line, so pollers of different
+// items do not share lines.
+constexpr int kDoneStride = 32;
+
+__device__ __forceinline__ int ld_acquire_s32(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_s32(int* p, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Every lane takes some of item i's dependencies; true once all are met,
+// false (and the error flag set) after `budget` ns or when another warp has
+// already failed. Warp-uniform.
+__device__ __forceinline__ bool wait_item_deps(const int32_t* __restrict__ dep_ptr,
+                                               const int32_t* __restrict__ deps, const int* done,
+                                               int i, int k, int* error, long long budget, int lane) {
+  bool ok = true;
+  const int e = __ldg(dep_ptr + i + 1);
+  for (int q = __ldg(dep_ptr + i) + lane; q < e && ok; q += 32) {
+    const int dj = __ldg(deps + q);
+    const int need = (dj & 1) ? k : k + 1;
+    long long t0 = 0;
+    for (unsigned it = 0; ld_acquire_s32(done + (dj >> 1) * kDoneStride) < need; ++it) {
+      if ((it & 63u) == 0u) {
+        const long long now = isingx::global_ns();
+        if (it == 0u) {
+          t0 = now;
+        } else if (now - t0 > budget || isingx::ld_relaxed_s32(error) != 0) {
+          atomicExch(error, 1);
+          ok = false;
+          break;
+        }
+      }
+    }
+  }
+  return __all_sync(isingx::kFullMask, ok);
+}
+
+template <bool PACKED>
+__global__ void __launch_bounds__(kPersistBlock, 2)
+    itemflow_kernel(DevGraph d, const int32_t* __restrict__ phase_items, int num_phases,
+                    uint64_t t_begin, uint32_t sweeps, uint64_t T, uint64_t T0, uint32_t replica,
+                    isingx::PhiloxRounds rk, const int32_t* __restrict__ dep_ptr,
+                    const int32_t* __restrict__ deps, int* done, int* error, long long budget) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * kPersistBlock + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * kPersistBlock) >> 5;
+  long long unused = 0;
+  isingx::Staged<PACKED> st;
+  for (uint32_t k = 0; k < sweeps; ++k) {
+    const SweepArgs a = sweep_args(t_begin + k, T, T0, replica);
+    for (int c = 0; c < num_phases; ++c) {
+      const int ie = __ldg(phase_items + c + 1);
+      for (int i = __ldg(phase_items + c) + warp; i < ie; i += nwarps) {
+        isingx::stage_item<PACKED>(d, d.items[i], a, rk, lane, st);
+        if (!wait_item_deps(dep_ptr, deps, done, i, static_cast<int>(k), error, budget, lane)) return;
+        isingx::finish_item<PACKED, kPassDet>(d, st, a, rk, lane, unused);
+        __syncwarp();
+        if (lane == 0) st_release_s32(done + i * kDoneStride, static_cast<int>(k) + 1);
+      }
+    }
+  }
+}
+
 // Dataflow engine: one cooperative launch runs every sweep with no grid
 // barrier. Warp w takes items w, w + nwarps, ... of each colour class in
 // (sweep, class) order; every neighbour gather waits until the neighbour's
@@ -322,7 +400,8 @@ void free_device(ising_graph* g) {
                   g->d_tmp,     g->d_class_items, g->d_all_items, g->d_barrier,
                   g->d_class_begin, g->d_trace, g->d_nflip_bits, g->d_nflip_list,
                   g->d_bias,    g->d_rowid, g->d_block_words, g->d_block_chunk_off,
-                  g->d_block_chunk_len, g->d_block_class_chunk};
+                  g->d_block_chunk_len, g->d_block_class_chunk, g->d_dep_ptr, g->d_deps,
+                  g->d_done};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -422,6 +501,43 @@ cudaError_t launch_persistent_t(ising_graph* g, const int32_t* phase_items, int 
   g->launches++;
   return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(kernel), dim3(grid),
                                      dim3(kPersistBlock), args, 0, g->stream);
+}
+
+template <bool PACKED>
+cudaError_t launch_itemflow_t(ising_graph* g, uint64_t t_begin, uint32_t sweeps, uint64_t T,
+                              uint64_t T0, uint32_t replica, const isingx::PhiloxRounds& rk_in) {
+  auto kernel = itemflow_kernel<PACKED>;
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kPersistBlock, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+  per_sm = std::min(per_sm, 2);
+  const int grid = per_sm * g->num_sms;
+  if ((e = barrier_init(g)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(g->d_done, 0, kDoneStride * sizeof(int32_t) * static_cast<size_t>(g->num_items),
+                           g->stream)) != cudaSuccess)
+    return e;
+  DevGraph d = g->dev();
+  const int32_t* phase_items = g->d_class_items;
+  int num_phases = g->num_colours;
+  isingx::PhiloxRounds rk = rk_in;
+  const int32_t* dep_ptr = g->d_dep_ptr;
+  const int32_t* deps = g->d_deps;
+  int* done = g->d_done;
+  int* error = &g->d_barrier->error;
+  long long budget = g->wait_budget_ns > 0 ? static_cast<long long>(g->wait_budget_ns)
+                                           : isingx::kBarrierBudgetNs;
+  void* args[] = {&d, &phase_items, &num_phases, &t_begin, &sweeps, &T, &T0, &replica, &rk,
+                  &dep_ptr, &deps, &done, &error, &budget};
+  g->launches++;
+  return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(kernel), dim3(grid),
+                                     dim3(kPersistBlock), args, 0, g->stream);
+}
+
+cudaError_t launch_itemflow(ising_graph* g, uint64_t t_begin, uint32_t sweeps, uint64_t T,
+                            uint64_t T0, uint32_t replica, const isingx::PhiloxRounds& rk) {
+  if (g->packed) return launch_itemflow_t<true>(g, t_begin, sweeps, T, T0, replica, rk);
+  return launch_itemflow_t<false>(g, t_begin, sweeps, T, T0, replica, rk);
 }
 
 cudaError_t launch_block(ising_graph* g, uint64_t t_begin, uint32_t sweeps, uint64_t T, uint64_t T0,
@@ -580,13 +696,14 @@ int ising_create(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, c
   g->num_items = static_cast<int32_t>(plan.items.size());
   g->num_slots = static_cast<int32_t>(plan.split_parts.size());
   isingx::BlockPlan block;
-  if (g->packed) {
-    try {
-      isingx::build_block_plan(hg, &block);
-    } catch (const std::bad_alloc&) {
-      delete g;
-      return ISING_ENOMEM;
-    }
+  std::vector<int32_t> dep_ptr, deps;  // item dependencies (before the columns are packed)
+  bool have_deps = false;
+  try {
+    if (g->packed) isingx::build_block_plan(hg, &block);
+    have_deps = isingx::build_item_deps(hg, plan, &dep_ptr, &deps);
+  } catch (const std::bad_alloc&) {
+    delete g;
+    return ISING_ENOMEM;
   }
 
   cudaError_t e = cudaSuccess;
@@ -635,6 +752,12 @@ int ising_create(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, c
     if ((e = alloc_copy(&g->d_all_items, all_items, 2, g->stream)) != cudaSuccess) break;
     if ((e = alloc_copy(&g->d_class_begin, hg.class_begin.data(), hg.class_begin.size(),
                         g->stream)) != cudaSuccess) break;
+    if (have_deps) {
+      if ((e = alloc_copy(&g->d_dep_ptr, dep_ptr.data(), dep_ptr.size(), g->stream)) != cudaSuccess) break;
+      if ((e = alloc_copy(&g->d_deps, deps.data(), deps.size(), g->stream)) != cudaSuccess) break;
+      if ((e = alloc_copy<int32_t>(&g->d_done, nullptr, kDoneStride * plan.items.size(), g->stream)) != cudaSuccess) break;
+      g->itemflow_ok = true;
+    }
     if (block.ok) {
       if ((e = alloc_copy(&g->d_block_words, block.words.data(), block.words.size(), g->stream)) != cudaSuccess) break;
       if ((e = alloc_copy(&g->d_block_chunk_off, block.chunk_off.data(), block.chunk_off.size(),
@@ -747,7 +870,16 @@ static int anneal_impl(ising_graph* g, const ising_schedule* sched, uint32_t swe
   if (engine == ISING_ENGINE_AUTO) {
     int coop = 0;
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, g->device);
-    engine = coop ? ISING_ENGINE_PERSISTENT : ISING_ENGINE_PHASE;
+    // small graphs: the block engine (inside PERSISTENT); graphs without
+    // sliced rows: the item-dataflow engine for deterministic linear
+    // schedules; else the grid barrier
+    if (!coop)
+      engine = ISING_ENGINE_PHASE;
+    else if (g->itemflow_ok && !g->block_ok && mode == ISING_MODE_DET &&
+             sched->kind == ISING_SCHED_LINEAR)
+      engine = ISING_ENGINE_ITEMFLOW;
+    else
+      engine = ISING_ENGINE_PERSISTENT;
   }
   // every sweep updates every vertex once, flipping its update parity
   const int par0 = g->parity;
@@ -758,15 +890,26 @@ static int anneal_impl(ising_graph* g, const ising_schedule* sched, uint32_t swe
   const uint32_t n0 = nflip ? sched->n0 : 0u;
   const uint64_t T0 = nflip ? 0 : linear_t0(sched->p0);
   if (engine == ISING_ENGINE_DATAFLOW && mode == ISING_MODE_DET && !nflip) {
+    g->engine_used = ISING_ENGINE_DATAFLOW;
     ISING_CUDA(g, launch_flow(g, sched->t_begin, sweeps, sched->t_total, T0, sched->replica, par0, rk));
     return ISING_OK;
   }
+  if (engine == ISING_ENGINE_ITEMFLOW) {
+    if (mode == ISING_MODE_DET && !nflip && g->itemflow_ok) {
+      g->engine_used = ISING_ENGINE_ITEMFLOW;
+      ISING_CUDA(g, launch_itemflow(g, sched->t_begin, sweeps, sched->t_total, T0, sched->replica, rk));
+      return ISING_OK;
+    }
+    engine = ISING_ENGINE_PERSISTENT_GRID;  // racy, N-flip or sliced rows
+  }
   if (engine == ISING_ENGINE_PERSISTENT && mode == ISING_MODE_DET && g->block_ok) {
+    g->engine_used = ISING_ENGINE_USED_BLOCK;
     ISING_CUDA(g, launch_block(g, sched->t_begin, sweeps, sched->t_total, T0, sched->replica, rk, n0));
     return ISING_OK;
   }
   if (engine == ISING_ENGINE_PERSISTENT || engine == ISING_ENGINE_DATAFLOW ||
       engine == ISING_ENGINE_PERSISTENT_GRID) {
+    g->engine_used = ISING_ENGINE_PERSISTENT_GRID;
     if (mode == ISING_MODE_RACY)
       ISING_CUDA(g, launch_persistent<kPassRacy>(g, g->d_class_items, g->num_colours,
                                                  sched->t_begin, sweeps, sched->t_total, T0,
@@ -777,6 +920,7 @@ static int anneal_impl(ising_graph* g, const ising_schedule* sched, uint32_t swe
                                                 sched->replica, rk, n0));
     return ISING_OK;
   }
+  g->engine_used = ISING_ENGINE_PHASE;
   SweepArgs a{};
   a.replica = sched->replica;
   for (uint32_t k = 0; k < sweeps; ++k) {
@@ -923,6 +1067,12 @@ int ising_launch_count(ising_graph* g, uint64_t* out) {
   return ISING_OK;
 }
 
+int ising_engine_used(ising_graph* g, int32_t* out) {
+  if (g == nullptr || out == nullptr) return ISING_EINVAL;
+  *out = g->engine_used;
+  return ISING_OK;
+}
+
 int ising_debug_fault(ising_graph* g, int kind, uint64_t wait_budget_ns) {
   if (g == nullptr) return ISING_EINVAL;
   if (kind != ISING_FAULT_NONE && kind != ISING_FAULT_SKIP_ARRIVAL && kind != ISING_FAULT_SHORT_COPY)
@@ -937,7 +1087,7 @@ int ising_set_engine(ising_graph* g, int engine) {
   if (g == nullptr) return ISING_EINVAL;
   if (engine != ISING_ENGINE_AUTO && engine != ISING_ENGINE_PHASE &&
       engine != ISING_ENGINE_PERSISTENT && engine != ISING_ENGINE_DATAFLOW &&
-      engine != ISING_ENGINE_PERSISTENT_GRID)
+      engine != ISING_ENGINE_PERSISTENT_GRID && engine != ISING_ENGINE_ITEMFLOW)
     return ISING_EINVAL;
   g->engine = engine;
   return ISING_OK;

@@ -16,6 +16,7 @@ struct ising_graph {
   cudaStream_t stream = nullptr;
   int status = ISING_OK;
   int engine = ISING_ENGINE_AUTO;
+  int engine_used = -1;  // the engine the last anneal call ran (ising_engine_used)
   int fault_kind = ISING_FAULT_NONE;  // ising_debug_fault
   uint64_t wait_budget_ns = 0;        // 0: the kernels' default bound
   int num_sms = 1;
@@ -56,6 +57,11 @@ struct ising_graph {
   int32_t* d_nflip_list = nullptr;         // N-flip: chosen vertices, n entries
   size_t trace_cap = 0;
   int32_t* d_all_items = nullptr;    // {0, num_items}: one phase over every item (energy)
+  // item-dataflow engine (graphs without sliced rows)
+  bool itemflow_ok = false;
+  int32_t* d_dep_ptr = nullptr;
+  int32_t* d_deps = nullptr;
+  int32_t* d_done = nullptr;
   // block engine of small graphs (host_graph.h, block.cuh)
   bool block_ok = false;
   int32_t block_num_chunks = 0;

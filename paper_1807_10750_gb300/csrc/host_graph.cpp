@@ -256,6 +256,38 @@ void build_work_plan(const HostGraph& g, int32_t target_warps, int32_t min_edges
   }
 }
 
+bool build_item_deps(const HostGraph& g, const WorkPlan& plan, std::vector<int32_t>* dep_ptr,
+                     std::vector<int32_t>* deps) {
+  dep_ptr->clear();
+  deps->clear();
+  const int32_t ni = (int32_t)plan.items.size();
+  std::vector<int32_t> item_of((size_t)g.n, -1), class_of((size_t)ni, 0);
+  for (int32_t c = 0; c < g.num_colours; ++c)
+    for (int32_t i = plan.class_item_begin[(size_t)c]; i < plan.class_item_begin[(size_t)c + 1]; ++i)
+      class_of[(size_t)i] = c;
+  for (int32_t i = 0; i < ni; ++i) {
+    const WorkItem& it = plan.items[(size_t)i];
+    if (it.v_end < 0) return false;  // a slice of a heavy row
+    for (int32_t v = it.v_begin; v < it.v_end; ++v) item_of[(size_t)v] = i;
+  }
+  dep_ptr->reserve((size_t)ni + 1);
+  dep_ptr->push_back(0);
+  // seen[j] == i + 1 marks j as already listed for item i (no sorting)
+  std::vector<int32_t> seen((size_t)ni, 0);
+  for (int32_t i = 0; i < ni; ++i) {
+    const WorkItem& it = plan.items[(size_t)i];
+    for (int32_t v = it.v_begin; v < it.v_end; ++v)
+      for (int32_t k = g.row_ptr[(size_t)v]; k < g.row_ptr[(size_t)v + 1]; ++k) {
+        const int32_t j = item_of[(size_t)g.col[(size_t)k]];
+        if (j == i || seen[(size_t)j] == i + 1) continue;
+        seen[(size_t)j] = i + 1;
+        deps->push_back((j << 1) | (class_of[(size_t)j] > class_of[(size_t)i] ? 1 : 0));
+      }
+    dep_ptr->push_back((int32_t)deps->size());
+  }
+  return true;
+}
+
 void build_block_plan(const HostGraph& g, BlockPlan* bp) {
   *bp = BlockPlan();
   const int32_t C = g.num_colours;

@@ -72,6 +72,16 @@ struct BlockPlan {
 // chunks; otherwise leaves bp->ok = false.
 void build_block_plan(const HostGraph& g, BlockPlan* bp);
 
+// Item dependencies for the item-dataflow engine. For graphs whose work
+// items are all light or group items (no row sliced across warps), item i
+// depends on every other item j holding a neighbour of one of i's rows;
+// deps[dep_ptr[i] .. dep_ptr[i + 1]) lists (j << 1) | later, later = 1 if j's
+// colour class comes after i's. In sweep t, i may update once every earlier
+// j has finished sweep t and every later j has finished sweep t - 1.
+// Returns false (and leaves the vectors empty) if some item is a slice.
+bool build_item_deps(const HostGraph& g, const WorkPlan& plan, std::vector<int32_t>* dep_ptr,
+                     std::vector<int32_t>* deps);
+
 // Returns 0, or a negative ISING_* status.
 int build_host_graph(int32_t n, int64_t m, const int32_t* src, const int32_t* dst,
                      const int32_t* w, HostGraph* out);

@@ -12,7 +12,7 @@ import synth
 
 pytestmark = pytest.mark.gpu
 
-ENGINES = ["phase", "persistent", "dataflow", "persistent_grid"]
+ENGINES = ["phase", "persistent", "dataflow", "persistent_grid", "itemflow"]
 
 
 @pytest.fixture(scope="module")
@@ -28,7 +28,8 @@ def P():
 def engine_id(P, name):
     return {"phase": P.ISING_ENGINE_PHASE, "persistent": P.ISING_ENGINE_PERSISTENT,
             "dataflow": P.ISING_ENGINE_DATAFLOW, "auto": P.ISING_ENGINE_AUTO,
-            "persistent_grid": P.ISING_ENGINE_PERSISTENT_GRID}[name]
+            "persistent_grid": P.ISING_ENGINE_PERSISTENT_GRID,
+            "itemflow": P.ISING_ENGINE_ITEMFLOW}[name]
 
 
 def gpu_anneal(P, g, s0, *, seed, p0, T, t_begin=0, sweeps=None, flags=0, engine="auto",
@@ -364,4 +365,17 @@ def test_block_engine_nflip_schedule(P, name):
         P.ising_anneal(h, t_total=T, seed=7, kind=P.ISING_SCHED_NFLIP, n0=n0)
         got = P.ising_get_spins(h)
     want = oracle.anneal_nflip(g.n, g.src, g.dst, g.w, s0, seed=7, n0=n0, T=T)
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("name", ["torus96", "er5k_sparse", "grid_open"])
+def test_itemflow_engine_matches_oracle_over_many_sweeps(P, name):
+    # graphs whose rows are never sliced across warps, so the item-dataflow
+    # engine runs them; many sweeps let items run ahead of one another
+    g = {"torus96": lambda: synth.torus_graph(96, 2, weights="pm1"),
+         "er5k_sparse": lambda: synth.random_small_graph(5000, 0.002, 3, weights="int8"),
+         "grid_open": lambda: synth.grid_graph(70, 53, 1, weights="int8")}[name]()
+    s0 = oracle.init_spins(g.n, 3)
+    got, _, _ = gpu_anneal(P, g, s0, seed=4, p0=0.15, T=300, engine="itemflow")
+    want = oracle.anneal(g.n, g.src, g.dst, g.w, s0, seed=4, p0=0.15, T=300)
     assert np.array_equal(got, want)
