@@ -199,62 +199,77 @@ __global__ void aggregate8_kernel(EdgeView ev, const int32_t* rowid, const float
   }
 }
 
-// out[row] += c_row * sum_j w_rj c_j h_j for width-64 rows: a warp walks
-// kAggChunk consecutive entries, lane l owns features 2l, 2l+1, and eight
-// neighbour rows are in flight at a time.
-__global__ void aggregate64_kernel(EdgeView ev, const int32_t* rowid, const float* cvec,
-                                   const bf162* h, int nnz, float* out) {
-  const int lane = threadIdx.x & 31;
+// out[row] += c_row * sum_j w_rj c_j h_j for width-64 rows. A warp walks
+// kAggChunk consecutive CSR entries, 32 at a time: each lane decodes one
+// entry (row, column, w c_col) into a per-warp shared buffer, then the two
+// half-warps take alternate entries -- lane l of a half owns features
+// 4(l mod 16) .. +3 and loads them with one 8-byte read -- four entries in
+// flight per half. Rows are sorted, so each half flushes its running sum with
+// one vector atomic where its row changes.
+__device__ __forceinline__ void agg_flush(float* out, const float* cvec, int row, int hl,
+                                          float4 acc) {
+  if (row < 0) return;
+  const float cr = __ldg(cvec + row);
+  atomicAdd(reinterpret_cast<float4*>(out + static_cast<size_t>(row) * 64 + 4 * hl),
+            make_float4(cr * acc.x, cr * acc.y, cr * acc.z, cr * acc.w));
+}
+
+__global__ void __launch_bounds__(256)
+    aggregate64_kernel(EdgeView ev, const int32_t* rowid, const float* cvec, const bf162* h,
+                       int nnz, float* out) {
+  __shared__ int4 meta[8][32];  // per warp of the 256-thread block
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int half = lane >> 4, hl = lane & 15;
   const long long warp = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const long long e_begin = warp * kAggChunk;
   if (e_begin >= nnz) return;
   const long long e_end = e_begin + kAggChunk < nnz ? e_begin + kAggChunk : nnz;
-  int cur = __ldg(rowid + e_begin);
-  float ax = 0.0f, ay = 0.0f;
+  const uint2* hq = reinterpret_cast<const uint2*>(h);  // 4 bf16 per uint2, 16 per row
+  int cur = -1;
+  float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   for (long long b = e_begin; b < e_end; b += 32) {
     const long long e = b + lane;
-    int row = -1, col = 0;
-    float coef = 0.0f;
+    int4 m = make_int4(-1, 0, 0, 0);
     if (e < e_end) {
-      int w;
+      int col, w;
       edge_at(ev, static_cast<int>(e), col, w);
-      row = __ldg(rowid + e);
-      coef = static_cast<float>(w) * __ldg(cvec + col);
+      m.x = __ldg(rowid + e);
+      m.y = col;
+      m.z = __float_as_int(static_cast<float>(w) * __ldg(cvec + col));
     }
+    meta[wib][lane] = m;
+    __syncwarp();
 #pragma unroll
     for (int j0 = 0; j0 < 32; j0 += 8) {
-      int rj[8];
-      float cj[8];
-      float2 hv[8];
+      int4 mm[4];
+      uint2 hv[4];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        rj[u] = __shfl_sync(kFull, row, j0 + u);
-        cj[u] = __shfl_sync(kFull, coef, j0 + u);
-        const int cu = __shfl_sync(kFull, col, j0 + u);
-        hv[u] = rj[u] >= 0 ? __bfloat1622float2(h[static_cast<size_t>(cu) * 32 + lane])
-                           : make_float2(0.0f, 0.0f);
+      for (int u = 0; u < 4; ++u) {
+        mm[u] = meta[wib][j0 + 2 * u + half];
+        hv[u] = mm[u].x >= 0 ? hq[static_cast<size_t>(mm[u].y) * 16 + hl] : make_uint2(0u, 0u);
       }
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        if (rj[u] != cur) {
-          if (cur >= 0) {
-            const float cr = __ldg(cvec + cur);
-            atomicAdd(out + static_cast<size_t>(cur) * 64 + 2 * lane, cr * ax);
-            atomicAdd(out + static_cast<size_t>(cur) * 64 + 2 * lane + 1, cr * ay);
-          }
-          ax = ay = 0.0f;
-          cur = rj[u];
+      for (int u = 0; u < 4; ++u) {
+        if (mm[u].x < 0) continue;  // past the chunk's end
+        if (mm[u].x != cur) {
+          agg_flush(out, cvec, cur, hl, acc);
+          acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+          cur = mm[u].x;
         }
-        ax += cj[u] * hv[u].x;
-        ay += cj[u] * hv[u].y;
+        const float coef = __int_as_float(mm[u].z);
+        bf162 p0, p1;
+        memcpy(&p0, &hv[u].x, 4);
+        memcpy(&p1, &hv[u].y, 4);
+        const float2 f0 = __bfloat1622float2(p0), f1 = __bfloat1622float2(p1);
+        acc.x += coef * f0.x;
+        acc.y += coef * f0.y;
+        acc.z += coef * f1.x;
+        acc.w += coef * f1.y;
       }
     }
+    __syncwarp();
   }
-  if (cur >= 0) {
-    const float cr = __ldg(cvec + cur);
-    atomicAdd(out + static_cast<size_t>(cur) * 64 + 2 * lane, cr * ax);
-    atomicAdd(out + static_cast<size_t>(cur) * 64 + 2 * lane + 1, cr * ay);
-  }
+  agg_flush(out, cvec, cur, hl, acc);
 }
 
 // ---------------------------------------------------------------------------
