@@ -379,3 +379,24 @@ def test_itemflow_engine_matches_oracle_over_many_sweeps(P, name):
     got, _, _ = gpu_anneal(P, g, s0, seed=4, p0=0.15, T=300, engine="itemflow")
     want = oracle.anneal(g.n, g.src, g.dst, g.w, s0, seed=4, p0=0.15, T=300)
     assert np.array_equal(got, want)
+
+
+def test_auto_engine_choice(P):
+    # small graph -> the one-block form; unsliced large graph -> item
+    # dataflow; a graph with sliced hub rows -> the grid engine; racy and
+    # N-flip anneals of an unsliced graph -> the grid engine
+    cases = [
+        (synth.random_small_graph(400, 0.03, 1, weights="int8"), {}, P.ISING_ENGINE_USED_BLOCK),
+        (synth.torus_graph(96, 2, weights="pm1"), {}, P.ISING_ENGINE_ITEMFLOW),
+        (synth.zipf_config_graph(20011, 2.1, 4, 3000, 5), {}, P.ISING_ENGINE_PERSISTENT_GRID),
+        (synth.torus_graph(96, 2, weights="pm1"), {"mode": P.ISING_MODE_RACY},
+         P.ISING_ENGINE_PERSISTENT_GRID),
+        (synth.torus_graph(96, 2, weights="pm1"), {"kind": P.ISING_SCHED_NFLIP, "n0": 50},
+         P.ISING_ENGINE_PERSISTENT_GRID),
+    ]
+    for g, kw, want in cases:
+        with P.ising_create(g.n, g.src, g.dst, g.w) as h:
+            assert P.ising_engine_used(h) == -1
+            P.ising_init_random(h, 1)
+            P.ising_anneal(h, p0=0.1, t_total=10, seed=1, **kw)
+            assert P.ising_engine_used(h) == want, (g.n, kw)
