@@ -24,16 +24,17 @@
 //      cut(s) = (W - H(s)) / 2, W = sum of the merged edge weights.
 //      The update is then s_i <- -sign(f_i) with f_i = sum_j w_ij s_j.
 //   R2 tie f_i = 0 (Eq. 2 allows either value): keep the current spin.
-//   R3 initial spins: s_i = +1 or -1 from bit 31 of Philox word 0 with
-//      counter (i, 0, replica, 1).
+//   R3 initial spins: s_i = +1 or -1 from bit 31 of replica r's draw on
+//      stream 1 (R5).
 //   R4 schedule: F_p decays linearly from p0 at sweep 0 to 0 at sweep T-1,
 //      as a 32-bit integer threshold thr[t] = floor(T0 (T-1-t) / (T-1)),
 //      T0 = round(p0 2^32) clamped to [0, 2^32-1]; a spin flips iff the 32-bit
 //      random word x0 < thr[t].
 //   R5 randomness: Philox4x32-10 (Salmon et al., SC'11), key = (lo32(seed),
-//      hi32(seed) ^ instance * 0x9E3779B9), counter = (original vertex id,
-//      sweep t, replica, stream) with stream 0 for flips, 1 for the initial
-//      spins; word x0 is used.
+//      hi32(seed) ^ instance * 0x9E3779B9); a flip (stream 0) or initial spin
+//      (stream 1) of replica r uses word r mod 4 of counter (original vertex
+//      id, sweep t (0 for the initial spins), floor(r / 4), stream), so four
+//      replicas share one evaluation (replica 0: word 0 of (id, t, 0, s)).
 //   R6 colouring: greedy first fit over the vertices in order of decreasing
 //      degree (ties: smaller id first), i.e. Welsh-Powell; classes are swept in
 //      increasing colour order, and inside a class the order is irrelevant
@@ -103,6 +104,18 @@ uint32_t random_word(uint64_t seed, uint32_t instance, uint32_t c0, uint32_t c1,
   uint32_t k1 = (uint32_t)(seed >> 32) ^ (uint32_t)(instance * kWeylA);
   Words4 c = {{c0, c1, c2, c3}};
   return philox4x32_10(c, k0, k1).x[0];
+}
+
+// R5: the draw of replica r for vertex c0 in sweep c1 on stream s (0 flips,
+// 1 initial spins): word r mod 4 of the counter (c0, c1, floor(r / 4), s), so
+// four replicas share one Philox evaluation; replica 0 is word 0 of
+// (c0, c1, 0, s).
+uint32_t replica_word(uint64_t seed, uint32_t instance, uint32_t c0, uint32_t c1,
+                      uint32_t replica, uint32_t stream) {
+  uint32_t k0 = (uint32_t)(seed & 0xffffffffu);
+  uint32_t k1 = (uint32_t)(seed >> 32) ^ (uint32_t)(instance * kWeylA);
+  Words4 c = {{c0, c1, replica >> 2, stream}};
+  return philox4x32_10(c, k0, k1).x[replica & 3u];
 }
 
 // ---------------------------------------------------------------------------
@@ -267,7 +280,7 @@ int oracle_init_spins(int32_t n, uint64_t seed, uint32_t instance, uint32_t repl
                       int8_t* s) {
   if (n <= 0) return -1;
   for (int32_t i = 0; i < n; ++i) {
-    uint32_t x = random_word(seed, instance, (uint32_t)i, 0u, replica, 1u);
+    uint32_t x = replica_word(seed, instance, (uint32_t)i, 0u, replica, 1u);
     s[i] = (x >> 31) ? (int8_t)-1 : (int8_t)1;
   }
   return 0;
@@ -329,7 +342,7 @@ int oracle_anneal_biased(int32_t n, int64_t m, const int32_t* src, const int32_t
           thr_v = ((uint64_t)thr * (uint64_t)bias[v]) >> 7;
           if (thr_v > 4294967295ull) thr_v = 4294967295ull;
         }
-        uint32_t x = random_word(seed, instance, (uint32_t)v, (uint32_t)t, replica, 0u);
+        uint32_t x = replica_word(seed, instance, (uint32_t)v, (uint32_t)t, replica, 0u);
         if ((uint64_t)x < thr_v) s[v] = (int8_t)(-s[v]);
       }
     }

@@ -443,3 +443,22 @@ def test_bias_threshold_clamps_at_the_top():
     s = oracle.anneal(n, e, e, e, s0, seed=6, p0=1.0, T=2, sweeps=1,
                       bias=np.full(n, 255, np.uint8))
     assert np.array_equal(s, -s0)
+
+
+@pytest.mark.parametrize("replica", range(8))
+def test_replica_draws_share_philox_evaluations(replica):
+    # R5: replica r's initial spin and flip use word r mod 4 of the counter
+    # (vertex, t, r // 4, stream), computed here with the KAT-pinned Philox.
+    n, seed, inst = 300, 0x0123456789ABCDEF, 3
+    key = [seed & 0xFFFFFFFF, ((seed >> 32) ^ (inst * 0x9E3779B9)) & 0xFFFFFFFF]
+    words = lambda v, t, s: oracle.philox([v, t, replica // 4, s], key)[replica % 4]
+    s0 = oracle.init_spins(n, seed, instance=inst, replica=replica)
+    want0 = np.array([-1 if words(v, 0, 1) >> 31 else 1 for v in range(n)], np.int8)
+    assert np.array_equal(s0, want0)
+    # edgeless graph, p0 = 1/2, T = 2: sweep 0 flips vertex v iff its word < 2^31
+    e = np.zeros(0, dtype=np.int32)
+    s1 = oracle.anneal(n, e, e, e, s0, seed=seed, instance=inst, replica=replica, p0=0.5, T=2,
+                       sweeps=1)
+    flipped = s1 != s0
+    want = np.array([words(v, 0, 0) < 2 ** 31 for v in range(n)])
+    assert np.array_equal(flipped, want)
