@@ -76,11 +76,11 @@ def algorithmic_bytes_per_sweep(n: int, nnz: int, entry_bytes: int) -> int:
 # the sweeps. The entry holds only while the kernel sources hash to `sources`:
 # once they change the counters are stale and traffic is reported as null.
 NCU_TRAFFIC = {
-    "torus1024": {"fixed": 23.9207e6, "per_sweep": 0.0, "kernel": "itemflow_kernel",
+    "torus1024": {"fixed": 23.982e6, "per_sweep": 0.0, "kernel": "itemflow_kernel",
                   "engine": "itemflow",
                   "files": ("sweep.cuh", "anneal.cu", "philox.cuh"),
-                  "sources": "37d2a87d22e3c338",
-                  "how": "ncu 20- and 60-sweep captures: 23.949 MB and 23.920 MB, so the "
+                  "sources": "902d42231c3e5f17",
+                  "how": "ncu 20- and 60-sweep captures: 23.966 MB and 23.996 MB, so the "
                          "working set is read once and then stays in L2"},
     "batched": {"fixed": 0.2383e9, "per_sweep": 0.18541e9, "kernel": "batch_anneal_kernel",
                 "files": ("batch.cu", "philox.cuh"),

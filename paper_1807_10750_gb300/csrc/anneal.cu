@@ -2,17 +2,23 @@
 //
 // Layout in device memory (all owned by the handle):
 //   row_ptr  int32[n+1]   CSR offsets, vertices ordered by colour class
-//   col      int32[nnz]   neighbour positions (rows sorted ascending)
-//   w        int8[nnz] or int32[nnz]   merged edge weights J_ij = w_ij
-//   spins    int8[n]      +1 / -1 by position
+//   adj      int32[nnz]   packed (col << 8) | (w & 0xff) entries, rows sorted by
+//                         neighbour position; or col / w int32[nnz] each (split)
+//   ell*     sliced-ELL copies of the light rows (host_graph.h)
+//   spins    int8[n+1]    state byte per position: bit 0 the spin (1 = -1), bit 1
+//                         the update parity; byte n is the pad entry's spin 0
 //   orig     int32[n]     position -> caller's vertex id (Philox counter word 0)
 //   pos      int32[n]     caller's vertex id -> position
-//   items    WorkItem[]   per-class warp work (see host_graph.h)
-//   slice_*  partial-field combine for rows sliced across warps (scratch)
+//   items    WorkItem[]   per-class warp work (host_graph.h)
+//   slice_*  partial-field combine for rows sliced across warps
+//   deps     item dependencies of the item-dataflow engine; block_* the
+//            packed words of the one-block engine (block.cuh)
 //
 // One warp processes one work item (sweep.cuh): the local fields
 // f_i = sum_j w_ij s_j of its rows (Eq. 2), then the update rule and the
-// random flip of Algorithm 2.
+// random flip of Algorithm 2. The engines differ in how a colour class waits
+// for the previous one: a launch per class, a grid barrier, per-neighbour or
+// per-item dataflow waits, or block barriers for small graphs.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -341,7 +347,7 @@ __global__ void nflip_kernel(DevGraph d, const int32_t* pos, unsigned* bitmap, i
 __global__ void init_random_kernel(int8_t* spins, const int32_t* orig, int n,
                                    isingx::PhiloxRounds rk, uint32_t replica) {
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-    const uint32_t x = isingx::philox4x32_10_word0(static_cast<uint32_t>(orig[p]), 0u, replica, 1u, rk);
+    const uint32_t x = isingx::replica_word(static_cast<uint32_t>(orig[p]), 0u, replica, 1u, rk);
     spins[p] = static_cast<int8_t>(isingx::state_byte((x >> 31) ? -1 : 1, 0));
   }
 }

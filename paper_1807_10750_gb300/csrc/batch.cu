@@ -52,8 +52,10 @@ struct BatchDev {
   uint8_t* spins;            // replica bits per position
 };
 
-__device__ __forceinline__ uint32_t batch_philox_word0(uint32_t x0, uint32_t x1, uint32_t x2,
-                                                       uint32_t x3, uint32_t ka, uint32_t kb) {
+// Philox4x32-10, all four words; replica r draws word r mod 4 of counter
+// (vertex, t, r / 4, stream), so one evaluation serves four replicas.
+__device__ __forceinline__ uint4 batch_philox(uint32_t x0, uint32_t x1, uint32_t x2,
+                                              uint32_t x3, uint32_t ka, uint32_t kb) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
     const uint64_t pa = static_cast<uint64_t>(0xD2511F53u) * x0;
@@ -67,7 +69,7 @@ __device__ __forceinline__ uint32_t batch_philox_word0(uint32_t x0, uint32_t x1,
     ka += 0x9E3779B9u;
     kb += 0xBB67AE85u;
   }
-  return x0;
+  return make_uint4(x0, x1, x2, x3);
 }
 
 // One instance per block iteration; all sweeps t_begin .. t_begin + sweeps - 1.
@@ -142,18 +144,24 @@ __global__ void __launch_bounds__(BLOCK)
           int nb = 0;
           const uint32_t o = static_cast<uint32_t>(__ldg(d.orig + G.vtx_base + v));
 #pragma unroll
-          for (int r = 0; r < 8; ++r) {
-            if (r >= replicas) break;
-            const int f = wsum - 2 * acc[r];
-            int bit = (own >> r) & 1;  // 1 = spin -1
-            if (f > 0)
-              bit = 1;
-            else if (f < 0)
-              bit = 0;
-            if (thr != 0u && batch_philox_word0(o, static_cast<uint32_t>(t), static_cast<uint32_t>(r),
-                                                0u, ka, kb) < thr)
-              bit ^= 1;
-            nb |= bit << r;
+          for (int q = 0; q < 2; ++q) {
+            if (4 * q >= replicas) break;
+            uint4 x = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
+            if (thr != 0u) x = batch_philox(o, static_cast<uint32_t>(t), static_cast<uint32_t>(q), 0u, ka, kb);
+            const uint32_t xs[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const int r = 4 * q + k;
+              if (r >= replicas) break;
+              const int f = wsum - 2 * acc[r];
+              int bit = (own >> r) & 1;  // 1 = spin -1
+              if (f > 0)
+                bit = 1;
+              else if (f < 0)
+                bit = 0;
+              if (xs[k] < thr) bit ^= 1;
+              nb |= bit << r;
+            }
           }
           sp[v] = static_cast<uint8_t>(nb);
         }
@@ -172,8 +180,12 @@ __global__ void batch_init_kernel(BatchDev d, uint32_t seed_lo, uint32_t seed_hi
   for (int v = threadIdx.x; v < G.n; v += blockDim.x) {
     const uint32_t o = static_cast<uint32_t>(d.orig[G.vtx_base + v]);
     int byte = 0;
-    for (int r = 0; r < replicas; ++r)
-      byte |= static_cast<int>(batch_philox_word0(o, 0u, static_cast<uint32_t>(r), 1u, seed_lo, kb) >> 31) << r;
+    for (int q = 0; 4 * q < replicas; ++q) {
+      const uint4 x = batch_philox(o, 0u, static_cast<uint32_t>(q), 1u, seed_lo, kb);
+      const uint32_t xs[4] = {x.x, x.y, x.z, x.w};
+      for (int k = 0; k < 4 && 4 * q + k < replicas; ++k)
+        byte |= static_cast<int>(xs[k] >> 31) << (4 * q + k);
+    }
     d.spins[G.vtx_base + v] = static_cast<uint8_t>(byte);
   }
 }

@@ -4,9 +4,10 @@
 // numbers: as easy as 1, 2, 3", SC'11): ten rounds, each multiplying counter
 // words 0 and 2 by two fixed odd constants (32x32 -> 64 bits), exchanging and
 // xoring the halves with the other counter words and the round key; the round
-// key advances by two Weyl increments between rounds. The sweeps only consume
-// output word 0, so the last round's other words are left to dead-code
-// elimination.
+// key advances by two Weyl increments between rounds. A flip or initial-spin
+// draw of replica r is word r mod 4 of the counter (vertex, t, r / 4, stream),
+// so four replicas share one evaluation (replica_word); where only word 0 is
+// used, the last round's other words are left to dead-code elimination.
 #pragma once
 
 #include <cstdint>
@@ -58,6 +59,36 @@ __device__ __forceinline__ uint32_t philox4x32_10_word0(uint32_t x0, uint32_t x1
     x2 = n2;
   }
   return x0;
+}
+
+// All four words of Philox4x32-10 for counter (x0, x1, x2, x3).
+__device__ __forceinline__ uint4 philox4x32_10(uint32_t x0, uint32_t x1, uint32_t x2, uint32_t x3,
+                                               const PhiloxRounds& rk) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t pa = static_cast<uint64_t>(0xD2511F53u) * x0;
+    const uint64_t pb = static_cast<uint64_t>(0xCD9E8D57u) * x2;
+    const uint32_t n0 = static_cast<uint32_t>(pb >> 32) ^ x1 ^ rk.lo[r];
+    const uint32_t n2 = static_cast<uint32_t>(pa >> 32) ^ x3 ^ rk.hi[r];
+    x1 = static_cast<uint32_t>(pb);
+    x3 = static_cast<uint32_t>(pa);
+    x0 = n0;
+    x2 = n2;
+  }
+  return make_uint4(x0, x1, x2, x3);
+}
+
+// The draw of replica r for vertex o in sweep t on stream s (0 flips, 1
+// initial spins): word r mod 4 of counter (o, t, r / 4, s).
+__device__ __forceinline__ uint32_t replica_word(uint32_t o, uint32_t t, uint32_t replica,
+                                                 uint32_t stream, const PhiloxRounds& rk) {
+  const uint4 w = philox4x32_10(o, t, replica >> 2, stream, rk);
+  switch (replica & 3u) {
+    case 0: return w.x;
+    case 1: return w.y;
+    case 2: return w.z;
+    default: return w.w;
+  }
 }
 
 }  // namespace isingx

@@ -213,7 +213,7 @@ __device__ __forceinline__ bool flip_drawn(const DevGraph& d, int v, uint32_t o,
         (static_cast<unsigned long long>(a.thr) * __ldg(d.bias + v)) >> 7;
     thr = t > 0xffffffffull ? 0xffffffffu : static_cast<uint32_t>(t);
   }
-  return philox4x32_10_word0(o, a.t, a.replica, 0u, rk) < thr;
+  return replica_word(o, a.t, a.replica, 0u, rk) < thr;
 }
 
 // Eq. 2 under the max-cut sign (s <- -sign f, f = 0 keeps s), then the flip;
