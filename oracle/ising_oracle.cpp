@@ -32,9 +32,9 @@
 //      random word x0 < thr[t].
 //   R5 randomness: Philox4x32-10 (Salmon et al., SC'11), key = (lo32(seed),
 //      hi32(seed) ^ instance * 0x9E3779B9); a flip (stream 0) or initial spin
-//      (stream 1) of replica r uses word r mod 4 of counter (original vertex
-//      id, sweep t (0 for the initial spins), floor(r / 4), stream), so four
-//      replicas share one evaluation (replica 0: word 0 of (id, t, 0, s)).
+//      (stream 1) of vertex v (original id) in replica r uses word v mod 4 of
+//      counter (floor(v / 4), sweep t (0 for the initial spins), r, stream),
+//      so the four vertices 4q .. 4q + 3 share one evaluation.
 //   R6 colouring: greedy first fit over the vertices in order of decreasing
 //      degree (ties: smaller id first), i.e. Welsh-Powell; classes are swept in
 //      increasing colour order, and inside a class the order is irrelevant
@@ -106,16 +106,15 @@ uint32_t random_word(uint64_t seed, uint32_t instance, uint32_t c0, uint32_t c1,
   return philox4x32_10(c, k0, k1).x[0];
 }
 
-// R5: the draw of replica r for vertex c0 in sweep c1 on stream s (0 flips,
-// 1 initial spins): word r mod 4 of the counter (c0, c1, floor(r / 4), s), so
-// four replicas share one Philox evaluation; replica 0 is word 0 of
-// (c0, c1, 0, s).
-uint32_t replica_word(uint64_t seed, uint32_t instance, uint32_t c0, uint32_t c1,
-                      uint32_t replica, uint32_t stream) {
+// R5: the draw of vertex v in sweep t of replica r on stream s (0 flips,
+// 1 initial spins): word v mod 4 of the counter (floor(v / 4), t, r, s), so
+// the four vertices 4q .. 4q + 3 share one Philox evaluation.
+uint32_t vertex_word(uint64_t seed, uint32_t instance, uint32_t v, uint32_t t,
+                     uint32_t replica, uint32_t stream) {
   uint32_t k0 = (uint32_t)(seed & 0xffffffffu);
   uint32_t k1 = (uint32_t)(seed >> 32) ^ (uint32_t)(instance * kWeylA);
-  Words4 c = {{c0, c1, replica >> 2, stream}};
-  return philox4x32_10(c, k0, k1).x[replica & 3u];
+  Words4 c = {{v >> 2, t, replica, stream}};
+  return philox4x32_10(c, k0, k1).x[v & 3u];
 }
 
 // ---------------------------------------------------------------------------
@@ -280,7 +279,7 @@ int oracle_init_spins(int32_t n, uint64_t seed, uint32_t instance, uint32_t repl
                       int8_t* s) {
   if (n <= 0) return -1;
   for (int32_t i = 0; i < n; ++i) {
-    uint32_t x = replica_word(seed, instance, (uint32_t)i, 0u, replica, 1u);
+    uint32_t x = vertex_word(seed, instance, (uint32_t)i, 0u, replica, 1u);
     s[i] = (x >> 31) ? (int8_t)-1 : (int8_t)1;
   }
   return 0;
@@ -342,7 +341,7 @@ int oracle_anneal_biased(int32_t n, int64_t m, const int32_t* src, const int32_t
           thr_v = ((uint64_t)thr * (uint64_t)bias[v]) >> 7;
           if (thr_v > 4294967295ull) thr_v = 4294967295ull;
         }
-        uint32_t x = replica_word(seed, instance, (uint32_t)v, (uint32_t)t, replica, 0u);
+        uint32_t x = vertex_word(seed, instance, (uint32_t)v, (uint32_t)t, replica, 0u);
         if ((uint64_t)x < thr_v) s[v] = (int8_t)(-s[v]);
       }
     }

@@ -299,14 +299,17 @@ def test_anneal_reaches_known_optimum(make, optimum):
 def test_anneal_vs_brute_force_optimum(seed):
     g = synth.random_small_graph(12, 0.4, seed, weights="int8")
     opt = brute_force_max_cut(g)
+    # every run stays at or below the optimum, and a fair share reaches it:
+    # the four graphs' hit rates are about 0.39 to 0.98, so 60 runs give at
+    # least 23 hits on average and fewer than 10 has probability ~1e-4
     hits = 0
-    for r in range(10):
+    for r in range(60):
         s = oracle.anneal(g.n, g.src, g.dst, g.w, oracle.init_spins(g.n, 100 + r), seed=r,
                           p0=0.1, T=300)
         cut = direct_cut(g, s)
         assert cut <= opt
         hits += cut == opt
-    assert hits >= 3
+    assert hits >= 10
 
 
 def test_split_anneal_equals_whole():
@@ -446,12 +449,12 @@ def test_bias_threshold_clamps_at_the_top():
 
 
 @pytest.mark.parametrize("replica", range(8))
-def test_replica_draws_share_philox_evaluations(replica):
-    # R5: replica r's initial spin and flip use word r mod 4 of the counter
-    # (vertex, t, r // 4, stream), computed here with the KAT-pinned Philox.
-    n, seed, inst = 300, 0x0123456789ABCDEF, 3
+def test_vertex_draws_share_philox_evaluations(replica):
+    # R5: vertex v's initial spin and flip in replica r use word v mod 4 of the
+    # counter (v // 4, t, r, stream), computed here with the KAT-pinned Philox.
+    n, seed, inst = 301, 0x0123456789ABCDEF, 3
     key = [seed & 0xFFFFFFFF, ((seed >> 32) ^ (inst * 0x9E3779B9)) & 0xFFFFFFFF]
-    words = lambda v, t, s: oracle.philox([v, t, replica // 4, s], key)[replica % 4]
+    words = lambda v, t, s: oracle.philox([v // 4, t, replica, s], key)[v % 4]
     s0 = oracle.init_spins(n, seed, instance=inst, replica=replica)
     want0 = np.array([-1 if words(v, 0, 1) >> 31 else 1 for v in range(n)], np.int8)
     assert np.array_equal(s0, want0)
