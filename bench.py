@@ -41,7 +41,9 @@ def parse_args():
     ap.add_argument("--workload", default="torus1024",
                     choices=["torus1024", "zipf1m", "er800", "batched", "warmstart", "gnn"])
     ap.add_argument("--engine", default="auto",
-                    choices=["auto", "phase", "persistent", "dataflow", "persistent_grid", "itemflow"])
+                    choices=["auto", "phase", "persistent", "dataflow", "persistent_grid", "itemflow", "halo"])
+    ap.add_argument("--halo-sweeps", type=int, default=0,
+                    help="sweeps per exchange of the halo engine (0: automatic)")
     ap.add_argument("--mode", default="det", choices=["det", "racy"],
                     help="deterministic colour phases (bit-exact) or the racy pass")
     ap.add_argument("--e2e-steps", type=int, default=2)
@@ -638,10 +640,11 @@ def main():
               "persistent": P.ISING_ENGINE_PERSISTENT,
               "dataflow": P.ISING_ENGINE_DATAFLOW,
               "persistent_grid": P.ISING_ENGINE_PERSISTENT_GRID,
-              "itemflow": P.ISING_ENGINE_ITEMFLOW}[args.engine]
+              "itemflow": P.ISING_ENGINE_ITEMFLOW, "halo": P.ISING_ENGINE_HALO}[args.engine]
 
     h = P.ising_create(g.n, g.src, g.dst, g.w, stream=stream)
     P.ising_set_engine(h, engine)
+    P.ising_set_halo_sweeps(h, args.halo_sweeps)
     mode = P.ISING_MODE_RACY if args.mode == "racy" else P.ISING_MODE_DET
     colours = P.ising_num_colours(h)
     m = P.ising_num_edges(h)
@@ -686,6 +689,7 @@ def main():
     launches = P.ising_launch_count(h) - launches0
     engine_name = {P.ISING_ENGINE_PHASE: "phase", P.ISING_ENGINE_PERSISTENT_GRID: "persistent",
                    P.ISING_ENGINE_DATAFLOW: "dataflow", P.ISING_ENGINE_ITEMFLOW: "itemflow",
+                   P.ISING_ENGINE_HALO: "halo",
                    P.ISING_ENGINE_USED_BLOCK: "block"}.get(P.ising_engine_used(h), "unknown")
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = sum(step_ms)
@@ -713,6 +717,7 @@ def main():
             t0 = time.perf_counter()
             with P.ising_create(g.n, src_p, dst_p, w_p, stream=stream) as h2:
                 P.ising_set_engine(h2, engine)
+                P.ising_set_halo_sweeps(h2, args.halo_sweeps)
                 P.ising_init_random(h2, seed + k)
                 P.ising_anneal(h2, p0=p0, t_total=T, seed=seed + k, stream=stream, mode=mode)
                 P.ising_cut(h2)
@@ -732,6 +737,7 @@ def main():
             dist.destroy_process_group()
         return
 
+    halo = P.ising_halo_info(h) if engine_name == "halo" else None
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(g, sch, args.cpu_seconds)
@@ -753,7 +759,7 @@ def main():
             "workload": args.workload, "n": g.n, "m": m, "colours": colours,
             "sweeps": T, "p0": p0, "schedule": "linear",
             "mode": "racy" if args.mode == "racy" else "deterministic",
-            "engine": args.engine, "engine_used": engine_name,
+            "engine": args.engine, "engine_used": engine_name, "halo": halo,
             "weights": "int8" if w_bytes == 1 else "int32",
             "csr_entry_bytes": entry_bytes,
             "replicas_per_gpu": 1, "parallelism": f"replicas{world}",

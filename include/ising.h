@@ -97,10 +97,11 @@ enum {
 
 /* Which kernel engine runs a deterministic anneal (all give identical spins). */
 enum {
-  ISING_ENGINE_AUTO = 0,       /* with cooperative launches: ITEMFLOW for deterministic linear
-                                  anneals of graphs without sliced rows (unless the graph is small
-                                  enough for PERSISTENT's one-block form), else PERSISTENT;
-                                  without: PHASE */
+  ISING_ENGINE_AUTO = 0,       /* with cooperative launches, for deterministic linear anneals:
+                                  PERSISTENT's one-block form for small graphs, else HALO when its
+                                  plan exists and repeats at most 1.6x the work, else ITEMFLOW for
+                                  graphs without sliced rows, else PERSISTENT; racy and N-flip
+                                  anneals: PERSISTENT; without cooperative launches: PHASE */
   ISING_ENGINE_PHASE = 1,      /* one kernel launch per colour class */
   ISING_ENGINE_PERSISTENT = 2, /* one cooperative launch per anneal call, bounded grid barrier;
                                   deterministic anneals of a graph with int8 weights and at most
@@ -111,12 +112,22 @@ enum {
                                   neighbour read waits (bounded) until the neighbour carries the
                                   update the colour order requires; racy mode runs as PERSISTENT */
   ISING_ENGINE_PERSISTENT_GRID = 4, /* PERSISTENT without the one-block form for small graphs */
-  ISING_ENGINE_ITEMFLOW = 5    /* one cooperative launch per anneal call without barriers: each
+  ISING_ENGINE_ITEMFLOW = 5,   /* one cooperative launch per anneal call without barriers: each
                                   warp's work item waits (bounded) for the items holding its
                                   rows' neighbours to finish the sweep the colour order requires
                                   (per-item counters, release/acquire); for graphs whose rows
                                   are not sliced across warps, deterministic linear schedule;
                                   otherwise runs as PERSISTENT_GRID */
+  ISING_ENGINE_HALO = 7        /* one cooperative launch per anneal call, one block per SM: the
+                                  graph is cut into one part per block (recursive breadth-first
+                                  bisection); a block keeps every vertex within D = S * K hops of
+                                  its part (K colour classes, S sweeps per exchange) in shared
+                                  memory, runs S sweeps there with block barriers only, then
+                                  exchanges its part's spins with the parts in its halo (bounded
+                                  release/acquire waits). For graphs with at most 4 colours, rows
+                                  of at most 63 entries, int8 weights and regions that fit in
+                                  shared memory; deterministic linear schedule; otherwise runs as
+                                  ITEMFLOW */
 };
 
 /* ising_create flags. */
@@ -250,6 +261,30 @@ int ising_num_edges(ising_graph* g, int64_t* out_m);
 /* ising_set_engine -- choose the deterministic-mode kernel engine
  * (ISING_ENGINE_*). Default ISING_ENGINE_AUTO. */
 int ising_set_engine(ising_graph* g, int engine);
+
+/* ising_set_halo_sweeps -- sweeps S per exchange of ISING_ENGINE_HALO
+ * (1 .. 16 / K), or 0 for the automatic choice (S = 2, or S = 1 when the S = 2
+ * plan does not fit or repeats more than 1.6x the work). The plan is rebuilt at the next anneal that uses the engine.
+ * ISING_EINVAL for S > 16. */
+int ising_set_halo_sweeps(ising_graph* g, uint32_t sweeps_per_exchange);
+
+/* ising_halo_info -- plans the halo engine if needed and reports its parts
+ * (blocks), sweeps per exchange, dynamic shared memory per block and the
+ * largest ratio of rows a block updates to the rows it owns. ISING_ESTATE if
+ * the graph does not qualify (see ISING_ENGINE_HALO); any pointer may be null. */
+int ising_halo_info(ising_graph* g, int32_t* out_parts, int32_t* out_sweeps,
+                    int32_t* out_smem_bytes, double* out_work_ratio);
+
+/* ising_plan_halo -- host only (no device): the halo engine's partition and
+ * plan for a graph given as in ising_create, with `parts` parts and S =
+ * sweeps_per_exchange (1 .. 16). out_part (n entries, by vertex id; may be
+ * null) receives every vertex's part whether or not a plan exists. Returns
+ * ISING_OK with the plan's shared memory per block and largest work ratio
+ * (pointers may be null), ISING_ESTATE if the graph does not qualify, or the
+ * ising_create errors. */
+int ising_plan_halo(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, const int32_t* w,
+                    int32_t parts, uint32_t sweeps_per_exchange, int32_t* out_part,
+                    int32_t* out_smem_bytes, double* out_work_ratio);
 
 /* ------------------------------------------------------------------------
  * Batched annealing of many independent instances.
@@ -410,7 +445,7 @@ void ising_gnn_destroy(ising_gnn* net);
 
 /* ising_engine_used -- the engine the last anneal call ran: ISING_ENGINE_PHASE,
  * ISING_ENGINE_PERSISTENT_GRID (the persistent grid-barrier kernel),
- * ISING_ENGINE_DATAFLOW, ISING_ENGINE_ITEMFLOW or ISING_ENGINE_USED_BLOCK
+ * ISING_ENGINE_DATAFLOW, ISING_ENGINE_ITEMFLOW, ISING_ENGINE_HALO or ISING_ENGINE_USED_BLOCK
  * (PERSISTENT's one-block form); -1 before the first anneal. */
 #define ISING_ENGINE_USED_BLOCK 6
 int ising_engine_used(ising_graph* g, int32_t* out);

@@ -38,6 +38,7 @@ ISING_ENGINE_PERSISTENT = 2
 ISING_ENGINE_DATAFLOW = 3
 ISING_ENGINE_PERSISTENT_GRID = 4
 ISING_ENGINE_ITEMFLOW = 5
+ISING_ENGINE_HALO = 7
 ISING_CREATE_WEIGHTS_I32 = 1
 ISING_STATIC_MAX_VERTICES = 1 << 24
 
@@ -53,7 +54,7 @@ EXPORTS = (
     "ising_set_flip_bias", "ising_get_flip_bias", "ising_gnn_create", "ising_gnn_set_params",
     "ising_gnn_get_params", "ising_gnn_forward", "ising_gnn_gradients", "ising_gnn_train_step",
     "ising_gnn_warm_start", "ising_gnn_launch_count", "ising_gnn_destroy", "ising_debug_fault",
-    "ising_engine_used",
+    "ising_engine_used", "ising_set_halo_sweeps", "ising_halo_info", "ising_plan_halo",
 )
 ISING_ENGINE_USED_BLOCK = 6
 ISING_FAULT_NONE = 0
@@ -137,6 +138,12 @@ def lib():
         L.ising_gnn_destroy.restype = None
         L.ising_debug_fault.argtypes = [vp, ctypes.c_int, ctypes.c_uint64]
         L.ising_engine_used.argtypes = [vp, ctypes.POINTER(ctypes.c_int32)]
+        L.ising_set_halo_sweeps.argtypes = [vp, ctypes.c_uint32]
+        L.ising_plan_halo.argtypes = [ctypes.c_int32, ctypes.c_int64, vp, vp, vp, ctypes.c_int32,
+                                      ctypes.c_uint32, vp, ctypes.POINTER(ctypes.c_int32),
+                                      ctypes.POINTER(ctypes.c_double)]
+        L.ising_halo_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                      ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)]
         L.ising_strerror.argtypes = [ctypes.c_int]
         L.ising_strerror.restype = ctypes.c_char_p
         for name in EXPORTS:
@@ -346,6 +353,41 @@ def ising_debug_fault(g: IsingGraph, kind: int, wait_budget_ns: int = 0) -> None
 
 def ising_set_engine(g: IsingGraph, engine: int) -> None:
     _check(lib().ising_set_engine(g.ptr, engine), "ising_set_engine")
+
+
+def ising_set_halo_sweeps(g: IsingGraph, sweeps_per_exchange: int) -> None:
+    """Sweeps per exchange of the halo engine (0: automatic)."""
+    _check(lib().ising_set_halo_sweeps(g.ptr, sweeps_per_exchange), "ising_set_halo_sweeps")
+
+
+def ising_plan_halo(n: int, src, dst, w, parts: int, sweeps_per_exchange: int):
+    """Host only: (part of every vertex, plan dict or None if the graph does not
+    qualify) -- the halo engine's partition and plan without a device."""
+    src = np.ascontiguousarray(src, dtype=np.int32)
+    dst = np.ascontiguousarray(dst, dtype=np.int32)
+    w = np.ascontiguousarray(w, dtype=np.int32)
+    out = np.empty(max(n, 1), np.int32)
+    smem, ratio = ctypes.c_int32(), ctypes.c_double()
+    rc = lib().ising_plan_halo(n, src.size, src.ctypes.data, dst.ctypes.data, w.ctypes.data, parts,
+                               sweeps_per_exchange, out.ctypes.data, ctypes.byref(smem), ctypes.byref(ratio))
+    if rc == ISING_ESTATE:
+        return out[:n], None
+    _check(rc, "ising_plan_halo")
+    return out[:n], {"smem_bytes": smem.value, "work_ratio": ratio.value}
+
+
+def ising_halo_info(g: IsingGraph) -> dict | None:
+    """The halo engine's plan (parts, sweeps per exchange, shared memory per
+    block, largest work ratio), or None if the graph does not qualify."""
+    parts, sweeps, smem = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    ratio = ctypes.c_double()
+    rc = lib().ising_halo_info(g.ptr, ctypes.byref(parts), ctypes.byref(sweeps), ctypes.byref(smem),
+                               ctypes.byref(ratio))
+    if rc == ISING_ESTATE:
+        return None
+    _check(rc, "ising_halo_info")
+    return {"parts": parts.value, "sweeps_per_exchange": sweeps.value, "smem_bytes": smem.value,
+            "work_ratio": ratio.value}
 
 
 def ising_energy_csr_static(n: int, row_ptr, col, w, spins, out, stream=None) -> None:

@@ -20,8 +20,8 @@ OUT = os.path.join(HERE, "libising_gb300.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["anneal.cu", "host_graph.cpp", "energy_static.cu", "batch.cu", "gnn.cu"]
-HEADERS = ["host_graph.h", "philox.cuh", "sweep.cuh", "graph_handle.h", "block.cuh"]
+SOURCES = ["anneal.cu", "host_graph.cpp", "halo_plan.cpp", "energy_static.cu", "batch.cu", "gnn.cu"]
+HEADERS = ["host_graph.h", "philox.cuh", "sweep.cuh", "graph_handle.h", "block.cuh", "halo.cuh"]
 
 
 def nvcc() -> str:

@@ -34,6 +34,7 @@
 #include "sweep.cuh"
 #include "block.cuh"
 #include "graph_handle.h"
+#include "halo.cuh"
 
 using isingx::HostGraph;
 using isingx::PhiloxKey;
@@ -45,6 +46,7 @@ namespace {
 using isingx::BarrierState;
 using isingx::DevGraph;
 using isingx::SweepArgs;
+using isingx::sweep_args;
 using isingx::kPassDet;
 using isingx::kPassEnergy;
 using isingx::kPassFlow;
@@ -53,6 +55,9 @@ using isingx::kPassRacy;
 constexpr int kBlock = 256;
 constexpr int kWarpsPerBlock = kBlock / 32;
 constexpr int kPersistBlock = 512;
+// AUTO takes the halo engine while no block updates more than this many
+// times the rows it owns per sweep
+constexpr double kHaloAutoRatio = 1.6;
 
 // Item kernel of the per-launch engine. Deterministic sweeps launch it once
 // per colour class (phase_begin + 1 == phase_end); the racy mode launches it
@@ -89,30 +94,19 @@ __global__ void __launch_bounds__(kBlock, 4)
   }
 }
 
-// Arguments of sweep t of a linear schedule of T sweeps starting at threshold
-// T0 (ISING_SCHED_LINEAR in ising.h).
-__device__ __forceinline__ SweepArgs sweep_args(uint64_t t, uint64_t T, uint64_t T0,
-                                                uint32_t replica) {
-  SweepArgs sa;
-  sa.class_lo = 0;
-  sa.par_cur = 0;
-  sa.t = static_cast<uint32_t>(t);
-  sa.replica = replica;
-  sa.thr = (T <= 1) ? 0u : static_cast<uint32_t>((T0 * (T - 1 - t)) / (T - 1));
-  return sa;
-}
-
 // First item of colour class cls for this warp. Deterministic passes: item
 // warp of every class (a barrier follows each class). The racy pass walks
-// all classes without a barrier, so there items are dealt round-robin over
-// the whole sweep -- item i, counted across classes, belongs to warp
-// i mod nwarps -- and a warp gets as many items as any other instead of one
-// in every class.
+// all classes without a barrier; when the sweep has at least as many items as
+// warps they are dealt round-robin over the whole sweep -- item i, counted
+// across classes, belongs to warp i mod nwarps -- so a warp gets as many items
+// as any other instead of one in every class. With fewer items than warps
+// that dealing would run every class at once (a synchronous update, which can
+// oscillate), so there a warp keeps item warp of every class, in class order.
 template <int PASS>
 __device__ __forceinline__ int class_start(const int32_t* phase_items, int cls, int warp,
-                                           int nwarps) {
+                                           int nwarps, bool rotate) {
   const int ib = __ldg(phase_items + cls);
-  if (PASS != kPassRacy) return ib + warp;
+  if (PASS != kPassRacy || !rotate) return ib + warp;
   int r = (warp - ib) % nwarps;
   if (r < 0) r += nwarps;
   return ib + r;
@@ -121,8 +115,8 @@ __device__ __forceinline__ int class_start(const int32_t* phase_items, int cls, 
 // The warp's first item of colour class cls, or an empty item if it has none.
 template <int PASS>
 __device__ __forceinline__ WorkItem first_item(const DevGraph& d, const int32_t* phase_items,
-                                               int cls, int warp, int nwarps) {
-  const int i = class_start<PASS>(phase_items, cls, warp, nwarps);
+                                               int cls, int warp, int nwarps, bool rotate) {
+  const int i = class_start<PASS>(phase_items, cls, warp, nwarps, rotate);
   WorkItem it = {0, 0, 0, 0};
   if (i < __ldg(phase_items + cls + 1)) it = d.items[i];
   return it;
@@ -148,12 +142,13 @@ __global__ void __launch_bounds__(kPersistBlock, 2)
   uint32_t k = 0;
   int c = 0;
   SweepArgs a = sweep_args(t_begin + 0, T, T0, replica);
-  int ib = class_start<PASS>(phase_items, 0, warp, nwarps), ie = __ldg(phase_items + 1);
+  const bool rotate = __ldg(phase_items + num_phases) >= nwarps;
+  int ib = class_start<PASS>(phase_items, 0, warp, nwarps, rotate), ie = __ldg(phase_items + 1);
   isingx::Staged<PACKED> st;
   bool have = ib < ie;
   if (have) isingx::stage_item<PACKED>(d, d.items[ib], a, rk, lane, st);
   // the warp's first item of the following class, loaded one class ahead
-  WorkItem next = first_item<PASS>(d, phase_items, num_phases > 1 ? 1 : 0, warp, nwarps);
+  WorkItem next = first_item<PASS>(d, phase_items, num_phases > 1 ? 1 : 0, warp, nwarps, rotate);
   // failure-detection tests: this block may skip its first barrier arrival
   bool skip_arrival = bs->skip_block == static_cast<int>(blockIdx.x) + 1;
   for (;;) {
@@ -190,11 +185,11 @@ __global__ void __launch_bounds__(kPersistBlock, 2)
     } else {
       ++c;
     }
-    ib = class_start<PASS>(phase_items, c, warp, nwarps);
+    ib = class_start<PASS>(phase_items, c, warp, nwarps, rotate);
     ie = __ldg(phase_items + c + 1);
     have = ib < ie;
     if (have) isingx::stage_item<PACKED>(d, next, a, rk, lane, st);
-    next = first_item<PASS>(d, phase_items, c + 1 < num_phases ? c + 1 : 0, warp, nwarps);
+    next = first_item<PASS>(d, phase_items, c + 1 < num_phases ? c + 1 : 0, warp, nwarps, rotate);
     if (sync) {
       target += gridDim.x;
       if (!isingx::barrier_wait(bs, target)) return;
@@ -347,7 +342,7 @@ __global__ void nflip_kernel(DevGraph d, const int32_t* pos, unsigned* bitmap, i
 __global__ void init_random_kernel(int8_t* spins, const int32_t* orig, int n,
                                    isingx::PhiloxRounds rk, uint32_t replica) {
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-    const uint32_t x = isingx::replica_word(static_cast<uint32_t>(orig[p]), 0u, replica, 1u, rk);
+    const uint32_t x = isingx::vertex_word(static_cast<uint32_t>(orig[p]), 0u, replica, 1u, rk);
     spins[p] = static_cast<int8_t>(isingx::state_byte((x >> 31) ? -1 : 1, 0));
   }
 }
@@ -407,9 +402,26 @@ void free_device(ising_graph* g) {
                   g->d_class_begin, g->d_trace, g->d_nflip_bits, g->d_nflip_list,
                   g->d_bias,    g->d_rowid, g->d_block_words, g->d_block_chunk_off,
                   g->d_block_chunk_len, g->d_block_class_chunk, g->d_dep_ptr, g->d_deps,
-                  g->d_done};
+                  g->d_done, g->d_halo_hdr, g->d_halo_words, g->d_halo_slices, g->d_halo_gpos,
+                  g->d_halo_imports, g->d_halo_nbrs, g->d_halo_exports, g->d_halo_quads, g->d_halo_flags,
+                  g->d_spins2};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+}
+
+// Drop the halo plan (its device arrays); the next anneal that asks for the
+// engine plans again.
+void free_halo(ising_graph* g) {
+  void* ptrs[] = {g->d_halo_hdr, g->d_halo_words, g->d_halo_slices, g->d_halo_gpos,
+                  g->d_halo_imports, g->d_halo_nbrs, g->d_halo_exports, g->d_halo_quads, g->d_halo_flags,
+                  g->d_spins2};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  g->d_halo_hdr = g->d_halo_words = g->d_halo_slices = g->d_halo_gpos = nullptr;
+  g->d_halo_imports = g->d_halo_nbrs = g->d_halo_exports = g->d_halo_quads = nullptr;
+  g->d_halo_flags = nullptr;
+  g->d_spins2 = nullptr;
+  g->halo_state = 0;
 }
 
 // Latch a CUDA failure in the handle.
@@ -614,6 +626,107 @@ cudaError_t launch_flow(ising_graph* g, uint64_t t_begin, uint32_t sweeps, uint6
   return launch_flow_t<false>(g, t_begin, sweeps, T, T0, replica, par0, rk);
 }
 
+// Plan the halo engine once (host_graph.h, build_halo_plan): one part per SM,
+// the requested sweeps per exchange, or S = 2 unless that plan does not fit
+// or repeats more than kHaloAutoRatio times the work and S = 1 fits; uploads
+// the tables. halo_state 1 on success, -1 if no plan is possible;
+// returns a CUDA error only.
+cudaError_t plan_halo(ising_graph* g) {
+  if (g->halo_state != 0) return cudaSuccess;
+  g->halo_state = -1;
+  if (!g->host) return cudaSuccess;
+  isingx::HaloPlan hp;
+  try {
+    if (g->halo_sweeps > 0) {
+      isingx::build_halo_plan(*g->host, g->num_sms, g->halo_sweeps, &hp);
+    } else {
+      isingx::build_halo_plan(*g->host, g->num_sms, 2, &hp);
+      if (!hp.ok || hp.max_work_ratio > kHaloAutoRatio) {
+        isingx::HaloPlan one;
+        isingx::build_halo_plan(*g->host, g->num_sms, 1, &one);
+        if (one.ok) hp = std::move(one);
+      }
+    }
+  } catch (const std::bad_alloc&) {
+    return cudaSuccess;
+  }
+  if (!hp.ok) return cudaSuccess;
+  auto kernel = isingx::halo_kernel;
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, hp.smem_bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cudaSuccess;  // the device cannot give this much shared memory: no plan
+  }
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, isingx::kHaloBlock, hp.smem_bytes);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaSuccess;
+  const size_t N = static_cast<size_t>(g->n);
+  do {
+    if ((e = alloc_copy(&g->d_halo_hdr, hp.hdr.data(), hp.hdr.size(), g->stream)) != cudaSuccess) break;
+    if ((e = alloc_copy(&g->d_halo_words, hp.words.data(), hp.words.size(), g->stream)) != cudaSuccess) break;
+    if ((e = alloc_copy(&g->d_halo_slices, hp.slices.data(), hp.slices.size(), g->stream)) != cudaSuccess) break;
+    if ((e = alloc_copy(&g->d_halo_gpos, hp.gpos.data(), hp.gpos.size(), g->stream)) != cudaSuccess) break;
+    if ((e = alloc_copy(&g->d_halo_imports, hp.imports.data(), std::max<size_t>(1, hp.imports.size()),
+                        g->stream)) != cudaSuccess) break;
+    if ((e = alloc_copy(&g->d_halo_nbrs, hp.nbrs.data(), std::max<size_t>(1, hp.nbrs.size()),
+                        g->stream)) != cudaSuccess) break;
+    if ((e = alloc_copy(&g->d_halo_exports, hp.exports.data(), std::max<size_t>(2, hp.exports.size()),
+                        g->stream)) != cudaSuccess) break;
+    if ((e = alloc_copy(&g->d_halo_quads, hp.quads.data(), std::max<size_t>(3, hp.quads.size()),
+                        g->stream)) != cudaSuccess) break;
+    if ((e = alloc_copy<unsigned>(&g->d_halo_flags, nullptr,
+                                  static_cast<size_t>(hp.parts) * isingx::kHaloFlagStride, g->stream)) != cudaSuccess)
+      break;
+    if ((e = alloc_copy<int8_t>(&g->d_spins2, nullptr, N + 1, g->stream)) != cudaSuccess) break;
+    // the host vectors are freed on return: wait for the copies
+    e = cudaStreamSynchronize(g->stream);
+  } while (false);
+  if (e != cudaSuccess) {
+    free_halo(g);
+    g->halo_state = -1;
+    return e == cudaErrorMemoryAllocation ? cudaSuccess : e;
+  }
+  g->halo_state = 1;
+  g->halo_parts = hp.parts;
+  g->halo_S = hp.sweeps_per_epoch;
+  g->halo_smem = hp.smem_bytes;
+  g->halo_ratio = hp.max_work_ratio;
+  return cudaSuccess;
+}
+
+cudaError_t launch_halo(ising_graph* g, uint64_t t_begin, uint32_t sweeps, uint64_t T, uint64_t T0,
+                        uint32_t replica, const isingx::PhiloxRounds& rk_in) {
+  cudaError_t e;
+  if ((e = barrier_init(g)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(g->d_halo_flags, 0,
+                           sizeof(unsigned) * isingx::kHaloFlagStride * static_cast<size_t>(g->halo_parts),
+                           g->stream)) != cudaSuccess)
+    return e;
+  DevGraph d = g->dev();
+  isingx::HaloArgs h{};
+  h.hdr = g->d_halo_hdr;
+  h.words = g->d_halo_words;
+  h.slices = g->d_halo_slices;
+  h.gpos = g->d_halo_gpos;
+  h.imports = g->d_halo_imports;
+  h.exports = g->d_halo_exports;
+  h.quads = g->d_halo_quads;
+  h.nbrs = g->d_halo_nbrs;
+  h.buf1 = g->d_spins2;
+  h.flags = g->d_halo_flags;
+  h.error = &g->d_barrier->error;
+  h.budget = g->wait_budget_ns > 0 ? static_cast<long long>(g->wait_budget_ns) : isingx::kBarrierBudgetNs;
+  h.skip_block = g->fault_kind == ISING_FAULT_SKIP_ARRIVAL ? 1 : 0;
+  h.classes = g->num_colours;
+  h.sweeps_per_epoch = g->halo_S;
+  isingx::PhiloxRounds rk = rk_in;
+  void* args[] = {&d, &h, &t_begin, &sweeps, &T, &T0, &replica, &rk};
+  g->launches++;
+  return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(isingx::halo_kernel), dim3(g->halo_parts),
+                                     dim3(isingx::kHaloBlock), args, static_cast<size_t>(g->halo_smem), g->stream);
+}
+
 // Enqueue twice the energy into *slot (device), no host synchronisation.
 int enqueue_energy(ising_graph* g, unsigned long long* slot) {
   ISING_CUDA(g, cudaMemsetAsync(slot, 0, sizeof(unsigned long long), g->stream));
@@ -707,6 +820,10 @@ int ising_create(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, c
   try {
     if (g->packed) isingx::build_block_plan(hg, &block);
     have_deps = isingx::build_item_deps(hg, plan, &dep_ptr, &deps);
+    // graphs the halo engine may take keep their host graph for its plan
+    if (g->packed && !block.ok && hg.num_colours <= isingx::kHaloMaxClasses &&
+        hg.max_degree <= isingx::kHaloMaxWidth && hg.n >= 64 * g->num_sms)
+      g->host.reset(new HostGraph(hg));
   } catch (const std::bad_alloc&) {
     delete g;
     return ISING_ENOMEM;
@@ -879,13 +996,17 @@ static int anneal_impl(ising_graph* g, const ising_schedule* sched, uint32_t swe
     // small graphs: the block engine (inside PERSISTENT); graphs without
     // sliced rows: the item-dataflow engine for deterministic linear
     // schedules; else the grid barrier
-    if (!coop)
+    if (!coop) {
       engine = ISING_ENGINE_PHASE;
-    else if (g->itemflow_ok && !g->block_ok && mode == ISING_MODE_DET &&
-             sched->kind == ISING_SCHED_LINEAR)
-      engine = ISING_ENGINE_ITEMFLOW;
-    else
+    } else if (!g->block_ok && mode == ISING_MODE_DET && sched->kind == ISING_SCHED_LINEAR) {
+      ISING_CUDA(g, plan_halo(g));
+      if (g->halo_state == 1 && g->halo_ratio <= kHaloAutoRatio)
+        engine = ISING_ENGINE_HALO;
+      else
+        engine = g->itemflow_ok ? ISING_ENGINE_ITEMFLOW : ISING_ENGINE_PERSISTENT;
+    } else {
       engine = ISING_ENGINE_PERSISTENT;
+    }
   }
   // every sweep updates every vertex once, flipping its update parity
   const int par0 = g->parity;
@@ -899,6 +1020,17 @@ static int anneal_impl(ising_graph* g, const ising_schedule* sched, uint32_t swe
     g->engine_used = ISING_ENGINE_DATAFLOW;
     ISING_CUDA(g, launch_flow(g, sched->t_begin, sweeps, sched->t_total, T0, sched->replica, par0, rk));
     return ISING_OK;
+  }
+  if (engine == ISING_ENGINE_HALO) {
+    if (mode == ISING_MODE_DET && !nflip) {
+      ISING_CUDA(g, plan_halo(g));
+      if (g->halo_state == 1) {
+        g->engine_used = ISING_ENGINE_HALO;
+        ISING_CUDA(g, launch_halo(g, sched->t_begin, sweeps, sched->t_total, T0, sched->replica, rk));
+        return ISING_OK;
+      }
+    }
+    engine = ISING_ENGINE_ITEMFLOW;  // racy, N-flip or no plan
   }
   if (engine == ISING_ENGINE_ITEMFLOW) {
     if (mode == ISING_MODE_DET && !nflip && g->itemflow_ok) {
@@ -1067,6 +1199,31 @@ int ising_plan_colouring(int32_t n, int64_t m, const int32_t* src, const int32_t
   return ISING_OK;
 }
 
+int ising_plan_halo(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, const int32_t* w,
+                    int32_t parts, uint32_t sweeps_per_exchange, int32_t* out_part,
+                    int32_t* out_smem_bytes, double* out_work_ratio) {
+  if (parts < 1 || sweeps_per_exchange < 1 || sweeps_per_exchange > static_cast<uint32_t>(isingx::kHaloMaxDepth))
+    return ISING_EINVAL;
+  HostGraph hg;
+  isingx::HaloPlan hp;
+  std::vector<int32_t> part;
+  try {
+    const int rc = isingx::build_host_graph(n, m, src, dst, w, &hg);
+    if (rc != ISING_OK) return rc;
+    if (out_part != nullptr) {
+      isingx::bisect_parts(hg, parts, &part);
+      for (int32_t o = 0; o < hg.n; ++o) out_part[o] = part[static_cast<size_t>(hg.pos[static_cast<size_t>(o)])];
+    }
+    isingx::build_halo_plan(hg, parts, static_cast<int32_t>(sweeps_per_exchange), &hp);
+  } catch (const std::bad_alloc&) {
+    return ISING_ENOMEM;
+  }
+  if (!hp.ok) return ISING_ESTATE;
+  if (out_smem_bytes) *out_smem_bytes = hp.smem_bytes;
+  if (out_work_ratio) *out_work_ratio = hp.max_work_ratio;
+  return ISING_OK;
+}
+
 int ising_launch_count(ising_graph* g, uint64_t* out) {
   if (g == nullptr || out == nullptr) return ISING_EINVAL;
   *out = g->launches;
@@ -1093,9 +1250,34 @@ int ising_set_engine(ising_graph* g, int engine) {
   if (g == nullptr) return ISING_EINVAL;
   if (engine != ISING_ENGINE_AUTO && engine != ISING_ENGINE_PHASE &&
       engine != ISING_ENGINE_PERSISTENT && engine != ISING_ENGINE_DATAFLOW &&
-      engine != ISING_ENGINE_PERSISTENT_GRID && engine != ISING_ENGINE_ITEMFLOW)
+      engine != ISING_ENGINE_PERSISTENT_GRID && engine != ISING_ENGINE_ITEMFLOW &&
+      engine != ISING_ENGINE_HALO)
     return ISING_EINVAL;
   g->engine = engine;
+  return ISING_OK;
+}
+
+int ising_set_halo_sweeps(ising_graph* g, uint32_t sweeps_per_exchange) {
+  int rc = enter(g);
+  if (rc != ISING_OK) return rc;
+  if (sweeps_per_exchange > static_cast<uint32_t>(isingx::kHaloMaxDepth)) return ISING_EINVAL;
+  if (static_cast<int>(sweeps_per_exchange) == g->halo_sweeps) return ISING_OK;
+  ISING_CUDA(g, cudaStreamSynchronize(g->stream));  // no launch still reads the old plan
+  free_halo(g);
+  g->halo_sweeps = static_cast<int>(sweeps_per_exchange);
+  return ISING_OK;
+}
+
+int ising_halo_info(ising_graph* g, int32_t* out_parts, int32_t* out_sweeps, int32_t* out_smem_bytes,
+                    double* out_work_ratio) {
+  int rc = enter(g);
+  if (rc != ISING_OK) return rc;
+  ISING_CUDA(g, plan_halo(g));
+  if (g->halo_state != 1) return ISING_ESTATE;
+  if (out_parts) *out_parts = g->halo_parts;
+  if (out_sweeps) *out_sweeps = g->halo_S;
+  if (out_smem_bytes) *out_smem_bytes = g->halo_smem;
+  if (out_work_ratio) *out_work_ratio = g->halo_ratio;
   return ISING_OK;
 }
 

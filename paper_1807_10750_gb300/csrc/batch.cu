@@ -50,10 +50,11 @@ struct BatchDev {
   const int32_t* orig;       // position -> vertex id within the instance
   const int32_t* class_pos;  // per instance: first position of each class, then n
   uint8_t* spins;            // replica bits per position
+  uint8_t* flips;            // the sweep's flip bits per vertex id (bit r = replica r)
 };
 
-// Philox4x32-10, all four words; replica r draws word r mod 4 of counter
-// (vertex, t, r / 4, stream), so one evaluation serves four replicas.
+// Philox4x32-10, all four words; vertex o of replica r draws word o mod 4
+// of counter (o / 4, t, r, stream), so one evaluation serves four vertices.
 __device__ __forceinline__ uint4 batch_philox(uint32_t x0, uint32_t x1, uint32_t x2,
                                               uint32_t x3, uint32_t ka, uint32_t kb) {
 #pragma unroll
@@ -96,6 +97,22 @@ __global__ void __launch_bounds__(BLOCK)
     for (uint32_t k = 0; k < sweeps; ++k) {
       const uint64_t t = t_begin + k;
       const uint32_t thr = (T <= 1) ? 0u : static_cast<uint32_t>((T0 * (T - 1 - t)) / (T - 1));
+      // the sweep's flips, four vertices per Philox evaluation and replica
+      // (R5), into the instance's flip bytes (read back through L2 below)
+      if (thr != 0u) {
+        for (int q = threadIdx.x; q < (G.n + 3) / 4; q += BLOCK) {
+          uint32_t fb = 0;  // byte k: vertex 4q + k, bit r: replica r
+          for (int r = 0; r < replicas; ++r) {
+            const uint4 x = batch_philox(static_cast<uint32_t>(q), static_cast<uint32_t>(t),
+                                         static_cast<uint32_t>(r), 0u, ka, kb);
+            fb |= (static_cast<uint32_t>(x.x < thr) << r) | (static_cast<uint32_t>(x.y < thr) << (8 + r)) |
+                  (static_cast<uint32_t>(x.z < thr) << (16 + r)) | (static_cast<uint32_t>(x.w < thr) << (24 + r));
+          }
+          uint8_t* fq = d.flips + G.vtx_base + 4 * q;
+          for (int k = 0; k < 4 && 4 * q + k < G.n; ++k) fq[k] = static_cast<uint8_t>(fb >> (8 * k));
+        }
+        __syncthreads();
+      }
       for (int c = 0; c < G.num_classes; ++c) {
         const int ce = __ldg(cls + c + 1);
         for (int v = __ldg(cls + c) + threadIdx.x; v < ce; v += BLOCK) {
@@ -142,26 +159,18 @@ __global__ void __launch_bounds__(BLOCK)
           // f_r = sum_j w_j s_j = wsum - 2 * sum over neighbours with spin -1
           const int own = sp[v];
           int nb = 0;
-          const uint32_t o = static_cast<uint32_t>(__ldg(d.orig + G.vtx_base + v));
+          const int fl = thr != 0u ? __ldcg(d.flips + G.vtx_base + __ldg(d.orig + G.vtx_base + v)) : 0;
 #pragma unroll
-          for (int q = 0; q < 2; ++q) {
-            if (4 * q >= replicas) break;
-            uint4 x = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
-            if (thr != 0u) x = batch_philox(o, static_cast<uint32_t>(t), static_cast<uint32_t>(q), 0u, ka, kb);
-            const uint32_t xs[4] = {x.x, x.y, x.z, x.w};
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-              const int r = 4 * q + k;
-              if (r >= replicas) break;
-              const int f = wsum - 2 * acc[r];
-              int bit = (own >> r) & 1;  // 1 = spin -1
-              if (f > 0)
-                bit = 1;
-              else if (f < 0)
-                bit = 0;
-              if (xs[k] < thr) bit ^= 1;
-              nb |= bit << r;
-            }
+          for (int r = 0; r < 8; ++r) {
+            if (r >= replicas) break;
+            const int f = wsum - 2 * acc[r];
+            int bit = (own >> r) & 1;  // 1 = spin -1
+            if (f > 0)
+              bit = 1;
+            else if (f < 0)
+              bit = 0;
+            bit ^= (fl >> r) & 1;
+            nb |= bit << r;
           }
           sp[v] = static_cast<uint8_t>(nb);
         }
@@ -180,11 +189,11 @@ __global__ void batch_init_kernel(BatchDev d, uint32_t seed_lo, uint32_t seed_hi
   for (int v = threadIdx.x; v < G.n; v += blockDim.x) {
     const uint32_t o = static_cast<uint32_t>(d.orig[G.vtx_base + v]);
     int byte = 0;
-    for (int q = 0; 4 * q < replicas; ++q) {
-      const uint4 x = batch_philox(o, 0u, static_cast<uint32_t>(q), 1u, seed_lo, kb);
-      const uint32_t xs[4] = {x.x, x.y, x.z, x.w};
-      for (int k = 0; k < 4 && 4 * q + k < replicas; ++k)
-        byte |= static_cast<int>(xs[k] >> 31) << (4 * q + k);
+    for (int r = 0; r < replicas; ++r) {
+      const uint4 x = batch_philox(o >> 2, 0u, static_cast<uint32_t>(r), 1u, seed_lo, kb);
+      const uint32_t k = o & 3u;
+      const uint32_t word = k == 0u ? x.x : (k == 1u ? x.y : (k == 2u ? x.z : x.w));
+      byte |= static_cast<int>(word >> 31) << r;
     }
     d.spins[G.vtx_base + v] = static_cast<uint8_t>(byte);
   }
@@ -252,6 +261,7 @@ struct ising_batch {
   int32_t* d_orig = nullptr;
   int32_t* d_class_pos = nullptr;
   uint8_t* d_spins = nullptr;
+  uint8_t* d_flips = nullptr;
   unsigned* d_work = nullptr;
   long long* d_energy2 = nullptr;
   // captured launch, reused while the block size stays the same
@@ -269,6 +279,7 @@ struct ising_batch {
     d.orig = d_orig;
     d.class_pos = d_class_pos;
     d.spins = d_spins;
+    d.flips = d_flips;
     return d;
   }
 };
@@ -279,7 +290,7 @@ void batch_free(ising_batch* b) {
   if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   void* ptrs[] = {b->d_graphs, b->d_order,  b->d_row_ptr, b->d_adj,    b->d_orig,
-                  b->d_class_pos, b->d_spins, b->d_work, b->d_energy2};
+                  b->d_class_pos, b->d_spins, b->d_flips, b->d_work, b->d_energy2};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -480,6 +491,7 @@ int ising_batch_create(int32_t num_graphs, const int32_t* n, const int64_t* m, c
     if ((e = upload(&b->d_class_pos, class_pos, b->stream)) != cudaSuccess) break;
     if ((e = cudaMalloc(reinterpret_cast<void**>(&b->d_spins), std::max<int64_t>(vtx, 16))) != cudaSuccess) break;
     if ((e = cudaMemsetAsync(b->d_spins, 0, std::max<int64_t>(vtx, 16), b->stream)) != cudaSuccess) break;
+    if ((e = cudaMalloc(reinterpret_cast<void**>(&b->d_flips), std::max<int64_t>(vtx, 16))) != cudaSuccess) break;
     if ((e = cudaMalloc(reinterpret_cast<void**>(&b->d_work), 16)) != cudaSuccess) break;
     if ((e = cudaMalloc(reinterpret_cast<void**>(&b->d_energy2),
                         sizeof(long long) * (size_t)num_graphs * replicas)) != cudaSuccess) break;

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <memory>
 #include <vector>
 
 #include "../../include/ising.h"
@@ -69,6 +70,23 @@ struct ising_graph {
   int32_t* d_block_chunk_off = nullptr;
   int32_t* d_block_chunk_len = nullptr;
   int32_t* d_block_class_chunk = nullptr;
+  // halo engine (halo.cuh): the host graph is kept for its plan when the graph
+  // can qualify; the plan is built at the first anneal that asks for it
+  std::unique_ptr<isingx::HostGraph> host;
+  int halo_state = 0;   // 0 not planned, 1 planned, -1 no plan possible
+  int halo_sweeps = 0;  // requested sweeps per exchange (0: automatic)
+  int32_t halo_parts = 0, halo_S = 0, halo_smem = 0;
+  double halo_ratio = 0.0;
+  int32_t* d_halo_hdr = nullptr;
+  int32_t* d_halo_words = nullptr;
+  int32_t* d_halo_slices = nullptr;
+  int32_t* d_halo_gpos = nullptr;
+  int32_t* d_halo_imports = nullptr;
+  int32_t* d_halo_nbrs = nullptr;
+  int32_t* d_halo_exports = nullptr;
+  int32_t* d_halo_quads = nullptr;
+  unsigned* d_halo_flags = nullptr;
+  int8_t* d_spins2 = nullptr;
   uint8_t* d_bias = nullptr;         // per-position flip bias (null: none)
   int32_t* d_rowid = nullptr;        // row of every CSR entry (built on first use)
   isingx::BarrierState* d_barrier = nullptr;

@@ -82,6 +82,92 @@ void build_block_plan(const HostGraph& g, BlockPlan* bp);
 bool build_item_deps(const HostGraph& g, const WorkPlan& plan, std::vector<int32_t>* dep_ptr,
                      std::vector<int32_t>* deps);
 
+// Halo engine (halo.cuh). The vertices are cut into P parts of n / P vertices
+// by recursive bisection along breadth-first orders; block p owns part p. An
+// epoch of S sweeps is D = S * K colour phases (K classes); its region is
+// every vertex within D hops of the part, so the block can run all D phases on
+// its own copy of the region -- phase j updates the class-(j-1) mod K vertices
+// at most D - j hops out, whose neighbours are all current -- and exchanges
+// only the halo (the region outside the part) between epochs.
+//
+// Per part the region's vertices get local indices ordered by (class, hops,
+// position); the rows that some phase updates (at most D - 1 hops) are stored
+// as 32-row slices in slot-major sliced ELL over local indices, word
+// (local col << 8) | (w & 0xff), padding (R << 8) with R the region size. A
+// header of kHaloHdr ints per part gives the offsets into the flat arrays and,
+// per class c, the first local index seg, the first slice, and cnt[l] = the
+// class's vertices at most l hops out (l = 0 .. D).
+constexpr int32_t kHaloHdr = 128;
+constexpr int32_t kHaloHdrClass = 16;  // per-class tables start here
+constexpr int32_t kHaloMaxClasses = 4;
+constexpr int32_t kHaloMaxDepth = 16;
+constexpr int32_t kHaloMaxWidth = 63;  // row degree limit (6-bit slice width)
+constexpr int32_t kHaloSmemLimit = 225 * 1024;
+enum HaloHdr {
+  kHaloR = 0,          // region vertices
+  kHaloWordsOff = 1,   // first word in `words` (multiple of 4)
+  kHaloWordsLen = 2,   // words (multiple of 4)
+  kHaloSlicesOff = 3,  // first entry in `slices`
+  kHaloSlicesLen = 4,
+  kHaloGposOff = 5,    // first entry in `gpos` (R entries)
+  kHaloImportOff = 6,  // first entry in `imports` (pairs)
+  kHaloImportLen = 7,  // halo vertices
+  kHaloNbrOff = 8,     // first entry in `nbrs`
+  kHaloNbrLen = 9,
+  kHaloOwned = 10,
+  kHaloFlipWords = 11,  // flip bitmap words of a full epoch: S * ceil(R / 32)
+  kHaloExportOff = 12,  // first entry in `exports` (pairs)
+  kHaloExportLen = 13,  // the part's vertices in some other part's halo
+  kHaloQuadOff = 14,    // first entry in `quads` (triples)
+  kHaloQuadLen = 15     // vertex quads with an updated row in the region
+};
+// The per-class table of class c starts at kHaloHdrClass + c * (D + 3):
+// seg, first slice, cnt[0 .. D].
+//
+// Flips: the vertices 4q .. 4q + 3 (original ids) share one Philox
+// evaluation per sweep, so a part lists every quad q with a row some phase
+// updates (at most D - 1 hops out) as (q, l0 | l1 << 16, l2 | l3 << 16), l_k
+// the local index of vertex 4q + k or 0xffff if it is not such a row; R must
+// stay below 0xffff.
+//
+// A block's shared memory, in this order: the header, the words, the slices
+// (padded to 4), the epoch's flip bitmap (S * ceil(R / 32) words), the quads
+// (3 words each), the region's state bytes (R + 1, padded to 16) and its flip
+// biases (R, padded to 16).
+inline int64_t halo_smem_bytes(int32_t R, int32_t words, int32_t slices, int32_t flip_words,
+                               int32_t quads) {
+  return int64_t(kHaloHdr) * 4 + int64_t(words) * 4 + int64_t((slices + 3) / 4 * 4) * 4 +
+         int64_t(flip_words) * 4 + int64_t(quads) * 12 + int64_t((R + 1 + 15) / 16 * 16) +
+         int64_t((R + 15) / 16 * 16);
+}
+
+struct HaloPlan {
+  bool ok = false;
+  int32_t parts = 0, sweeps_per_epoch = 0, depth = 0, classes = 0;
+  int32_t smem_bytes = 0;         // dynamic shared memory of the largest part
+  double max_work_ratio = 0.0;    // max over parts: rows updated per sweep / owned rows
+  std::vector<int32_t> hdr;       // kHaloHdr per part
+  std::vector<int32_t> words;     // sliced ELL
+  std::vector<int32_t> slices;    // (word offset within the part << 6) | width
+  std::vector<int32_t> gpos;      // local index -> position
+  std::vector<int32_t> imports;   // (local index, position) of halo vertices (> 0 hops)
+  std::vector<int32_t> exports;   // (local index, position) of own vertices other parts import
+  std::vector<int32_t> quads;     // (q, l0 | l1 << 16, l2 | l3 << 16) per quad
+  std::vector<int32_t> nbrs;      // parts owning some vertex of the halo
+};
+
+// Parts of n / P vertices by recursive bisection: a subset is ordered
+// breadth-first from a far vertex (the last one reached from its first
+// vertex; further components follow in order) and split in proportion to the
+// parts each side gets. part[v] for every position v.
+void bisect_parts(const HostGraph& g, int32_t parts, std::vector<int32_t>* part);
+
+// Fills hp (ok = true) when K <= kHaloMaxClasses, D = S * K <= kHaloMaxDepth,
+// every row has at most kHaloMaxWidth entries and int8 weights, every part is
+// non-empty and each part's tables fit in kHaloSmemLimit bytes of shared
+// memory; otherwise hp->ok = false.
+void build_halo_plan(const HostGraph& g, int32_t parts, int32_t sweeps_per_epoch, HaloPlan* hp);
+
 // Returns 0, or a negative ISING_* status.
 int build_host_graph(int32_t n, int64_t m, const int32_t* src, const int32_t* dst,
                      const int32_t* w, HostGraph* out);

@@ -5,8 +5,8 @@
 // words 0 and 2 by two fixed odd constants (32x32 -> 64 bits), exchanging and
 // xoring the halves with the other counter words and the round key; the round
 // key advances by two Weyl increments between rounds. A flip or initial-spin
-// draw of replica r is word r mod 4 of the counter (vertex, t, r / 4, stream),
-// so four replicas share one evaluation (replica_word); where only word 0 is
+// draw of vertex o is word o mod 4 of the counter (o / 4, t, replica, stream),
+// so four vertices share one evaluation (vertex_word); where only word 0 is
 // used, the last round's other words are left to dead-code elimination.
 #pragma once
 
@@ -78,17 +78,14 @@ __device__ __forceinline__ uint4 philox4x32_10(uint32_t x0, uint32_t x1, uint32_
   return make_uint4(x0, x1, x2, x3);
 }
 
-// The draw of replica r for vertex o in sweep t on stream s (0 flips, 1
-// initial spins): word r mod 4 of counter (o, t, r / 4, s).
-__device__ __forceinline__ uint32_t replica_word(uint32_t o, uint32_t t, uint32_t replica,
-                                                 uint32_t stream, const PhiloxRounds& rk) {
-  const uint4 w = philox4x32_10(o, t, replica >> 2, stream, rk);
-  switch (replica & 3u) {
-    case 0: return w.x;
-    case 1: return w.y;
-    case 2: return w.z;
-    default: return w.w;
-  }
+// The draw of vertex o (original id) in sweep t of replica r on stream s (0
+// flips, 1 initial spins): word o mod 4 of counter (o / 4, t, r, s), so the
+// four vertices 4q .. 4q + 3 share one evaluation.
+__device__ __forceinline__ uint32_t vertex_word(uint32_t o, uint32_t t, uint32_t replica,
+                                                uint32_t stream, const PhiloxRounds& rk) {
+  const uint4 w = philox4x32_10(o >> 2, t, replica, stream, rk);
+  const uint32_t k = o & 3u;
+  return k == 0u ? w.x : (k == 1u ? w.y : (k == 2u ? w.z : w.w));
 }
 
 }  // namespace isingx

@@ -84,6 +84,19 @@ struct SweepArgs {
   int par_cur;       // kPassFlow: update parity every vertex had at the sweep's start
 };
 
+// Arguments of sweep t of a linear schedule of T sweeps starting at threshold
+// T0 (ISING_SCHED_LINEAR in ising.h).
+__device__ __forceinline__ SweepArgs sweep_args(uint64_t t, uint64_t T, uint64_t T0,
+                                                uint32_t replica) {
+  SweepArgs sa;
+  sa.class_lo = 0;
+  sa.par_cur = 0;
+  sa.t = static_cast<uint32_t>(t);
+  sa.replica = replica;
+  sa.thr = (T <= 1) ? 0u : static_cast<uint32_t>((T0 * (T - 1 - t)) / (T - 1));
+  return sa;
+}
+
 // Sliced rows: each slice adds (1 << 48) + (partial + 2^31) to one 64-bit
 // word. The high 16 bits count the slices, the low 48 bits hold the biased sum
 // (at most 65535 slices of 32-bit partials, so no carry reaches the count).
@@ -213,7 +226,7 @@ __device__ __forceinline__ bool flip_drawn(const DevGraph& d, int v, uint32_t o,
         (static_cast<unsigned long long>(a.thr) * __ldg(d.bias + v)) >> 7;
     thr = t > 0xffffffffull ? 0xffffffffu : static_cast<uint32_t>(t);
   }
-  return replica_word(o, a.t, a.replica, 0u, rk) < thr;
+  return vertex_word(o, a.t, a.replica, 0u, rk) < thr;
 }
 
 // Eq. 2 under the max-cut sign (s <- -sign f, f = 0 keeps s), then the flip;

@@ -57,6 +57,22 @@ def test_injected_fault_reports_timeout(P, engine, kind, n):
     _context_still_works(P)
 
 
+def test_halo_engine_missing_publication_reports_timeout(P):
+    # block 0 of the halo engine never publishes its epochs: its neighbour
+    # parts' waits run out, every block returns
+    g = synth.torus_graph(128, 2, weights="pm1")
+    with P.ising_create(g.n, g.src, g.dst, g.w) as h:
+        P.ising_set_engine(h, P.ISING_ENGINE_HALO)
+        P.ising_debug_fault(h, P.ISING_FAULT_SKIP_ARRIVAL, 50_000_000)   # 50 ms
+        P.ising_init_random(h, 1)
+        P.ising_anneal(h, p0=0.1, t_total=30, seed=3)
+        assert P.ising_engine_used(h) == P.ISING_ENGINE_HALO
+        with pytest.raises(P.IsingError) as e:
+            P.ising_cut(h)
+        assert e.value.code == P.ISING_ETIMEOUT
+    _context_still_works(P)
+
+
 def test_debug_fault_arguments(P):
     g = synth.random_small_graph(50, 0.1, 1)
     with P.ising_create(g.n, g.src, g.dst, g.w) as h:

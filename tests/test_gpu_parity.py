@@ -12,7 +12,7 @@ import synth
 
 pytestmark = pytest.mark.gpu
 
-ENGINES = ["phase", "persistent", "dataflow", "persistent_grid", "itemflow"]
+ENGINES = ["phase", "persistent", "dataflow", "persistent_grid", "itemflow", "halo"]
 
 
 @pytest.fixture(scope="module")
@@ -29,7 +29,7 @@ def engine_id(P, name):
     return {"phase": P.ISING_ENGINE_PHASE, "persistent": P.ISING_ENGINE_PERSISTENT,
             "dataflow": P.ISING_ENGINE_DATAFLOW, "auto": P.ISING_ENGINE_AUTO,
             "persistent_grid": P.ISING_ENGINE_PERSISTENT_GRID,
-            "itemflow": P.ISING_ENGINE_ITEMFLOW}[name]
+            "itemflow": P.ISING_ENGINE_ITEMFLOW, "halo": P.ISING_ENGINE_HALO}[name]
 
 
 def gpu_anneal(P, g, s0, *, seed, p0, T, t_begin=0, sweeps=None, flags=0, engine="auto",
@@ -382,12 +382,17 @@ def test_itemflow_engine_matches_oracle_over_many_sweeps(P, name):
 
 
 def test_auto_engine_choice(P):
-    # small graph -> the one-block form; unsliced large graph -> item
-    # dataflow; a graph with sliced hub rows -> the grid engine; racy and
-    # N-flip anneals of an unsliced graph -> the grid engine
+    # small graph -> the one-block form; a lattice with about 1000 vertices
+    # per SM -> halo; unsliced large graph without a halo plan (or with too
+    # much repeated work) -> item dataflow; a graph with sliced hub rows ->
+    # the grid engine; racy and N-flip anneals of an unsliced graph -> the
+    # grid engine
     cases = [
         (synth.random_small_graph(400, 0.03, 1, weights="int8"), {}, P.ISING_ENGINE_USED_BLOCK),
+        (synth.torus_graph(384, 2, weights="pm1"), {}, P.ISING_ENGINE_HALO),
+        (synth.torus_graph(128, 2, weights="pm1"), {}, P.ISING_ENGINE_ITEMFLOW),
         (synth.torus_graph(96, 2, weights="pm1"), {}, P.ISING_ENGINE_ITEMFLOW),
+        (synth.random_small_graph(20000, 4e-4, 2), {}, P.ISING_ENGINE_ITEMFLOW),
         (synth.zipf_config_graph(20011, 2.1, 4, 3000, 5), {}, P.ISING_ENGINE_PERSISTENT_GRID),
         (synth.torus_graph(96, 2, weights="pm1"), {"mode": P.ISING_MODE_RACY},
          P.ISING_ENGINE_PERSISTENT_GRID),
