@@ -696,7 +696,7 @@ cudaError_t plan_halo(ising_graph* g) {
 }
 
 cudaError_t launch_halo(ising_graph* g, uint64_t t_begin, uint32_t sweeps, uint64_t T, uint64_t T0,
-                        uint32_t replica, const isingx::PhiloxRounds& rk_in) {
+                        uint32_t replica, const isingx::PhiloxRounds& rk_in, int par0) {
   cudaError_t e;
   if ((e = barrier_init(g)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(g->d_halo_flags, 0,
@@ -721,7 +721,7 @@ cudaError_t launch_halo(ising_graph* g, uint64_t t_begin, uint32_t sweeps, uint6
   h.classes = g->num_colours;
   h.sweeps_per_epoch = g->halo_S;
   isingx::PhiloxRounds rk = rk_in;
-  void* args[] = {&d, &h, &t_begin, &sweeps, &T, &T0, &replica, &rk};
+  void* args[] = {&d, &h, &t_begin, &sweeps, &T, &T0, &replica, &rk, &par0};
   g->launches++;
   return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(isingx::halo_kernel), dim3(g->halo_parts),
                                      dim3(isingx::kHaloBlock), args, static_cast<size_t>(g->halo_smem), g->stream);
@@ -1026,7 +1026,7 @@ static int anneal_impl(ising_graph* g, const ising_schedule* sched, uint32_t swe
       ISING_CUDA(g, plan_halo(g));
       if (g->halo_state == 1) {
         g->engine_used = ISING_ENGINE_HALO;
-        ISING_CUDA(g, launch_halo(g, sched->t_begin, sweeps, sched->t_total, T0, sched->replica, rk));
+        ISING_CUDA(g, launch_halo(g, sched->t_begin, sweeps, sched->t_total, T0, sched->replica, rk, par0));
         return ISING_OK;
       }
     }

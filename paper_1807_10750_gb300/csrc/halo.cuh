@@ -1,8 +1,8 @@
 // Halo engine: one block per part of the graph (host_graph.h, HaloPlan), one
 // cooperative launch per anneal call, every sweep of it.
 //
-// A block keeps its region's state bytes, sliced-ELL rows and the epoch's flip
-// bits in shared memory. An epoch of S sweeps runs D = S * K colour phases
+// A block keeps its region's spins (int8 +1 / -1), sliced-ELL rows and the
+// epoch's flip bits in shared memory. An epoch of S sweeps runs D = S * K colour phases
 // there with only block barriers between them (phase j: class (j - 1) mod K,
 // rows at most D - j hops out). At the end of the epoch the block writes its
 // own vertices' state bytes to the epoch's spin buffer (two buffers
@@ -87,9 +87,68 @@ __device__ __forceinline__ bool halo_wait(const HaloArgs& h, const int* nbr, int
   return *abort_flag == 0;
 }
 
+// Rows [0, rows) of one class's phase (local indices base + r, slices from
+// sbeg; spins as int8 +1 / -1): the local field f_i = sum_j w_ij s_j over the
+// row's sliced-ELL words, the update of Eq. 2 under the max-cut sign (s_i <-
+// -sign f_i, f_i = 0 keeps s_i) and the drawn flip (bit `lane` of the slice's
+// word in `bits`). Rows of one class never neighbour one another, so a warp
+// gathers up to kChunk of its slices before it writes any update.
+__device__ __forceinline__ void halo_rows(const int32_t* sw, const int32_t* ssl, int8_t* sp,
+                                          const unsigned* bits, int base, int sbeg, int rows,
+                                          int warp, int lane) {
+  constexpr int kWarps = kHaloBlock / 32;
+  constexpr int kChunk = 4;
+  const int ns = (rows + 31) >> 5;
+  for (int s0 = warp; s0 < ns; s0 += kChunk * kWarps) {
+    int f[kChunk];
+#pragma unroll
+    for (int u = 0; u < kChunk; ++u) {
+      const int s = s0 + u * kWarps;
+      f[u] = 0;
+      if (s < ns) {
+        const int sl = ssl[sbeg + s];
+        const int32_t* wp = sw + (sl >> 6) + lane;
+        const int width = sl & 63;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          if (k < width) {
+            const int word = wp[32 * k];
+            f[u] += ((word << 24) >> 24) * sp[static_cast<unsigned>(word) >> 8];
+          }
+        }
+        for (int k = 4; k < width; ++k) {
+          const int word = wp[32 * k];
+          f[u] += ((word << 24) >> 24) * sp[static_cast<unsigned>(word) >> 8];
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kChunk; ++u) {
+      const int s = s0 + u * kWarps;
+      const int r = 32 * s + lane;
+      if (s < ns && r < rows) {
+        int sv = sp[base + r];
+        if (f[u] > 0)
+          sv = -1;
+        else if (f[u] < 0)
+          sv = 1;
+        if ((bits[sbeg + s] >> lane) & 1u) sv = -sv;
+        sp[base + r] = static_cast<int8_t>(sv);
+      }
+    }
+  }
+}
+
+// State byte of spin sv with update parity par (bit 0: spin -1; bit 1: parity).
+__device__ __forceinline__ int8_t halo_state(int sv, int par) {
+  return static_cast<int8_t>((sv < 0 ? 1 : 0) | (par << 1));
+}
+
+// par0: the update parity every state byte carries at the launch (every
+// sweep updates every vertex once, so it stays uniform).
 __global__ void __launch_bounds__(kHaloBlock, 1)
     halo_kernel(DevGraph d, HaloArgs h, uint64_t t_begin, uint32_t sweeps, uint64_t T, uint64_t T0,
-                uint32_t replica, PhiloxRounds rk) {
+                uint32_t replica, PhiloxRounds rk, int par0) {
   extern __shared__ __align__(16) unsigned char halo_smem[];
   __shared__ int abort_flag;
   __shared__ uint32_t sthr[kHaloMaxDepth];  // the epoch's sweep thresholds
@@ -97,25 +156,23 @@ __global__ void __launch_bounds__(kHaloBlock, 1)
   const int p = blockIdx.x;
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  constexpr int kWarps = kHaloBlock / 32;
   if (threadIdx.x < kHaloHdr) hd[threadIdx.x] = __ldg(h.hdr + static_cast<size_t>(p) * kHaloHdr + threadIdx.x);
   if (threadIdx.x == 0) abort_flag = 0;
   __syncthreads();
   const int R = hd[kHaloR];
   const int words_len = hd[kHaloWordsLen];
   const int nslices = hd[kHaloSlicesLen];
+  const int nquads = hd[kHaloQuadLen];
   const int K = h.classes;
   const int S = h.sweeps_per_epoch;
   const int D = S * K;
   const int ct = kHaloHdrClass;  // class c's table: hd[ct + c * (D + 3) + ...]
-  int32_t* sw = hd + kHaloHdr;                                      // words
-  int32_t* ssl = sw + words_len;                                    // slices
-  unsigned* sflip = reinterpret_cast<unsigned*>(ssl + (nslices + 3) / 4 * 4);  // flip bitmap
-  const int nquads = hd[kHaloQuadLen];
-  uint32_t* squad = sflip + hd[kHaloFlipWords];                     // quads, 3 words each
-  uint8_t* sp = reinterpret_cast<uint8_t*>(squad + 3 * nquads);     // state bytes, R + 1
-  uint8_t* sq = sp + (R + 1 + 15) / 16 * 16;                        // flip biases, R
-  const int fw = (R + 31) >> 5;                                     // bitmap words per sweep
+  int32_t* sw = hd + kHaloHdr;                                                    // words
+  int32_t* ssl = sw + words_len;                                                  // slices
+  unsigned* sflip = reinterpret_cast<unsigned*>(ssl + (nslices + 3) / 4 * 4);     // flip bitmap
+  uint32_t* squad = sflip + hd[kHaloFlipWords];                                   // quads
+  int8_t* sp = reinterpret_cast<int8_t*>(squad + 3 * nquads);                     // spins, R + 1
+  uint8_t* sq = reinterpret_cast<uint8_t*>(sp) + (R + 1 + 15) / 16 * 16;          // biases by slot
   const int32_t* gp = h.gpos + hd[kHaloGposOff];
   const int2* imp = reinterpret_cast<const int2*>(h.imports) + hd[kHaloImportOff] / 2;
   const int2* exq = reinterpret_cast<const int2*>(h.exports) + hd[kHaloExportOff] / 2;
@@ -129,12 +186,18 @@ __global__ void __launch_bounds__(kHaloBlock, 1)
     for (int i = threadIdx.x; i < nslices; i += kHaloBlock) ssl[i] = __ldg(h.slices + hd[kHaloSlicesOff] + i);
     for (int i = threadIdx.x; i < 3 * nquads; i += kHaloBlock)
       squad[i] = static_cast<uint32_t>(__ldg(h.quads + hd[kHaloQuadOff] + i));
-    for (int l = threadIdx.x; l < R; l += kHaloBlock) {
-      const int v = __ldg(gp + l);
-      sp[l] = static_cast<uint8_t>(__ldcg(d.spins + v));
-      sq[l] = d.bias != nullptr ? __ldg(d.bias + v) : static_cast<uint8_t>(128);
-    }
+    for (int l = threadIdx.x; l < R; l += kHaloBlock)
+      sp[l] = static_cast<int8_t>(1 - 2 * (__ldcg(d.spins + __ldg(gp + l)) & 1));
     if (threadIdx.x == 0) sp[R] = 0;  // the padding entries' spin (weight 0)
+    if (d.bias != nullptr) {
+      // slot 32 * slice + lane of class c: row (slice - first slice) * 32 + lane
+      for (int c = 0; c < K; ++c) {
+        const int* tc = hd + ct + c * (D + 3);
+        const int U = tc[2 + D - 1];
+        for (int r = threadIdx.x; r < U; r += kHaloBlock)
+          sq[(tc[1] + (r >> 5)) * 32 + (r & 31)] = __ldg(d.bias + __ldg(gp + tc[0] + r));
+      }
+    }
   }
   __syncthreads();
 
@@ -144,30 +207,30 @@ __global__ void __launch_bounds__(kHaloBlock, 1)
     const int De = se * K;
     const uint64_t t0 = t_begin + static_cast<uint64_t>(e) * static_cast<uint64_t>(S);
     if (threadIdx.x < se) sthr[threadIdx.x] = sweep_args(t0 + threadIdx.x, T, T0, replica).thr;
-    for (int i = threadIdx.x; i < se * fw; i += kHaloBlock) sflip[i] = 0u;
+    for (int i = threadIdx.x; i < se * nslices; i += kHaloBlock) sflip[i] = 0u;
     __syncthreads();
     // the epoch's flip decisions (Algorithm 2 with R5's draws): one Philox
-    // evaluation per quad and sweep sets bit l of sweep i's bitmap words for
-    // every member row l that flips
+    // evaluation per quad and sweep sets the bit of every member row that
+    // flips in sweep i's bitmap
     for (int i = 0; i < se; ++i) {
       const uint32_t thr0 = sthr[i];
       if (thr0 == 0u) continue;
       const uint32_t t = static_cast<uint32_t>(t0) + static_cast<uint32_t>(i);
-      unsigned* bits = sflip + i * fw;
+      unsigned* bits = sflip + i * nslices;
       for (int q = threadIdx.x; q < nquads; q += kHaloBlock) {
         const uint4 x = philox4x32_10(squad[3 * q], t, replica, 0u, rk);
-        const uint32_t l01 = squad[3 * q + 1], l23 = squad[3 * q + 2];
+        const uint32_t s01 = squad[3 * q + 1], s23 = squad[3 * q + 2];
         const uint32_t xs[4] = {x.x, x.y, x.z, x.w};
-        const uint32_t ls[4] = {l01 & 0xffffu, l01 >> 16, l23 & 0xffffu, l23 >> 16};
+        const uint32_t slot[4] = {s01 & 0xffffu, s01 >> 16, s23 & 0xffffu, s23 >> 16};
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          if (ls[k] == 0xffffu) continue;
+          if (slot[k] == 0xffffu) continue;
           uint32_t thr = thr0;
           if (d.bias != nullptr) {
-            const unsigned long long tq = (static_cast<unsigned long long>(thr0) * sq[ls[k]]) >> 7;
+            const unsigned long long tq = (static_cast<unsigned long long>(thr0) * sq[slot[k]]) >> 7;
             thr = tq > 0xffffffffull ? 0xffffffffu : static_cast<uint32_t>(tq);
           }
-          if (xs[k] < thr) atomicOr(bits + (ls[k] >> 5), 1u << (ls[k] & 31u));
+          if (xs[k] < thr) atomicOr(bits + (slot[k] >> 5), 1u << (slot[k] & 31u));
         }
       }
     }
@@ -177,73 +240,32 @@ __global__ void __launch_bounds__(kHaloBlock, 1)
       const int nimp = hd[kHaloImportLen];
       for (int q = threadIdx.x; q < nimp; q += kHaloBlock) {
         const int2 lv = __ldg(imp + q);
-        sp[lv.x] = static_cast<uint8_t>(__ldcg(src + lv.y));
+        sp[lv.x] = static_cast<int8_t>(1 - 2 * (__ldcg(src + lv.y) & 1));
       }
     }
     __syncthreads();
-    // D_e phases (Eq. 2 under the max-cut sign, then the drawn flip)
+    // D_e phases: phase j updates class (j - 1) mod K at most D_e - j hops out
     for (int j = 1; j <= De; ++j) {
-      const unsigned* bits = sflip + ((j - 1) / K) * fw;
-      const int c = (j - 1) % K;
-      const int* tc = hd + ct + c * (D + 3);
-      const int rows = tc[2 + De - j];
-      const int ns = (rows + 31) >> 5;
-      const int base = tc[0];
-      const int sbeg = tc[1];
-      // a phase's rows read only other classes' state bytes, so a warp
-      // gathers up to kChunk of its slices before it writes any update
-      constexpr int kChunk = 4;
-      for (int s0 = warp; s0 < ns; s0 += kChunk * kWarps) {
-        int f[kChunk];
-#pragma unroll
-        for (int u = 0; u < kChunk; ++u) {
-          const int s = s0 + u * kWarps;
-          f[u] = 0;
-          if (s < ns) {
-            const int sl = ssl[sbeg + s];
-            const int32_t* wp = sw + (sl >> 6) + lane;
-            const int width = sl & 63;
-#pragma unroll 4
-            for (int k = 0; k < width; ++k) {
-              const int word = wp[32 * k];
-              const int wgt = (word << 24) >> 24;
-              f[u] += (sp[static_cast<unsigned>(word) >> 8] & 1) ? -wgt : wgt;
-            }
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < kChunk; ++u) {
-          const int s = s0 + u * kWarps;
-          const int r = 32 * s + lane;
-          if (s < ns && r < rows) {
-            const int b = sp[base + r];
-            int bit = b & 1;  // 1 = spin -1
-            if (f[u] > 0)
-              bit = 1;
-            else if (f[u] < 0)
-              bit = 0;
-            bit ^= static_cast<int>((bits[(base + r) >> 5] >> ((base + r) & 31)) & 1u);
-            sp[base + r] = static_cast<uint8_t>(bit | ((b ^ 2) & 2));
-          }
-        }
-      }
+      const int* tc = hd + ct + ((j - 1) % K) * (D + 3);
+      halo_rows(sw, ssl, sp, sflip + ((j - 1) / K) * nslices, tc[0], tc[1], tc[2 + De - j], warp, lane);
       __syncthreads();
     }
     // publish the part's own state bytes for epoch e + 1: those other parts
     // import; after the last epoch every own vertex, into the handle's buffer
     // (directly after an even number of epochs, below after an odd one)
+    const int par = par0 ^ static_cast<int>(min((e + 1u) * static_cast<uint32_t>(S), sweeps) & 1u);
     int8_t* dst = ((e + 1u) & 1u) ? h.buf1 : d.spins;
     if (e + 1u < E) {
       const int nexp = hd[kHaloExportLen];
       for (int q = threadIdx.x; q < nexp; q += kHaloBlock) {
         const int2 lv = __ldg(exq + q);
-        dst[lv.y] = static_cast<int8_t>(sp[lv.x]);
+        dst[lv.y] = halo_state(sp[lv.x], par);
       }
     } else if ((E & 1u) == 0u) {
       for (int c = 0; c < K; ++c) {
         const int* tc = hd + ct + c * (D + 3);
         for (int r = threadIdx.x; r < tc[2]; r += kHaloBlock)
-          dst[__ldg(gp + tc[0] + r)] = static_cast<int8_t>(sp[tc[0] + r]);
+          dst[__ldg(gp + tc[0] + r)] = halo_state(sp[tc[0] + r], par);
       }
     }
     __syncthreads();
@@ -256,10 +278,11 @@ __global__ void __launch_bounds__(kHaloBlock, 1)
   // E - 1: write the part's vertices once every neighbour has published E
   if (E & 1u) {
     if (!halo_wait(h, nbr, nbr_len, E, &abort_flag)) return;
+    const int par = par0 ^ static_cast<int>(sweeps & 1u);
     for (int c = 0; c < K; ++c) {
       const int* tc = hd + ct + c * (D + 3);
       for (int r = threadIdx.x; r < tc[2]; r += kHaloBlock)
-        d.spins[__ldg(gp + tc[0] + r)] = static_cast<int8_t>(sp[tc[0] + r]);
+        d.spins[__ldg(gp + tc[0] + r)] = halo_state(sp[tc[0] + r], par);
     }
   }
 }

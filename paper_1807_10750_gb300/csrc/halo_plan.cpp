@@ -106,11 +106,16 @@ void bisect_parts(const HostGraph& g, int32_t parts, std::vector<int32_t>* part)
         next[2 * static_cast<size_t>(i)].parts = next[2 * static_cast<size_t>(i) + 1].parts = 0;
         return;
       }
-      // breadth-first order from the start vertex; further components follow
+      // breadth-first order from a far vertex (the last one a pass from the
+      // start vertex reaches); further components follow
       for (int32_t v : t.verts) mark[static_cast<size_t>(v)].store(t.id, std::memory_order_relaxed);
       std::vector<int32_t> order;
       order.reserve(t.verts.size());
       bfs(t.start, t.id, order);
+      const int32_t far = order.back();
+      for (int32_t v : order) mark[static_cast<size_t>(v)].store(t.id, std::memory_order_relaxed);
+      order.clear();
+      bfs(far, t.id, order);
       if (order.size() < t.verts.size())
         for (int32_t v : t.verts) bfs(v, t.id, order);
       const int32_t pl = t.parts / 2;
@@ -123,8 +128,7 @@ void bisect_parts(const HostGraph& g, int32_t parts, std::vector<int32_t>* part)
       lo.base = t.base;
       hi.parts = t.parts - pl;
       hi.base = t.base + pl;
-      // the low side is a ball around the start: continue from its rim; the
-      // high side from the vertex farthest from the start
+      // each side's next pass starts from a vertex on its far rim
       lo.start = lo.verts.empty() ? 0 : lo.verts.back();
       hi.start = hi.verts.empty() ? 0 : hi.verts.back();
       t.verts = std::vector<int32_t>();
@@ -245,17 +249,19 @@ void build_part(const HostGraph& g, const std::vector<int32_t>& part, const std:
   int64_t rows = 0;
   for (int32_t j = 1; j <= D; ++j) rows += H[kHaloHdrClass + ((j - 1) % K) * (D + 3) + 2 + (D - j)];
   pt->ratio = static_cast<double>(rows) / (static_cast<double>(S) * owned);
-  const int32_t flipw = S * ((R + 31) / 32);
+  const int32_t flipw = S * H[kHaloSlicesLen];
   H[kHaloFlipWords] = flipw;
-  // quads of the updated rows (at most D - 1 hops out), by quad id
-  if (R >= 0xffff) return;
-  std::vector<uint64_t> qk;  // (q << 34) | (k << 32) | l
+  // quads of the updated rows (at most D - 1 hops out), by quad id, with
+  // every member's slot
+  if (int64_t(H[kHaloSlicesLen]) * 32 >= 0xffff) return;
+  std::vector<uint64_t> qk;  // (q << 34) | (k << 32) | slot
   for (int32_t c = 0; c < K; ++c) {
     const int32_t* T = H + kHaloHdrClass + c * (D + 3);
-    for (int32_t l = T[0]; l < T[0] + T[2 + D - 1]; ++l) {
+    for (int32_t r = 0; r < T[2 + D - 1]; ++r) {
+      const int32_t l = T[0] + r;
       const uint32_t o = static_cast<uint32_t>(g.perm[static_cast<size_t>(pt->gpos[static_cast<size_t>(l)])]);
-      qk.push_back((static_cast<uint64_t>(o >> 2) << 34) | (static_cast<uint64_t>(o & 3u) << 32) |
-                   static_cast<uint32_t>(l));
+      const uint32_t slot = static_cast<uint32_t>((T[1] + (r >> 5)) * 32 + (r & 31));
+      qk.push_back((static_cast<uint64_t>(o >> 2) << 34) | (static_cast<uint64_t>(o & 3u) << 32) | slot);
     }
   }
   std::sort(qk.begin(), qk.end());

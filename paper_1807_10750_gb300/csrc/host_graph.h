@@ -115,7 +115,7 @@ enum HaloHdr {
   kHaloNbrOff = 8,     // first entry in `nbrs`
   kHaloNbrLen = 9,
   kHaloOwned = 10,
-  kHaloFlipWords = 11,  // flip bitmap words of a full epoch: S * ceil(R / 32)
+  kHaloFlipWords = 11,  // flip bitmap words of a full epoch: S * slices
   kHaloExportOff = 12,  // first entry in `exports` (pairs)
   kHaloExportLen = 13,  // the part's vertices in some other part's halo
   kHaloQuadOff = 14,    // first entry in `quads` (triples)
@@ -124,21 +124,22 @@ enum HaloHdr {
 // The per-class table of class c starts at kHaloHdrClass + c * (D + 3):
 // seg, first slice, cnt[0 .. D].
 //
-// Flips: the vertices 4q .. 4q + 3 (original ids) share one Philox
-// evaluation per sweep, so a part lists every quad q with a row some phase
-// updates (at most D - 1 hops out) as (q, l0 | l1 << 16, l2 | l3 << 16), l_k
-// the local index of vertex 4q + k or 0xffff if it is not such a row; R must
-// stay below 0xffff.
+// An updated row's slot is 32 * (its slice) + (its lane in the slice), slices
+// counted from the part's first. Flips: the vertices 4q .. 4q + 3 (original
+// ids) share one Philox evaluation per sweep, so a part lists every quad q
+// with an updated row as (q, s0 | s1 << 16, s2 | s3 << 16), s_k the slot of
+// vertex 4q + k or 0xffff if it is not an updated row here; a sweep's flip
+// bitmap has one word per slice, bit `lane` for the row in that lane.
 //
 // A block's shared memory, in this order: the header, the words, the slices
-// (padded to 4), the epoch's flip bitmap (S * ceil(R / 32) words), the quads
-// (3 words each), the region's state bytes (R + 1, padded to 16) and its flip
-// biases (R, padded to 16).
+// (padded to 4), the epoch's flip bitmap (S words per slice), the quads (3
+// words each), the region's spins (int8 +1 / -1, R + 1, padded to 16) and the
+// updated rows' flip biases by slot (32 per slice).
 inline int64_t halo_smem_bytes(int32_t R, int32_t words, int32_t slices, int32_t flip_words,
                                int32_t quads) {
   return int64_t(kHaloHdr) * 4 + int64_t(words) * 4 + int64_t((slices + 3) / 4 * 4) * 4 +
          int64_t(flip_words) * 4 + int64_t(quads) * 12 + int64_t((R + 1 + 15) / 16 * 16) +
-         int64_t((R + 15) / 16 * 16);
+         int64_t(slices) * 32;
 }
 
 struct HaloPlan {
@@ -157,9 +158,9 @@ struct HaloPlan {
 };
 
 // Parts of n / P vertices by recursive bisection: a subset is ordered
-// breadth-first from a far vertex (the last one reached from its first
-// vertex; further components follow in order) and split in proportion to the
-// parts each side gets. part[v] for every position v.
+// breadth-first from a far vertex (the last one a pass from a vertex on the
+// subset's rim reaches; further components follow in order) and split in
+// proportion to the parts each side gets. part[v] for every position v.
 void bisect_parts(const HostGraph& g, int32_t parts, std::vector<int32_t>* part);
 
 // Fills hp (ok = true) when K <= kHaloMaxClasses, D = S * K <= kHaloMaxDepth,

@@ -153,8 +153,8 @@ def test_halo_info_and_auto_choice(P):
         assert P.ising_engine_used(h) == P.ISING_ENGINE_HALO
         P.ising_set_halo_sweeps(h, 1)
         assert P.ising_halo_info(h)["sweeps_per_exchange"] == 1
-    # 108 vertices per part: too much repeated work for AUTO, item dataflow runs
-    g = HALO_GRAPHS["torus128_pm1"]()
+    # 66 vertices per part: too much repeated work for AUTO, item dataflow runs
+    g = synth.torus_graph(100, 1, weights="pm1")
     with P.ising_create(g.n, g.src, g.dst, g.w) as h:
         assert P.ising_halo_info(h)["work_ratio"] > 1.6
         P.ising_init_random(h, 1)

@@ -390,7 +390,7 @@ def test_auto_engine_choice(P):
     cases = [
         (synth.random_small_graph(400, 0.03, 1, weights="int8"), {}, P.ISING_ENGINE_USED_BLOCK),
         (synth.torus_graph(384, 2, weights="pm1"), {}, P.ISING_ENGINE_HALO),
-        (synth.torus_graph(128, 2, weights="pm1"), {}, P.ISING_ENGINE_ITEMFLOW),
+        (synth.torus_graph(100, 2, weights="pm1"), {}, P.ISING_ENGINE_ITEMFLOW),
         (synth.torus_graph(96, 2, weights="pm1"), {}, P.ISING_ENGINE_ITEMFLOW),
         (synth.random_small_graph(20000, 4e-4, 2), {}, P.ISING_ENGINE_ITEMFLOW),
         (synth.zipf_config_graph(20011, 2.1, 4, 3000, 5), {}, P.ISING_ENGINE_PERSISTENT_GRID),
