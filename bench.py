@@ -78,16 +78,16 @@ def algorithmic_bytes_per_sweep(n: int, nnz: int, entry_bytes: int) -> int:
 # the sweeps. The entry holds only while the kernel sources hash to `sources`:
 # once they change the counters are stale and traffic is reported as null.
 NCU_TRAFFIC = {
-    "torus1024": {"fixed": 23.982e6, "per_sweep": 0.0, "kernel": "itemflow_kernel",
-                  "engine": "itemflow",
-                  "files": ("sweep.cuh", "anneal.cu", "philox.cuh"),
-                  "sources": "902d42231c3e5f17",
-                  "how": "ncu 20- and 60-sweep captures: 23.966 MB and 23.996 MB, so the "
-                         "working set is read once and then stays in L2"},
-    "batched": {"fixed": 0.2383e9, "per_sweep": 0.18541e9, "kernel": "batch_anneal_kernel",
-                "files": ("batch.cu", "philox.cuh"),
-                "sources": "d907bff657ba27b4",
-                "how": "ncu 20- and 60-sweep captures: 3.946 GB and 11.362 GB"},
+    "torus1024": {"fixed": 32.66e6, "per_sweep": 10.9e3, "kernel": "halo_kernel",
+                  "engine": "halo",
+                  "files": ('halo.cuh', 'halo_plan.cpp', 'host_graph.h', 'anneal.cu', 'philox.cuh', 'sweep.cuh'),
+                  "sources": "16dc3e131daaf3bc",
+                  "how": "ncu 20- and 60-sweep captures: 32.877 MB and 33.314 MB, so the "
+                         "working set is read once and then stays in shared memory and L2"},
+    "batched": {"fixed": 0.169e9, "per_sweep": 0.2154e9, "kernel": "batch_anneal_kernel",
+                "files": ('batch.cu', 'philox.cuh'),
+                "sources": "a9ecc799c04ecb1b",
+                "how": "ncu 20- and 60-sweep captures: 4.477 GB and 13.093 GB"},
 }
 
 
@@ -645,6 +645,10 @@ def main():
     h = P.ising_create(g.n, g.src, g.dst, g.w, stream=stream)
     P.ising_set_engine(h, engine)
     P.ising_set_halo_sweeps(h, args.halo_sweeps)
+    if args.engine in ("auto", "halo"):
+        # setup, like ising_create: let the host planner finish so that every
+        # timed step runs the engine AUTO settles on (None: no halo plan)
+        P.ising_halo_info(h)
     mode = P.ISING_MODE_RACY if args.mode == "racy" else P.ISING_MODE_DET
     colours = P.ising_num_colours(h)
     m = P.ising_num_edges(h)

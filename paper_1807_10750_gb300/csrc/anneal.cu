@@ -26,6 +26,7 @@
 #include <cstdint>
 #include <cstring>
 #include <new>
+#include <system_error>
 #include <vector>
 
 #include "../../include/ising.h"
@@ -626,30 +627,72 @@ cudaError_t launch_flow(ising_graph* g, uint64_t t_begin, uint32_t sweeps, uint6
   return launch_flow_t<false>(g, t_begin, sweeps, T, T0, replica, par0, rk);
 }
 
-// Plan the halo engine once (host_graph.h, build_halo_plan): one part per SM,
-// the requested sweeps per exchange, or S = 2 unless that plan does not fit
-// or repeats more than kHaloAutoRatio times the work and S = 1 fits; uploads
-// the tables. halo_state 1 on success, -1 if no plan is possible;
-// returns a CUDA error only.
-cudaError_t plan_halo(ising_graph* g) {
-  if (g->halo_state != 0) return cudaSuccess;
-  g->halo_state = -1;
-  if (!g->host) return cudaSuccess;
-  isingx::HaloPlan hp;
+// The halo plan for sweeps-per-exchange request S (host_graph.h,
+// build_halo_plan): one part per SM; S as requested, or S = 2 unless that
+// plan does not fit or repeats more than kHaloAutoRatio times the work and
+// S = 1 fits. Host only.
+void choose_halo_plan(const HostGraph& hg, int32_t parts, int32_t S, isingx::HaloPlan* hp,
+                      const std::atomic<bool>* cancel) {
   try {
-    if (g->halo_sweeps > 0) {
-      isingx::build_halo_plan(*g->host, g->num_sms, g->halo_sweeps, &hp);
+    if (S > 0) {
+      isingx::build_halo_plan(hg, parts, S, hp, cancel);
     } else {
-      isingx::build_halo_plan(*g->host, g->num_sms, 2, &hp);
-      if (!hp.ok || hp.max_work_ratio > kHaloAutoRatio) {
+      isingx::build_halo_plan(hg, parts, 2, hp, cancel);
+      if (!hp->ok || hp->max_work_ratio > kHaloAutoRatio) {
         isingx::HaloPlan one;
-        isingx::build_halo_plan(*g->host, g->num_sms, 1, &one);
-        if (one.ok) hp = std::move(one);
+        isingx::build_halo_plan(hg, parts, 1, &one, cancel);
+        if (one.ok) *hp = std::move(one);
       }
     }
   } catch (const std::bad_alloc&) {
+    *hp = isingx::HaloPlan();
+  }
+}
+
+// Start the planner thread for the handle's current request (no-op without
+// a host graph or while one runs); without threads, plan right here.
+void start_planner(ising_graph* g) {
+  if (!g->host || g->planner.joinable() || g->pending) return;
+  g->pending.reset(new (std::nothrow) isingx::HaloPlan());
+  if (!g->pending) return;
+  g->planned.store(false, std::memory_order_relaxed);
+  const HostGraph* hg = g->host.get();
+  isingx::HaloPlan* out = g->pending.get();
+  std::atomic<bool>* done = &g->planned;
+  const std::atomic<bool>* cancel = &g->plan_cancel;
+  const int32_t parts = g->num_sms, S = g->halo_sweeps;
+  try {
+    g->planner = std::thread([hg, out, done, cancel, parts, S] {
+      choose_halo_plan(*hg, parts, S, out, cancel);
+      done->store(true, std::memory_order_release);
+    });
+  } catch (const std::system_error&) {
+    choose_halo_plan(*hg, parts, S, out, cancel);
+    g->planned.store(true, std::memory_order_release);
+  }
+}
+
+void join_planner(ising_graph* g) {
+  if (g->planner.joinable()) g->planner.join();
+}
+
+// Upload the halo plan once it exists. wait = false: if the planner is still
+// running, return with halo_state 0 (not planned yet; a planner is started
+// if none ran). halo_state 1 on success, -1 if no plan is possible; returns a
+// CUDA error only.
+cudaError_t plan_halo(ising_graph* g, bool wait) {
+  if (g->halo_state != 0) return cudaSuccess;
+  if (!g->host) {
+    g->halo_state = -1;
     return cudaSuccess;
   }
+  start_planner(g);
+  if (!wait && !g->planned.load(std::memory_order_acquire)) return cudaSuccess;
+  join_planner(g);
+  g->halo_state = -1;
+  if (!g->pending) return cudaSuccess;
+  isingx::HaloPlan hp = std::move(*g->pending);
+  g->pending.reset();
   if (!hp.ok) return cudaSuccess;
   auto kernel = isingx::halo_kernel;
   cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, hp.smem_bytes);
@@ -817,17 +860,17 @@ int ising_create(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, c
   isingx::BlockPlan block;
   std::vector<int32_t> dep_ptr, deps;  // item dependencies (before the columns are packed)
   bool have_deps = false;
+  std::vector<int32_t> packed_words;  // graphs kept for the halo plan pack into a copy
   try {
     if (g->packed) isingx::build_block_plan(hg, &block);
     have_deps = isingx::build_item_deps(hg, plan, &dep_ptr, &deps);
-    // graphs the halo engine may take keep their host graph for its plan
-    if (g->packed && !block.ok && hg.num_colours <= isingx::kHaloMaxClasses &&
-        hg.max_degree <= isingx::kHaloMaxWidth && hg.n >= 64 * g->num_sms)
-      g->host.reset(new HostGraph(hg));
   } catch (const std::bad_alloc&) {
     delete g;
     return ISING_ENOMEM;
   }
+  // graphs the halo engine may take keep their host graph for its plan
+  const bool keep_host = g->packed && !block.ok && hg.num_colours <= isingx::kHaloMaxClasses &&
+                         hg.max_degree <= isingx::kHaloMaxWidth && hg.n >= 64 * g->num_sms;
 
   cudaError_t e = cudaSuccess;
   const size_t N = static_cast<size_t>(hg.n);
@@ -835,11 +878,22 @@ int ising_create(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, c
   do {
     if ((e = alloc_copy(&g->d_row_ptr, hg.row_ptr.data(), N + 1, g->stream)) != cudaSuccess) break;
     if (g->packed) {
-      // reuse the host column array for the packed words
+      // the packed words go into the host column array, or into a copy when
+      // the host graph is kept
+      int32_t* words = hg.col.data();
+      if (keep_host) {
+        try {
+          packed_words.resize(NNZ);
+        } catch (const std::bad_alloc&) {
+          e = cudaErrorMemoryAllocation;
+          break;
+        }
+        words = packed_words.data();
+      }
       for (size_t k = 0; k < NNZ; ++k)
-        hg.col[k] = static_cast<int32_t>((static_cast<uint32_t>(hg.col[k]) << 8) |
-                                         (static_cast<uint32_t>(hg.w[k]) & 0xffu));
-      if ((e = alloc_copy(&g->d_adj, hg.col.data(), NNZ, g->stream)) != cudaSuccess) break;
+        words[k] = static_cast<int32_t>((static_cast<uint32_t>(hg.col[k]) << 8) |
+                                        (static_cast<uint32_t>(hg.w[k]) & 0xffu));
+      if ((e = alloc_copy(&g->d_adj, words, NNZ, g->stream)) != cudaSuccess) break;
     } else {
       if ((e = alloc_copy(&g->d_col, hg.col.data(), NNZ, g->stream)) != cudaSuccess) break;
       if ((e = alloc_copy(&g->d_w, hg.w.data(), NNZ, g->stream)) != cudaSuccess) break;
@@ -906,12 +960,18 @@ int ising_create(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, c
     delete g;
     return e == cudaErrorMemoryAllocation ? ISING_ENOMEM : ISING_ECUDA;
   }
+  if (keep_host) {
+    g->host.reset(new (std::nothrow) HostGraph(std::move(hg)));
+    start_planner(g);
+  }
   *out = g;
   return ISING_OK;
 }
 
 void ising_destroy(ising_graph* g) {
   if (g == nullptr) return;
+  g->plan_cancel.store(true, std::memory_order_relaxed);
+  join_planner(g);
   cudaSetDevice(g->device);
   cudaStreamSynchronize(g->stream);
   cudaGetLastError();
@@ -999,7 +1059,7 @@ static int anneal_impl(ising_graph* g, const ising_schedule* sched, uint32_t swe
     if (!coop) {
       engine = ISING_ENGINE_PHASE;
     } else if (!g->block_ok && mode == ISING_MODE_DET && sched->kind == ISING_SCHED_LINEAR) {
-      ISING_CUDA(g, plan_halo(g));
+      ISING_CUDA(g, plan_halo(g, false));
       if (g->halo_state == 1 && g->halo_ratio <= kHaloAutoRatio)
         engine = ISING_ENGINE_HALO;
       else
@@ -1023,7 +1083,7 @@ static int anneal_impl(ising_graph* g, const ising_schedule* sched, uint32_t swe
   }
   if (engine == ISING_ENGINE_HALO) {
     if (mode == ISING_MODE_DET && !nflip) {
-      ISING_CUDA(g, plan_halo(g));
+      ISING_CUDA(g, plan_halo(g, true));
       if (g->halo_state == 1) {
         g->engine_used = ISING_ENGINE_HALO;
         ISING_CUDA(g, launch_halo(g, sched->t_begin, sweeps, sched->t_total, T0, sched->replica, rk, par0));
@@ -1263,6 +1323,8 @@ int ising_set_halo_sweeps(ising_graph* g, uint32_t sweeps_per_exchange) {
   if (sweeps_per_exchange > static_cast<uint32_t>(isingx::kHaloMaxDepth)) return ISING_EINVAL;
   if (static_cast<int>(sweeps_per_exchange) == g->halo_sweeps) return ISING_OK;
   ISING_CUDA(g, cudaStreamSynchronize(g->stream));  // no launch still reads the old plan
+  join_planner(g);
+  g->pending.reset();
   free_halo(g);
   g->halo_sweeps = static_cast<int>(sweeps_per_exchange);
   return ISING_OK;
@@ -1272,7 +1334,7 @@ int ising_halo_info(ising_graph* g, int32_t* out_parts, int32_t* out_sweeps, int
                     double* out_work_ratio) {
   int rc = enter(g);
   if (rc != ISING_OK) return rc;
-  ISING_CUDA(g, plan_halo(g));
+  ISING_CUDA(g, plan_halo(g, true));
   if (g->halo_state != 1) return ISING_ESTATE;
   if (out_parts) *out_parts = g->halo_parts;
   if (out_sweeps) *out_sweeps = g->halo_S;

@@ -4,8 +4,10 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <memory>
+#include <thread>
 #include <vector>
 
 #include "../../include/ising.h"
@@ -71,8 +73,14 @@ struct ising_graph {
   int32_t* d_block_chunk_len = nullptr;
   int32_t* d_block_class_chunk = nullptr;
   // halo engine (halo.cuh): the host graph is kept for its plan when the graph
-  // can qualify; the plan is built at the first anneal that asks for it
+  // can qualify; a host thread started by ising_create builds the plan while
+  // the caller goes on (AUTO uses the engine once it is ready), and the first
+  // call that needs it uploads it
   std::unique_ptr<isingx::HostGraph> host;
+  std::unique_ptr<isingx::HaloPlan> pending;  // written by the planner thread
+  std::thread planner;
+  std::atomic<bool> planned{false};           // the planner has finished `pending`
+  std::atomic<bool> plan_cancel{false};       // ising_destroy: stop the planner early
   int halo_state = 0;   // 0 not planned, 1 planned, -1 no plan possible
   int halo_sweeps = 0;  // requested sweeps per exchange (0: automatic)
   int32_t halo_parts = 0, halo_S = 0, halo_smem = 0;

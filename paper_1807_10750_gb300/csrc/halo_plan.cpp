@@ -43,12 +43,17 @@ void parallel_for(int32_t count, int32_t threads, Fn fn) {
 
 int32_t plan_threads() {
   const unsigned hw = std::thread::hardware_concurrency();
-  return static_cast<int32_t>(std::max(1u, std::min(hw == 0 ? 1u : hw, 8u)));
+  return static_cast<int32_t>(std::max(1u, std::min(hw == 0 ? 1u : hw, 16u)));
 }
 
 }  // namespace
 
-void bisect_parts(const HostGraph& g, int32_t parts, std::vector<int32_t>* part) {
+static bool cancelled(const std::atomic<bool>* cancel) {
+  return cancel != nullptr && cancel->load(std::memory_order_relaxed);
+}
+
+void bisect_parts(const HostGraph& g, int32_t parts, std::vector<int32_t>* part,
+                  const std::atomic<bool>* cancel) {
   const int32_t n = g.n;
   part->assign(static_cast<size_t>(n), 0);
   if (parts <= 1 || n == 0) return;
@@ -93,7 +98,7 @@ void bisect_parts(const HostGraph& g, int32_t parts, std::vector<int32_t>* part)
   }
   const int32_t threads = plan_threads();
   int32_t next_id = 2;
-  while (!level.empty()) {
+  while (!level.empty() && !cancelled(cancel)) {
     std::vector<Task> next(2 * level.size());
     for (size_t i = 0; i < level.size(); ++i) {
       next[2 * i].id = next_id++;
@@ -280,7 +285,8 @@ void build_part(const HostGraph& g, const std::vector<int32_t>& part, const std:
 
 }  // namespace
 
-void build_halo_plan(const HostGraph& g, int32_t parts, int32_t sweeps_per_epoch, HaloPlan* hp) {
+void build_halo_plan(const HostGraph& g, int32_t parts, int32_t sweeps_per_epoch, HaloPlan* hp,
+                     const std::atomic<bool>* cancel) {
   *hp = HaloPlan();
   const int32_t K = g.num_colours;
   const int32_t n = g.n;
@@ -291,7 +297,8 @@ void build_halo_plan(const HostGraph& g, int32_t parts, int32_t sweeps_per_epoch
   if (kHaloHdrClass + K * (D + 3) > kHaloHdr) return;
 
   std::vector<int32_t> part;
-  bisect_parts(g, parts, &part);
+  bisect_parts(g, parts, &part, cancel);
+  if (cancelled(cancel)) return;
   std::vector<int32_t> cls(static_cast<size_t>(n));
   for (int32_t c = 0; c < K; ++c)
     for (int32_t v = g.class_begin[static_cast<size_t>(c)]; v < g.class_begin[static_cast<size_t>(c) + 1]; ++v)
@@ -312,6 +319,7 @@ void build_halo_plan(const HostGraph& g, int32_t parts, int32_t sweeps_per_epoch
   const int32_t threads = std::min(plan_threads(), parts);
   std::vector<std::vector<int64_t>> tags(static_cast<size_t>(threads));
   parallel_for(parts, threads, [&](int32_t p, int32_t w) {
+    if (cancelled(cancel)) return;  // the part stays !ok
     std::vector<int64_t>& tag = tags[static_cast<size_t>(w)];
     if (tag.empty()) tag.assign(static_cast<size_t>(n), 0);
     const int32_t b = part_ptr[static_cast<size_t>(p)];

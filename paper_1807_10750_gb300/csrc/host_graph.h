@@ -3,6 +3,7 @@
 // kernels consume.
 #pragma once
 
+#include <atomic>
 #include <cstdint>
 #include <vector>
 
@@ -161,13 +162,18 @@ struct HaloPlan {
 // breadth-first from a far vertex (the last one a pass from a vertex on the
 // subset's rim reaches; further components follow in order) and split in
 // proportion to the parts each side gets. part[v] for every position v.
-void bisect_parts(const HostGraph& g, int32_t parts, std::vector<int32_t>* part);
+// `cancel` (may be null) stops the work early once it reads true; the result
+// is then incomplete.
+void bisect_parts(const HostGraph& g, int32_t parts, std::vector<int32_t>* part,
+                  const std::atomic<bool>* cancel = nullptr);
 
 // Fills hp (ok = true) when K <= kHaloMaxClasses, D = S * K <= kHaloMaxDepth,
 // every row has at most kHaloMaxWidth entries and int8 weights, every part is
 // non-empty and each part's tables fit in kHaloSmemLimit bytes of shared
-// memory; otherwise hp->ok = false.
-void build_halo_plan(const HostGraph& g, int32_t parts, int32_t sweeps_per_epoch, HaloPlan* hp);
+// memory; otherwise hp->ok = false. Once `cancel` (may be null) reads true it
+// stops early with hp->ok = false.
+void build_halo_plan(const HostGraph& g, int32_t parts, int32_t sweeps_per_epoch, HaloPlan* hp,
+                     const std::atomic<bool>* cancel = nullptr);
 
 // Returns 0, or a negative ISING_* status.
 int build_host_graph(int32_t n, int64_t m, const int32_t* src, const int32_t* dst,

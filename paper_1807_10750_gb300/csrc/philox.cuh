@@ -81,11 +81,28 @@ __device__ __forceinline__ uint4 philox4x32_10(uint32_t x0, uint32_t x1, uint32_
 // The draw of vertex o (original id) in sweep t of replica r on stream s (0
 // flips, 1 initial spins): word o mod 4 of counter (o / 4, t, r, s), so the
 // four vertices 4q .. 4q + 3 share one evaluation.
+// The last round's words 0 and 1 come from one product (B * x2) and words 2
+// and 3 from the other (A * x0), so only the product the wanted word needs
+// is formed there.
 __device__ __forceinline__ uint32_t vertex_word(uint32_t o, uint32_t t, uint32_t replica,
                                                 uint32_t stream, const PhiloxRounds& rk) {
-  const uint4 w = philox4x32_10(o >> 2, t, replica, stream, rk);
+  uint32_t x0 = o >> 2, x1 = t, x2 = replica, x3 = stream;
+#pragma unroll
+  for (int r = 0; r < 9; ++r) {
+    const uint64_t pa = static_cast<uint64_t>(0xD2511F53u) * x0;
+    const uint64_t pb = static_cast<uint64_t>(0xCD9E8D57u) * x2;
+    const uint32_t n0 = static_cast<uint32_t>(pb >> 32) ^ x1 ^ rk.lo[r];
+    const uint32_t n2 = static_cast<uint32_t>(pa >> 32) ^ x3 ^ rk.hi[r];
+    x1 = static_cast<uint32_t>(pb);
+    x3 = static_cast<uint32_t>(pa);
+    x0 = n0;
+    x2 = n2;
+  }
   const uint32_t k = o & 3u;
-  return k == 0u ? w.x : (k == 1u ? w.y : (k == 2u ? w.z : w.w));
+  const bool low_pair = k < 2u;  // words 0, 1: B * x2; words 2, 3: A * x0
+  const uint64_t prod = static_cast<uint64_t>(low_pair ? 0xCD9E8D57u : 0xD2511F53u) * (low_pair ? x2 : x0);
+  if (k & 1u) return static_cast<uint32_t>(prod);
+  return static_cast<uint32_t>(prod >> 32) ^ (low_pair ? (x1 ^ rk.lo[9]) : (x3 ^ rk.hi[9]));
 }
 
 }  // namespace isingx

@@ -402,6 +402,7 @@ def test_auto_engine_choice(P):
     for g, kw, want in cases:
         with P.ising_create(g.n, g.src, g.dst, g.w) as h:
             assert P.ising_engine_used(h) == -1
+            P.ising_halo_info(h)  # the halo plan is built by a host thread: wait for it
             P.ising_init_random(h, 1)
             P.ising_anneal(h, p0=0.1, t_total=10, seed=1, **kw)
             assert P.ising_engine_used(h) == want, (g.n, kw)
