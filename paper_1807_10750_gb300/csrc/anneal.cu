@@ -144,6 +144,40 @@ __global__ void __launch_bounds__(kPersistBlock, 2)
   int c = 0;
   SweepArgs a = sweep_args(t_begin + 0, T, T0, replica);
   const bool rotate = __ldg(phase_items + num_phases) >= nwarps;
+  if (PASS == kPassRacy && rotate) {
+    // racy pass over at least as many items as warps: item i of the sweep
+    // (classes in order) belongs to warp i mod nwarps, so a warp meets its
+    // items in class order without walking the classes; a grid barrier ends
+    // every sweep
+    const int ni = __ldg(phase_items + num_phases);
+    bool skip = bs->skip_block == static_cast<int>(blockIdx.x) + 1;
+    isingx::Staged<PACKED> sr;
+    for (uint32_t kk = 0; kk < sweeps; ++kk) {
+      const SweepArgs ak = sweep_args(t_begin + kk, T, T0, replica);
+      for (int i = warp; i < ni; i += nwarps) {
+        isingx::stage_item<PACKED>(d, d.items[i], ak, rk, lane, sr);
+        isingx::finish_item<PACKED, PASS>(d, sr, ak, rk, lane, unused);
+      }
+      if (nflip0 != 0u) {
+        // Algorithm 1: once every update of the sweep is visible, one warp
+        // flips the sweep's N random spins; the barrier below publishes them
+        isingx::barrier_arrive(bs, skip);
+        skip = false;
+        target += gridDim.x;
+        if (!isingx::barrier_wait(bs, target)) return;
+        const uint32_t N = isingx::nflip_count(nflip0, T, t_begin + kk);
+        if (blockIdx.x == 0 && threadIdx.x < 32 && N > 0u)
+          isingx::nflip_step(d, pos, bitmap, picked, N, static_cast<uint32_t>(t_begin + kk), replica,
+                             rk, lane);
+      }
+      if (kk + 1 == sweeps) break;
+      isingx::barrier_arrive(bs, skip);
+      skip = false;
+      target += gridDim.x;
+      if (!isingx::barrier_wait(bs, target)) return;
+    }
+    return;
+  }
   int ib = class_start<PASS>(phase_items, 0, warp, nwarps, rotate), ie = __ldg(phase_items + 1);
   isingx::Staged<PACKED> st;
   bool have = ib < ie;

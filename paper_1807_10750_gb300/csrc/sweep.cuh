@@ -406,8 +406,6 @@ __device__ __forceinline__ void finish_item(const DevGraph& d, const Staged<PACK
   }
   f += strided_field<PACKED, PASS>(d, s.it.e_begin + lane + 128, s.it.e_end, 32, a);
   const int v = s.it.v_begin;
-  const bool flip = (PASS != kPassEnergy && lane == 0) &&
-                    flip_drawn(d, v, static_cast<uint32_t>(__ldg(d.orig + v)), a, rk);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(kFullMask, f, o);
   if (PASS == kPassEnergy) {
@@ -426,7 +424,8 @@ __device__ __forceinline__ void finish_item(const DevGraph& d, const Staged<PACK
       const long long low = static_cast<long long>((old & kSliceLowMask) + (mine & kSliceLowMask));
       const int total = static_cast<int>(low - static_cast<long long>(parts) * kSliceBias);
       d.slice_acc[slot] = 0ull;
-      apply_update<PASS>(d, v, total, flip, a);
+      // only the slice that completes the row draws its flip
+      apply_update<PASS>(d, v, total, flip_drawn(d, v, static_cast<uint32_t>(__ldg(d.orig + v)), a, rk), a);
     }
   }
 }
