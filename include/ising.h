@@ -99,7 +99,9 @@ enum {
 enum {
   ISING_ENGINE_AUTO = 0,       /* with cooperative launches, for deterministic linear anneals:
                                   PERSISTENT's one-block form for small graphs, else HALO when its
-                                  plan exists and repeats at most 1.6x the work, else ITEMFLOW for
+                                  plan is ready and repeats at most 1.6x the work (a host thread
+                                  builds the plan from the handle's second such call on; no call
+                                  waits for it), else ITEMFLOW for
                                   graphs without sliced rows, else PERSISTENT; racy and N-flip
                                   anneals: PERSISTENT; without cooperative launches: PHASE */
   ISING_ENGINE_PHASE = 1,      /* one kernel launch per colour class */

@@ -994,10 +994,7 @@ int ising_create(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, c
     delete g;
     return e == cudaErrorMemoryAllocation ? ISING_ENOMEM : ISING_ECUDA;
   }
-  if (keep_host) {
-    g->host.reset(new (std::nothrow) HostGraph(std::move(hg)));
-    start_planner(g);
-  }
+  if (keep_host) g->host.reset(new (std::nothrow) HostGraph(std::move(hg)));
   *out = g;
   return ISING_OK;
 }
@@ -1093,7 +1090,9 @@ static int anneal_impl(ising_graph* g, const ising_schedule* sched, uint32_t swe
     if (!coop) {
       engine = ISING_ENGINE_PHASE;
     } else if (!g->block_ok && mode == ISING_MODE_DET && sched->kind == ISING_SCHED_LINEAR) {
-      ISING_CUDA(g, plan_halo(g, false));
+      // a handle that anneals more than once gets the halo plan: the second
+      // call starts the planner, and no call waits for it
+      if (g->auto_calls++ > 0) ISING_CUDA(g, plan_halo(g, false));
       if (g->halo_state == 1 && g->halo_ratio <= kHaloAutoRatio)
         engine = ISING_ENGINE_HALO;
       else

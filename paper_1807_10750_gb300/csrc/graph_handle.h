@@ -73,9 +73,9 @@ struct ising_graph {
   int32_t* d_block_chunk_len = nullptr;
   int32_t* d_block_class_chunk = nullptr;
   // halo engine (halo.cuh): the host graph is kept for its plan when the graph
-  // can qualify; a host thread started by ising_create builds the plan while
-  // the caller goes on (AUTO uses the engine once it is ready), and the first
-  // call that needs it uploads it
+  // can qualify; a host thread builds the plan while the caller goes on
+  // (started by AUTO's second anneal call, or by a call that asks for the
+  // engine and waits), and the first call that needs it uploads it
   std::unique_ptr<isingx::HostGraph> host;
   std::unique_ptr<isingx::HaloPlan> pending;  // written by the planner thread
   std::thread planner;
@@ -83,6 +83,7 @@ struct ising_graph {
   std::atomic<bool> plan_cancel{false};       // ising_destroy: stop the planner early
   int halo_state = 0;   // 0 not planned, 1 planned, -1 no plan possible
   int halo_sweeps = 0;  // requested sweeps per exchange (0: automatic)
+  uint64_t auto_calls = 0;  // AUTO's deterministic linear anneal calls
   int32_t halo_parts = 0, halo_S = 0, halo_smem = 0;
   double halo_ratio = 0.0;
   int32_t* d_halo_hdr = nullptr;

@@ -141,19 +141,25 @@ def test_halo_fallbacks(P):
 
 
 def test_auto_does_not_wait_for_the_plan_and_destroy_cancels_it(P):
-    # AUTO runs another engine while the host planner is busy; either way the
-    # result is the oracle's, and destroying the handle stops the planner
+    # AUTO's first call never plans and later calls run another engine while
+    # the host planner is busy; either way the result is the oracle's, and
+    # destroying the handle stops the planner
     import time
     g = synth.torus_graph(512, 3, weights="pm1")
     s0 = oracle.init_spins(g.n, 4)
     want = oracle.anneal(g.n, g.src, g.dst, g.w, s0, seed=5, p0=0.1, T=6)
     with P.ising_create(g.n, g.src, g.dst, g.w) as h:
         P.ising_set_spins(h, s0)
-        P.ising_anneal(h, p0=0.1, t_total=6, seed=5)
+        P.ising_anneal(h, p0=0.1, t_total=6, seed=5, sweeps=2)   # the first call never plans
+        assert P.ising_engine_used(h) == P.ISING_ENGINE_ITEMFLOW
+        P.ising_anneal(h, p0=0.1, t_total=6, seed=5, t_begin=2)  # starts the planner
         assert P.ising_engine_used(h) in (P.ISING_ENGINE_HALO, P.ISING_ENGINE_ITEMFLOW)
         assert np.array_equal(P.ising_get_spins(h), want)
     t0 = time.perf_counter()
     h = P.ising_create(g.n, g.src, g.dst, g.w)
+    P.ising_init_random(h, 1)
+    for _ in range(2):
+        P.ising_anneal(h, p0=0.1, t_total=4, seed=1)
     P.ising_destroy(h)
     assert time.perf_counter() - t0 < 5.0
 
