@@ -338,42 +338,74 @@ __device__ __forceinline__ void finish_light_shape(const DevGraph& d, const Stag
   }
 }
 
-// Rows too heavy for a light item but not sliced: lane groups of g lanes
-// (power of two >= a quarter of the mean degree) gather one CSR row per pass,
-// 32 / g rows per pass; the 32 fields of a chunk are then moved to one lane each.
+// Rows too heavy for a light item but not sliced, 32 at a time: their CSR
+// entries are contiguous, so the warp streams them lane-strided (lane l takes
+// entries e0 + l + 32 k, four in flight), finds each entry's row among the
+// block's 33 row offsets (one binary search per batch, then forward steps),
+// and adds each run of a row's terms into the row's shared accumulator; lane
+// l then updates row l. Every kernel that finishes items runs at most
+// kGroupWarps warps per block.
+constexpr int kGroupWarps = 16;
+
 template <bool PACKED, int PASS>
 __device__ __forceinline__ void finish_group_rows(const DevGraph& d, const WorkItem& it,
                                                   const SweepArgs& a, const PhiloxRounds& rk,
                                                   int lane, long long& energy) {
-  const int nv = it.v_end - it.v_begin;
-  const int mean = (it.e_end - it.e_begin + nv - 1) / nv;
-  int lg = 0;
-  while ((4 << lg) < mean && lg < 5) ++lg;
-  const int g = 1 << lg;
-  const int rows_per_pass = 32 >> lg;
-  const int sub = lane & (g - 1);
-  const int grp = lane >> lg;
+  __shared__ int group_scratch[kGroupWarps][65];  // per warp: 33 row offsets, 32 fields
+  int* rp = group_scratch[threadIdx.x >> 5];
+  int* acc = rp + 33;
   for (int base = it.v_begin; base < it.v_end; base += 32) {
     const int rows = min(32, it.v_end - base);
-    const int passes = (rows + rows_per_pass - 1) / rows_per_pass;
-    int my_f = 0;
-    for (int p = 0; p < passes; ++p) {
-      const int v = base + p * rows_per_pass + grp;
-      int f = 0;
-      if (v < it.v_end)
-        f = strided_field<PACKED, PASS>(d, __ldg(d.row_ptr + v) + sub, __ldg(d.row_ptr + v + 1), g,
-                                        a);
-      for (int o = g >> 1; o > 0; o >>= 1) f += __shfl_xor_sync(kFullMask, f, o);
-      const int got = __shfl_sync(kFullMask, f, (lane % rows_per_pass) << lg);
-      if (lane / rows_per_pass == p) my_f = got;
+    if (lane < rows) rp[lane] = __ldg(d.row_ptr + base + lane);
+    if (lane == 0) rp[rows] = __ldg(d.row_ptr + base + rows);
+    acc[lane] = 0;
+    __syncwarp();
+    const int e0 = rp[0], e1 = rp[rows];
+    for (int eb = e0; eb < e1; eb += 128) {
+      Edge<PACKED> x[4];
+      int b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) x[u].load(d, eb + lane + 32 * u, eb + lane + 32 * u < e1);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) b[u] = load_state<PASS>(d, x[u].col());
+      int e = eb + lane;
+      if (e < e1) {
+        // the row holding entry e: the largest r with rp[r] <= e
+        int lo = 0, hi = rows - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (rp[mid] <= e)
+            lo = mid;
+          else
+            hi = mid - 1;
+        }
+        int r = lo;
+        int run = 0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          e = eb + lane + 32 * u;
+          if (e < e1) {
+            while (rp[r + 1] <= e) {
+              if (run != 0) atomicAdd(acc + r, run);
+              run = 0;
+              ++r;
+            }
+            run += x[u].weight() * ready_spin<PASS>(d, x[u].col(), b[u], a);
+          }
+        }
+        if (run != 0) atomicAdd(acc + r, run);
+      }
     }
+    __syncwarp();
     const int v = base + lane;
-    if (v < it.v_end) {
+    if (lane < rows) {
+      const int f = acc[lane];
       if (PASS == kPassEnergy)
-        energy += static_cast<long long>(spin_of(d.spins[v])) * my_f;
+        energy += static_cast<long long>(spin_of(d.spins[v])) * f;
       else
-        apply_update<PASS>(d, v, my_f, flip_drawn(d, v, static_cast<uint32_t>(__ldg(d.orig + v)), a, rk), a);
+        apply_update<PASS>(d, v, f, flip_drawn(d, v, static_cast<uint32_t>(__ldg(d.orig + v)), a, rk), a);
     }
+    __syncwarp();
   }
 }
 
