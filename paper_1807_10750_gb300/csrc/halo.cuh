@@ -268,11 +268,11 @@ __global__ void __launch_bounds__(kHaloBlock, 1)
           dst[__ldg(gp + tc[0] + r)] = halo_state(sp[tc[0] + r], par);
       }
     }
+    // the block barrier orders every thread's export before thread 0's
+    // release, and a release covers all writes ordered before it
     __syncthreads();
-    if (threadIdx.x == 0 && h.skip_block != p + 1) {
-      __threadfence();
+    if (threadIdx.x == 0 && h.skip_block != p + 1)
       halo_st_release(h.flags + static_cast<size_t>(p) * kHaloFlagStride, e + 1u);
-    }
   }
   // after an odd number of epochs the handle's buffer was read in epoch
   // E - 1: write the part's vertices once every neighbour has published E
