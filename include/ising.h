@@ -81,10 +81,11 @@ enum {
    * applied as a 32-bit integer threshold:
    *   T0     = floor(p0 * 2^32 + 0.5) clamped to [0, 2^32 - 1]
    *   thr[t] = t_total <= 1 ? 0 : floor(T0 * (t_total - 1 - t) / (t_total - 1))
-   * and spin i flips in sweep t iff x < thr[t], where x is word 0 of
-   * Philox4x32-10 (Salmon et al., SC'11) with
+   * and spin i flips in sweep t iff x < thr[t], where, with o the original
+   * id of i, x is word o mod 4 of Philox4x32-10 (Salmon et al., SC'11) with
    *   key     = (lo32(seed), hi32(seed))
-   *   counter = (original id of i, t, replica, 0).                        */
+   *   counter = (floor(o / 4), t, replica, 0)
+   * (the four vertices 4q .. 4q + 3 share one evaluation).                */
   ISING_SCHED_LINEAR = 0,
   /* Algorithm 1: a sweep updates every spin (no per-spin flips), then flips
    * N_t distinct randomly chosen spins, N_t = floor(n0 (t_total-1-t) /
@@ -237,8 +238,9 @@ int ising_set_spins(ising_graph* g, const int8_t* in, int on_device);
 
 /*
  * ising_init_random -- initial spins (Algorithm 2, "initialize all sigma_i"):
- * s_i = -1 if bit 31 of Philox word 0 with counter (i, 0, replica, 1) and key
- * (lo32(seed), hi32(seed)) is set, else +1.
+ * s_i = -1 if bit 31 of word o mod 4 of Philox4x32-10 with counter
+ * (floor(o / 4), 0, replica, 1) and key (lo32(seed), hi32(seed)) is set, else
+ * +1, o the original id of i.
  */
 int ising_init_random(ising_graph* g, uint64_t seed, uint32_t replica);
 
@@ -295,8 +297,9 @@ int ising_plan_halo(int32_t n, int64_t m, const int32_t* src, const int32_t* dst
  * `replicas` independent replicas by the deterministic colour-class schedule
  * of ISING_MODE_DET, all in one persistent kernel launch (captured in a CUDA
  * graph and replayed). The randomness of instance g, replica r is Philox4x32-10
- * with key (lo32(seed), hi32(seed) ^ g * 0x9E3779B9) and counter
- * (vertex id within g, sweep t, r, 0) for flips and (vertex id, 0, r, 1) for
+ * with key (lo32(seed), hi32(seed) ^ g * 0x9E3779B9): vertex v (id within g)
+ * draws word v mod 4 of counter (floor(v / 4), sweep t, r, 0) for flips and
+ * of (floor(v / 4), 0, r, 1) for
  * ising_batch_init_random -- so each instance/replica reproduces a single-graph
  * anneal keyed by that instance and replica exactly.
  * ------------------------------------------------------------------------ */

@@ -77,7 +77,7 @@ struct DevGraph {
 };
 
 struct SweepArgs {
-  uint32_t thr;      // flip iff Philox word 0 < thr
+  uint32_t thr;      // flip iff the vertex's Philox word (vertex_word) < thr
   uint32_t t;        // sweep index (counter word 1)
   uint32_t replica;  // counter word 2
   int class_lo;      // kPassFlow: first position of the current colour class
