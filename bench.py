@@ -243,17 +243,19 @@ def run_reference(args, world, rank):
 
 def oracle_sweep_cost(g, sch):
     """Seconds per sweep of the oracle on this graph, without the fixed cost
-    of its adjacency build: two calls of different length, differenced."""
+    of its adjacency build: two calls of different length, differenced; never
+    below a tenth of the longer call's time per sweep (the difference is noisy
+    when the build dominates)."""
     import oracle
     oracle.build()
     T = sch["sweeps"]
     s = oracle.init_spins(g.n, sch["seed"])
     cost = []
-    for k in (1, 5):
+    for k in (2, 10):
         t0 = time.perf_counter()
-        oracle.anneal(g.n, g.src, g.dst, g.w, s, seed=sch["seed"], p0=sch["p0"], T=T, sweeps=k)
+        oracle.anneal(g.n, g.src, g.dst, g.w, s, seed=sch["seed"], p0=sch["p0"], T=T, sweeps=min(k, T))
         cost.append(time.perf_counter() - t0)
-    return max((cost[1] - cost[0]) / 4, 1e-6)
+    return max((cost[1] - cost[0]) / 8, 0.1 * cost[1] / 10, 1e-6)
 
 
 def cpu_baseline(g, sch, target_s: float):
