@@ -762,7 +762,9 @@ cudaError_t plan_halo(ising_graph* g, bool wait) {
   if (e != cudaSuccess) {
     free_halo(g);
     g->halo_state = -1;
-    return e == cudaErrorMemoryAllocation ? cudaSuccess : e;
+    if (e != cudaErrorMemoryAllocation) return e;
+    cudaGetLastError();  // out of memory: no plan, and no error left for later checks
+    return cudaSuccess;
   }
   g->halo_state = 1;
   g->halo_parts = hp.parts;

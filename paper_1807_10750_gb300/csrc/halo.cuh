@@ -2,10 +2,11 @@
 // cooperative launch per anneal call, every sweep of it.
 //
 // A block keeps its region's spins (int8 +1 / -1), sliced-ELL rows and the
-// epoch's flip bits in shared memory. An epoch of S sweeps runs D = S * K colour phases
-// there with only block barriers between them (phase j: class (j - 1) mod K,
-// rows at most D - j hops out). At the end of the epoch the block writes its
-// own vertices' state bytes to the epoch's spin buffer (two buffers
+// epoch's flip bits in shared memory. An epoch of S sweeps runs D = S * K
+// colour phases there with only block barriers between them (phase j: class
+// (j - 1) mod K, rows at most D - j hops out). At the end of the epoch the
+// block writes the state bytes of its vertices that other parts import (all of
+// its vertices after the last epoch) to the epoch's spin buffer (two buffers
 // alternate), publishes the epoch number with a release store, and before the
 // next epoch waits (bounded) until every part whose vertices lie in its halo
 // has published the same epoch, then reloads the halo from that buffer. The
