@@ -738,7 +738,6 @@ cudaError_t plan_halo(ising_graph* g, bool wait) {
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, isingx::kHaloBlock, hp.smem_bytes);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaSuccess;
-  const size_t N = static_cast<size_t>(g->n);
   do {
     if ((e = alloc_copy(&g->d_halo_hdr, hp.hdr.data(), hp.hdr.size(), g->stream)) != cudaSuccess) break;
     if ((e = alloc_copy(&g->d_halo_words, hp.words.data(), hp.words.size(), g->stream)) != cudaSuccess) break;
@@ -755,7 +754,10 @@ cudaError_t plan_halo(ising_graph* g, bool wait) {
     if ((e = alloc_copy<unsigned>(&g->d_halo_flags, nullptr,
                                   static_cast<size_t>(hp.parts) * isingx::kHaloFlagStride, g->stream)) != cudaSuccess)
       break;
-    if ((e = alloc_copy<int8_t>(&g->d_spins2, nullptr, N + 1, g->stream)) != cudaSuccess) break;
+    if ((e = alloc_copy<int8_t>(&g->d_spins2, nullptr, 2 * static_cast<size_t>(hp.mailbox_slots) + 2,
+                                g->stream)) != cudaSuccess)
+      break;
+    g->halo_mail = static_cast<size_t>(hp.mailbox_slots) + 1;
     // the host vectors are freed on return: wait for the copies
     e = cudaStreamSynchronize(g->stream);
   } while (false);
@@ -792,7 +794,8 @@ cudaError_t launch_halo(ising_graph* g, uint64_t t_begin, uint32_t sweeps, uint6
   h.exports = g->d_halo_exports;
   h.quads = g->d_halo_quads;
   h.nbrs = g->d_halo_nbrs;
-  h.buf1 = g->d_spins2;
+  h.mail0 = g->d_spins2;
+  h.mail1 = g->d_spins2 + g->halo_mail;
   h.flags = g->d_halo_flags;
   h.error = &g->d_barrier->error;
   h.budget = g->wait_budget_ns > 0 ? static_cast<long long>(g->wait_budget_ns) : isingx::kBarrierBudgetNs;

@@ -95,7 +95,8 @@ struct ising_graph {
   int32_t* d_halo_exports = nullptr;
   int32_t* d_halo_quads = nullptr;
   unsigned* d_halo_flags = nullptr;
-  int8_t* d_spins2 = nullptr;
+  int8_t* d_spins2 = nullptr;        // the two mailbox buffers of the halo engine
+  size_t halo_mail = 0;              // bytes of one mailbox buffer
   uint8_t* d_bias = nullptr;         // per-position flip bias (null: none)
   int32_t* d_rowid = nullptr;        // row of every CSR entry (built on first use)
   isingx::BarrierState* d_barrier = nullptr;

@@ -5,15 +5,18 @@
 // epoch's flip bits in shared memory. An epoch of S sweeps runs D = S * K
 // colour phases there with only block barriers between them (phase j: class
 // (j - 1) mod K, rows at most D - j hops out). At the end of the epoch the
-// block writes the state bytes of its vertices that other parts import (all of
-// its vertices after the last epoch) to the epoch's spin buffer (two buffers
-// alternate), publishes the epoch number with a release store, and before the
-// next epoch waits (bounded) until every part whose vertices lie in its halo
-// has published the same epoch, then reloads the halo from that buffer. The
-// Philox flip decisions of Algorithm 2 do not depend on the spins, so a block
-// draws the next epoch's flips before it waits.
+// block writes the state bytes of its vertices that other parts import into
+// their mailbox slots (one slot per import, laid out in each importer's
+// order; two mailbox buffers alternate by epoch), publishes the epoch number
+// with a release store, and before the next epoch waits (bounded) until every
+// part whose vertices lie in its halo has published the same epoch, then
+// reloads its halo from its own contiguous slots. The Philox flip decisions of
+// Algorithm 2 do not depend on the spins, so a block draws the next epoch's
+// flips before it waits. After the last epoch every block writes its
+// vertices into the handle's spin buffer, which the other blocks read only
+// for their first epoch.
 //
-// Buffer reuse is safe: a block writes buffer (e + 1) & 1 at the end of epoch
+// Mailbox reuse is safe: a block writes buffer (e + 1) & 1 at the end of epoch
 // e, after it has seen every neighbour part publish epoch e, i.e. after those
 // parts finished reading that buffer in epoch e - 1 (the neighbour relation is
 // symmetric: within D hops either way).
@@ -39,7 +42,8 @@ struct HaloArgs {
   const int32_t* exports;
   const int32_t* quads;
   const int32_t* nbrs;
-  int8_t* buf1;       // second spin buffer (the first is DevGraph::spins)
+  int8_t* mail0;      // mailbox buffers (one slot per import of every part), by epoch parity
+  int8_t* mail1;
   unsigned* flags;    // per part: epochs published in this launch
   int* error;         // a wait that gave up sets it
   long long budget;   // ns per wait
@@ -237,12 +241,10 @@ __global__ void __launch_bounds__(kHaloBlock, 1)
     }
     if (e > 0) {
       if (!halo_wait(h, nbr, nbr_len, e, &abort_flag)) return;
-      const int8_t* src = (e & 1u) ? h.buf1 : d.spins;
+      const int8_t* mail = ((e & 1u) ? h.mail1 : h.mail0) + hd[kHaloImportOff] / 2;
       const int nimp = hd[kHaloImportLen];
-      for (int q = threadIdx.x; q < nimp; q += kHaloBlock) {
-        const int2 lv = __ldg(imp + q);
-        sp[lv.x] = static_cast<int8_t>(1 - 2 * (__ldcg(src + lv.y) & 1));
-      }
+      for (int q = threadIdx.x; q < nimp; q += kHaloBlock)
+        sp[__ldg(imp + q).x] = static_cast<int8_t>(1 - 2 * (__ldcg(mail + q) & 1));
     }
     __syncthreads();
     // D_e phases: phase j updates class (j - 1) mod K at most D_e - j hops out
@@ -251,22 +253,23 @@ __global__ void __launch_bounds__(kHaloBlock, 1)
       halo_rows(sw, ssl, sp, sflip + ((j - 1) / K) * nslices, tc[0], tc[1], tc[2 + De - j], warp, lane);
       __syncthreads();
     }
-    // publish the part's own state bytes for epoch e + 1: those other parts
-    // import; after the last epoch every own vertex, into the handle's buffer
-    // (directly after an even number of epochs, below after an odd one)
+    // publish: the mailbox slots other parts import for epoch e + 1; after
+    // the last epoch (from the second on, every neighbour has finished the
+    // first epoch's load of the handle's buffer) every own vertex into the
+    // handle's buffer
     const int par = par0 ^ static_cast<int>(min((e + 1u) * static_cast<uint32_t>(S), sweeps) & 1u);
-    int8_t* dst = ((e + 1u) & 1u) ? h.buf1 : d.spins;
     if (e + 1u < E) {
+      int8_t* mail = ((e + 1u) & 1u) ? h.mail1 : h.mail0;
       const int nexp = hd[kHaloExportLen];
       for (int q = threadIdx.x; q < nexp; q += kHaloBlock) {
-        const int2 lv = __ldg(exq + q);
-        dst[lv.y] = halo_state(sp[lv.x], par);
+        const int2 ls = __ldg(exq + q);
+        mail[ls.y] = halo_state(sp[ls.x], par);
       }
-    } else if ((E & 1u) == 0u) {
+    } else if (E > 1u) {
       for (int c = 0; c < K; ++c) {
         const int* tc = hd + ct + c * (D + 3);
         for (int r = threadIdx.x; r < tc[2]; r += kHaloBlock)
-          dst[__ldg(gp + tc[0] + r)] = halo_state(sp[tc[0] + r], par);
+          d.spins[__ldg(gp + tc[0] + r)] = halo_state(sp[tc[0] + r], par);
       }
     }
     // the block barrier orders every thread's export before thread 0's
@@ -275,10 +278,10 @@ __global__ void __launch_bounds__(kHaloBlock, 1)
     if (threadIdx.x == 0 && h.skip_block != p + 1)
       halo_st_release(h.flags + static_cast<size_t>(p) * kHaloFlagStride, e + 1u);
   }
-  // after an odd number of epochs the handle's buffer was read in epoch
-  // E - 1: write the part's vertices once every neighbour has published E
-  if (E & 1u) {
-    if (!halo_wait(h, nbr, nbr_len, E, &abort_flag)) return;
+  // a single epoch: write the part's vertices once every neighbour has
+  // finished it (and with it its load of the handle's buffer)
+  if (E == 1u) {
+    if (!halo_wait(h, nbr, nbr_len, 1u, &abort_flag)) return;
     const int par = par0 ^ static_cast<int>(sweeps & 1u);
     for (int c = 0; c < K; ++c) {
       const int* tc = hd + ct + c * (D + 3);

@@ -326,10 +326,37 @@ void build_halo_plan(const HostGraph& g, int32_t parts, int32_t sweeps_per_epoch
     build_part(g, part, cls, part_verts.data() + b, part_ptr[static_cast<size_t>(p) + 1] - b, p, K, D,
                sweeps_per_epoch, tag, &tables[static_cast<size_t>(p)]);
   });
-  // own vertices that some other part imports are exported between epochs
-  std::vector<uint8_t> exported(static_cast<size_t>(n), 0);
-  for (const PartTables& pt : tables)
-    for (size_t q = 1; q < pt.imports.size(); q += 2) exported[static_cast<size_t>(pt.imports[q])] = 1;
+  // mailboxes: import i of a part reads slot (the part's first import) + i;
+  // its vertex's owner writes that slot between epochs, from its own copy
+  std::vector<int32_t> owner_local(static_cast<size_t>(n), 0);
+  std::vector<int64_t> import_base(static_cast<size_t>(parts) + 1, 0);
+  for (int32_t p = 0; p < parts; ++p) {
+    const PartTables& pt = tables[static_cast<size_t>(p)];
+    if (!pt.ok) {
+      *hp = HaloPlan();
+      return;
+    }
+    import_base[static_cast<size_t>(p) + 1] = import_base[static_cast<size_t>(p)] + static_cast<int64_t>(pt.imports.size() / 2);
+    for (int32_t c = 0; c < K; ++c) {
+      const int32_t* T = pt.hdr + kHaloHdrClass + c * (D + 3);
+      for (int32_t l = T[0]; l < T[0] + T[2]; ++l) owner_local[static_cast<size_t>(pt.gpos[static_cast<size_t>(l)])] = l;
+    }
+  }
+  if (import_base[static_cast<size_t>(parts)] >= (int64_t(1) << 31)) {
+    *hp = HaloPlan();
+    return;
+  }
+  std::vector<std::vector<int32_t>> out(static_cast<size_t>(parts));  // per owner: (local, slot)
+  for (int32_t q = 0; q < parts; ++q) {
+    const PartTables& pt = tables[static_cast<size_t>(q)];
+    for (size_t i = 0; 2 * i < pt.imports.size(); ++i) {
+      const int32_t v = pt.imports[2 * i + 1];
+      std::vector<int32_t>& o = out[static_cast<size_t>(part[static_cast<size_t>(v)])];
+      o.push_back(owner_local[static_cast<size_t>(v)]);
+      o.push_back(static_cast<int32_t>(import_base[static_cast<size_t>(q)] + static_cast<int64_t>(i)));
+    }
+  }
+  hp->mailbox_slots = import_base[static_cast<size_t>(parts)];
   hp->hdr.assign(static_cast<size_t>(parts) * kHaloHdr, 0);
   int64_t smem_max = 0;
   for (int32_t p = 0; p < parts; ++p) {
@@ -348,17 +375,9 @@ void build_halo_plan(const HostGraph& g, int32_t parts, int32_t sweeps_per_epoch
     H[kHaloQuadOff] = static_cast<int32_t>(hp->quads.size());
     hp->quads.insert(hp->quads.end(), pt.quads.begin(), pt.quads.end());
     H[kHaloExportOff] = static_cast<int32_t>(hp->exports.size());
-    for (int32_t c = 0; c < K; ++c) {
-      const int32_t* T = pt.hdr + kHaloHdrClass + c * (D + 3);
-      for (int32_t l = T[0]; l < T[0] + T[2]; ++l) {
-        const int32_t v = pt.gpos[static_cast<size_t>(l)];
-        if (exported[static_cast<size_t>(v)]) {
-          hp->exports.push_back(l);
-          hp->exports.push_back(v);
-        }
-      }
-    }
-    H[kHaloExportLen] = (static_cast<int32_t>(hp->exports.size()) - H[kHaloExportOff]) / 2;
+    hp->exports.insert(hp->exports.end(), out[static_cast<size_t>(p)].begin(), out[static_cast<size_t>(p)].end());
+    H[kHaloExportLen] = static_cast<int32_t>(out[static_cast<size_t>(p)].size() / 2);
+    out[static_cast<size_t>(p)] = std::vector<int32_t>();
     hp->words.insert(hp->words.end(), pt.words.begin(), pt.words.end());
     hp->slices.insert(hp->slices.end(), pt.slices.begin(), pt.slices.end());
     hp->gpos.insert(hp->gpos.end(), pt.gpos.begin(), pt.gpos.end());

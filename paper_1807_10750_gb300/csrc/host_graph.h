@@ -118,7 +118,7 @@ enum HaloHdr {
   kHaloOwned = 10,
   kHaloFlipWords = 11,  // flip bitmap words of a full epoch: S * slices
   kHaloExportOff = 12,  // first entry in `exports` (pairs)
-  kHaloExportLen = 13,  // the part's vertices in some other part's halo
+  kHaloExportLen = 13,  // mailbox slots the part writes between epochs
   kHaloQuadOff = 14,    // first entry in `quads` (triples)
   kHaloQuadLen = 15     // vertex quads with an updated row in the region
 };
@@ -152,8 +152,10 @@ struct HaloPlan {
   std::vector<int32_t> words;     // sliced ELL
   std::vector<int32_t> slices;    // (word offset within the part << 6) | width
   std::vector<int32_t> gpos;      // local index -> position
-  std::vector<int32_t> imports;   // (local index, position) of halo vertices (> 0 hops)
-  std::vector<int32_t> exports;   // (local index, position) of own vertices other parts import
+  std::vector<int32_t> imports;   // (local index, position) of halo vertices (> 0 hops); import i
+                                  // of a part reads mailbox slot (the part's first import / 2) + i
+  std::vector<int32_t> exports;   // (local index, mailbox slot): an own vertex some part imports
+  int64_t mailbox_slots = 0;      // all parts' imports
   std::vector<int32_t> quads;     // (q, l0 | l1 << 16, l2 | l3 << 16) per quad
   std::vector<int32_t> nbrs;      // parts owning some vertex of the halo
 };
