@@ -39,7 +39,8 @@ struct BatchGraph {
   int32_t vtx_base;    // first vertex in the concatenated vertex arrays
   int32_t row_base;    // first entry of this instance's row_ptr (n + 1 entries)
   int32_t class_base;  // first entry of this instance's class bounds (num_classes + 1)
-  int32_t byte_lanes;  // 1: every row's sum of |w| is at most 255 (byte-lane sums apply)
+  int32_t byte_lanes;  // 1: every row's sum of |w| is at most 255 (byte-lane sums apply);
+                       // 2: moreover every weight is +1 or -1
 };
 
 struct BatchDev {
@@ -119,7 +120,29 @@ __global__ void __launch_bounds__(BLOCK)
           const int e1 = __ldg(rp + v + 1);
           int wsum = 0;
           int acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-          if (G.byte_lanes) {
+          if (G.byte_lanes == 2) {
+            // +-1 weights: w_j s_j = -1 exactly when the neighbour's spin bit
+            // differs from the weight's sign bit, so with x = b ^ (0xff if
+            // w < 0) the byte lanes count the negative products and
+            // f_r = degree - 2 * count_r (each nibble of x spread into byte
+            // lanes as below)
+            uint32_t lo = 0, hi = 0;
+            const int e0 = __ldg(rp + v);
+            for (int e = e0; e < e1; ++e) {
+              const uint32_t word = static_cast<uint32_t>(__ldg(d.adj + e));
+              // 0, or 0xffffffff for a negative weight byte
+              const uint32_t neg = static_cast<uint32_t>(static_cast<int32_t>(word << 24) >> 31);
+              const uint32_t b = sp[word >> 8];
+              lo += (((b ^ neg) & 0xfu) * 0x00204081u) & 0x01010101u;
+              hi += ((((b >> 4) ^ neg) & 0xfu) * 0x00204081u) & 0x01010101u;
+            }
+            wsum = e1 - e0;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+              acc[r] = static_cast<int>((lo >> (8 * r)) & 0xffu);
+              acc[r + 4] = static_cast<int>((hi >> (8 * r)) & 0xffu);
+            }
+          } else if (G.byte_lanes) {
             // the 8 replica bits of a neighbour spread into 8 byte lanes (4 per
             // word: x * 0x00204081 puts bit k of a nibble at bit 8k), weighted
             // by |w| into a positive and a negative accumulator; no lane can
@@ -446,7 +469,9 @@ int ising_batch_create(int32_t num_graphs, const int32_t* n, const int64_t* m, c
           row += std::abs(static_cast<int64_t>(hg.w[(size_t)k]));
         widest = std::max(widest, row);
       }
-      G.byte_lanes = widest <= 255 ? 1 : 0;
+      bool unit = true;  // every weight +1 or -1
+      for (size_t k = 0; k < (size_t)hg.nnz && unit; ++k) unit = hg.w[k] == 1 || hg.w[k] == -1;
+      G.byte_lanes = widest <= 255 ? (unit ? 2 : 1) : 0;
       for (size_t v = 0; v <= (size_t)hg.n; ++v)
         row_ptr.push_back(static_cast<int32_t>(edge_off + hg.row_ptr[v]));
       for (size_t k = 0; k < (size_t)hg.nnz; ++k)
