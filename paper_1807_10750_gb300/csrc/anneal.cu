@@ -31,6 +31,7 @@
 
 #include "../../include/ising.h"
 #include "host_graph.h"
+#include "host_parallel.h"
 #include "philox.cuh"
 #include "sweep.cuh"
 #include "block.cuh"
@@ -929,9 +930,11 @@ int ising_create(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, c
         }
         words = packed_words.data();
       }
-      for (size_t k = 0; k < NNZ; ++k)
-        words[k] = static_cast<int32_t>((static_cast<uint32_t>(hg.col[k]) << 8) |
-                                        (static_cast<uint32_t>(hg.w[k]) & 0xffu));
+      isingx::parallel_ranges(static_cast<int64_t>(NNZ), int64_t(1) << 18, [&](int64_t lo, int64_t hi) {
+        for (int64_t k = lo; k < hi; ++k)
+          words[k] = static_cast<int32_t>((static_cast<uint32_t>(hg.col[k]) << 8) |
+                                          (static_cast<uint32_t>(hg.w[k]) & 0xffu));
+      });
       if ((e = alloc_copy(&g->d_adj, words, NNZ, g->stream)) != cudaSuccess) break;
     } else {
       if ((e = alloc_copy(&g->d_col, hg.col.data(), NNZ, g->stream)) != cudaSuccess) break;

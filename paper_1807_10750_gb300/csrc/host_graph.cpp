@@ -11,10 +11,13 @@
 // ties broken by smaller id (Welsh-Powell). On a regular graph such as an even
 // torus this is natural order, which gives the checkerboard.
 #include "host_graph.h"
+#include "host_parallel.h"
 
 #include <algorithm>
 #include <cstdlib>
 #include <limits>
+#include <memory>
+#include <new>
 
 #include "../../include/ising.h"
 
@@ -25,93 +28,113 @@ int build_host_graph(int32_t n, int64_t m, const int32_t* src, const int32_t* ds
   if (out == nullptr || n <= 0 || m < 0) return ISING_EINVAL;
   if (m >= (int64_t(1) << 30)) return ISING_ERANGE;
   if (m > 0 && (src == nullptr || dst == nullptr || w == nullptr)) return ISING_EINVAL;
-  for (int64_t e = 0; e < m; ++e) {
-    int32_t u = src[e], v = dst[e];
-    if (u < 0 || u >= n || v < 0 || v >= n || u == v) return ISING_EINVAL;
-  }
+  constexpr int64_t kGrain = 1 << 18;  // indices per block: smaller graphs stay on one thread
+  std::atomic<bool> bad(false);
+  parallel_ranges(m, kGrain, [&](int64_t lo, int64_t hi) {
+    for (int64_t e = lo; e < hi; ++e) {
+      const int32_t u = src[e], v = dst[e];
+      if (u < 0 || u >= n || v < 0 || v >= n || u == v) {
+        bad.store(true, std::memory_order_relaxed);
+        return;
+      }
+    }
+  });
+  if (bad.load()) return ISING_EINVAL;
   HostGraph& g = *out;
   g = HostGraph();
   g.n = n;
   const size_t N = (size_t)n;
 
-  // Pass 1: unsorted directed rows.
+  // Directed rows: every edge (u, v, w) becomes the entries v of row u and u
+  // of row v, each held as the key (neighbour << 32) | (uint32) w. Entries
+  // land in a row in any order; sorting each row's keys orders it by
+  // neighbour (then weight), so repeated neighbours are adjacent.
+  // the edge passes run on several threads (atomic counters) only when m is
+  // at least two blocks of kGrain
+  const bool shared = m >= 2 * kGrain && host_threads() > 1;
+  auto bump = [shared](int64_t* p) {
+    return shared ? __atomic_fetch_add(p, 1, __ATOMIC_RELAXED) : (*p)++;
+  };
   std::vector<int64_t> off(N + 1, 0);
-  for (int64_t e = 0; e < m; ++e) {
-    off[(size_t)src[e] + 1]++;
-    off[(size_t)dst[e] + 1]++;
-  }
+  parallel_ranges(m, kGrain, [&](int64_t lo, int64_t hi) {
+    for (int64_t e = lo; e < hi; ++e) {
+      bump(&off[(size_t)src[e] + 1]);
+      bump(&off[(size_t)dst[e] + 1]);
+    }
+  });
   for (size_t i = 0; i < N; ++i) off[i + 1] += off[i];
   const size_t D = (size_t)off[N];
-  std::vector<int32_t> nb1(D), wt1(D);
+  // scratch, left uninitialised (every slot is written before it is read)
+  std::unique_ptr<uint64_t[]> key(new uint64_t[std::max<size_t>(D, 1)]);
   {
     std::vector<int64_t> fill(off.begin(), off.end() - 1);
-    for (int64_t e = 0; e < m; ++e) {
-      int32_t u = src[e], v = dst[e];
-      size_t a = (size_t)fill[(size_t)u]++;
-      nb1[a] = v;
-      wt1[a] = w[e];
-      size_t b = (size_t)fill[(size_t)v]++;
-      nb1[b] = u;
-      wt1[b] = w[e];
-    }
-  }
-  // Pass 2: rows sorted by neighbour id. Row x lists the y with an entry
-  // (y -> x); visiting x in increasing order appends x to row y in order.
-  std::vector<int32_t> nb2(D), wt2(D);
-  {
-    std::vector<int64_t> fill(off.begin(), off.end() - 1);
-    for (size_t x = 0; x < N; ++x) {
-      for (int64_t k = off[x]; k < off[x + 1]; ++k) {
-        size_t y = (size_t)nb1[(size_t)k];
-        size_t a = (size_t)fill[y]++;
-        nb2[a] = (int32_t)x;
-        wt2[a] = wt1[(size_t)k];
+    parallel_ranges(m, kGrain, [&](int64_t lo, int64_t hi) {
+      for (int64_t e = lo; e < hi; ++e) {
+        const uint32_t u = (uint32_t)src[e], v = (uint32_t)dst[e], wt = (uint32_t)w[e];
+        key[(size_t)bump(&fill[u])] = ((uint64_t)v << 32) | wt;
+        key[(size_t)bump(&fill[v])] = ((uint64_t)u << 32) | wt;
       }
-    }
+    });
   }
-  nb1.clear();
-  nb1.shrink_to_fit();
-  wt1.clear();
-  wt1.shrink_to_fit();
 
-  // Merge repeated neighbours, drop zero sums, bound every field.
+  // Merge repeated neighbours, drop zero sums, bound every field. Each row's
+  // merged entries are written over the front of its own key range.
+  std::vector<int32_t> mdeg(N, 0);
+  std::atomic<bool> too_wide(false), not8(false);
+  std::atomic<int64_t> total_directed(0);
+  parallel_rows((int64_t)N, off.data(), [&](int64_t lo, int64_t hi) {
+    int64_t total = 0;
+    bool over = false, wide8 = false;
+    for (int64_t u = lo; u < hi && !over; ++u) {
+      uint64_t* row = key.get() + off[(size_t)u];
+      const int64_t len = off[(size_t)u + 1] - off[(size_t)u];
+      std::sort(row, row + len);
+      int64_t k = 0, out_k = 0, abs_sum = 0;
+      while (k < len) {
+        const uint32_t v = (uint32_t)(row[k] >> 32);
+        int64_t s = 0;
+        while (k < len && (uint32_t)(row[k] >> 32) == v) {
+          s += (int32_t)(uint32_t)row[k];
+          ++k;
+        }
+        if (s == 0) continue;
+        abs_sum += s < 0 ? -s : s;
+        if (abs_sum > (int64_t)std::numeric_limits<int32_t>::max()) {
+          over = true;
+          break;
+        }
+        if (s > 127 || s < -127) wide8 = true;
+        row[out_k++] = ((uint64_t)v << 32) | (uint32_t)(int32_t)s;
+        total += s;
+      }
+      mdeg[(size_t)u] = (int32_t)out_k;
+    }
+    if (over) too_wide.store(true, std::memory_order_relaxed);
+    if (wide8) not8.store(true, std::memory_order_relaxed);
+    total_directed.fetch_add(total, std::memory_order_relaxed);
+  });
+  if (too_wide.load()) return ISING_ERANGE;
   std::vector<int64_t> moff(N + 1, 0);
-  std::vector<int32_t> mnb;
-  std::vector<int32_t> mwt;
-  mnb.reserve(D);
-  mwt.reserve(D);
-  int64_t total_directed = 0;
-  bool fits8 = true;
   int32_t maxdeg = 0;
   for (size_t u = 0; u < N; ++u) {
-    int64_t k = off[u];
-    int64_t abs_sum = 0;
-    while (k < off[u + 1]) {
-      int32_t v = nb2[(size_t)k];
-      int64_t s = 0;
-      while (k < off[u + 1] && nb2[(size_t)k] == v) {
-        s += wt2[(size_t)k];
-        ++k;
-      }
-      if (s == 0) continue;
-      abs_sum += s < 0 ? -s : s;
-      if (abs_sum > (int64_t)std::numeric_limits<int32_t>::max()) return ISING_ERANGE;
-      if (s > 127 || s < -127) fits8 = false;
-      mnb.push_back(v);
-      mwt.push_back((int32_t)s);
-      total_directed += s;
-    }
-    moff[u + 1] = (int64_t)mnb.size();
-    maxdeg = std::max<int32_t>(maxdeg, (int32_t)(moff[u + 1] - moff[u]));
+    moff[u + 1] = moff[u] + mdeg[u];
+    maxdeg = std::max(maxdeg, mdeg[u]);
   }
-  nb2.clear();
-  nb2.shrink_to_fit();
-  wt2.clear();
-  wt2.shrink_to_fit();
-  g.nnz = (int64_t)mnb.size();
+  std::unique_ptr<int32_t[]> mnb(new int32_t[std::max<int64_t>(moff[N], 1)]);
+  std::unique_ptr<int32_t[]> mwt(new int32_t[std::max<int64_t>(moff[N], 1)]);
+  parallel_rows((int64_t)N, moff.data(), [&](int64_t lo, int64_t hi) {
+    for (int64_t u = lo; u < hi; ++u) {
+      const uint64_t* row = key.get() + off[(size_t)u];
+      for (int64_t k = 0; k < mdeg[(size_t)u]; ++k) {
+        mnb[(size_t)(moff[(size_t)u] + k)] = (int32_t)(row[k] >> 32);
+        mwt[(size_t)(moff[(size_t)u] + k)] = (int32_t)(uint32_t)row[k];
+      }
+    }
+  });
+  g.nnz = moff[N];
   g.num_edges = g.nnz / 2;
-  g.total_weight = total_directed / 2;
-  g.fits_int8 = fits8;
+  g.total_weight = total_directed.load() / 2;
+  g.fits_int8 = !not8.load();
   g.max_degree = maxdeg;
 
   // Welsh-Powell order: degree descending, id ascending (bucketed by degree).
@@ -156,24 +179,28 @@ int build_host_graph(int32_t n, int64_t m, const int32_t* src, const int32_t* ds
       g.pos[(size_t)v] = p;
     }
   }
-  // Colour-ordered CSR with each row sorted by neighbour position (visit
-  // target positions in increasing order and append to the rows that list it).
+  // Colour-ordered CSR with each row sorted by neighbour position: row p
+  // lists vertex perm[p]'s neighbours as (position << 32) | weight keys,
+  // sorted (positions in a row are distinct), in the key buffer's front.
   g.row_ptr.assign(N + 1, 0);
   for (size_t p = 0; p < N; ++p) g.row_ptr[p + 1] = g.row_ptr[p] + degree((size_t)g.perm[p]);
   g.col.assign((size_t)g.nnz, 0);
   g.w.assign((size_t)g.nnz, 0);
-  {
-    std::vector<int32_t> fill(g.row_ptr.begin(), g.row_ptr.end() - 1);
-    for (size_t p = 0; p < N; ++p) {
-      const size_t x = (size_t)g.perm[p];
-      for (int64_t k = moff[x]; k < moff[x + 1]; ++k) {
-        const size_t row = (size_t)g.pos[(size_t)mnb[(size_t)k]];
-        const size_t a = (size_t)fill[row]++;
-        g.col[a] = (int32_t)p;
-        g.w[a] = mwt[(size_t)k];
+  parallel_rows((int64_t)N, g.row_ptr.data(), [&](int64_t lo, int64_t hi) {
+    for (int64_t p = lo; p < hi; ++p) {
+      const size_t x = (size_t)g.perm[(size_t)p];
+      uint64_t* row = key.get() + g.row_ptr[(size_t)p];
+      const int64_t len = moff[x + 1] - moff[x];
+      for (int64_t k = 0; k < len; ++k)
+        row[k] = ((uint64_t)(uint32_t)g.pos[(size_t)mnb[(size_t)(moff[x] + k)]] << 32) |
+                 (uint32_t)mwt[(size_t)(moff[x] + k)];
+      std::sort(row, row + len);
+      for (int64_t k = 0; k < len; ++k) {
+        g.col[(size_t)(g.row_ptr[(size_t)p] + k)] = (int32_t)(row[k] >> 32);
+        g.w[(size_t)(g.row_ptr[(size_t)p] + k)] = (int32_t)(uint32_t)row[k];
       }
     }
-  }
+  });
   return ISING_OK;
 }
 
@@ -189,6 +216,8 @@ void build_work_plan(const HostGraph& g, int32_t target_warps, int32_t min_edges
   if (min_edges < light_slots) min_edges = light_slots;
   if (max_rows < 1) max_rows = 1;
   auto degree = [&](int32_t v) { return (int64_t)g.row_ptr[(size_t)v + 1] - g.row_ptr[(size_t)v]; };
+  std::vector<int32_t> light;  // the light items, filled after the split
+  int64_t ell_words = 0;
   for (int32_t c = 0; c < g.num_colours; ++c) {
     const int32_t vb = g.class_begin[(size_t)c], ve = g.class_begin[(size_t)c + 1];
     const int64_t E = (int64_t)g.row_ptr[(size_t)ve] - g.row_ptr[(size_t)vb];
@@ -235,18 +264,9 @@ void build_work_plan(const HostGraph& g, int32_t target_warps, int32_t min_edges
         ++end;
       }
       const int32_t nv = end - v;
-      const int64_t off = (int64_t)plan->ell_col.size();
-      plan->ell_col.resize((size_t)(off + (int64_t)D * nv), -1);
-      plan->ell_w.resize((size_t)(off + (int64_t)D * nv), 0);
-      for (int32_t r = 0; r < nv; ++r) {
-        const int64_t rb = g.row_ptr[(size_t)(v + r)];
-        const int64_t deg = degree(v + r);
-        for (int64_t k = 0; k < deg; ++k) {
-          plan->ell_col[(size_t)(off + k * nv + r)] = g.col[(size_t)(rb + k)];
-          plan->ell_w[(size_t)(off + k * nv + r)] = g.w[(size_t)(rb + k)];
-        }
-      }
-      plan->items.push_back({v, end, (int32_t)off, -(D + 1)});
+      light.push_back((int32_t)plan->items.size());
+      plan->items.push_back({v, end, (int32_t)ell_words, -(D + 1)});
+      ell_words += (int64_t)D * nv;
       v = end;
     }
     plan->class_item_begin[(size_t)c + 1] = (int32_t)plan->items.size();
@@ -254,6 +274,26 @@ void build_work_plan(const HostGraph& g, int32_t target_warps, int32_t min_edges
         plan->max_class_items,
         plan->class_item_begin[(size_t)c + 1] - plan->class_item_begin[(size_t)c]);
   }
+  // Sliced ELL of the light items: slot k of row r of an item with nv rows
+  // at word off is word off + k * nv + r; slots past a row's degree keep
+  // (-1, 0). Items own disjoint word ranges.
+  plan->ell_col.assign((size_t)ell_words, -1);
+  plan->ell_w.assign((size_t)ell_words, 0);
+  parallel_ranges((int64_t)light.size(), 1024, [&](int64_t lo, int64_t hi) {
+    for (int64_t q = lo; q < hi; ++q) {
+      const WorkItem& it = plan->items[(size_t)light[(size_t)q]];
+      const int32_t nv = it.v_end - it.v_begin;
+      const int64_t off = it.e_begin;
+      for (int32_t r = 0; r < nv; ++r) {
+        const int64_t rb = g.row_ptr[(size_t)(it.v_begin + r)];
+        const int64_t deg = degree(it.v_begin + r);
+        for (int64_t k = 0; k < deg; ++k) {
+          plan->ell_col[(size_t)(off + k * nv + r)] = g.col[(size_t)(rb + k)];
+          plan->ell_w[(size_t)(off + k * nv + r)] = g.w[(size_t)(rb + k)];
+        }
+      }
+    }
+  });
 }
 
 bool build_item_deps(const HostGraph& g, const WorkPlan& plan, std::vector<int32_t>* dep_ptr,
@@ -270,20 +310,46 @@ bool build_item_deps(const HostGraph& g, const WorkPlan& plan, std::vector<int32
     if (it.v_end < 0) return false;  // a slice of a heavy row
     for (int32_t v = it.v_begin; v < it.v_end; ++v) item_of[(size_t)v] = i;
   }
+  // Items in contiguous blocks, one per thread, each with its own marker
+  // array: seen[j] == i + 1 marks j as already listed for item i. The blocks'
+  // lists are joined in item order, so the result does not depend on the
+  // number of threads.
+  const int32_t threads = g.nnz < (int64_t(1) << 19) ? 1 : host_threads();
+  const int64_t grain = std::max<int64_t>(1, ((int64_t)ni + threads - 1) / threads);
+  std::vector<std::vector<int32_t>> block_deps, block_cnt;
+  const int64_t nblocks = ni == 0 ? 0 : ((int64_t)ni + grain - 1) / grain;
+  block_deps.resize((size_t)nblocks);
+  block_cnt.resize((size_t)nblocks);
+  std::atomic<bool> no_memory(false);  // an allocation failed in a worker
+  parallel_ranges(nblocks, 1, [&](int64_t b0, int64_t b1) {
+    try {
+      std::vector<int32_t> seen((size_t)ni, 0);
+      for (int64_t b = b0; b < b1; ++b) {
+        std::vector<int32_t>& out = block_deps[(size_t)b];
+        std::vector<int32_t>& cnt = block_cnt[(size_t)b];
+        for (int64_t i = b * grain; i < std::min<int64_t>(ni, (b + 1) * grain); ++i) {
+          const WorkItem& it = plan.items[(size_t)i];
+          const size_t before = out.size();
+          for (int32_t v = it.v_begin; v < it.v_end; ++v)
+            for (int32_t k = g.row_ptr[(size_t)v]; k < g.row_ptr[(size_t)v + 1]; ++k) {
+              const int32_t j = item_of[(size_t)g.col[(size_t)k]];
+              if (j == i || seen[(size_t)j] == i + 1) continue;
+              seen[(size_t)j] = (int32_t)i + 1;
+              out.push_back((j << 1) | (class_of[(size_t)j] > class_of[(size_t)i] ? 1 : 0));
+            }
+          cnt.push_back((int32_t)(out.size() - before));
+        }
+      }
+    } catch (const std::bad_alloc&) {
+      no_memory.store(true);
+    }
+  });
+  if (no_memory.load()) throw std::bad_alloc();
   dep_ptr->reserve((size_t)ni + 1);
   dep_ptr->push_back(0);
-  // seen[j] == i + 1 marks j as already listed for item i (no sorting)
-  std::vector<int32_t> seen((size_t)ni, 0);
-  for (int32_t i = 0; i < ni; ++i) {
-    const WorkItem& it = plan.items[(size_t)i];
-    for (int32_t v = it.v_begin; v < it.v_end; ++v)
-      for (int32_t k = g.row_ptr[(size_t)v]; k < g.row_ptr[(size_t)v + 1]; ++k) {
-        const int32_t j = item_of[(size_t)g.col[(size_t)k]];
-        if (j == i || seen[(size_t)j] == i + 1) continue;
-        seen[(size_t)j] = i + 1;
-        deps->push_back((j << 1) | (class_of[(size_t)j] > class_of[(size_t)i] ? 1 : 0));
-      }
-    dep_ptr->push_back((int32_t)deps->size());
+  for (int64_t b = 0; b < nblocks; ++b) {
+    for (int32_t c : block_cnt[(size_t)b]) dep_ptr->push_back(dep_ptr->back() + c);
+    deps->insert(deps->end(), block_deps[(size_t)b].begin(), block_deps[(size_t)b].end());
   }
   return true;
 }
