@@ -83,6 +83,37 @@ def test_host_colouring_equals_oracle(P, make):
     assert np.array_equal(col, col2)
 
 
+def _big_duplicates_graph(seed):
+    # 600k edge entries (the host build's multi-threaded passes start at
+    # 2^19), a fifth of them repeated and some repeats cancelling to zero
+    rng = np.random.default_rng(seed)
+    n, m = 300_000, 500_000
+    src = rng.integers(0, n, m)
+    dst = rng.integers(0, n, m)
+    keep = src != dst
+    src, dst = src[keep], dst[keep]
+    w = rng.integers(-8, 9, src.size)
+    rep = rng.random(src.size) < 0.2
+    w_rep = np.where(rng.random(rep.sum()) < 0.5, -w[rep], rng.integers(-8, 9, rep.sum()))
+    return synth.Graph(n, np.concatenate([src, dst[rep]]).astype(np.int32),
+                       np.concatenate([dst, src[rep]]).astype(np.int32),
+                       np.concatenate([w, w_rep]).astype(np.int32))
+
+
+@pytest.mark.parametrize("make", [
+    lambda: _big_duplicates_graph(1),
+    lambda: synth.zipf_config_graph(200_000, 2.1, 4, 5000, 7, weights="int8"),
+])
+def test_multithreaded_host_colouring_equals_oracle(P, make):
+    g = make()
+    assert g.src.size >= 1 << 19
+    C, col = P.ising_plan_colouring(g.n, g.src, g.dst, g.w)
+    C2, col2 = oracle.colouring(g.n, g.src, g.dst, g.w)
+    assert C == C2
+    assert np.array_equal(col, col2)
+    assert P.ising_plan_colouring(g.n, g.src, g.dst, g.w)[1].tobytes() == col.tobytes()
+
+
 def test_host_colouring_edgeless_and_single_vertex(P):
     e = np.zeros(0, np.int32)
     C, col = P.ising_plan_colouring(5, e, e, e)
