@@ -48,9 +48,9 @@ int build_host_graph(int32_t n, int64_t m, const int32_t* src, const int32_t* ds
   // Directed rows: every edge (u, v, w) becomes the entries v of row u and u
   // of row v, each held as the key (neighbour << 32) | (uint32) w. Entries
   // land in a row in any order; sorting each row's keys orders it by
-  // neighbour (then weight), so repeated neighbours are adjacent.
-  // the edge passes run on several threads (atomic counters) only when m is
-  // at least two blocks of kGrain
+  // neighbour (then weight), so repeated neighbours are adjacent. The edge
+  // passes use atomic counters only when they run on several threads (m of
+  // at least two blocks of kGrain).
   const bool shared = m >= 2 * kGrain && host_threads() > 1;
   auto bump = [shared](int64_t* p) {
     return shared ? __atomic_fetch_add(p, 1, __ATOMIC_RELAXED) : (*p)++;
