@@ -46,20 +46,22 @@ int build_host_graph(int32_t n, int64_t m, const int32_t* src, const int32_t* ds
   const size_t N = (size_t)n;
 
   // Directed rows: every edge (u, v, w) becomes the entries v of row u and u
-  // of row v, each held as the key (neighbour << 32) | (uint32) w. Entries
-  // land in a row in any order; sorting each row's keys orders it by
-  // neighbour (then weight), so repeated neighbours are adjacent. The edge
-  // passes use atomic counters only when they run on several threads (m of
-  // at least two blocks of kGrain).
-  const bool shared = m >= 2 * kGrain && host_threads() > 1;
-  auto bump = [shared](int64_t* p) {
-    return shared ? __atomic_fetch_add(p, 1, __ATOMIC_RELAXED) : (*p)++;
-  };
+  // of row v, each held as the key (neighbour << 32) | (uint32) w; sorting
+  // each row's keys then orders it by neighbour (then weight), so repeated
+  // neighbours are adjacent. On several threads each thread owns a
+  // contiguous range of rows, scans every edge and fills only its own rows,
+  // so no counter is shared and a row's entries arrive in edge order.
+  const int64_t parts = m >= 2 * kGrain ? host_threads() : 1;
+  auto part_lo = [&](int64_t t) { return (int64_t)N * t / parts; };
   std::vector<int64_t> off(N + 1, 0);
-  parallel_ranges(m, kGrain, [&](int64_t lo, int64_t hi) {
-    for (int64_t e = lo; e < hi; ++e) {
-      bump(&off[(size_t)src[e] + 1]);
-      bump(&off[(size_t)dst[e] + 1]);
+  parallel_ranges(parts, 1, [&](int64_t t0, int64_t t1) {
+    for (int64_t t = t0; t < t1; ++t) {
+      const uint32_t lo = (uint32_t)part_lo(t), span = (uint32_t)(part_lo(t + 1) - part_lo(t));
+      for (int64_t e = 0; e < m; ++e) {
+        const uint32_t u = (uint32_t)src[e], v = (uint32_t)dst[e];
+        if (u - lo < span) ++off[(size_t)u + 1];
+        if (v - lo < span) ++off[(size_t)v + 1];
+      }
     }
   });
   for (size_t i = 0; i < N; ++i) off[i + 1] += off[i];
@@ -68,11 +70,14 @@ int build_host_graph(int32_t n, int64_t m, const int32_t* src, const int32_t* ds
   std::unique_ptr<uint64_t[]> key(new uint64_t[std::max<size_t>(D, 1)]);
   {
     std::vector<int64_t> fill(off.begin(), off.end() - 1);
-    parallel_ranges(m, kGrain, [&](int64_t lo, int64_t hi) {
-      for (int64_t e = lo; e < hi; ++e) {
-        const uint32_t u = (uint32_t)src[e], v = (uint32_t)dst[e], wt = (uint32_t)w[e];
-        key[(size_t)bump(&fill[u])] = ((uint64_t)v << 32) | wt;
-        key[(size_t)bump(&fill[v])] = ((uint64_t)u << 32) | wt;
+    parallel_ranges(parts, 1, [&](int64_t t0, int64_t t1) {
+      for (int64_t t = t0; t < t1; ++t) {
+        const uint32_t lo = (uint32_t)part_lo(t), span = (uint32_t)(part_lo(t + 1) - part_lo(t));
+        for (int64_t e = 0; e < m; ++e) {
+          const uint32_t u = (uint32_t)src[e], v = (uint32_t)dst[e], wt = (uint32_t)w[e];
+          if (u - lo < span) key[(size_t)fill[u]++] = ((uint64_t)v << 32) | wt;
+          if (v - lo < span) key[(size_t)fill[v]++] = ((uint64_t)u << 32) | wt;
+        }
       }
     });
   }
