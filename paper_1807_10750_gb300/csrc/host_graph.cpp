@@ -143,7 +143,7 @@ int build_host_graph(int32_t n, int64_t m, const int32_t* src, const int32_t* ds
   g.max_degree = maxdeg;
 
   // Welsh-Powell order: degree descending, id ascending (bucketed by degree).
-  auto degree = [&](size_t v) { return (int32_t)(moff[v + 1] - moff[v]); };
+  auto degree = [&](size_t v) { return mdeg[v]; };
   std::vector<int32_t> order(N);
   {
     std::vector<int64_t> bucket((size_t)maxdeg + 2, 0);
