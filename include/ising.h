@@ -366,13 +366,18 @@ void ising_batch_destroy(ising_batch* b);
  *
  * Scratch: one file-scope device array of ISING_STATIC_MAX_VERTICES / 1024
  * pairs of int64 (256 KiB). Every GPU that loads the library holds it until
- * the process exits. The first call on a device looks up the array's address;
- * make that first call before any stream capture. All calls on a device share
- * the array (each call rewrites what it reads, so nothing needs clearing);
- * calls whose kernels overlap on the GPU race and return wrong results, so
- * order them. The call never allocates or frees device or host memory.
- * Errors: ISING_EINVAL (n <= 0 or a null row_ptr/spins/out), ISING_ERANGE,
- * ISING_ECUDA.
+ * the process exits. The first call on a device looks up the array's address
+ * and keeps it; make that first call before any stream capture. The kept
+ * address does not survive cudaDeviceReset: do not call this entry point on
+ * a device after resetting it. All calls on a device share the array (each
+ * call rewrites what it reads, so nothing needs clearing); calls whose
+ * kernels overlap on the GPU race and return wrong results, so order them.
+ * The call never allocates or frees device or host memory.
+ * Errors: ISING_EINVAL (n <= 0, or a null row_ptr, col, w, spins or out; a
+ * graph without entries may pass any valid col/w pointer), ISING_ERANGE,
+ * ISING_ECUDA (a launch failed, or a CUDA error was already pending when the
+ * call started: then nothing is launched and the pending error is left for
+ * its owner to read).
  */
 int ising_energy_csr_static(int32_t n, const int32_t* row_ptr, const int32_t* col,
                             const int32_t* w, const int8_t* spins, int64_t* out,

@@ -393,16 +393,31 @@ def ising_halo_info(g: IsingGraph) -> dict | None:
 def ising_energy_csr_static(n: int, row_ptr, col, w, spins, out, stream=None) -> None:
     """Energy and cut of ``spins`` on a caller-owned device CSR graph into the
     device int64[2] ``out``, allocating nothing (see include/ising.h). All
-    arguments are torch CUDA tensors: row_ptr/col/w int32, spins int8."""
+    arguments are torch CUDA tensors on the current device: row_ptr int32[n+1],
+    col and w int32 of equal length, spins int8[n], out int64[2]. Lengths are
+    checked here because the kernels cannot check them."""
+    if int(n) <= 0:
+        raise ValueError("n must be positive")
+    lengths = {"row_ptr": (row_ptr, n + 1), "spins": (spins, n), "out": (out, 2)}
+    for name, (t, want) in lengths.items():
+        if not hasattr(t, "numel") or t.numel() != want:
+            raise ValueError(f"{name} must have {want} elements")
+    if not hasattr(col, "numel") or not hasattr(w, "numel") or col.numel() != w.numel():
+        raise ValueError("col and w must have the same length")
+
     def ptr(t, dtype):
         p, on_dev, _ = _buffer(t, dtype, None, False)
         if not on_dev:
             raise TypeError("ising_energy_csr_static takes device tensors")
         return p
-    _check(lib().ising_energy_csr_static(n, ptr(row_ptr, np.int32), ptr(col, np.int32),
-                                         ptr(w, np.int32), ptr(spins, np.int8),
-                                         ptr(out, np.int64), _stream(stream)),
-           "ising_energy_csr_static")
+    ptrs = [ptr(row_ptr, np.int32), ptr(col, np.int32), ptr(w, np.int32), ptr(spins, np.int8),
+            ptr(out, np.int64)]
+    import torch  # device tensors imply torch
+    dev = torch.cuda.current_device()
+    for t in (row_ptr, col, w, spins, out):
+        if t.device.index != dev:
+            raise ValueError("every tensor must be on the current CUDA device")
+    _check(lib().ising_energy_csr_static(n, *ptrs, _stream(stream)), "ising_energy_csr_static")
 
 
 def ising_launch_count(g: IsingGraph) -> int:

@@ -101,7 +101,9 @@ __global__ void __launch_bounds__(kStaticBlock)
 }
 
 // Device address of the scratch array for the current device, looked up once
-// per device (the first call on a device does it).
+// per device (the first call on a device does it) and kept for the life of the
+// process. cudaDeviceReset unloads the module and may move the array, so the
+// cached address is not valid across a reset of the device.
 int partials_for_current_device(long long (**out)[2]) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -128,13 +130,21 @@ extern "C" int ising_energy_csr_static(int32_t n, const int32_t* row_ptr, const 
                                        const int32_t* w, const int8_t* spins, int64_t* out,
                                        void* cuda_stream) {
   if (n <= 0 || row_ptr == nullptr || spins == nullptr || out == nullptr) return ISING_EINVAL;
+  // the kernels read col and w only for rows with entries, but a null pointer
+  // there is never what the caller meant: an edgeless graph may pass any
+  // valid pointer
+  if (col == nullptr || w == nullptr) return ISING_EINVAL;
   if (n > ISING_STATIC_MAX_VERTICES) return ISING_ERANGE;
+  // an error left pending by earlier, unrelated work is reported and left in
+  // place for its owner: nothing is launched behind it
+  if (cudaPeekAtLastError() != cudaSuccess) return ISING_ECUDA;
   long long (*partials)[2] = nullptr;
   const int rc = partials_for_current_device(&partials);
   if (rc != ISING_OK) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   const int chunks = (n + kRowsPerChunk - 1) / kRowsPerChunk;
   static_energy_chunks<<<chunks, kStaticBlock, 0, s>>>(n, row_ptr, col, w, spins, partials);
+  if (cudaGetLastError() != cudaSuccess) return ISING_ECUDA;
   static_energy_finish<<<1, kStaticBlock, 0, s>>>(chunks, partials, out);
   if (cudaGetLastError() != cudaSuccess) return ISING_ECUDA;
   return ISING_OK;

@@ -128,3 +128,45 @@ def test_zero_weight_merge_changes_colouring(P):
     w = np.array([2, 3, 4, -4, 1], np.int32)
     C, col = P.ising_plan_colouring(3, src, dst, w)
     assert C == 2 and list(col) == [0, 1, 1]
+
+
+def test_static_energy_rejects_bad_arguments_before_any_device_work(P):
+    """ising_energy_csr_static checks its scalar arguments and null pointers
+    before its first CUDA call, so these run without a GPU: n beyond the
+    scratch array's capacity, n <= 0, and a null col or w."""
+    import ctypes
+    L = P.lib()
+    buf = (ctypes.c_int32 * 4)()
+    sp = (ctypes.c_int8 * 4)()
+    out = (ctypes.c_int64 * 2)()
+    a = ctypes.cast(buf, ctypes.c_void_p)
+    s = ctypes.cast(sp, ctypes.c_void_p)
+    o = ctypes.cast(out, ctypes.c_void_p)
+    assert L.ising_energy_csr_static(P.ISING_STATIC_MAX_VERTICES + 1, a, a, a, s, o, None) == P.ISING_ERANGE
+    assert L.ising_energy_csr_static(0, a, a, a, s, o, None) == P.ISING_EINVAL
+    assert L.ising_energy_csr_static(4, a, None, a, s, o, None) == P.ISING_EINVAL
+    assert L.ising_energy_csr_static(4, a, a, None, s, o, None) == P.ISING_EINVAL
+    assert L.ising_energy_csr_static(4, None, a, a, s, o, None) == P.ISING_EINVAL
+
+
+def test_static_energy_wrapper_checks_lengths(P):
+    """The Python binding checks every tensor's length before the call (the
+    kernels cannot): row_ptr n + 1, spins n, out 2, col and w equal. CPU
+    tensors of the right lengths are refused as not on the device."""
+    import torch
+    n = 5
+    good = dict(row_ptr=torch.zeros(n + 1, dtype=torch.int32), col=torch.zeros(8, dtype=torch.int32),
+                w=torch.zeros(8, dtype=torch.int32), spins=torch.ones(n, dtype=torch.int8),
+                out=torch.zeros(2, dtype=torch.int64))
+    bad = [dict(row_ptr=torch.zeros(n, dtype=torch.int32)),
+           dict(spins=torch.ones(n + 1, dtype=torch.int8)),
+           dict(out=torch.zeros(1, dtype=torch.int64)),
+           dict(w=torch.zeros(7, dtype=torch.int32))]
+    for change in bad:
+        args = dict(good, **change)
+        with pytest.raises(ValueError):
+            P.ising_energy_csr_static(n, args["row_ptr"], args["col"], args["w"], args["spins"],
+                                      args["out"])
+    with pytest.raises(TypeError):
+        P.ising_energy_csr_static(n, good["row_ptr"], good["col"], good["w"], good["spins"],
+                                  good["out"])

@@ -5,9 +5,10 @@ do not control, they run under a fixed memory budget, or they sit in a loop
 where cudaMalloc's host blocking and device synchronisation are not acceptable.
 For them the library computes energy and cut of spins on a CSR graph the
 caller owns, with its scratch in a fixed device array instead of an
-allocation. This test calls it through the C ABI twice in a row and checks it
-against the handle-based ising_energy / ising_cut on the same graph and spins
-(exact integers, so equality).
+allocation. This test calls it through the C ABI twice in a row and checks
+both results against the CPU oracle's energy and cut of the same edge list and
+spins (exact integers, so equality). The existing handle-based ising_energy /
+ising_cut must agree with both.
 
 This file is named to be collected last.
 """
@@ -15,6 +16,7 @@ This file is named to be collected last.
 import numpy as np
 import pytest
 
+import oracle
 import synth
 
 pytestmark = pytest.mark.gpu
@@ -36,8 +38,11 @@ def caller_csr(g):
 @pytest.mark.parametrize("make", [
     lambda: synth.random_small_graph(3001, 0.004, 21, weights="int8", duplicates=80),
     lambda: synth.torus_graph(300, 4, weights="pm1"),
-])
-def test_static_energy_matches_handle_on_two_calls(make):
+    # 300,001 rows: 293 chunks of 1024 rows (more than the finishing kernel's
+    # 256 threads, so some threads sum several partials) and a ragged last chunk
+    lambda: synth.random_small_graph(300001, 6.0 / 300000, 22, weights="int8", duplicates=500),
+], ids=["er3001", "torus300", "er300001"])
+def test_static_energy_matches_oracle_on_two_calls(make):
     import torch
     from paper_1807_10750_gb300 import _build
     _build.build()
@@ -55,21 +60,11 @@ def test_static_energy_matches_handle_on_two_calls(make):
     with P.ising_create(g.n, g.src, g.dst, g.w) as h:
         for call in range(2):
             s = (rng.integers(0, 2, g.n) * 2 - 1).astype(np.int8)
-            P.ising_set_spins(h, s)
-            want = (P.ising_energy(h), P.ising_cut(h))
+            H, _, cut = oracle.energy_cut(g.n, g.src, g.dst, g.w, s)
             out.fill_(-12345)
             P.ising_energy_csr_static(g.n, rp_d, col_d, w_d, torch.from_numpy(s).to(dev), out,
                                       stream=stream)
             torch.cuda.synchronize()
-            assert tuple(int(x) for x in out.cpu()) == want, f"call {call}"
-
-
-def test_static_energy_rejects_sizes_beyond_its_scratch():
-    import torch
-    import paper_1807_10750_gb300 as P
-    t = torch.zeros(4, dtype=torch.int32, device="cuda")
-    s = torch.ones(4, dtype=torch.int8, device="cuda")
-    out = torch.zeros(2, dtype=torch.int64, device="cuda")
-    with pytest.raises(P.IsingError) as e:
-        P.ising_energy_csr_static(P.ISING_STATIC_MAX_VERTICES + 1, t, t, t, s, out)
-    assert e.value.code == P.ISING_ERANGE
+            assert tuple(int(x) for x in out.cpu()) == (H, cut), f"call {call}"
+            P.ising_set_spins(h, s)
+            assert (P.ising_energy(h), P.ising_cut(h)) == (H, cut), f"call {call}"
