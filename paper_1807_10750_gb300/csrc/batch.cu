@@ -12,8 +12,10 @@
 //
 // Randomness (Algorithm 2's flips and the initial spins) follows ising.h with
 // the instance folded into the key: key = (lo32(seed), hi32(seed) ^
-// instance * 0x9E3779B9), counter = (vertex id within the instance, sweep t,
-// replica, 0) for flips and (vertex, 0, replica, 1) for initial spins.
+// instance * 0x9E3779B9). Vertex v (id within the instance) of replica r
+// draws word v mod 4 of counter (floor(v / 4), sweep t, r, 0) for its flip
+// and of (floor(v / 4), 0, r, 1) for its initial spin, so the four vertices
+// 4q .. 4q + 3 share one Philox evaluation.
 #include <cuda_runtime.h>
 
 #include <algorithm>
