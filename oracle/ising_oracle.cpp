@@ -36,8 +36,13 @@
 //      counter (floor(v / 4), sweep t (0 for the initial spins), r, stream),
 //      so the four vertices 4q .. 4q + 3 share one evaluation.
 //   R6 colouring: greedy first fit over the vertices in order of decreasing
-//      degree (ties: smaller id first), i.e. Welsh-Powell; classes are swept in
-//      increasing colour order, and inside a class the order is irrelevant
+//      degree (ties: smaller id first), i.e. Welsh-Powell, in two tiers. A
+//      vertex with at least 256 distinct neighbours is a hub. The hubs take
+//      colours 0 .. m-1 by first fit among themselves; every other vertex
+//      takes the smallest colour >= m that no already coloured neighbour has,
+//      so hub and non-hub vertices never share a class. A graph without hubs
+//      gets plain Welsh-Powell. Classes are swept in increasing colour order
+//      (the hub classes first), and inside a class the order is irrelevant
 //      because no two vertices of a class are adjacent.
 //   R11 flip bias (project addition, oracle_anneal_biased): a per-vertex
 //      factor q_v / 128 on the flip threshold, in integers.
@@ -186,31 +191,47 @@ int build_adjacency(int32_t n, int64_t m, const int32_t* src, const int32_t* dst
   return 0;
 }
 
-// R6: Welsh-Powell greedy colouring. Returns the number of colours.
+// R6: two-tier Welsh-Powell greedy colouring. Returns the number of colours.
+const int64_t kHubDegree = 256;  // a vertex with this many neighbours or more is a hub
+
 int32_t colour_graph(const Adjacency& adj, std::vector<int32_t>* colour) {
   const int32_t n = adj.n;
   std::vector<int32_t> order((size_t)n);
   for (int32_t v = 0; v < n; ++v) order[(size_t)v] = v;
+  auto degree = [&](int32_t v) { return adj.start[(size_t)v + 1] - adj.start[(size_t)v]; };
   std::sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
-    int64_t da = adj.start[(size_t)a + 1] - adj.start[(size_t)a];
-    int64_t db = adj.start[(size_t)b + 1] - adj.start[(size_t)b];
-    if (da != db) return da > db;
+    if (degree(a) != degree(b)) return degree(a) > degree(b);
     return a < b;
   });
   colour->assign((size_t)n, -1);
-  int32_t num_colours = 0;
-  std::vector<char> used;
-  for (int32_t v : order) {
-    int64_t deg = adj.start[(size_t)v + 1] - adj.start[(size_t)v];
-    used.assign((size_t)deg + 2, 0);
+  // smallest colour >= lowest that no coloured neighbour of v has
+  auto first_free = [&](int32_t v, int32_t lowest) {
+    std::vector<int32_t> taken;
     for (int64_t k = adj.start[(size_t)v]; k < adj.start[(size_t)v + 1]; ++k) {
       int32_t c = (*colour)[(size_t)adj.neighbour[(size_t)k]];
-      if (c >= 0 && c <= deg + 1) used[(size_t)c] = 1;
+      if (c >= lowest) taken.push_back(c);
     }
-    int32_t c = 0;
-    while (used[(size_t)c]) ++c;
+    std::sort(taken.begin(), taken.end());
+    int32_t c = lowest;
+    for (int32_t t : taken)
+      if (t == c) ++c;
+    return c;
+  };
+  // tier 1: the hubs, first fit among the hubs coloured before them
+  int32_t hub_colours = 0;
+  for (int32_t v : order) {
+    if (degree(v) < kHubDegree) continue;
+    int32_t c = first_free(v, 0);
     (*colour)[(size_t)v] = c;
-    if (c + 1 > num_colours) num_colours = c + 1;
+    hub_colours = std::max(hub_colours, c + 1);
+  }
+  // tier 2: every other vertex, in the same order, above the hub colours
+  int32_t num_colours = hub_colours;
+  for (int32_t v : order) {
+    if (degree(v) >= kHubDegree) continue;
+    int32_t c = first_free(v, hub_colours);
+    (*colour)[(size_t)v] = c;
+    num_colours = std::max(num_colours, c + 1);
   }
   return num_colours;
 }

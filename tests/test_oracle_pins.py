@@ -200,6 +200,95 @@ def test_colouring_special_graphs():
     assert C == 2 and col[5] == 0 and set(col[:5]) == {1}
 
 
+def _double_star(leaves):
+    """Centres 0 and 1 joined to each other, each with `leaves` leaves of its
+    own: both centres have degree leaves + 1."""
+    src = [0]
+    dst = [1]
+    nxt = 2
+    for c in (0, 1):
+        for _ in range(leaves):
+            src.append(c)
+            dst.append(nxt)
+            nxt += 1
+    a = lambda x: np.array(x, dtype=np.int32)
+    return nxt, a(src), a(dst), a([1] * len(src))
+
+
+def test_colouring_hub_tier_threshold_is_256_neighbours():
+    # R6: a vertex with at least 256 distinct neighbours is a hub; hubs take
+    # the low colours among themselves, every other vertex starts above them.
+    # Centres of degree 256: hubs 0 and 1 get colours 0 and 1, and every leaf
+    # gets colour 2 (plain Welsh-Powell would give the leaves of centre 0
+    # colour 1 and those of centre 1 colour 0).
+    n, src, dst, w = _double_star(255)
+    C, col = oracle.colouring(n, src, dst, w)
+    assert C == 3 and col[0] == 0 and col[1] == 1 and set(col[2:]) == {2}
+    # Centres of degree 255 are not hubs: plain Welsh-Powell.
+    n, src, dst, w = _double_star(254)
+    C, col = oracle.colouring(n, src, dst, w)
+    assert C == 2 and col[0] == 0 and col[1] == 1
+    assert set(col[2:2 + 254]) == {1} and set(col[2 + 254:]) == {0}
+
+
+def test_colouring_hub_degree_counts_merged_neighbours():
+    # 300 edges from vertex 0, but 100 of them repeat a pair and 20 of those
+    # cancel to weight 0: vertex 0 has 200 - 20 = 180 distinct neighbours, so
+    # it is no hub. Plain Welsh-Powell then gives the 20 vertices left
+    # isolated colour 0 (a hub 0 would push them to colour 1).
+    src = np.zeros(300, np.int32)
+    dst = np.concatenate([np.arange(1, 201), np.arange(1, 101)]).astype(np.int32)
+    w = np.ones(300, np.int32)
+    w[200:220] = -1
+    C, col = oracle.colouring(201, src, dst, w)
+    assert C == 2 and col[0] == 0
+    assert set(col[1:21]) == {0} and set(col[21:]) == {1}
+
+
+def _merged_adjacency(g):
+    merged = {}
+    for u, v, w in zip(g.src, g.dst, g.w):
+        k = (min(u, v), max(u, v))
+        merged[k] = merged.get(k, 0) + int(w)
+    adj = [set() for _ in range(g.n)]
+    for (u, v), w in merged.items():
+        if w != 0:
+            adj[u].add(v); adj[v].add(u)
+    return adj
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_colouring_two_tiers_on_a_graph_with_hubs(seed):
+    # A power-law graph whose largest degrees exceed 256: the colouring is
+    # proper; hub colours are all below non-hub colours; within each tier it
+    # is first fit (a vertex of colour c has, among its own tier's
+    # neighbours, every colour of its tier below c); hubs are coloured in
+    # Welsh-Powell order, so class 0 holds the largest-degree vertex.
+    g = synth.zipf_config_graph(6000, 2.0, 3, 1500, 40 + seed)
+    adj = _merged_adjacency(g)
+    deg = np.array([len(a) for a in adj])
+    hub = deg >= 256
+    assert 3 <= hub.sum() < g.n // 10
+    C, col = oracle.colouring(g.n, g.src, g.dst, g.w)
+    m = int(col[hub].max()) + 1
+    assert col[~hub].min() == m and C == col.max() + 1
+    for v in range(g.n):
+        assert all(col[u] != col[v] for u in adj[v])
+        same_tier = {col[u] for u in adj[v] if hub[u] == hub[v]}
+        low = 0 if hub[v] else m
+        assert set(range(low, col[v])) <= same_tier
+    top = int(np.lexsort((np.arange(g.n), -deg))[0])
+    assert col[top] == 0
+
+
+def test_colouring_complete_graph_of_hubs():
+    # K_300: every vertex has 299 neighbours, so all are hubs: 300 classes,
+    # vertex i in class i (equal degrees, smaller id first).
+    g = synth.complete_graph(300)
+    C, col = oracle.colouring(g.n, g.src, g.dst, g.w)
+    assert C == 300 and np.array_equal(col, np.arange(300))
+
+
 # ---------------------------------------------------------------------------
 # the annealing sweep
 # ---------------------------------------------------------------------------
@@ -361,6 +450,59 @@ def test_nflip_flips_exactly_n_distinct_spins_on_an_edgeless_graph():
         s2 = oracle.anneal_nflip(n, e, e, e, s, seed=3, n0=N0, T=T, t_begin=t, sweeps=1)
         assert int((s2 != s).sum()) == N0 * (T - 1 - t) // (T - 1)
         s = s2
+
+
+def _nflip_candidates(n, N, seed, t, replica, instance=0):
+    """Reading R10 recomputed from the known-answer-pinned Philox: candidate j
+    is floor(x_j * n / 2^32), x_j = word 0 of Philox4x32-10 at counter
+    (j, t, replica, 2) under the key (lo32 seed, hi32 seed ^ instance *
+    0x9E3779B9); the first N distinct candidates are chosen."""
+    key = [seed & 0xFFFFFFFF, ((seed >> 32) ^ (instance * 0x9E3779B9)) & 0xFFFFFFFF]
+    chosen, seen, j = [], set(), 0
+    while len(chosen) < N:
+        x = int(oracle.philox([j, t, replica, 2], key)[0])
+        c = (x * n) >> 32
+        if c not in seen:
+            seen.add(c)
+            chosen.append(c)
+        j += 1
+    return set(chosen), j
+
+
+@pytest.mark.parametrize("n,N0,T,seed,t,replica", [
+    (5000, 1234, 6, 3, 0, 0),
+    (5000, 1234, 6, 3, 4, 0),
+    (5000, 700, 9, 2 ** 33 + 5, 2, 3),   # high key word in use
+    (64, 60, 2, 11, 0, 1),               # N close to n: many repeated candidates
+    (50, 45, 3, 17, 1, 2),
+])
+def test_nflip_changes_exactly_the_first_distinct_candidates(n, N0, T, seed, t, replica):
+    # On an edgeless graph Eq. 2 leaves every spin as it is, so the spins that
+    # change in sweep t are exactly Algorithm 1's N_t random choices. They must
+    # be the first N_t distinct values of floor(x_j n / 2^32) (R10). A map
+    # x mod n, another output word, another stream or counter layout, or
+    # taking N_t candidates without skipping repeats all give another set.
+    e = np.zeros(0, dtype=np.int32)
+    s = oracle.init_spins(n, 7, replica=replica)
+    s2 = oracle.anneal_nflip(n, e, e, e, s, seed=seed, n0=N0, T=T, t_begin=t, sweeps=1,
+                             replica=replica)
+    Nt = N0 * (T - 1 - t) // (T - 1)
+    want, draws = _nflip_candidates(n, Nt, seed, t, replica)
+    assert set(np.nonzero(s2 != s)[0].tolist()) == want
+    if n <= 64:
+        assert draws > Nt  # repeats were skipped in this case
+
+
+def test_nflip_candidate_map_takes_the_high_bits():
+    # For n = 2^k, floor(x n / 2^32) is the top k bits of x: one vertex of
+    # an edgeless 2^k-vertex graph flipped at N_t = 1 is x_0 >> (32 - k).
+    e = np.zeros(0, dtype=np.int32)
+    for k, seed in ((4, 1), (10, 2), (16, 3)):
+        n = 1 << k
+        s = np.ones(n, np.int8)
+        s2 = oracle.anneal_nflip(n, e, e, e, s, seed=seed, n0=1, T=2, sweeps=1)
+        x0 = int(oracle.philox([0, 0, 0, 2], [seed, 0])[0])
+        assert np.nonzero(s2 != s)[0].tolist() == [x0 >> (32 - k)]
 
 
 def test_nflip_all_spins_when_n0_equals_n():
