@@ -59,6 +59,10 @@ enum {
   ISING_ERANGE = -6    /* sizes or weights beyond the supported range */
 };
 
+/* Degree (distinct neighbours after merging) from which a vertex is a hub:
+ * hubs are coloured among themselves and their classes are swept first. */
+#define ISING_HUB_DEGREE 256
+
 /* Annealing modes. */
 enum {
   /* Colour classes are swept one after another in increasing colour order (the
@@ -168,7 +172,12 @@ typedef struct ising_schedule {
  *   out      receives the handle.
  *
  * The host colours the graph greedily (largest degree first, ties by smaller
- * id; first fit), orders vertices by colour, and uploads a CSR adjacency
+ * id; first fit) in two tiers: vertices with at least ISING_HUB_DEGREE
+ * distinct neighbours (hubs) take colours 0 .. m-1 among themselves, and every
+ * other vertex takes the smallest colour >= m that none of its already
+ * coloured neighbours has. A graph without hubs gets plain first fit (an even
+ * torus: the checkerboard). The host then orders vertices by colour and
+ * uploads a CSR adjacency
  * (int32 column indices, int8 or int32 weights). Spins start at +1; call
  * ising_init_random() or ising_set_spins() to choose them.
  * Errors: ISING_EINVAL (null pointer, id out of range, self-loop, n <= 0, m < 0),

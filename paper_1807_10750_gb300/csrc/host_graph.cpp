@@ -8,8 +8,12 @@
 //
 // Deterministic sweeps need a colouring (the checkerboard of Sec. IV-B, made
 // general): greedy first fit over the vertices in order of decreasing degree,
-// ties broken by smaller id (Welsh-Powell). On a regular graph such as an even
-// torus this is natural order, which gives the checkerboard.
+// ties broken by smaller id (Welsh-Powell), in two tiers. Vertices with at
+// least ISING_HUB_DEGREE distinct neighbours (hubs) lead that order and are
+// coloured among themselves; every later vertex takes the smallest colour at
+// or above the hubs' colour count, so hub classes hold hubs only and come
+// first in the sweep. On a regular graph such as an even torus there are no
+// hubs and the order is natural order, which gives the checkerboard.
 #include "host_graph.h"
 #include "host_parallel.h"
 
@@ -151,21 +155,35 @@ int build_host_graph(int32_t n, int64_t m, const int32_t* src, const int32_t* ds
     for (size_t d = 0; d + 1 < bucket.size(); ++d) bucket[d + 1] += bucket[d];
     for (size_t v = 0; v < N; ++v) order[(size_t)bucket[(size_t)(maxdeg - degree(v))]++] = (int32_t)v;
   }
-  // First-fit colouring.
+  // First-fit colouring in two tiers. The hubs come first in the order; once
+  // the order reaches a non-hub, colours are counted from `base`, the hubs'
+  // colour count, and the (smaller) colours of hub neighbours are ignored.
   g.colour.assign(N, -1);
   {
     std::vector<int32_t> mark((size_t)maxdeg + 2, -1);
-    int32_t C = 0;
-    for (int32_t v : order) {
+    int32_t C = 0, base = 0;
+    bool hubs = true;
+    for (size_t i = 0; i < N; ++i) {
+      const int32_t v = order[i];
       const int32_t d = degree((size_t)v);
+      if (hubs && d < kHubDegree) {
+        hubs = false;
+        base = C;
+        g.hub_colours = C;
+        g.num_hubs = (int32_t)i;
+      }
       for (int64_t k = moff[(size_t)v]; k < moff[(size_t)v + 1]; ++k) {
-        int32_t c = g.colour[(size_t)mnb[(size_t)k]];
+        const int32_t c = g.colour[(size_t)mnb[(size_t)k]] - base;
         if (c >= 0 && c <= d) mark[(size_t)c] = v;
       }
       int32_t c = 0;
       while (mark[(size_t)c] == v) ++c;
-      g.colour[(size_t)v] = c;
-      C = std::max(C, c + 1);
+      g.colour[(size_t)v] = base + c;
+      C = std::max(C, base + c + 1);
+    }
+    if (hubs) {  // every vertex is a hub
+      g.hub_colours = C;
+      g.num_hubs = (int32_t)N;
     }
     g.num_colours = C;
   }

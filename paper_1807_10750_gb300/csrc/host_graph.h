@@ -7,6 +7,8 @@
 #include <cstdint>
 #include <vector>
 
+#include "../../include/ising.h"
+
 namespace isingx {
 
 // A unit of sweep work for one warp. Three kinds:
@@ -21,8 +23,13 @@ struct WorkItem {
   int32_t v_begin, v_end, e_begin, e_end;
 };
 
+// Vertices with at least this many distinct neighbours are hubs (ising.h).
+constexpr int32_t kHubDegree = ISING_HUB_DEGREE;
+
 struct HostGraph {
   int32_t n = 0;
+  int32_t num_hubs = 0;      // hubs hold positions [0, num_hubs)
+  int32_t hub_colours = 0;   // hub classes are colours [0, hub_colours)
   int64_t num_edges = 0;      // merged undirected edges
   int64_t nnz = 0;            // directed CSR entries (2 * num_edges)
   int64_t total_weight = 0;   // W

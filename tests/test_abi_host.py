@@ -74,6 +74,8 @@ def test_plan_colouring_rejects_the_same_inputs(P):
     lambda: synth.random_small_graph(50, 0.5, 4, weights="pm1", duplicates=200),
     lambda: synth.zipf_config_graph(5000, 2.1, 2, 400, 5),
     lambda: synth.complete_graph(9),
+    lambda: synth.zipf_config_graph(6000, 2.0, 3, 1500, 41),   # hubs: two colour tiers
+    lambda: synth.complete_graph(300),                        # every vertex a hub
 ])
 def test_host_colouring_equals_oracle(P, make):
     g = make()
