@@ -3,8 +3,12 @@
 
 One *step* is one whole anneal of the workload: random initial spins, the full
 sweep schedule (every colour class of every sweep: field gather, update, random
-flip), then the energy/cut reduction. The default workload is the 1024 x 1024
-torus with +-1 weights, 2000 sweeps, flip probability linear 0.1 -> 0.
+flip), then the energy/cut reduction. The default workload is the 2^20-vertex
+power-law graph (erased configuration model, degrees ~ d^-2.1 on [4, 10000],
+weights uniform in [-8, 8] without 0), 2000 sweeps, flip probability linear
+0.1 -> 0. ``--workload all`` prints one line for every workload (the 800-vertex
+random graph, the 1024 x 1024 torus, the power-law graph, the batched set and
+the learned warm start), each from its own process.
 
 Prints one JSON line (rank 0). ``value`` is spin-updates/s over all ranks with
 the graph resident in HBM; ``e2e`` is the same metric through the public C ABI
@@ -35,13 +39,14 @@ import numpy as np  # noqa: E402
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="torus1024",
-                    choices=["torus1024", "zipf1m", "er800", "batched", "warmstart", "gnn"])
+    ap.add_argument("--workload", default="zipf1m",
+                    choices=["torus1024", "zipf1m", "er800", "batched", "warmstart", "gnn", "all"])
     ap.add_argument("--engine", default="auto",
-                    choices=["auto", "phase", "persistent", "dataflow", "persistent_grid", "itemflow", "halo"])
+                    choices=["auto", "phase", "persistent", "dataflow", "persistent_grid", "itemflow",
+                             "halo", "hub"])
     ap.add_argument("--halo-sweeps", type=int, default=0,
                     help="sweeps per exchange of the halo engine (0: automatic)")
     ap.add_argument("--mode", default="det", choices=["det", "racy"],
@@ -63,10 +68,10 @@ def dist_env():
 
 
 def algorithmic_bytes_per_sweep(n: int, nnz: int, entry_bytes: int) -> int:
-    """Compulsory traffic of one sweep in the library's layout: every CSR entry
-    streamed once (4 bytes when column and int8 weight are packed into one
-    word, else 8), the int32 row offsets once, and every spin read and written
-    once (int8)."""
+    """Compulsory traffic of one sweep: every directed CSR entry streamed once
+    (an int32 column index plus the weight: 4 + 1 bytes for int8 weights,
+    4 + 4 for int32), the int32 row offsets once, and every int8 spin read and
+    written once. `entry_bytes` is the column plus weight size."""
     return nnz * entry_bytes + 4 * (n + 1) + 2 * n
 
 
@@ -209,8 +214,9 @@ def run_reference(args, world, rank):
     T = sch["sweeps"]
     s = oracle.init_spins(g.n, sch["seed"])
     # size the per-step sample so that the whole run stays within a few minutes
-    budget = max(2.0, 150.0 / max(1, args.steps + args.warmup))
-    sweeps = int(max(2, min(T, budget / oracle_sweep_cost(g, sch))))
+    budget = max(1.0, 150.0 / max(1, args.steps + args.warmup))
+    per_sweep, setup = oracle_sweep_cost(g, sch)
+    sweeps = int(max(2, min(T, budget / per_sweep)))
     times = []
     t = 0
     for k in range(args.warmup + args.steps):
@@ -219,7 +225,9 @@ def run_reference(args, world, rank):
         t0 = time.perf_counter()
         s = oracle.anneal(g.n, g.src, g.dst, g.w, s, seed=sch["seed"], p0=sch["p0"], T=T,
                           t_begin=t, sweeps=sweeps)
-        dt = time.perf_counter() - t0
+        # the oracle rebuilds its adjacency and colouring on every call: that
+        # fixed cost (a zero-sweep call, measured) is not sweep work
+        dt = max(time.perf_counter() - t0 - setup, 1e-9)
         t += sweeps
         if k >= args.warmup:
             times.append(dt)
@@ -233,8 +241,9 @@ def run_reference(args, world, rank):
                    "p0": sch["p0"]},
         "cpu_baseline": {"value": value, "unit": "spin-updates/s", "cores": 1, "kind": "oracle",
                          "sample": f"{sweeps} consecutive sweeps of the {T}-sweep schedule per "
-                                   f"step, full graph, one oracle_anneal call (incl. its "
-                                   f"adjacency rebuild) per step, single thread"},
+                                   f"step, full graph, one oracle_anneal call per step minus "
+                                   f"its measured {setup:.2f} s adjacency and colouring rebuild, "
+                                   f"single thread"},
         "e2e": {"value": value, "unit": "spin-updates/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -242,33 +251,37 @@ def run_reference(args, world, rank):
 
 
 def oracle_sweep_cost(g, sch):
-    """Seconds per sweep of the oracle on this graph, without the fixed cost
-    of its adjacency build: two calls of different length, differenced; never
-    below a tenth of the longer call's time per sweep (the difference is noisy
-    when the build dominates)."""
+    """(seconds per sweep, seconds of fixed setup) of the oracle on this graph.
+    Every oracle call rebuilds its adjacency and colouring; a zero-sweep call
+    measures that setup, and a short call less the setup gives the per-sweep
+    cost (never below a tenth of the short call's time per sweep)."""
     import oracle
     oracle.build()
     T = sch["sweeps"]
     s = oracle.init_spins(g.n, sch["seed"])
-    cost = []
-    for k in (2, 10):
-        t0 = time.perf_counter()
-        oracle.anneal(g.n, g.src, g.dst, g.w, s, seed=sch["seed"], p0=sch["p0"], T=T, sweeps=min(k, T))
-        cost.append(time.perf_counter() - t0)
-    return max((cost[1] - cost[0]) / 8, 0.1 * cost[1] / 10, 1e-6)
+    t0 = time.perf_counter()
+    oracle.anneal(g.n, g.src, g.dst, g.w, s, seed=sch["seed"], p0=sch["p0"], T=T, sweeps=0)
+    setup = time.perf_counter() - t0
+    k = min(8, T)
+    t0 = time.perf_counter()
+    oracle.anneal(g.n, g.src, g.dst, g.w, s, seed=sch["seed"], p0=sch["p0"], T=T, sweeps=k)
+    call = time.perf_counter() - t0
+    return max((call - setup) / k, 0.1 * call / k, 1e-6), setup
 
 
 def cpu_baseline(g, sch, target_s: float):
     import oracle
     T = sch["sweeps"]
     s = oracle.init_spins(g.n, sch["seed"])
-    sweeps = int(max(2, min(T, target_s / oracle_sweep_cost(g, sch))))
+    per_sweep, setup = oracle_sweep_cost(g, sch)
+    sweeps = int(max(2, min(T, target_s / per_sweep)))
     t0 = time.perf_counter()
     oracle.anneal(g.n, g.src, g.dst, g.w, s, seed=sch["seed"], p0=sch["p0"], T=T, sweeps=sweeps)
-    dt = time.perf_counter() - t0
+    dt = max(time.perf_counter() - t0 - setup, 1e-9)
     return {"value": g.n * sweeps / dt, "unit": "spin-updates/s", "cores": 1, "kind": "oracle",
             "sample": f"sweeps 0..{sweeps - 1} of the {T}-sweep schedule on the full graph "
-                      f"({dt:.1f} s, single thread, one oracle_anneal call incl. adjacency build)"}
+                      f"({dt:.1f} s of sweeps, single thread: one oracle_anneal call less its "
+                      f"measured {setup:.2f} s adjacency and colouring rebuild)"}
 
 
 def run_batched(args, world, rank, P, torch, dist):
@@ -590,8 +603,79 @@ def run_gnn(args, world, rank, P, torch, dist):
     net.close()
 
 
+# Shared-memory traffic of the halo kernel per sweep: l1tex shared-memory
+# wavefronts (one wavefront moves up to 128 bytes) from ncu captures, slope
+# over the sweep count; valid while the kernel sources hash to `sources`.
+NCU_SMEM = {}
+
+
+def roofline_entry(args, engine_name, T, B, B_lib, achieved, peak, peak_kind, sweep_s, clk):
+    """The roofline object of the dominant kernel. The grid and hub engines
+    stream the CSR through L2 and HBM every sweep: bound "hbm", achieved =
+    algorithmic bytes (survey formula: 5 bytes per directed entry with int8
+    weights) over time. The halo engine reads its part of the graph from HBM
+    once per launch and then works from shared memory, so its bound is the
+    SMs' shared-memory bandwidth (152 SMs x 128 bytes per clock at the
+    sampled SM clock); the HBM figure is kept as a labelled secondary one."""
+    hbm = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+           "frac": achieved / peak,
+           "traffic": (kernel_traffic(args.workload, T, engine_name) if args.mode == "det" else None),
+           "peak_kind": peak_kind, "bytes_per_sweep": B, "bytes_per_launch": B * T,
+           "bytes_per_sweep_library_layout": B_lib,
+           "kernel": f"{engine_name} sweep kernel(s) of one anneal call"}
+    if engine_name != "halo":
+        return hbm
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz = (clk or {}).get("sm_mhz") or 2070.0
+    smem_peak = sms * 128 * mhz * 1e6 / 1e9
+    e = NCU_SMEM.get(args.workload)
+    smem_bytes = None
+    if e is not None:
+        import hashlib
+        h = hashlib.sha256()
+        for f in e["files"]:
+            with open(os.path.join(ROOT, "paper_1807_10750_gb300", "csrc", f), "rb") as fh:
+                h.update(fh.read())
+        if h.hexdigest()[:16] == e["sources"]:
+            smem_bytes = 128 * e["wavefronts_per_sweep"]
+    smem_achieved = smem_bytes / sweep_s / 1e9 if smem_bytes else None
+    return {"bound": "smem", "achieved": smem_achieved, "peak": smem_peak, "unit": "GB/s",
+            "frac": smem_achieved / smem_peak if smem_achieved else None,
+            "traffic": hbm["traffic"], "peak_kind": "nominal: SMs x 128 B/clock x sampled SM clock",
+            "smem_bytes_per_sweep": smem_bytes,
+            "kernel": "halo_kernel (one launch per anneal call)",
+            "hbm_secondary": {k: hbm[k] for k in ("achieved", "peak", "frac", "bytes_per_sweep",
+                                                   "bytes_per_launch", "peak_kind")}}
+
+
+WORKLOADS_ALL = ["er800", "torus1024", "zipf1m", "batched", "warmstart"]
+
+
+def run_all(args):
+    """One line per workload, each from its own process with the same flags."""
+    if dist_env()[0] > 1:
+        raise SystemExit("--workload all runs on one GPU (no torchrun)")
+    rc = 0
+    # the CPU oracle arm covers the single-graph workloads
+    names = WORKLOADS_ALL if args.impl == "ours" else ["er800", "torus1024", "zipf1m"]
+    for wl in names:
+        cmd = [sys.executable, os.path.abspath(__file__), "--workload", wl, "--steps", str(args.steps),
+               "--warmup", str(args.warmup), "--impl", args.impl, "--e2e-steps", str(args.e2e_steps),
+               "--cpu-seconds", str(args.cpu_seconds)]
+        if args.no_cpu_baseline:
+            cmd.append("--no-cpu-baseline")
+        r = subprocess.run(cmd, stdout=subprocess.PIPE, text=True)
+        sys.stdout.write(r.stdout)
+        sys.stdout.flush()
+        rc = rc or r.returncode
+    raise SystemExit(rc)
+
+
 def main():
     args = parse_args()
+    if args.workload == "all":
+        run_all(args)
     world, rank, local = dist_env()
     if args.impl == "reference":
         run_reference(args, world, rank)
@@ -642,7 +726,8 @@ def main():
               "persistent": P.ISING_ENGINE_PERSISTENT,
               "dataflow": P.ISING_ENGINE_DATAFLOW,
               "persistent_grid": P.ISING_ENGINE_PERSISTENT_GRID,
-              "itemflow": P.ISING_ENGINE_ITEMFLOW, "halo": P.ISING_ENGINE_HALO}[args.engine]
+              "itemflow": P.ISING_ENGINE_ITEMFLOW, "halo": P.ISING_ENGINE_HALO,
+              "hub": P.ISING_ENGINE_HUB}[args.engine]
 
     h = P.ising_create(g.n, g.src, g.dst, g.w, stream=stream)
     P.ising_set_engine(h, engine)
@@ -657,7 +742,7 @@ def main():
     nnz = 2 * m
     w_bytes = 1 if np.abs(g.w).max(initial=0) <= 127 else 4
     # the library packs (column, int8 weight) into one int32 when it can
-    entry_bytes = 4 if (w_bytes == 1 and g.n < (1 << 24) - 1) else 8
+    lib_entry_bytes = 4 if (w_bytes == 1 and g.n < (1 << 24) - 1) else 8
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
     def step(k):
@@ -695,7 +780,7 @@ def main():
     launches = P.ising_launch_count(h) - launches0
     engine_name = {P.ISING_ENGINE_PHASE: "phase", P.ISING_ENGINE_PERSISTENT_GRID: "persistent",
                    P.ISING_ENGINE_DATAFLOW: "dataflow", P.ISING_ENGINE_ITEMFLOW: "itemflow",
-                   P.ISING_ENGINE_HALO: "halo",
+                   P.ISING_ENGINE_HALO: "halo", P.ISING_ENGINE_HUB: "hub",
                    P.ISING_ENGINE_USED_BLOCK: "block"}.get(P.ising_engine_used(h), "unknown")
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = sum(step_ms)
@@ -705,7 +790,8 @@ def main():
     value = job_throughput(g.n * T * args.steps, world, total_ms / 1e3)
 
     # roofline of the sweep kernels: algorithmic bytes per sweep / time per sweep
-    B = algorithmic_bytes_per_sweep(g.n, nnz, entry_bytes)
+    B = algorithmic_bytes_per_sweep(g.n, nnz, 4 + w_bytes)
+    B_lib = algorithmic_bytes_per_sweep(g.n, nnz, lib_entry_bytes)
     sweep_s = (sum(anneal_ms) / len(anneal_ms)) / 1e3 / T
     achieved = B / sweep_s / 1e9
     peak, peak_kind = measured_peaks()
@@ -718,24 +804,36 @@ def main():
         w_p = torch.from_numpy(g.w).pin_memory().numpy()
         spins_out = torch.empty(g.n, dtype=torch.int8).pin_memory().numpy()
         torch.cuda.synchronize()
-        e2e_t = []
+        e2e_t, create_t = [], []
+        e2e_engine = None
         for k in range(args.e2e_steps + 1):
             t0 = time.perf_counter()
             with P.ising_create(g.n, src_p, dst_p, w_p, stream=stream) as h2:
+                t1 = time.perf_counter()
                 P.ising_set_engine(h2, engine)
                 P.ising_set_halo_sweeps(h2, args.halo_sweeps)
                 P.ising_init_random(h2, seed + k)
                 P.ising_anneal(h2, p0=p0, t_total=T, seed=seed + k, stream=stream, mode=mode)
                 P.ising_cut(h2)
                 P.ising_get_spins(h2, spins_out)
+                e2e_engine = P.ising_engine_used(h2)
             dt = time.perf_counter() - t0
             if k > 0:
                 e2e_t.append(dt)
+                create_t.append(t1 - t0)
         e2e_total = sum(e2e_t)
         e2e_total = max_over_ranks(e2e_total, world, dist, "cuda")
         e2e = {"value": g.n * T * len(e2e_t) * world / e2e_total, "unit": "spin-updates/s",
                "h2d_bytes_per_step": int(3 * 4 * g.m), "d2h_bytes_per_step": int(g.n + 8),
-               "ms_per_step": 1e3 * e2e_total / len(e2e_t)}
+               "ms_per_step": 1e3 * e2e_total / len(e2e_t),
+               # a new handle every step: the host graph build (ising_create) is
+               # inside the timed region, and a one-shot handle never waits for
+               # the halo plan
+               "create_ms_per_step": 1e3 * sum(create_t) / len(create_t),
+               "engine_used": {P.ISING_ENGINE_PHASE: "phase", P.ISING_ENGINE_PERSISTENT_GRID: "persistent",
+                               P.ISING_ENGINE_DATAFLOW: "dataflow", P.ISING_ENGINE_ITEMFLOW: "itemflow",
+                               P.ISING_ENGINE_HALO: "halo", P.ISING_ENGINE_HUB: "hub",
+                               P.ISING_ENGINE_USED_BLOCK: "block"}.get(e2e_engine, "unknown")}
 
     if rank != 0:
         if world > 1:
@@ -767,19 +865,15 @@ def main():
             "mode": "racy" if args.mode == "racy" else "deterministic",
             "engine": args.engine, "engine_used": engine_name, "halo": halo,
             "weights": "int8" if w_bytes == 1 else "int32",
-            "csr_entry_bytes": entry_bytes,
+            "csr_entry_bytes": lib_entry_bytes,
             "replicas_per_gpu": 1, "parallelism": f"replicas{world}",
             "l2": "512 MiB buffer zeroed between timed steps (outside the events)",
         },
         "sweeps_per_s": T * args.steps * world / (total_ms / 1e3),
         "algorithmic_gbs": achieved,
         "final_cut_mean": float(np.mean(cuts)),
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak,
-                     "traffic": (kernel_traffic(args.workload, T, engine_name)
-                                 if args.mode == "det" else None),
-                     "peak_kind": peak_kind, "bytes_per_sweep": B, "bytes_per_launch": B * T,
-                     "kernel": f"{engine_name} sweep kernel(s) of one anneal call"},
+        "roofline": roofline_entry(args, engine_name, T, B, B_lib, achieved, peak, peak_kind,
+                                   sweep_s, clocks.summary()),
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": int(launches),

@@ -103,7 +103,8 @@ enum {
 /* Which kernel engine runs a deterministic anneal (all give identical spins). */
 enum {
   ISING_ENGINE_AUTO = 0,       /* with cooperative launches, for deterministic linear anneals:
-                                  PERSISTENT's one-block form for small graphs, else HALO when its
+                                  PERSISTENT's one-block form for small graphs, else HUB for graphs
+                                  with hubs it can hold, else HALO when its
                                   plan is ready and repeats at most 1.6x the work (a host thread
                                   builds the plan from the handle's second such call on; no call
                                   waits for it), else ITEMFLOW for
@@ -125,7 +126,7 @@ enum {
                                   (per-item counters, release/acquire); for graphs whose rows
                                   are not sliced across warps, deterministic linear schedule;
                                   otherwise runs as PERSISTENT_GRID */
-  ISING_ENGINE_HALO = 7        /* one cooperative launch per anneal call, one block per SM: the
+  ISING_ENGINE_HALO = 7,       /* one cooperative launch per anneal call, one block per SM: the
                                   graph is cut into one part per block (recursive breadth-first
                                   bisection); a block keeps every vertex within D = S * K hops of
                                   its part (K colour classes, S sweeps per exchange) in shared
@@ -135,6 +136,14 @@ enum {
                                   of at most 63 entries, int8 weights and regions that fit in
                                   shared memory; deterministic linear schedule; otherwise runs as
                                   ITEMFLOW */
+  ISING_ENGINE_HUB = 8         /* one cooperative launch per anneal call for graphs with 1 to 10240
+                                  hubs (ISING_HUB_DEGREE): one block runs every hub class with
+                                  block barriers, keeping the hubs' fields in shared memory and
+                                  updating them from the rows of the hubs that change; the other
+                                  blocks sum the hubs' fields from the other vertices and run the
+                                  other classes with a bounded grid barrier after each.
+                                  Deterministic linear schedule (flip bias allowed); otherwise runs
+                                  as PERSISTENT_GRID */
 };
 
 /* ising_create flags. */
@@ -464,7 +473,8 @@ void ising_gnn_destroy(ising_gnn* net);
 
 /* ising_engine_used -- the engine the last anneal call ran: ISING_ENGINE_PHASE,
  * ISING_ENGINE_PERSISTENT_GRID (the persistent grid-barrier kernel),
- * ISING_ENGINE_DATAFLOW, ISING_ENGINE_ITEMFLOW, ISING_ENGINE_HALO or ISING_ENGINE_USED_BLOCK
+ * ISING_ENGINE_DATAFLOW, ISING_ENGINE_ITEMFLOW, ISING_ENGINE_HALO, ISING_ENGINE_HUB or
+ * ISING_ENGINE_USED_BLOCK
  * (PERSISTENT's one-block form); -1 before the first anneal. */
 #define ISING_ENGINE_USED_BLOCK 6
 int ising_engine_used(ising_graph* g, int32_t* out);

@@ -39,6 +39,7 @@ ISING_ENGINE_DATAFLOW = 3
 ISING_ENGINE_PERSISTENT_GRID = 4
 ISING_ENGINE_ITEMFLOW = 5
 ISING_ENGINE_HALO = 7
+ISING_ENGINE_HUB = 8
 ISING_CREATE_WEIGHTS_I32 = 1
 ISING_STATIC_MAX_VERTICES = 1 << 24
 

@@ -37,6 +37,7 @@
 #include "block.cuh"
 #include "graph_handle.h"
 #include "halo.cuh"
+#include "hub.cuh"
 
 using isingx::HostGraph;
 using isingx::PhiloxKey;
@@ -440,7 +441,7 @@ void free_device(ising_graph* g) {
                   g->d_block_chunk_len, g->d_block_class_chunk, g->d_dep_ptr, g->d_deps,
                   g->d_done, g->d_halo_hdr, g->d_halo_words, g->d_halo_slices, g->d_halo_gpos,
                   g->d_halo_imports, g->d_halo_nbrs, g->d_halo_exports, g->d_halo_quads, g->d_halo_flags,
-                  g->d_spins2};
+                  g->d_spins2, g->d_hub_end, g->d_hub_sums, g->d_hub_acc, g->d_hub_flips};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -810,6 +811,80 @@ cudaError_t launch_halo(ising_graph* g, uint64_t t_begin, uint32_t sweeps, uint6
                                      dim3(isingx::kHaloBlock), args, static_cast<size_t>(g->halo_smem), g->stream);
 }
 
+// The hub engine (hub.cuh): one cooperative launch, block 0 runs the hub
+// classes. Returns cudaErrorCooperativeLaunchTooLarge when fewer than two
+// blocks fit on the device.
+template <bool PACKED>
+cudaError_t launch_hub_t(ising_graph* g, uint64_t t_begin, uint32_t sweeps, uint64_t T, uint64_t T0,
+                         uint32_t replica, const isingx::PhiloxRounds& rk_in) {
+  auto kernel = isingx::hub_kernel<PACKED>;
+  const int smem = isingx::hub_smem_bytes(g->num_hubs, g->hub_colours);
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, isingx::kHubBlock, smem);
+  if (e != cudaSuccess) return e;
+  per_sm = std::min(per_sm, 2);
+  const int grid = per_sm * g->num_sms;
+  if (grid < 2) return cudaErrorCooperativeLaunchTooLarge;
+  if ((e = barrier_init(g)) != cudaSuccess) return e;
+  // the sums start at zero (a launch that gave up may have left partial sums)
+  if ((e = cudaMemsetAsync(g->d_hub_acc, 0, 2 * sizeof(int32_t) * static_cast<size_t>(g->num_hubs),
+                           g->stream)) != cudaSuccess)
+    return e;
+  DevGraph d = g->dev();
+  isingx::HubArgs h{};
+  h.hubs = g->num_hubs;
+  h.hub_classes = g->hub_colours;
+  h.classes = g->num_colours;
+  h.class_begin = g->d_class_begin;
+  h.class_items = g->d_class_items;
+  h.hub_end = g->d_hub_end;
+  h.sums = g->d_hub_sums;
+  h.num_b_items = g->hub_num_b;
+  h.num_items = g->hub_num_items;
+  h.acc = g->d_hub_acc;
+  h.flips = g->d_hub_flips;
+  isingx::PhiloxRounds rk = rk_in;
+  BarrierState* bs = g->d_barrier;
+  void* args[] = {&d, &h, &t_begin, &sweeps, &T, &T0, &replica, &rk, &bs};
+  g->launches++;
+  return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(kernel), dim3(grid),
+                                     dim3(isingx::kHubBlock), args, static_cast<size_t>(smem), g->stream);
+}
+
+cudaError_t launch_hub(ising_graph* g, uint64_t t_begin, uint32_t sweeps, uint64_t T, uint64_t T0,
+                       uint32_t replica, const isingx::PhiloxRounds& rk) {
+  if (g->packed) return launch_hub_t<true>(g, t_begin, sweeps, T, T0, replica, rk);
+  return launch_hub_t<false>(g, t_begin, sweeps, T, T0, replica, rk);
+}
+
+// Host plan of the hub engine: per hub the end of its hub entries (rows are
+// sorted by neighbour position and the hubs hold the first positions), and
+// the field-sum items over the hubs' rows, kHubSumChunk entries each: first
+// the hub entries (B, summed once per launch), then the other entries (A,
+// summed every sweep).
+void build_hub_plan(const HostGraph& hg, std::vector<int32_t>* hub_end, std::vector<int4>* items,
+                    int32_t* num_b) {
+  const int32_t X = hg.num_hubs;
+  hub_end->assign(static_cast<size_t>(X), 0);
+  for (int32_t u = 0; u < X; ++u) {
+    const int32_t* b = hg.col.data() + hg.row_ptr[static_cast<size_t>(u)];
+    const int32_t* e = hg.col.data() + hg.row_ptr[static_cast<size_t>(u) + 1];
+    (*hub_end)[static_cast<size_t>(u)] = static_cast<int32_t>(std::lower_bound(b, e, X) - hg.col.data());
+  }
+  items->clear();
+  for (int kind = 1; kind >= 0; --kind) {
+    for (int32_t u = 0; u < X; ++u) {
+      const int32_t lo = kind == 1 ? hg.row_ptr[static_cast<size_t>(u)] : (*hub_end)[static_cast<size_t>(u)];
+      const int32_t hi = kind == 1 ? (*hub_end)[static_cast<size_t>(u)] : hg.row_ptr[static_cast<size_t>(u) + 1];
+      for (int32_t e = lo; e < hi; e += isingx::kHubSumChunk)
+        items->push_back(make_int4(u, e, std::min(hi, e + isingx::kHubSumChunk), kind));
+    }
+    if (kind == 1) *num_b = static_cast<int32_t>(items->size());
+  }
+}
+
 // Enqueue twice the energy into *slot (device), no host synchronisation.
 int enqueue_energy(ising_graph* g, unsigned long long* slot) {
   ISING_CUDA(g, cudaMemsetAsync(slot, 0, sizeof(unsigned long long), g->stream));
@@ -897,6 +972,20 @@ int ising_create(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, c
   }
   g->num_items = static_cast<int32_t>(plan.items.size());
   g->num_slots = static_cast<int32_t>(plan.split_parts.size());
+  // the hub engine's plan (before the columns are packed)
+  std::vector<int32_t> hub_end;
+  std::vector<int4> hub_items;
+  g->num_hubs = hg.num_hubs;
+  g->hub_colours = hg.hub_colours;
+  if (hg.num_hubs >= 1 && hg.num_hubs <= isingx::kHubMaxHubs) {
+    try {
+      build_hub_plan(hg, &hub_end, &hub_items, &g->hub_num_b);
+    } catch (const std::bad_alloc&) {
+      delete g;
+      return ISING_ENOMEM;
+    }
+    g->hub_num_items = static_cast<int32_t>(hub_items.size());
+  }
   isingx::BlockPlan block;
   std::vector<int32_t> dep_ptr, deps;  // item dependencies (before the columns are packed)
   bool have_deps = false;
@@ -987,6 +1076,14 @@ int ising_create(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, c
                           g->stream)) != cudaSuccess) break;
       g->block_ok = true;
       g->block_num_chunks = static_cast<int32_t>(block.chunk_off.size());
+    }
+    if (!hub_end.empty()) {
+      const size_t X = hub_end.size();
+      if ((e = alloc_copy(&g->d_hub_end, hub_end.data(), X, g->stream)) != cudaSuccess) break;
+      if ((e = alloc_copy(&g->d_hub_sums, hub_items.data(), hub_items.size(), g->stream)) != cudaSuccess) break;
+      if ((e = alloc_copy<int32_t>(&g->d_hub_acc, nullptr, 2 * X, g->stream)) != cudaSuccess) break;
+      if ((e = alloc_copy<uint32_t>(&g->d_hub_flips, nullptr, (X + 31) / 32, g->stream)) != cudaSuccess) break;
+      g->hub_ok = true;
     }
     if ((e = alloc_copy<unsigned>(&g->d_nflip_bits, nullptr, (N + 31) / 32, g->stream)) != cudaSuccess) break;
     if ((e = alloc_copy<int32_t>(&g->d_nflip_list, nullptr, N, g->stream)) != cudaSuccess) break;
@@ -1097,6 +1194,9 @@ static int anneal_impl(ising_graph* g, const ising_schedule* sched, uint32_t swe
     // schedules; else the grid barrier
     if (!coop) {
       engine = ISING_ENGINE_PHASE;
+    } else if (!g->block_ok && mode == ISING_MODE_DET && sched->kind == ISING_SCHED_LINEAR &&
+               g->hub_ok) {
+      engine = ISING_ENGINE_HUB;
     } else if (!g->block_ok && mode == ISING_MODE_DET && sched->kind == ISING_SCHED_LINEAR) {
       // a handle that anneals more than once gets the halo plan: the second
       // call starts the planner, and no call waits for it
@@ -1121,6 +1221,18 @@ static int anneal_impl(ising_graph* g, const ising_schedule* sched, uint32_t swe
     g->engine_used = ISING_ENGINE_DATAFLOW;
     ISING_CUDA(g, launch_flow(g, sched->t_begin, sweeps, sched->t_total, T0, sched->replica, par0, rk));
     return ISING_OK;
+  }
+  if (engine == ISING_ENGINE_HUB) {
+    if (mode == ISING_MODE_DET && !nflip && g->hub_ok) {
+      const cudaError_t e = launch_hub(g, sched->t_begin, sweeps, sched->t_total, T0, sched->replica, rk);
+      if (e == cudaSuccess) {
+        g->engine_used = ISING_ENGINE_HUB;
+        return ISING_OK;
+      }
+      if (e != cudaErrorCooperativeLaunchTooLarge) return cuda_fail(g, e);
+      cudaGetLastError();
+    }
+    engine = ISING_ENGINE_PERSISTENT_GRID;  // racy, N-flip, no hub plan or too few blocks
   }
   if (engine == ISING_ENGINE_HALO) {
     if (mode == ISING_MODE_DET && !nflip) {
@@ -1352,7 +1464,7 @@ int ising_set_engine(ising_graph* g, int engine) {
   if (engine != ISING_ENGINE_AUTO && engine != ISING_ENGINE_PHASE &&
       engine != ISING_ENGINE_PERSISTENT && engine != ISING_ENGINE_DATAFLOW &&
       engine != ISING_ENGINE_PERSISTENT_GRID && engine != ISING_ENGINE_ITEMFLOW &&
-      engine != ISING_ENGINE_HALO)
+      engine != ISING_ENGINE_HALO && engine != ISING_ENGINE_HUB)
     return ISING_EINVAL;
   g->engine = engine;
   return ISING_OK;

@@ -12,7 +12,7 @@ import synth
 
 pytestmark = pytest.mark.gpu
 
-ENGINES = ["phase", "persistent", "dataflow", "persistent_grid", "itemflow", "halo"]
+ENGINES = ["phase", "persistent", "dataflow", "persistent_grid", "itemflow", "halo", "hub"]
 
 
 @pytest.fixture(scope="module")
@@ -29,7 +29,8 @@ def engine_id(P, name):
     return {"phase": P.ISING_ENGINE_PHASE, "persistent": P.ISING_ENGINE_PERSISTENT,
             "dataflow": P.ISING_ENGINE_DATAFLOW, "auto": P.ISING_ENGINE_AUTO,
             "persistent_grid": P.ISING_ENGINE_PERSISTENT_GRID,
-            "itemflow": P.ISING_ENGINE_ITEMFLOW, "halo": P.ISING_ENGINE_HALO}[name]
+            "itemflow": P.ISING_ENGINE_ITEMFLOW, "halo": P.ISING_ENGINE_HALO,
+            "hub": P.ISING_ENGINE_HUB}[name]
 
 
 def gpu_anneal(P, g, s0, *, seed, p0, T, t_begin=0, sweeps=None, flags=0, engine="auto",
