@@ -43,7 +43,8 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="zipf1m",
-                    choices=["torus1024", "zipf1m", "er800", "batched", "warmstart", "gnn", "all"])
+                    choices=["torus1024", "zipf1m", "er800", "batched", "warmstart", "gnn", "region",
+                             "all"])
     ap.add_argument("--engine", default="auto",
                     choices=["auto", "phase", "persistent", "dataflow", "persistent_grid", "itemflow",
                              "halo", "hub"])
@@ -649,7 +650,7 @@ def roofline_entry(args, engine_name, T, B, B_lib, achieved, peak, peak_kind, sw
                                                    "bytes_per_launch", "peak_kind")}}
 
 
-WORKLOADS_ALL = ["er800", "torus1024", "zipf1m", "batched", "warmstart"]
+WORKLOADS_ALL = ["er800", "torus1024", "zipf1m", "batched", "warmstart", "region"]
 
 
 def run_all(args):
@@ -670,6 +671,49 @@ def run_all(args):
         sys.stdout.flush()
         rc = rc or r.returncode
     raise SystemExit(rc)
+
+
+def run_region(args, world, rank, P, torch, dist):
+    """The paper's convergence study (Sec. V-C, Fig. 4) on the 800-vertex
+    random graph: 10 seeded runs of the 1000-sweep schedule, the cut after
+    every 50 sweeps, and its min / max over the runs (ising_convergence_region).
+    The timed quantity is the whole region (10 runs and their checkpoints)."""
+    g, sch = build_workload("er800", args.sweeps)
+    T, p0 = sch["sweeps"], sch["p0"]
+    every, seeds = 50, [sch["seed"] + 7919 * rank + k for k in range(10)]
+    stream = torch.cuda.Stream()
+    h = P.ising_create(g.n, g.src, g.dst, g.w, stream=stream)
+    for _ in range(args.warmup):
+        P.ising_convergence_region(h, seeds=seeds, p0=p0, t_total=T, every=every, stream=stream)
+    torch.cuda.synchronize()
+    times = []
+    launches0 = P.ising_launch_count(h)
+    with ClockSampler(torch.cuda.current_device()) as clocks:
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            idx, cuts, lo, hi = P.ising_convergence_region(h, seeds=seeds, p0=p0, t_total=T,
+                                                           every=every, stream=stream)
+            times.append(time.perf_counter() - t0)
+    launches = P.ising_launch_count(h) - launches0
+    total = max_over_ranks(sum(times), world, dist, "cuda")
+    if rank == 0:
+        line = {
+            "metric": "spin_updates_per_s", "value": g.n * T * len(seeds) * args.steps * world / total,
+            "unit": "spin-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int8", "data": "synthetic",
+            "config": {"workload": "region", "graph": "er800", "n": g.n, "m": P.ising_num_edges(h),
+                       "sweeps": T, "p0": p0, "runs": len(seeds), "every": every,
+                       "parallelism": f"replicas{world}",
+                       "timing": "host wall clock around each ising_convergence_region call "
+                                 "(it synchronises after every chunk)"},
+            "region": {"sweep": idx.tolist(), "min_cut": lo.tolist(), "max_cut": hi.tolist(),
+                       "one_run_cut": cuts[0].tolist(), "mean_final_cut": float(cuts[:, -1].mean())},
+            "roofline": None, "cpu_baseline": None, "e2e": None,
+            "gpu_launches": int(launches), "clocks": clocks.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    h.close()
 
 
 def main():
@@ -707,6 +751,13 @@ def main():
 
     if args.workload == "warmstart":
         run_warmstart(args, world, rank, P, torch, dist)
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    if args.workload == "region":
+        run_region(args, world, rank, P, torch, dist)
         if world > 1:
             dist.barrier()
             dist.destroy_process_group()

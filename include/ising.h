@@ -229,6 +229,25 @@ int ising_anneal_trace(ising_graph* g, const ising_schedule* sched, uint32_t swe
                        int mode, uint32_t every, int64_t* out_energy, void* cuda_stream);
 
 /*
+ * ising_convergence_region -- the paper's convergence study (Sec. V-C, Fig. 4:
+ * the range of cut values that runs from different random starts reach after
+ * each number of sweeps, and one run inside it). For seed k = 0 .. num_seeds-1
+ * the call sets random spins from seeds[k] (as ising_init_random with
+ * sched->replica), anneals with seed seeds[k] in chunks of `every` sweeps as
+ * ising_anneal_trace does, and after chunk i stores the exact cut
+ * (W - H) / 2 (Eq. 4) in out_cut[k * P + i], P = ceil(sweeps / every).
+ * out_min[i] / out_max[i] receive the smallest / largest cut over the seeds
+ * after chunk i; row 0 of out_cut is the one-run curve. All outputs are host
+ * int64 arrays. The handle's spins end as seed num_seeds - 1 left them.
+ * Synchronises the stream. Errors as ising_anneal_trace, plus ISING_EINVAL for
+ * a null seeds / out_cut / out_min / out_max or num_seeds == 0.
+ */
+int ising_convergence_region(ising_graph* g, const ising_schedule* sched, uint32_t sweeps,
+                             const uint64_t* seeds, uint32_t num_seeds, int mode, uint32_t every,
+                             int64_t* out_cut, int64_t* out_min, int64_t* out_max,
+                             void* cuda_stream);
+
+/*
  * ising_energy -- H(s) = sum over merged undirected edges of w_ij s_i s_j
  * (Eq. 3/5 with J = -w), computed from scratch in int64. Synchronises the stream.
  */

@@ -56,6 +56,7 @@ EXPORTS = (
     "ising_gnn_get_params", "ising_gnn_forward", "ising_gnn_gradients", "ising_gnn_train_step",
     "ising_gnn_warm_start", "ising_gnn_launch_count", "ising_gnn_destroy", "ising_debug_fault",
     "ising_engine_used", "ising_set_halo_sweeps", "ising_halo_info", "ising_plan_halo",
+    "ising_convergence_region",
 )
 ISING_ENGINE_USED_BLOCK = 6
 ISING_FAULT_NONE = 0
@@ -111,6 +112,9 @@ def lib():
         L.ising_energy_csr_static.argtypes = [ctypes.c_int32, vp, vp, vp, vp, vp, vp]
         L.ising_anneal_trace.argtypes = [vp, ctypes.POINTER(ising_schedule), ctypes.c_uint32,
                                          ctypes.c_uint64, ctypes.c_int, ctypes.c_uint32, vp, vp]
+        L.ising_convergence_region.argtypes = [vp, ctypes.POINTER(ising_schedule), ctypes.c_uint32,
+                                               vp, ctypes.c_uint32, ctypes.c_int, ctypes.c_uint32,
+                                               vp, vp, vp, vp]
         L.ising_batch_create.argtypes = [ctypes.c_int32, vp, vp, vp, vp, vp, ctypes.c_uint32, vp,
                                          ctypes.POINTER(vp)]
         L.ising_batch_init_random.argtypes = [vp, ctypes.c_uint64]
@@ -254,19 +258,25 @@ def ising_anneal_trace(g: IsingGraph, *, t_total: int, seed: int, every: int, p0
     return out
 
 
-def convergence_region(g: IsingGraph, *, seeds, p0: float, t_total: int, every: int,
-                       init_seed_offset: int = 1000, mode: int = ISING_MODE_DET, stream=None):
-    """Cut value versus sweep for several seeds (the paper's Fig. 4 view):
-    returns (sweep index after each chunk, cuts[seed, checkpoint])."""
-    W = ising_total_weight(g)
-    rows = []
-    for sd in seeds:
-        ising_init_random(g, sd + init_seed_offset)
-        H = ising_anneal_trace(g, p0=p0, t_total=t_total, seed=sd, every=every, mode=mode,
-                               stream=stream)
-        rows.append((W - H) // 2)
-    idx = np.minimum(np.arange(1, len(rows[0]) + 1) * every, t_total)
-    return idx, np.array(rows)
+def ising_convergence_region(g: IsingGraph, *, seeds, p0: float, t_total: int, every: int,
+                             sweeps: int | None = None, t_begin: int = 0, replica: int = 0,
+                             mode: int = ISING_MODE_DET, stream=None):
+    """The Fig. 4 view, computed by the library (include/ising.h): returns
+    (sweep reached after each chunk, cuts[seed, chunk], min over seeds, max
+    over seeds). Row 0 of cuts is the one-run curve."""
+    if sweeps is None:
+        sweeps = t_total - t_begin
+    sd = np.ascontiguousarray([int(x) & (2 ** 64 - 1) for x in seeds], dtype=np.uint64)
+    points = -(-sweeps // every) if every > 0 else 0
+    cuts = np.zeros((sd.size, points), dtype=np.int64)
+    lo = np.zeros(points, dtype=np.int64)
+    hi = np.zeros(points, dtype=np.int64)
+    sched = ising_schedule(ISING_SCHED_LINEAR, replica, p0, t_begin, t_total, 0, 0)
+    _check(lib().ising_convergence_region(g.ptr, ctypes.byref(sched), sweeps, sd.ctypes.data, sd.size,
+                                          mode, every, cuts.ctypes.data, lo.ctypes.data, hi.ctypes.data,
+                                          _stream(stream)), "ising_convergence_region")
+    idx = t_begin + np.minimum(np.arange(1, points + 1) * every, sweeps)
+    return idx, cuts, lo, hi
 
 
 def ising_energy(g: IsingGraph) -> int:

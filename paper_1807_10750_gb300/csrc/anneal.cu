@@ -441,7 +441,8 @@ void free_device(ising_graph* g) {
                   g->d_block_chunk_len, g->d_block_class_chunk, g->d_dep_ptr, g->d_deps,
                   g->d_done, g->d_halo_hdr, g->d_halo_words, g->d_halo_slices, g->d_halo_gpos,
                   g->d_halo_imports, g->d_halo_nbrs, g->d_halo_exports, g->d_halo_quads, g->d_halo_flags,
-                  g->d_spins2, g->d_hub_end, g->d_hub_sums, g->d_hub_acc, g->d_hub_flips};
+                  g->d_spins2, g->d_hub_split, g->d_hub_end, g->d_hub_sums, g->d_hub_acc,
+                  g->d_hub_flips};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -829,7 +830,7 @@ cudaError_t launch_hub_t(ising_graph* g, uint64_t t_begin, uint32_t sweeps, uint
   if (grid < 2) return cudaErrorCooperativeLaunchTooLarge;
   if ((e = barrier_init(g)) != cudaSuccess) return e;
   // the sums start at zero (a launch that gave up may have left partial sums)
-  if ((e = cudaMemsetAsync(g->d_hub_acc, 0, 2 * sizeof(int32_t) * static_cast<size_t>(g->num_hubs),
+  if ((e = cudaMemsetAsync(g->d_hub_acc, 0, 3 * sizeof(int32_t) * static_cast<size_t>(g->num_hubs),
                            g->stream)) != cudaSuccess)
     return e;
   DevGraph d = g->dev();
@@ -839,6 +840,7 @@ cudaError_t launch_hub_t(ising_graph* g, uint64_t t_begin, uint32_t sweeps, uint
   h.classes = g->num_colours;
   h.class_begin = g->d_class_begin;
   h.class_items = g->d_class_items;
+  h.hub_split = g->d_hub_split;
   h.hub_end = g->d_hub_end;
   h.sums = g->d_hub_sums;
   h.num_b_items = g->hub_num_b;
@@ -859,19 +861,27 @@ cudaError_t launch_hub(ising_graph* g, uint64_t t_begin, uint32_t sweeps, uint64
   return launch_hub_t<false>(g, t_begin, sweeps, T, T0, replica, rk);
 }
 
-// Host plan of the hub engine: per hub the end of its hub entries (rows are
-// sorted by neighbour position and the hubs hold the first positions), and
-// the field-sum items over the hubs' rows, kHubSumChunk entries each: first
-// the hub entries (B, summed once per launch), then the other entries (A,
-// summed every sweep).
-void build_hub_plan(const HostGraph& hg, std::vector<int32_t>* hub_end, std::vector<int4>* items,
-                    int32_t* num_b) {
+// Host plan of the hub engine. Rows are sorted by neighbour position and the
+// hubs hold the first positions, class by class, so a hub's row lists its
+// neighbours in earlier hub classes, then those in later hub classes, then
+// the non-hubs: per hub the start of the later-class entries (hub_split) and
+// of the non-hub entries (hub_end). Then the field-sum items over the hubs'
+// rows, kHubSumChunk entries each: first the hub entries (B, summed once per
+// launch), then the other entries (A, summed every sweep).
+void build_hub_plan(const HostGraph& hg, std::vector<int32_t>* hub_split, std::vector<int32_t>* hub_end,
+                    std::vector<int4>* items, int32_t* num_b) {
   const int32_t X = hg.num_hubs;
+  hub_split->assign(static_cast<size_t>(X), 0);
   hub_end->assign(static_cast<size_t>(X), 0);
+  int32_t c = 0;
   for (int32_t u = 0; u < X; ++u) {
+    while (hg.class_begin[static_cast<size_t>(c) + 1] <= u) ++c;
     const int32_t* b = hg.col.data() + hg.row_ptr[static_cast<size_t>(u)];
     const int32_t* e = hg.col.data() + hg.row_ptr[static_cast<size_t>(u) + 1];
-    (*hub_end)[static_cast<size_t>(u)] = static_cast<int32_t>(std::lower_bound(b, e, X) - hg.col.data());
+    const int32_t* he = std::lower_bound(b, e, X);
+    (*hub_end)[static_cast<size_t>(u)] = static_cast<int32_t>(he - hg.col.data());
+    (*hub_split)[static_cast<size_t>(u)] = static_cast<int32_t>(
+        std::lower_bound(b, he, hg.class_begin[static_cast<size_t>(c) + 1]) - hg.col.data());
   }
   items->clear();
   for (int kind = 1; kind >= 0; --kind) {
@@ -973,13 +983,13 @@ int ising_create(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, c
   g->num_items = static_cast<int32_t>(plan.items.size());
   g->num_slots = static_cast<int32_t>(plan.split_parts.size());
   // the hub engine's plan (before the columns are packed)
-  std::vector<int32_t> hub_end;
+  std::vector<int32_t> hub_split, hub_end;
   std::vector<int4> hub_items;
   g->num_hubs = hg.num_hubs;
   g->hub_colours = hg.hub_colours;
   if (hg.num_hubs >= 1 && hg.num_hubs <= isingx::kHubMaxHubs) {
     try {
-      build_hub_plan(hg, &hub_end, &hub_items, &g->hub_num_b);
+      build_hub_plan(hg, &hub_split, &hub_end, &hub_items, &g->hub_num_b);
     } catch (const std::bad_alloc&) {
       delete g;
       return ISING_ENOMEM;
@@ -1079,9 +1089,10 @@ int ising_create(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, c
     }
     if (!hub_end.empty()) {
       const size_t X = hub_end.size();
+      if ((e = alloc_copy(&g->d_hub_split, hub_split.data(), X, g->stream)) != cudaSuccess) break;
       if ((e = alloc_copy(&g->d_hub_end, hub_end.data(), X, g->stream)) != cudaSuccess) break;
       if ((e = alloc_copy(&g->d_hub_sums, hub_items.data(), hub_items.size(), g->stream)) != cudaSuccess) break;
-      if ((e = alloc_copy<int32_t>(&g->d_hub_acc, nullptr, 2 * X, g->stream)) != cudaSuccess) break;
+      if ((e = alloc_copy<int32_t>(&g->d_hub_acc, nullptr, 3 * X, g->stream)) != cudaSuccess) break;
       if ((e = alloc_copy<uint32_t>(&g->d_hub_flips, nullptr, (X + 31) / 32, g->stream)) != cudaSuccess) break;
       g->hub_ok = true;
     }
@@ -1144,6 +1155,9 @@ int ising_anneal(ising_graph* g, const ising_schedule* sched, uint32_t sweeps, u
   return anneal_impl(g, sched, sweeps, seed, mode);
 }
 
+static int anneal_trace_impl(ising_graph* g, const ising_schedule* sched, uint32_t sweeps,
+                             uint64_t seed, int mode, uint32_t every, int64_t* out_energy);
+
 int ising_anneal_trace(ising_graph* g, const ising_schedule* sched, uint32_t sweeps, uint64_t seed,
                        int mode, uint32_t every, int64_t* out_energy, void* cuda_stream) {
   int rc = enter(g);
@@ -1152,6 +1166,49 @@ int ising_anneal_trace(ising_graph* g, const ising_schedule* sched, uint32_t swe
   if (rc != ISING_OK) return rc;
   if (every == 0 || out_energy == nullptr) return ISING_EINVAL;
   g->stream = static_cast<cudaStream_t>(cuda_stream);
+  return anneal_trace_impl(g, sched, sweeps, seed, mode, every, out_energy);
+}
+
+static int init_random_impl(ising_graph* g, uint64_t seed, uint32_t replica);
+
+int ising_convergence_region(ising_graph* g, const ising_schedule* sched, uint32_t sweeps,
+                             const uint64_t* seeds, uint32_t num_seeds, int mode, uint32_t every,
+                             int64_t* out_cut, int64_t* out_min, int64_t* out_max,
+                             void* cuda_stream) {
+  int rc = enter(g);
+  if (rc != ISING_OK) return rc;
+  rc = check_anneal_args(g, sched, sweeps, mode);
+  if (rc != ISING_OK) return rc;
+  if (every == 0 || seeds == nullptr || num_seeds == 0 || out_cut == nullptr || out_min == nullptr ||
+      out_max == nullptr)
+    return ISING_EINVAL;
+  g->stream = static_cast<cudaStream_t>(cuda_stream);
+  const size_t points = (static_cast<size_t>(sweeps) + every - 1) / every;
+  std::vector<int64_t> energy;
+  try {
+    energy.resize(points);
+  } catch (const std::bad_alloc&) {
+    return ISING_ENOMEM;
+  }
+  for (uint32_t k = 0; k < num_seeds; ++k) {
+    rc = init_random_impl(g, seeds[k], sched->replica);
+    if (rc != ISING_OK) return rc;
+    rc = anneal_trace_impl(g, sched, sweeps, seeds[k], mode, every, energy.data());
+    if (rc != ISING_OK) return rc;
+    for (size_t i = 0; i < points; ++i) {
+      // Eq. 4 under reading R1: cut = (W - H) / 2
+      const int64_t cut = (g->total_weight - energy[i]) / 2;
+      out_cut[static_cast<size_t>(k) * points + i] = cut;
+      out_min[i] = k == 0 ? cut : std::min(out_min[i], cut);
+      out_max[i] = k == 0 ? cut : std::max(out_max[i], cut);
+    }
+  }
+  return ISING_OK;
+}
+
+static int anneal_trace_impl(ising_graph* g, const ising_schedule* sched, uint32_t sweeps,
+                             uint64_t seed, int mode, uint32_t every, int64_t* out_energy) {
+  int rc;
   const size_t points = (static_cast<size_t>(sweeps) + every - 1) / every;
   if (points == 0) return ISING_OK;
   if (points > g->trace_cap) {
@@ -1369,6 +1426,10 @@ int ising_set_spins(ising_graph* g, const int8_t* in, int on_device) {
 int ising_init_random(ising_graph* g, uint64_t seed, uint32_t replica) {
   int rc = enter(g);
   if (rc != ISING_OK) return rc;
+  return init_random_impl(g, seed, replica);
+}
+
+static int init_random_impl(ising_graph* g, uint64_t seed, uint32_t replica) {
   const int grid = grid_for(g->n, 256, g->num_sms * 8);
   g->launches++;
   g->parity = 0;

@@ -101,9 +101,10 @@ struct ising_graph {
   bool hub_ok = false;
   int32_t num_hubs = 0, hub_colours = 0;
   int32_t hub_num_b = 0, hub_num_items = 0;
+  int32_t* d_hub_split = nullptr;    // per hub: first CSR entry in a later hub class
   int32_t* d_hub_end = nullptr;      // per hub: first CSR entry past its hub neighbours
   int4* d_hub_sums = nullptr;        // field-sum items
-  int32_t* d_hub_acc = nullptr;      // 2 * num_hubs sums
+  int32_t* d_hub_acc = nullptr;      // 3 * num_hubs sums (A by sweep parity, B)
   uint32_t* d_hub_flips = nullptr;   // flip bits of the chain's hubs
   uint8_t* d_bias = nullptr;         // per-position flip bias (null: none)
   int32_t* d_rowid = nullptr;        // row of every CSR entry (built on first use)

@@ -46,7 +46,10 @@ constexpr int kHubBlock = 512;
 constexpr int kHubWarps = kHubBlock / 32;
 constexpr int kHubMaxHubs = 10240;  // shared memory of the chain block (hub_smem_bytes)
 constexpr int kHubSumChunk = 512;   // CSR entries per field-sum item
-constexpr int kHubPiece = 256;      // entries of a changed hub's row pushed by one warp task
+constexpr int kHubSlot = 512;       // row entries per push task (16 per lane)
+constexpr int kHubListCap = 768;    // push tasks one block-wide decision step can list
+constexpr int kHubDeferCap = 2048;  // changed hubs whose earlier-class pushes wait
+constexpr int kHubSmallClass = 32;  // classes up to this size are decided by warp 0 alone
 
 struct HubArgs {
   int32_t hubs;         // X: hubs hold positions [0, X)
@@ -54,50 +57,56 @@ struct HubArgs {
   int32_t classes;      // C
   const int32_t* class_begin;  // C + 1 first positions
   const int32_t* class_items;  // C + 1 first work items
+  const int32_t* hub_split;    // per hub: first CSR entry of its row in a later hub class
   const int32_t* hub_end;      // per hub: first CSR entry of its row past the hubs
   const int4* sums;            // field-sum items (hub, first entry, end entry, 0 = A / 1 = B)
   int32_t num_b_items;         // items [0, num_b_items) sum B, the rest A
   int32_t num_items;
-  int32_t* acc;                // [0, X): A sums, [X, 2X): B sums; zero between uses
+  int32_t* acc;                // [0, X) and [X, 2X): A by sweep parity, [2X, 3X): B; zero
+                               // between uses
   uint32_t* flips;             // ceil(X / 32) words: flip bits of the coming chain
 };
 
-// Shared memory of the chain block: A[X], B[X] (int32), the state bytes S[X]
-// (padded to 4), the flip bits F[W], the class table cls[m + 1], the list of
-// one step's changed hubs (kHubBlock int4) and two step counters.
+// Shared memory of the chain block, in this order: the push tasks of one
+// block-wide step (kHubListCap int4: hub | sign << 31, first entry, end
+// entry, unused), the deferred hubs (kHubDeferCap int: hub | sign << 31),
+// the fields F[X] = A + B (int32), the flip bits fl[W], the class table
+// cls[m + 1], four counters and the state bytes S[X].
 __host__ __device__ inline int hub_smem_bytes(int X, int m) {
   const int W = (X + 31) / 32;
-  return 8 * X + ((X + 3) / 4) * 4 + 4 * W + 4 * (m + 1) + 16 * kHubBlock + 8 + 16;
+  return 16 * kHubListCap + 4 * kHubDeferCap + 4 * X + 4 * W + 4 * (m + 1) + 16 +
+         ((X + 3) / 4) * 4 + 16;
 }
 
 struct HubSmem {
-  int32_t* A;
-  int32_t* B;
-  uint8_t* S;
-  uint32_t* F;
-  int32_t* cls;
   int4* list;
-  int* cnt;
+  int32_t* defer;
+  int32_t* F;
+  uint32_t* fl;
+  int32_t* cls;
+  int* cnt;  // [0], [1]: push tasks of a block-wide step, by step parity; [2]: deferred hubs
+  uint8_t* S;
 };
 
 __device__ __forceinline__ HubSmem hub_smem(unsigned char* base, int X, int m) {
   HubSmem s;
   const int W = (X + 31) / 32;
-  int4* list = reinterpret_cast<int4*>(base);  // 16-byte aligned first
-  s.list = list;
-  s.A = reinterpret_cast<int32_t*>(list + kHubBlock);
-  s.B = s.A + X;
-  s.F = reinterpret_cast<uint32_t*>(s.B + X);
-  s.cls = reinterpret_cast<int32_t*>(s.F + W);
+  s.list = reinterpret_cast<int4*>(base);  // 16-byte aligned first
+  s.defer = reinterpret_cast<int32_t*>(s.list + kHubListCap);
+  s.F = s.defer + kHubDeferCap;
+  s.fl = reinterpret_cast<uint32_t*>(s.F + X);
+  s.cls = reinterpret_cast<int32_t*>(s.fl + W);
   s.cnt = s.cls + (m + 1);
-  s.S = reinterpret_cast<uint8_t*>(s.cnt + 2);
+  s.S = reinterpret_cast<uint8_t*>(s.cnt + 4);
   return s;
 }
 
 // Field-sum item i: sum of w * s over CSR entries [e0, e1) of hub u, added
-// into acc[kind * X + u]. Eight loads in flight per lane.
+// into the A array of sweep parity `par` (kind 0) or into B (kind 1). Eight
+// loads in flight per lane.
 template <bool PACKED>
-__device__ __forceinline__ void hub_sum_item(const DevGraph& d, const HubArgs& h, int i, int lane) {
+__device__ __forceinline__ void hub_sum_item(const DevGraph& d, const HubArgs& h, int i, int par,
+                                             int lane) {
   const int4 it = __ldg(h.sums + i);
   int f = 0;
   for (int e = it.y + lane; e < it.z; e += 32 * 8) {
@@ -112,7 +121,7 @@ __device__ __forceinline__ void hub_sum_item(const DevGraph& d, const HubArgs& h
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(kFullMask, f, o);
-  if (lane == 0 && f != 0) atomicAdd(h.acc + it.w * h.hubs + it.x, f);
+  if (lane == 0 && f != 0) atomicAdd(h.acc + (it.w == 1 ? 2 : par) * h.hubs + it.x, f);
 }
 
 // Flip bits of hubs 32 j .. 32 j + 31 in sweep a.t (Algorithm 2; the flip
@@ -127,93 +136,242 @@ __device__ __forceinline__ void hub_flip_word(const DevGraph& d, const HubArgs& 
   if (lane == 0) h.flips[j] = bits;
 }
 
-// Push hub u's change (new spin ns) into B of its hub neighbours: entries
-// [e0, e1) of its row. Piece p of list entry k (kHubPiece entries) belongs to
-// warp (k + p) mod kHubWarps, so a few changed hubs with long rows still
-// spread over every warp.
+// Push entries [e0, e1) of a changed hub's row (at most kHubSlot of them,
+// 16 per lane, all loaded before any is applied): each entry (v, w) adds
+// 2 w ns to F_v, ns the hub's new spin.
 template <bool PACKED>
-__device__ __forceinline__ void hub_push(const DevGraph& d, const HubSmem& s, int K, int warp,
-                                         int lane) {
-  for (int k = 0; k < K; ++k) {
-    const int4 e = s.list[k];  // (u, new spin, first entry, end entry)
-    const int pieces = (e.w - e.z + kHubPiece - 1) / kHubPiece;
-    int p = (warp - k) % kHubWarps;
-    if (p < 0) p += kHubWarps;
-    for (; p < pieces; p += kHubWarps) {
-      const int e0 = e.z + p * kHubPiece;
-      const int e1 = min(e.w, e0 + kHubPiece);
-      Edge<PACKED> x[kHubPiece / 32];
+__device__ __forceinline__ void hub_push_range(const DevGraph& d, const HubSmem& s, int e0, int e1,
+                                               int ns, int lane) {
+  constexpr int U = kHubSlot / 32;
+  Edge<PACKED> x[U];
 #pragma unroll
-      for (int i = 0; i < kHubPiece / 32; ++i) x[i].load(d, e0 + lane + 32 * i, e0 + lane + 32 * i < e1);
+  for (int i = 0; i < U; ++i) x[i].load(d, e0 + lane + 32 * i, e0 + lane + 32 * i < e1);
 #pragma unroll
-      for (int i = 0; i < kHubPiece / 32; ++i)
-        if (e0 + lane + 32 * i < e1) atomicAdd(s.B + x[i].col(), 2 * e.y * x[i].weight());
+  for (int i = 0; i < U; ++i)
+    if (e0 + lane + 32 * i < e1) atomicAdd(s.F + x[i].col(), 2 * ns * x[i].weight());
+}
+
+// A whole row range pushed by one warp, kHubSlot entries per round.
+template <bool PACKED>
+__device__ __forceinline__ void hub_push_rows(const DevGraph& d, const HubSmem& s, int e0, int e1,
+                                              int ns, int lane) {
+  for (int e = e0; e < e1; e += kHubSlot) hub_push_range<PACKED>(d, s, e, min(e1, e + kHubSlot), ns, lane);
+}
+
+// Bring hub row entries [e0, e1) into L2 (one prefetch per 128-byte line),
+// so that the chain's pushes from them do not wait on HBM.
+template <bool PACKED>
+__device__ __forceinline__ void hub_prefetch(const DevGraph& d, int e0, int e1, int lane) {
+  const int per_line = 32;  // int32 entries per 128-byte line
+  for (int e = (e0 & ~(per_line - 1)) + lane * per_line; e < e1; e += 32 * per_line) {
+    if (PACKED) {
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(d.adj + e));
+    } else {
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(d.col + e));
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(d.w + e));
     }
+  }
+}
+
+// The decision of hub v (Eq. 2 under the max-cut sign, then Algorithm 2's
+// flip): returns the new spin and writes the new state byte to shared and
+// global memory (its update parity flips).
+__device__ __forceinline__ int hub_decide(const DevGraph& d, const HubSmem& s, int v, int* old_spin) {
+  const int b = s.S[v];
+  const int sv = spin_of(b);
+  const int f = s.F[v];
+  int ns = sv;
+  if (f > 0)
+    ns = -1;
+  else if (f < 0)
+    ns = 1;
+  if ((s.fl[v >> 5] >> (v & 31)) & 1u) ns = -ns;
+  const int nb = state_byte(ns, ((b >> 1) & 1) ^ 1);
+  s.S[v] = static_cast<uint8_t>(nb);
+  d.spins[v] = static_cast<int8_t>(nb);
+  *old_spin = sv;
+  return ns;
+}
+
+// A changed hub whose row reaches earlier hub classes: queue it (its pushes
+// there are needed only in the next sweep); push at once if the queue is full.
+template <bool PACKED>
+__device__ __forceinline__ void hub_defer(const DevGraph& d, const HubSmem& s, bool want, int v,
+                                          int ns, int r0, int sp, int lane) {
+  const unsigned ball = __ballot_sync(kFullMask, want);
+  if (ball == 0u) return;
+  int at = 0;
+  if (lane == 0) at = atomicAdd(s.cnt + 2, __popc(ball));
+  at = __shfl_sync(kFullMask, at, 0) + __popc(ball & ((1u << lane) - 1u));
+  const bool full = want && at >= kHubDeferCap;
+  if (want && !full) s.defer[at] = v | (ns < 0 ? static_cast<int>(0x80000000u) : 0);
+  unsigned over = __ballot_sync(kFullMask, full);
+  while (over != 0u) {
+    const int src = __ffs(over) - 1;
+    over &= over - 1;
+    hub_push_rows<PACKED>(d, s, __shfl_sync(kFullMask, r0, src), __shfl_sync(kFullMask, sp, src),
+                          __shfl_sync(kFullMask, ns, src), lane);
+  }
+}
+
+// The pushes of the queued hubs into earlier hub classes, by the whole chain
+// block while the other blocks run the non-hub classes: warp w takes queued
+// hubs w, w + kHubWarps, ...
+template <bool PACKED>
+__device__ __forceinline__ void hub_deferred(const DevGraph& d, const HubArgs& h, const HubSmem& s,
+                                             int warp, int lane) {
+  const int nq = min(s.cnt[2], kHubDeferCap);
+  for (int q = warp; q < nq; q += kHubWarps) {
+    const int x = s.defer[q];
+    const int u = x & 0x7fffffff;
+    hub_push_rows<PACKED>(d, s, __ldg(d.row_ptr + u), __ldg(h.hub_split + u), x < 0 ? -1 : 1, lane);
   }
 }
 
 // The m hub classes of one sweep, run by the chain block. `first`: the
-// launch's first sweep (B and the state bytes are loaded from global memory).
-// `step` counts decision steps across the launch (it selects the counter of
-// the step's changed list).
+// launch's first sweep (B and the state bytes come from global memory).
+// `step` counts block-wide decision steps (it selects the step's counter).
+//
+// Classes of at most kHubSmallClass hubs are decided by warp 0 alone, which
+// also pushes their changes, with warp barriers only; larger classes use the
+// whole block: decide, list the push tasks, block barrier, push, block
+// barrier. Only the pushes into later hub classes are made here; the rest
+// wait in the deferred queue (hub_deferred).
 template <bool PACKED>
 __device__ __forceinline__ void hub_chain(const DevGraph& d, const HubArgs& h, const HubSmem& s,
-                                          bool first, int& step) {
+                                          uint32_t k, int& step) {
   const int X = h.hubs, m = h.hub_classes;
   const int W = (X + 31) / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int par = static_cast<int>(k & 1u);
+  // F = A + B: the new A replaces the previous sweep's (both are in global
+  // memory); the previous one is cleared for the next sweep's sums
+  int32_t* a_new = h.acc + par * X;
+  int32_t* a_old = h.acc + (par ^ 1) * X;
   for (int v = threadIdx.x; v < X; v += kHubBlock) {
-    s.A[v] = h.acc[v];
-    h.acc[v] = 0;
-    if (first) {
-      s.B[v] = h.acc[X + v];
-      h.acc[X + v] = 0;
+    if (k == 0) {
+      s.F[v] = a_new[v] + h.acc[2 * X + v];
+      h.acc[2 * X + v] = 0;
       s.S[v] = static_cast<uint8_t>(d.spins[v]);
+    } else {
+      s.F[v] += a_new[v] - a_old[v];
+      a_old[v] = 0;
     }
   }
-  for (int j = threadIdx.x; j < W; j += kHubBlock) s.F[j] = h.flips[j];
-  if (first)
+  for (int j = threadIdx.x; j < W; j += kHubBlock) s.fl[j] = h.flips[j];
+  if (k == 0)
     for (int c = threadIdx.x; c <= m; c += kHubBlock) s.cls[c] = __ldg(h.class_begin + c);
+  if (threadIdx.x == 0) s.cnt[2] = 0;
   __syncthreads();
-  for (int c = 0; c < m; ++c) {
-    const int cb = s.cls[c], ce = s.cls[c + 1];
-    for (int base = cb; base < ce; base += kHubBlock) {
-      const int v = base + static_cast<int>(threadIdx.x);
-      bool changed = false;
-      int ns = 0, e0 = 0, e1 = 0;
-      if (v < ce) {
-        e0 = __ldg(d.row_ptr + v);
-        e1 = __ldg(h.hub_end + v);
-        const int b = s.S[v];
-        const int sv = spin_of(b);
-        const int f = s.A[v] + s.B[v];
-        ns = sv;
-        if (f > 0)
-          ns = -1;
-        else if (f < 0)
-          ns = 1;
-        if ((s.F[v >> 5] >> (v & 31)) & 1u) ns = -ns;
-        const int nb = state_byte(ns, ((b >> 1) & 1) ^ 1);
-        s.S[v] = static_cast<uint8_t>(nb);
-        d.spins[v] = static_cast<int8_t>(nb);
-        changed = ns != sv && e1 > e0;
-      }
-      const unsigned ball = __ballot_sync(kFullMask, changed);
-      int at = 0;
-      if (lane == 0 && ball != 0u) at = atomicAdd(s.cnt + (step & 1), __popc(ball));
-      at = __shfl_sync(kFullMask, at, 0);
-      if (changed) s.list[at + __popc(ball & ((1u << lane) - 1u))] = make_int4(v, ns, e0, e1);
-      if (threadIdx.x == 0) s.cnt[(step + 1) & 1] = 0;
-      __syncthreads();
-      const int K = s.cnt[step & 1];
-      ++step;
-      if (K == 0) continue;
-      hub_push<PACKED>(d, s, K, warp, lane);
-      __syncthreads();
-    }
+  // Steps: class c, hubs [base, base + kHubBlock). Each thread loads its hub's
+  // row bounds one step ahead, so no global load waits before a decision.
+  int c = 0, base = s.cls[0];
+  int r0n = 0, spn = 0, hen = 0;
+  if (m > 0 && base + static_cast<int>(threadIdx.x) < s.cls[1]) {
+    r0n = __ldg(d.row_ptr + base + threadIdx.x);
+    spn = __ldg(h.hub_split + base + threadIdx.x);
+    hen = __ldg(h.hub_end + base + threadIdx.x);
   }
+  bool small_run = false;  // warp 0 has decided small classes since the last block barrier
+  while (c < m) {
+    const int cb = s.cls[c];
+    const int ce = s.cls[c + 1];
+    const int v = base + static_cast<int>(threadIdx.x);
+    const int r0 = r0n, sp = spn, he = hen;
+    const bool small = ce - cb <= kHubSmallClass;
+    int nc = c, nbase = base + kHubBlock;
+    if (nbase >= ce) {
+      nc = c + 1;
+      nbase = ce;  // class c + 1 starts where class c ends
+    }
+    if (nc < m && nbase + static_cast<int>(threadIdx.x) < s.cls[nc + 1]) {
+      r0n = __ldg(d.row_ptr + nbase + threadIdx.x);
+      spn = __ldg(h.hub_split + nbase + threadIdx.x);
+      hen = __ldg(h.hub_end + nbase + threadIdx.x);
+    }
+    c = nc;
+    base = nbase;
+    if (small) {
+      if (warp == 0) {
+        int ns = 0, sv = 0;
+        if (v < ce) ns = hub_decide(d, s, v, &sv);
+        const bool changed = v < ce && ns != sv;
+        // pushes into later classes now, one changed hub at a time
+        unsigned ch = __ballot_sync(kFullMask, changed && he > sp);
+        while (ch != 0u) {
+          const int src = __ffs(ch) - 1;
+          ch &= ch - 1;
+          hub_push_rows<PACKED>(d, s, __shfl_sync(kFullMask, sp, src), __shfl_sync(kFullMask, he, src),
+                                __shfl_sync(kFullMask, ns, src), lane);
+        }
+        hub_defer<PACKED>(d, s, changed && sp > r0, v, ns, r0, sp, lane);
+        __syncwarp();
+      }
+      small_run = true;
+      continue;
+    }
+    if (small_run) {  // warp 0's small classes are complete and visible
+      __syncthreads();
+      small_run = false;
+    }
+    int ns = 0, sv = 0;
+    if (v < ce) ns = hub_decide(d, s, v, &sv);
+    const bool changed = v < ce && ns != sv;
+    hub_defer<PACKED>(d, s, changed && sp > r0, v, ns, r0, sp, lane);
+    // list the push tasks into later classes: one per kHubSlot entries; the
+    // warp reserves its tasks with one atomic (exclusive scan of the counts)
+    const int ntask = changed ? (he - sp + kHubSlot - 1) / kHubSlot : 0;
+    int incl = ntask;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(kFullMask, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int warp_tasks = __shfl_sync(kFullMask, incl, 31);
+    int at = 0;
+    if (lane == 0 && warp_tasks != 0) at = atomicAdd(s.cnt + (step & 1), warp_tasks);
+    at = __shfl_sync(kFullMask, at, 0) + incl - ntask;
+    // tasks past the list's capacity stay with the deciding lane
+    bool spill = false;
+    for (int j = 0; j < ntask; ++j) {
+      if (at + j < kHubListCap)
+        s.list[at + j] = make_int4(v | (ns < 0 ? static_cast<int>(0x80000000u) : 0),
+                                   sp + j * kHubSlot, min(he, sp + (j + 1) * kHubSlot), 0);
+      else
+        spill = true;
+    }
+    if (threadIdx.x == 0) s.cnt[(step + 1) & 1] = 0;
+    __syncthreads();
+    const int Q = s.cnt[step & 1];
+    ++step;
+    if (Q == 0) continue;
+    for (int q = warp; q < min(Q, kHubListCap); q += kHubWarps) {
+      const int4 e = s.list[q];
+      hub_push_range<PACKED>(d, s, e.y, e.z, e.x < 0 ? -1 : 1, lane);
+    }
+    // rare: tasks that did not fit, pushed by the warp that decided them
+    unsigned spw = __ballot_sync(kFullMask, spill);
+    while (spw != 0u) {
+      const int src = __ffs(spw) - 1;
+      spw &= spw - 1;
+      const int sat = __shfl_sync(kFullMask, at, src), sn = __shfl_sync(kFullMask, ntask, src);
+      const int s0 = __shfl_sync(kFullMask, sp, src), s1 = __shfl_sync(kFullMask, he, src);
+      const int sns = __shfl_sync(kFullMask, ns, src);
+      for (int j = 0; j < sn; ++j)
+        if (sat + j >= kHubListCap)
+          hub_push_range<PACKED>(d, s, s0 + j * kHubSlot, min(s1, s0 + (j + 1) * kHubSlot), sns, lane);
+    }
+    __syncthreads();
+  }
+  if (small_run) __syncthreads();
 }
 
+// One launch: sweeps t_begin .. t_begin + sweeps - 1.
+//
+// Grid barrier bookkeeping: per sweep the counter grows by G (the chain
+// barrier: G - 1 workers, then the chain block) and by G - 1 for each of the
+// P non-hub classes (workers only: the chain block does not take part and
+// meanwhile pushes its deferred hubs).
 template <bool PACKED>
 __global__ void __launch_bounds__(kHubBlock, 2)
     hub_kernel(DevGraph d, HubArgs h, uint64_t t_begin, uint32_t sweeps, uint64_t T, uint64_t T0,
@@ -224,45 +382,55 @@ __global__ void __launch_bounds__(kHubBlock, 2)
   const int warp = (static_cast<int>(blockIdx.x) - 1) * kHubWarps + static_cast<int>(threadIdx.x >> 5);
   const int nwarps = (static_cast<int>(gridDim.x) - 1) * kHubWarps;
   const int W = (h.hubs + 31) / 32;
+  const unsigned G = gridDim.x;
+  const int P = h.classes - h.hub_classes;
   HubSmem s = hub_smem(hub_shared, h.hubs, h.hub_classes);
-  if (chain && threadIdx.x < 2) s.cnt[threadIdx.x] = 0;
+  if (chain && threadIdx.x < 4) s.cnt[threadIdx.x] = 0;
   bool skip = bs->skip_block == static_cast<int>(blockIdx.x) + 1;
   unsigned target = 0;
   int step = 0;
   long long unused = 0;
   for (uint32_t k = 0; k < sweeps; ++k) {
     const SweepArgs a = sweep_args(t_begin + k, T, T0, replica);
-    target += gridDim.x;
+    target += G;
     if (!chain) {
-      // 1. the hubs' field sums and flip bits of sweep t
+      // 1. the hubs' field sums and flip bits of sweep t; the hub rows the
+      // chain pushes from into L2; then wait, polling sparsely, while the
+      // chain block runs the hub classes
       for (int i = (k == 0 ? 0 : h.num_b_items) + warp; i < h.num_items; i += nwarps)
-        hub_sum_item<PACKED>(d, h, i, lane);
+        hub_sum_item<PACKED>(d, h, i, static_cast<int>(k & 1u), lane);
       for (int j = warp; j < W; j += nwarps) hub_flip_word(d, h, j, a, rk, lane);
+      if (k > 0)
+        for (int i = warp; i < h.num_b_items; i += nwarps) {
+          const int4 it = __ldg(h.sums + i);
+          hub_prefetch<PACKED>(d, it.y, it.z, lane);
+        }
       barrier_arrive(bs, skip);
       skip = false;
-    } else {
-      // 2. the hub classes, once every worker has arrived
-      if (!barrier_wait(bs, target - 1)) return;
-      hub_chain<PACKED>(d, h, s, k == 0, step);
-      barrier_arrive(bs, skip);
-      skip = false;
-    }
-    if (!barrier_wait(bs, target)) return;
-    // 3. the other classes
-    for (int c = h.hub_classes; c < h.classes; ++c) {
-      if (!chain) {
+      if (!barrier_wait_sleep(bs, target, 256)) return;
+      // 3. the other classes, a workers-only grid barrier after each
+      for (int c = h.hub_classes; c < h.classes; ++c) {
         const int ie = __ldg(h.class_items + c + 1);
         for (int i = __ldg(h.class_items + c) + warp; i < ie; i += nwarps) {
           Staged<PACKED> st;
           stage_item<PACKED>(d, d.items[i], a, rk, lane, st);
           finish_item<PACKED, kPassDet>(d, st, a, rk, lane, unused);
         }
+        if (c + 1 == h.classes && k + 1 == sweeps) break;
+        barrier_arrive(bs, false);
+        target += G - 1;
+        if (!barrier_wait(bs, target)) return;
       }
-      if (c + 1 == h.classes && k + 1 == sweeps) break;
+    } else {
+      // 2. the hub classes, once every worker has arrived; then the deferred
+      // pushes while the workers run the other classes
+      if (!barrier_wait(bs, target - 1)) return;
+      hub_chain<PACKED>(d, h, s, k, step);
       barrier_arrive(bs, skip);
       skip = false;
-      target += gridDim.x;
-      if (!barrier_wait(bs, target)) return;
+      hub_deferred<PACKED>(d, h, s, threadIdx.x >> 5, lane);
+      __syncthreads();
+      target += static_cast<unsigned>(P) * (G - 1);
     }
   }
 }

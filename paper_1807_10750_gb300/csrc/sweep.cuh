@@ -340,12 +340,13 @@ __device__ __forceinline__ void finish_light_shape(const DevGraph& d, const Stag
 
 // Rows too heavy for a light item but not sliced, 32 at a time: their CSR
 // entries are contiguous, so the warp streams them lane-strided (lane l takes
-// entries e0 + l + 32 k, four in flight), finds each entry's row among the
-// block's 33 row offsets (one binary search per batch, then forward steps),
-// and adds each run of a row's terms into the row's shared accumulator; lane
-// l then updates row l. Every kernel that finishes items runs at most
-// kGroupWarps warps per block.
+// entries e0 + l + 32 k, kGroupLoads in flight), finds each entry's row among
+// the block's 33 row offsets (one binary search per batch, then forward
+// steps), and adds each run of a row's terms into the row's shared
+// accumulator; lane l then updates row l. Every kernel that finishes items
+// runs at most kGroupWarps warps per block.
 constexpr int kGroupWarps = 16;
+constexpr int kGroupLoads = 4;
 
 template <bool PACKED, int PASS>
 __device__ __forceinline__ void finish_group_rows(const DevGraph& d, const WorkItem& it,
@@ -361,13 +362,13 @@ __device__ __forceinline__ void finish_group_rows(const DevGraph& d, const WorkI
     acc[lane] = 0;
     __syncwarp();
     const int e0 = rp[0], e1 = rp[rows];
-    for (int eb = e0; eb < e1; eb += 128) {
-      Edge<PACKED> x[4];
-      int b[4];
+    for (int eb = e0; eb < e1; eb += 32 * kGroupLoads) {
+      Edge<PACKED> x[kGroupLoads];
+      int b[kGroupLoads];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) x[u].load(d, eb + lane + 32 * u, eb + lane + 32 * u < e1);
+      for (int u = 0; u < kGroupLoads; ++u) x[u].load(d, eb + lane + 32 * u, eb + lane + 32 * u < e1);
 #pragma unroll
-      for (int u = 0; u < 4; ++u) b[u] = load_state<PASS>(d, x[u].col());
+      for (int u = 0; u < kGroupLoads; ++u) b[u] = load_state<PASS>(d, x[u].col());
       int e = eb + lane;
       if (e < e1) {
         // the row holding entry e: the largest r with rp[r] <= e
@@ -382,7 +383,7 @@ __device__ __forceinline__ void finish_group_rows(const DevGraph& d, const WorkI
         int r = lo;
         int run = 0;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < kGroupLoads; ++u) {
           e = eb + lane + 32 * u;
           if (e < e1) {
             while (rp[r + 1] <= e) {
@@ -579,6 +580,35 @@ __device__ __forceinline__ bool barrier_wait(BarrierState* bs, unsigned target) 
   }
   __syncthreads();
   return ok_shared != 0;
+}
+
+// barrier_wait for a wait known to be long (the hub engine's workers while
+// one block runs the hub classes): thread 0 sleeps sleep_ns between polls, so
+// hundreds of waiting blocks do not keep the counter's L2 line busy. Bounded
+// like barrier_wait.
+__device__ __forceinline__ bool barrier_wait_sleep(BarrierState* bs, unsigned target,
+                                                   unsigned sleep_ns) {
+  __shared__ int ok_sleep;
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const long long budget = bs->budget_ns > 0 ? bs->budget_ns : kBarrierBudgetNs;
+    const long long t0 = global_ns();
+    while (static_cast<int>(ld_acquire_u32(&bs->count) - target) < 0) {
+      if (ld_relaxed_s32(&bs->error) != 0) {
+        ok = 0;
+        break;
+      }
+      if (global_ns() - t0 > budget) {
+        atomicExch(&bs->error, 1);
+        ok = 0;
+        break;
+      }
+      __nanosleep(sleep_ns);
+    }
+    ok_sleep = ok;
+  }
+  __syncthreads();
+  return ok_sleep != 0;
 }
 
 }  // namespace isingx

@@ -254,13 +254,24 @@ def test_energy_trace_matches_oracle_checkpoints(P, engine):
         assert trace[i] == oracle.energy_cut(g.n, g.src, g.dst, g.w, s)[0], i
 
 
-def test_convergence_region_shape(P):
+def test_convergence_region_matches_oracle(P):
+    # Fig. 4's region: per seed, random start and anneal with that seed; the
+    # library's cut after every chunk, and its min / max over the seeds, equal
+    # the oracle's.
     g = synth.torus_graph(32, 5, weights="pm1")
+    T, every, seeds = 100, 10, [3, 9, 27, 81]
     with P.ising_create(g.n, g.src, g.dst, g.w) as h:
-        idx, cuts = P.convergence_region(h, seeds=range(4), p0=0.1, t_total=100, every=10)
-        W = P.ising_total_weight(h)
+        idx, cuts, lo, hi = P.ising_convergence_region(h, seeds=seeds, p0=0.1, t_total=T, every=every)
     assert idx.tolist() == list(range(10, 101, 10))
-    assert cuts.shape == (4, 10) and np.all(np.abs(cuts) <= g.m)
+    want = np.zeros((len(seeds), T // every), np.int64)
+    for k, sd in enumerate(seeds):
+        s = oracle.init_spins(g.n, sd)
+        for i in range(T // every):
+            s = oracle.anneal(g.n, g.src, g.dst, g.w, s, seed=sd, p0=0.1, T=T, t_begin=i * every,
+                              sweeps=every)
+            want[k, i] = oracle.energy_cut(g.n, g.src, g.dst, g.w, s)[2]
+    assert np.array_equal(cuts, want)
+    assert np.array_equal(lo, want.min(axis=0)) and np.array_equal(hi, want.max(axis=0))
     # annealing improves the cut from early to late checkpoints on average
     assert cuts[:, -1].mean() > cuts[:, 0].mean()
 
