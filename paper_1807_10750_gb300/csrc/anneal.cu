@@ -442,7 +442,7 @@ void free_device(ising_graph* g) {
                   g->d_done, g->d_halo_hdr, g->d_halo_words, g->d_halo_slices, g->d_halo_gpos,
                   g->d_halo_imports, g->d_halo_nbrs, g->d_halo_exports, g->d_halo_quads, g->d_halo_flags,
                   g->d_spins2, g->d_hub_split, g->d_hub_end, g->d_hub_sums, g->d_hub_acc,
-                  g->d_hub_flips};
+                  g->d_hub_flips, g->d_hub_bits};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -819,13 +819,21 @@ template <bool PACKED>
 cudaError_t launch_hub_t(ising_graph* g, uint64_t t_begin, uint32_t sweeps, uint64_t T, uint64_t T0,
                          uint32_t replica, const isingx::PhiloxRounds& rk_in) {
   auto kernel = isingx::hub_kernel<PACKED>;
-  const int smem = isingx::hub_smem_bytes(g->num_hubs, g->hub_colours);
-  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  const int bit_words = g->n / 32 + 2;
+  // the worker blocks keep a copy of the spin map when it fits beside the
+  // chain block's tables in one block's shared memory
+  int optin = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, g->device);
+  if (e != cudaSuccess) return e;
+  const bool stage = isingx::hub_smem_bytes(g->num_hubs, g->hub_colours, bit_words, true) <= optin;
+  const int smem = isingx::hub_smem_bytes(g->num_hubs, g->hub_colours, bit_words, stage);
+  if (smem > optin) return cudaErrorCooperativeLaunchTooLarge;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, isingx::kHubBlock, smem);
   if (e != cudaSuccess) return e;
-  per_sm = std::min(per_sm, 2);
+  per_sm = std::min(per_sm, 1);
   const int grid = per_sm * g->num_sms;
   if (grid < 2) return cudaErrorCooperativeLaunchTooLarge;
   if ((e = barrier_init(g)) != cudaSuccess) return e;
@@ -847,6 +855,10 @@ cudaError_t launch_hub_t(ising_graph* g, uint64_t t_begin, uint32_t sweeps, uint
   h.num_items = g->hub_num_items;
   h.acc = g->d_hub_acc;
   h.flips = g->d_hub_flips;
+  h.bits = g->d_hub_bits;
+  h.bit_words = bit_words;
+  h.stage_bits = stage ? 1 : 0;
+  h.par_end = g->parity;  // anneal_impl has already advanced it by this call's sweeps
   isingx::PhiloxRounds rk = rk_in;
   BarrierState* bs = g->d_barrier;
   void* args[] = {&d, &h, &t_begin, &sweeps, &T, &T0, &replica, &rk, &bs};
@@ -1094,6 +1106,7 @@ int ising_create(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, c
       if ((e = alloc_copy(&g->d_hub_sums, hub_items.data(), hub_items.size(), g->stream)) != cudaSuccess) break;
       if ((e = alloc_copy<int32_t>(&g->d_hub_acc, nullptr, 3 * X, g->stream)) != cudaSuccess) break;
       if ((e = alloc_copy<uint32_t>(&g->d_hub_flips, nullptr, (X + 31) / 32, g->stream)) != cudaSuccess) break;
+      if ((e = alloc_copy<uint32_t>(&g->d_hub_bits, nullptr, N / 32 + 2, g->stream)) != cudaSuccess) break;
       g->hub_ok = true;
     }
     if ((e = alloc_copy<unsigned>(&g->d_nflip_bits, nullptr, (N + 31) / 32, g->stream)) != cudaSuccess) break;

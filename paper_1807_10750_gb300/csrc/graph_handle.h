@@ -106,6 +106,7 @@ struct ising_graph {
   int4* d_hub_sums = nullptr;        // field-sum items
   int32_t* d_hub_acc = nullptr;      // 3 * num_hubs sums (A by sweep parity, B)
   uint32_t* d_hub_flips = nullptr;   // flip bits of the chain's hubs
+  uint32_t* d_hub_bits = nullptr;    // the spin map of a launch (n / 32 + 2 words)
   uint8_t* d_bias = nullptr;         // per-position flip bias (null: none)
   int32_t* d_rowid = nullptr;        // row of every CSR entry (built on first use)
   isingx::BarrierState* d_barrier = nullptr;

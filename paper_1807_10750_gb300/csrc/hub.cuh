@@ -17,20 +17,32 @@
 // are updated (their classes come later), so A_v is summed once per sweep by
 // the workers. B_v is kept current incrementally: when hub u changes from -s
 // to s, every hub neighbour v gets B_v += 2 w_uv s, one shared-memory atomic
-// per entry of u's hub row, before the next class is decided. Only the rows
-// of hubs that change are read, a few hundred per sweep.
+// per entry of u's hub row. Only the entries into later hub classes are
+// pushed before the next class is decided; those into earlier classes are
+// needed only in the next sweep and are pushed while the workers run the
+// other classes.
+//
+// Spins during a launch live in a bit map (bit p set for spin -1), with one
+// copy in global memory and, when it fits, one in every worker block's shared
+// memory. The vertices of a class hold a contiguous range of positions, so
+// after each grid barrier a worker block refreshes only the words of the
+// class just updated, and every neighbour read of a sweep is a shared-memory
+// read instead of a random L2 access. New spins go to the global map: the
+// warp that decides 32 consecutive positions xors their changed bits in with
+// at most two atomics. The state bytes are rebuilt from the map once, at the
+// end of the launch (every vertex's update parity has flipped once per sweep).
 //
 // One sweep t:
-//   1. workers: A_v for every hub from the current non-hub spins (and, in the
+//   1. workers: A_v for every hub from the non-hub spins (and, in the
 //      launch's first sweep, B_v from the hub spins), added into a global
 //      array with atomics; the chain's flip bits of sweep t (Algorithm 2's
 //      draws, optional flip bias); then they arrive at the grid barrier;
 //   2. chain block: waits for every worker's arrival, loads A (and B), runs
-//      the m hub classes (decide from A_v + B_v, flip, write the state byte,
-//      push the changed hubs' rows into B), arrives at the barrier;
-//   3. workers: the non-hub classes m .. C-1 with the sweep kernels' work
-//      items (sweep.cuh), reading the hubs' new spins; a grid barrier after
-//      each class (the chain block only arrives and waits).
+//      the m hub classes, arrives at the barrier, then pushes the deferred
+//      entries;
+//   3. workers: refresh the hub words of their map copy, then the non-hub
+//      classes m .. C-1 from the sweep's work items, a workers-only grid
+//      barrier and a refresh of the class's words after each.
 // Every wait is bounded (sweep.cuh, barrier_wait).
 #pragma once
 
@@ -42,7 +54,7 @@
 
 namespace isingx {
 
-constexpr int kHubBlock = 512;
+constexpr int kHubBlock = 1024;
 constexpr int kHubWarps = kHubBlock / 32;
 constexpr int kHubMaxHubs = 10240;  // shared memory of the chain block (hub_smem_bytes)
 constexpr int kHubSumChunk = 512;   // CSR entries per field-sum item
@@ -50,6 +62,8 @@ constexpr int kHubSlot = 512;       // row entries per push task (16 per lane)
 constexpr int kHubListCap = 768;    // push tasks one block-wide decision step can list
 constexpr int kHubDeferCap = 2048;  // changed hubs whose earlier-class pushes wait
 constexpr int kHubSmallClass = 32;  // classes up to this size are decided by warp 0 alone
+constexpr int kHubGroupLoads = 8;   // CSR words in flight per lane in a group-row batch
+constexpr int kHubGroupScratch = 65;  // per warp: 33 row offsets and 32 fields
 
 struct HubArgs {
   int32_t hubs;         // X: hubs hold positions [0, X)
@@ -65,17 +79,30 @@ struct HubArgs {
   int32_t* acc;                // [0, X) and [X, 2X): A by sweep parity, [2X, 3X): B; zero
                                // between uses
   uint32_t* flips;             // ceil(X / 32) words: flip bits of the coming chain
+  uint32_t* bits;              // the spin map: bit p of word p / 32 set for spin -1 (the pad
+                               // position n reads 0); bit_words words, zero at launch
+  int32_t bit_words;
+  int32_t stage_bits;          // 1: worker blocks keep a copy of the map in shared memory
+  int32_t par_end;             // update parity of every state byte after the launch
 };
 
-// Shared memory of the chain block, in this order: the push tasks of one
-// block-wide step (kHubListCap int4: hub | sign << 31, first entry, end
-// entry, unused), the deferred hubs (kHubDeferCap int: hub | sign << 31),
-// the fields F[X] = A + B (int32), the flip bits fl[W], the class table
-// cls[m + 1], four counters and the state bytes S[X].
-__host__ __device__ inline int hub_smem_bytes(int X, int m) {
+// Shared memory. The chain block: the push tasks of one block-wide step
+// (kHubListCap int4: hub | sign << 31, first entry, end entry, unused), the
+// deferred hubs (kHubDeferCap int: hub | sign << 31), the fields F[X] = A + B
+// (int32), the flip bits fl[W], the class table cls[m + 1], four counters and
+// the state bytes S[X]. A worker block: the group-row scratch (kHubWarps x
+// kHubGroupScratch int) and, with stage_bits, the copy of the spin map.
+__host__ __device__ inline int hub_chain_smem(int X, int m) {
   const int W = (X + 31) / 32;
   return 16 * kHubListCap + 4 * kHubDeferCap + 4 * X + 4 * W + 4 * (m + 1) + 16 +
          ((X + 3) / 4) * 4 + 16;
+}
+__host__ __device__ inline int hub_worker_smem(int bit_words, bool stage) {
+  return 4 * kHubWarps * kHubGroupScratch + (stage ? 4 * bit_words : 0) + 16;
+}
+__host__ __device__ inline int hub_smem_bytes(int X, int m, int bit_words, bool stage) {
+  const int c = hub_chain_smem(X, m), w = hub_worker_smem(bit_words, stage);
+  return c > w ? c : w;
 }
 
 struct HubSmem {
@@ -101,23 +128,46 @@ __device__ __forceinline__ HubSmem hub_smem(unsigned char* base, int X, int m) {
   return s;
 }
 
+// Spin-map reads: the bit of position p (1 for spin -1) and the spin.
+__device__ __forceinline__ int map_bit(const uint32_t* sb, int p) { return (sb[p >> 5] >> (p & 31)) & 1; }
+__device__ __forceinline__ int map_spin(const uint32_t* sb, int p) { return 1 - 2 * map_bit(sb, p); }
+
+// Lane l of the warp owns position p0 + l: xor the bits of the lanes whose
+// spin changed into the global map (at most two words, one atomic each).
+__device__ __forceinline__ void map_publish(uint32_t* g, int p0, bool changed, int lane) {
+  const unsigned m = __ballot_sync(kFullMask, changed);
+  if (lane == 0 && m != 0u) {
+    const int w = p0 >> 5, sh = p0 & 31;
+    atomicXor(g + w, m << sh);
+    if (sh != 0 && (m >> (32 - sh)) != 0u) atomicXor(g + w + 1, m >> (32 - sh));
+  }
+}
+
+// Eq. 2 under the max-cut sign (f > 0 gives -1, f < 0 gives +1, f = 0 keeps
+// the spin), then Algorithm 2's flip, on map bits (1 = spin -1).
+__device__ __forceinline__ int decide_bit(int f, int old, bool flip) {
+  int b = old;
+  if (f > 0)
+    b = 1;
+  else if (f < 0)
+    b = 0;
+  return flip ? b ^ 1 : b;
+}
+
 // Field-sum item i: sum of w * s over CSR entries [e0, e1) of hub u, added
 // into the A array of sweep parity `par` (kind 0) or into B (kind 1). Eight
 // loads in flight per lane.
 template <bool PACKED>
-__device__ __forceinline__ void hub_sum_item(const DevGraph& d, const HubArgs& h, int i, int par,
-                                             int lane) {
+__device__ __forceinline__ void hub_sum_item(const DevGraph& d, const HubArgs& h,
+                                             const uint32_t* sb, int i, int par, int lane) {
   const int4 it = __ldg(h.sums + i);
   int f = 0;
   for (int e = it.y + lane; e < it.z; e += 32 * 8) {
     Edge<PACKED> x[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) x[u].load(d, e + 32 * u, e + 32 * u < it.z);
-    int b[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) b[u] = d.spins[x[u].col()];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) f += x[u].weight() * spin_of(b[u]);
+    for (int u = 0; u < 8; ++u) f += x[u].weight() * map_spin(sb, x[u].col());
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(kFullMask, f, o);
@@ -174,9 +224,9 @@ __device__ __forceinline__ void hub_prefetch(const DevGraph& d, int e0, int e1, 
 }
 
 // The decision of hub v (Eq. 2 under the max-cut sign, then Algorithm 2's
-// flip): returns the new spin and writes the new state byte to shared and
-// global memory (its update parity flips).
-__device__ __forceinline__ int hub_decide(const DevGraph& d, const HubSmem& s, int v, int* old_spin) {
+// flip): returns the new spin and keeps the new state byte in shared memory
+// (its update parity flips); the caller publishes the spin to the map.
+__device__ __forceinline__ int hub_decide(const HubSmem& s, int v, int* old_spin) {
   const int b = s.S[v];
   const int sv = spin_of(b);
   const int f = s.F[v];
@@ -188,7 +238,6 @@ __device__ __forceinline__ int hub_decide(const DevGraph& d, const HubSmem& s, i
   if ((s.fl[v >> 5] >> (v & 31)) & 1u) ns = -ns;
   const int nb = state_byte(ns, ((b >> 1) & 1) ^ 1);
   s.S[v] = static_cast<uint8_t>(nb);
-  d.spins[v] = static_cast<int8_t>(nb);
   *old_spin = sv;
   return ns;
 }
@@ -294,8 +343,9 @@ __device__ __forceinline__ void hub_chain(const DevGraph& d, const HubArgs& h, c
     if (small) {
       if (warp == 0) {
         int ns = 0, sv = 0;
-        if (v < ce) ns = hub_decide(d, s, v, &sv);
+        if (v < ce) ns = hub_decide(s, v, &sv);
         const bool changed = v < ce && ns != sv;
+        map_publish(h.bits, cb, changed, lane);
         // pushes into later classes now, one changed hub at a time
         unsigned ch = __ballot_sync(kFullMask, changed && he > sp);
         while (ch != 0u) {
@@ -314,31 +364,34 @@ __device__ __forceinline__ void hub_chain(const DevGraph& d, const HubArgs& h, c
       __syncthreads();
       small_run = false;
     }
-    int ns = 0, sv = 0;
-    if (v < ce) ns = hub_decide(d, s, v, &sv);
-    const bool changed = v < ce && ns != sv;
-    hub_defer<PACKED>(d, s, changed && sp > r0, v, ns, r0, sp, lane);
-    // list the push tasks into later classes: one per kHubSlot entries; the
-    // warp reserves its tasks with one atomic (exclusive scan of the counts)
-    const int ntask = changed ? (he - sp + kHubSlot - 1) / kHubSlot : 0;
-    int incl = ntask;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(kFullMask, incl, o);
-      if (lane >= o) incl += y;
-    }
-    const int warp_tasks = __shfl_sync(kFullMask, incl, 31);
-    int at = 0;
-    if (lane == 0 && warp_tasks != 0) at = atomicAdd(s.cnt + (step & 1), warp_tasks);
-    at = __shfl_sync(kFullMask, at, 0) + incl - ntask;
-    // tasks past the list's capacity stay with the deciding lane
+    int ns = 0, at = 0, ntask = 0;
     bool spill = false;
-    for (int j = 0; j < ntask; ++j) {
-      if (at + j < kHubListCap)
-        s.list[at + j] = make_int4(v | (ns < 0 ? static_cast<int>(0x80000000u) : 0),
-                                   sp + j * kHubSlot, min(he, sp + (j + 1) * kHubSlot), 0);
-      else
-        spill = true;
+    if (v - lane < ce) {  // warps past the class's end skip the decision step
+      int sv = 0;
+      if (v < ce) ns = hub_decide(s, v, &sv);
+      const bool changed = v < ce && ns != sv;
+      map_publish(h.bits, v - lane, changed, lane);  // the warp's 32 consecutive positions
+      hub_defer<PACKED>(d, s, changed && sp > r0, v, ns, r0, sp, lane);
+      // list the push tasks into later classes: one per kHubSlot entries; the
+      // warp reserves its tasks with one atomic (exclusive scan of the counts)
+      ntask = changed ? (he - sp + kHubSlot - 1) / kHubSlot : 0;
+      int incl = ntask;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFullMask, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const int warp_tasks = __shfl_sync(kFullMask, incl, 31);
+      if (lane == 0 && warp_tasks != 0) at = atomicAdd(s.cnt + (step & 1), warp_tasks);
+      at = __shfl_sync(kFullMask, at, 0) + incl - ntask;
+      // tasks past the list's capacity stay with the deciding lane
+      for (int j = 0; j < ntask; ++j) {
+        if (at + j < kHubListCap)
+          s.list[at + j] = make_int4(v | (ns < 0 ? static_cast<int>(0x80000000u) : 0),
+                                     sp + j * kHubSlot, min(he, sp + (j + 1) * kHubSlot), 0);
+        else
+          spill = true;
+      }
     }
     if (threadIdx.x == 0) s.cnt[(step + 1) & 1] = 0;
     __syncthreads();
@@ -366,14 +419,179 @@ __device__ __forceinline__ void hub_chain(const DevGraph& d, const HubArgs& h, c
   if (small_run) __syncthreads();
 }
 
+// ---------------------------------------------------------------------------
+// Worker items (the non-hub classes), on the spin map `sb` (the block's copy
+// or the global map). New spins go to the global map.
+// ---------------------------------------------------------------------------
+
+// Light rows (sliced ELL, staged by stage_item: words and flip draws).
+template <bool PACKED, int R>
+__device__ __forceinline__ void hub_light(const HubArgs& h, const uint32_t* sb,
+                                          const Staged<PACKED>& st, int lane) {
+  constexpr int DM = light_slots(PACKED) / R;
+  const int nv = st.it.v_end - st.it.v_begin;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    int f = 0;
+#pragma unroll
+    for (int k = 0; k < DM; ++k) f += st.x[r * DM + k].weight() * map_spin(sb, st.x[r * DM + k].col());
+    const int row = lane + 32 * r;
+    const int p = st.it.v_begin + row;
+    bool changed = false;
+    if (row < nv) {
+      const int old = map_bit(sb, p);
+      changed = decide_bit(f, old, (st.flips >> r) & 1u) != old;
+    }
+    map_publish(h.bits, st.it.v_begin + 32 * r, changed, lane);
+  }
+}
+
+// Rows between the light and the sliced sizes, 32 at a time: their CSR
+// entries are contiguous, streamed lane-strided kHubGroupLoads per lane at a
+// time; each lane finds its entries' rows among the 33 row offsets and adds
+// runs of one row's terms into that row's shared accumulator; lane l then
+// decides row l.
+template <bool PACKED>
+__device__ __forceinline__ void hub_group(const DevGraph& d, const HubArgs& h, const uint32_t* sb,
+                                          int* scratch, const WorkItem& it, const SweepArgs& a,
+                                          const PhiloxRounds& rk, int lane) {
+  int* rp = scratch;
+  int* acc = scratch + 33;
+  for (int base = it.v_begin; base < it.v_end; base += 32) {
+    const int rows = min(32, it.v_end - base);
+    const bool own = lane < rows;
+    if (own) rp[lane] = __ldg(d.row_ptr + base + lane);
+    if (lane == 0) rp[rows] = __ldg(d.row_ptr + base + rows);
+    const bool flip = own && flip_drawn(d, base + lane, static_cast<uint32_t>(__ldg(d.orig + base + lane)), a, rk);
+    acc[lane] = 0;
+    __syncwarp();
+    const int e0 = rp[0], e1 = rp[rows];
+    for (int eb = e0; eb < e1; eb += 32 * kHubGroupLoads) {
+      Edge<PACKED> x[kHubGroupLoads];
+#pragma unroll
+      for (int u = 0; u < kHubGroupLoads; ++u) x[u].load(d, eb + lane + 32 * u, eb + lane + 32 * u < e1);
+      int e = eb + lane;
+      if (e < e1) {
+        // the row holding entry e: the largest r with rp[r] <= e
+        int lo = 0, hi = rows - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (rp[mid] <= e)
+            lo = mid;
+          else
+            hi = mid - 1;
+        }
+        int r = lo, run = 0;
+#pragma unroll
+        for (int u = 0; u < kHubGroupLoads; ++u) {
+          e = eb + lane + 32 * u;
+          if (e < e1) {
+            while (rp[r + 1] <= e) {
+              if (run != 0) atomicAdd(acc + r, run);
+              run = 0;
+              ++r;
+            }
+            run += x[u].weight() * map_spin(sb, x[u].col());
+          }
+        }
+        if (run != 0) atomicAdd(acc + r, run);
+      }
+    }
+    __syncwarp();
+    bool changed = false;
+    if (own) {
+      const int old = map_bit(sb, base + lane);
+      changed = decide_bit(acc[lane], old, flip) != old;
+    }
+    map_publish(h.bits, base, changed, lane);
+    __syncwarp();
+  }
+}
+
+// A slice of a heavy row: its partial field joins the row's 64-bit
+// accumulator (count and biased sum, as in sweep.cuh); the slice that
+// completes the row decides it.
+template <bool PACKED>
+__device__ __forceinline__ void hub_slice(const DevGraph& d, const HubArgs& h, const uint32_t* sb,
+                                          const WorkItem& it, const SweepArgs& a,
+                                          const PhiloxRounds& rk, int lane) {
+  int f = 0;
+  for (int e = it.e_begin + lane; e < it.e_end; e += 32 * kHubGroupLoads) {
+    Edge<PACKED> x[kHubGroupLoads];
+#pragma unroll
+    for (int u = 0; u < kHubGroupLoads; ++u) x[u].load(d, e + 32 * u, e + 32 * u < it.e_end);
+#pragma unroll
+    for (int u = 0; u < kHubGroupLoads; ++u) f += x[u].weight() * map_spin(sb, x[u].col());
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(kFullMask, f, o);
+  if (lane == 0) {
+    const int v = it.v_begin;
+    const int slot = 2 * (-it.v_end - 1);
+    const int parts = __ldg(d.slice_parts + (-it.v_end - 1));
+    const unsigned long long mine =
+        kSliceUnit + static_cast<unsigned long long>(static_cast<long long>(f) + kSliceBias);
+    const unsigned long long old = atomicAdd(d.slice_acc + slot, mine);
+    if (static_cast<int>(old >> 48) == parts - 1) {
+      const long long low = static_cast<long long>((old & kSliceLowMask) + (mine & kSliceLowMask));
+      const int total = static_cast<int>(low - static_cast<long long>(parts) * kSliceBias);
+      d.slice_acc[slot] = 0ull;
+      const int ob = map_bit(sb, v);
+      if (decide_bit(total, ob, flip_drawn(d, v, static_cast<uint32_t>(__ldg(d.orig + v)), a, rk)) != ob)
+        atomicXor(h.bits + (v >> 5), 1u << (v & 31));
+    }
+  }
+}
+
+template <bool PACKED>
+__device__ __forceinline__ void hub_item(const DevGraph& d, const HubArgs& h, const uint32_t* sb,
+                                         int* scratch, const WorkItem& it, const SweepArgs& a,
+                                         const PhiloxRounds& rk, int lane) {
+  const int kind = item_kind(it);
+  if (kind == kStageGroup) {
+    hub_group<PACKED>(d, h, sb, scratch, it, a, rk, lane);
+    return;
+  }
+  if (kind == kStageSlice) {
+    hub_slice<PACKED>(d, h, sb, it, a, rk, lane);
+    return;
+  }
+  Staged<PACKED> st;
+  stage_item<PACKED>(d, it, a, rk, lane, st);
+  const int R = light_rows_per_lane(-it.e_end - 1, PACKED);
+  if (R == 4)
+    hub_light<PACKED, 4>(h, sb, st, lane);
+  else if (R == 2)
+    hub_light<PACKED, 2>(h, sb, st, lane);
+  else
+    hub_light<PACKED, 1>(h, sb, st, lane);
+}
+
+// Copy map words [w0, w1) from global memory into the block's copy: every
+// thread issues up to 16 loads before it stores any, so a class of up to
+// 16 x 32 x 1024 vertices costs one L2 round trip.
+__device__ __forceinline__ void map_refresh(uint32_t* sb, const uint32_t* g, int w0, int w1) {
+  constexpr int U = 16;
+  for (int wb = w0 + static_cast<int>(threadIdx.x); wb < w1; wb += U * kHubBlock) {
+    uint32_t x[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) x[u] = wb + u * kHubBlock < w1 ? __ldcg(g + wb + u * kHubBlock) : 0u;
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (wb + u * kHubBlock < w1) sb[wb + u * kHubBlock] = x[u];
+  }
+  __syncthreads();
+}
+
 // One launch: sweeps t_begin .. t_begin + sweeps - 1.
 //
-// Grid barrier bookkeeping: per sweep the counter grows by G (the chain
-// barrier: G - 1 workers, then the chain block) and by G - 1 for each of the
-// P non-hub classes (workers only: the chain block does not take part and
-// meanwhile pushes its deferred hubs).
+// Grid barrier bookkeeping (the counter only grows): the prologue barrier
+// counts the G - 1 workers; per sweep the chain barrier counts G (G - 1
+// workers, then the chain block) and each of the P non-hub classes G - 1
+// (workers only: the chain block meanwhile pushes its deferred hubs); the
+// epilogue barrier counts the workers again.
 template <bool PACKED>
-__global__ void __launch_bounds__(kHubBlock, 2)
+__global__ void __launch_bounds__(kHubBlock, 1)
     hub_kernel(DevGraph d, HubArgs h, uint64_t t_begin, uint32_t sweeps, uint64_t T, uint64_t T0,
                uint32_t replica, PhiloxRounds rk, BarrierState* bs) {
   extern __shared__ __align__(16) unsigned char hub_shared[];
@@ -385,11 +603,30 @@ __global__ void __launch_bounds__(kHubBlock, 2)
   const unsigned G = gridDim.x;
   const int P = h.classes - h.hub_classes;
   HubSmem s = hub_smem(hub_shared, h.hubs, h.hub_classes);
+  int* scratch = reinterpret_cast<int*>(hub_shared) + (threadIdx.x >> 5) * kHubGroupScratch;
+  uint32_t* sb_copy = reinterpret_cast<uint32_t*>(hub_shared) + kHubWarps * kHubGroupScratch;
+  const uint32_t* sb = h.stage_bits ? sb_copy : h.bits;
   if (chain && threadIdx.x < 4) s.cnt[threadIdx.x] = 0;
   bool skip = bs->skip_block == static_cast<int>(blockIdx.x) + 1;
   unsigned target = 0;
   int step = 0;
   long long unused = 0;
+  (void)unused;
+  // prologue: the workers build the global map from the state bytes, then
+  // (after a workers-only barrier) their copies
+  target += G - 1;
+  if (!chain) {
+    for (int j = warp; j < h.bit_words; j += nwarps) {
+      const int p = 32 * j + lane;
+      const bool neg = p < d.pad_col && (d.spins[p] & 1);
+      const unsigned m = __ballot_sync(kFullMask, neg);
+      if (lane == 0) h.bits[j] = m;
+    }
+    barrier_arrive(bs, skip);
+    skip = false;
+    if (!barrier_wait(bs, target)) return;
+    if (h.stage_bits) map_refresh(sb_copy, h.bits, 0, h.bit_words);
+  }
   for (uint32_t k = 0; k < sweeps; ++k) {
     const SweepArgs a = sweep_args(t_begin + k, T, T0, replica);
     target += G;
@@ -398,7 +635,7 @@ __global__ void __launch_bounds__(kHubBlock, 2)
       // chain pushes from into L2; then wait, polling sparsely, while the
       // chain block runs the hub classes
       for (int i = (k == 0 ? 0 : h.num_b_items) + warp; i < h.num_items; i += nwarps)
-        hub_sum_item<PACKED>(d, h, i, static_cast<int>(k & 1u), lane);
+        hub_sum_item<PACKED>(d, h, sb, i, static_cast<int>(k & 1u), lane);
       for (int j = warp; j < W; j += nwarps) hub_flip_word(d, h, j, a, rk, lane);
       if (k > 0)
         for (int i = warp; i < h.num_b_items; i += nwarps) {
@@ -408,18 +645,17 @@ __global__ void __launch_bounds__(kHubBlock, 2)
       barrier_arrive(bs, skip);
       skip = false;
       if (!barrier_wait_sleep(bs, target, 256)) return;
+      if (h.stage_bits) map_refresh(sb_copy, h.bits, 0, W);
       // 3. the other classes, a workers-only grid barrier after each
       for (int c = h.hub_classes; c < h.classes; ++c) {
         const int ie = __ldg(h.class_items + c + 1);
-        for (int i = __ldg(h.class_items + c) + warp; i < ie; i += nwarps) {
-          Staged<PACKED> st;
-          stage_item<PACKED>(d, d.items[i], a, rk, lane, st);
-          finish_item<PACKED, kPassDet>(d, st, a, rk, lane, unused);
-        }
-        if (c + 1 == h.classes && k + 1 == sweeps) break;
+        for (int i = __ldg(h.class_items + c) + warp; i < ie; i += nwarps)
+          hub_item<PACKED>(d, h, sb, scratch, d.items[i], a, rk, lane);
         barrier_arrive(bs, false);
         target += G - 1;
         if (!barrier_wait(bs, target)) return;
+        if (h.stage_bits)
+          map_refresh(sb_copy, h.bits, __ldg(h.class_begin + c) >> 5, (__ldg(h.class_begin + c + 1) + 31) >> 5);
       }
     } else {
       // 2. the hub classes, once every worker has arrived; then the deferred
@@ -433,6 +669,12 @@ __global__ void __launch_bounds__(kHubBlock, 2)
       target += static_cast<unsigned>(P) * (G - 1);
     }
   }
+  // epilogue: the state bytes from the map, every vertex's update parity
+  // flipped once per sweep (the last class's barrier above orders the map)
+  if (!chain)
+    for (int p = (static_cast<int>(blockIdx.x) - 1) * kHubBlock + static_cast<int>(threadIdx.x);
+         p < d.pad_col; p += (static_cast<int>(G) - 1) * kHubBlock)
+      d.spins[p] = static_cast<int8_t>(state_byte(1 - 2 * map_bit(h.bits, p), h.par_end));
 }
 
 }  // namespace isingx
