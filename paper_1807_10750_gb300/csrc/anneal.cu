@@ -442,7 +442,7 @@ void free_device(ising_graph* g) {
                   g->d_done, g->d_halo_hdr, g->d_halo_words, g->d_halo_slices, g->d_halo_gpos,
                   g->d_halo_imports, g->d_halo_nbrs, g->d_halo_exports, g->d_halo_quads, g->d_halo_flags,
                   g->d_spins2, g->d_hub_split, g->d_hub_end, g->d_hub_sums, g->d_hub_acc,
-                  g->d_hub_flips, g->d_hub_bits};
+                  g->d_hub_flips, g->d_hub_bits, g->d_hub_pflips, g->d_hub_blk};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -815,17 +815,17 @@ cudaError_t launch_halo(ising_graph* g, uint64_t t_begin, uint32_t sweeps, uint6
 // The hub engine (hub.cuh): one cooperative launch, block 0 runs the hub
 // classes. Returns cudaErrorCooperativeLaunchTooLarge when fewer than two
 // blocks fit on the device.
-template <bool PACKED>
+template <bool PACKED, bool STAGE>
 cudaError_t launch_hub_t(ising_graph* g, uint64_t t_begin, uint32_t sweeps, uint64_t T, uint64_t T0,
                          uint32_t replica, const isingx::PhiloxRounds& rk_in) {
-  auto kernel = isingx::hub_kernel<PACKED>;
+  auto kernel = isingx::hub_kernel<PACKED, STAGE>;
   const int bit_words = g->n / 32 + 2;
   // the worker blocks keep a copy of the spin map when it fits beside the
   // chain block's tables in one block's shared memory
   int optin = 0;
   cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, g->device);
   if (e != cudaSuccess) return e;
-  const bool stage = isingx::hub_smem_bytes(g->num_hubs, g->hub_colours, bit_words, true) <= optin;
+  const bool stage = STAGE;
   const int smem = isingx::hub_smem_bytes(g->num_hubs, g->hub_colours, bit_words, stage);
   if (smem > optin) return cudaErrorCooperativeLaunchTooLarge;
   e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -835,7 +835,8 @@ cudaError_t launch_hub_t(ising_graph* g, uint64_t t_begin, uint32_t sweeps, uint
   if (e != cudaSuccess) return e;
   per_sm = std::min(per_sm, 1);
   const int grid = per_sm * g->num_sms;
-  if (grid < 2) return cudaErrorCooperativeLaunchTooLarge;
+  // the work split of the non-hub classes was made for one block per SM
+  if (grid < 2 || grid != g->hub_grid) return cudaErrorCooperativeLaunchTooLarge;
   if ((e = barrier_init(g)) != cudaSuccess) return e;
   // the sums start at zero (a launch that gave up may have left partial sums)
   if ((e = cudaMemsetAsync(g->d_hub_acc, 0, 3 * sizeof(int32_t) * static_cast<size_t>(g->num_hubs),
@@ -859,6 +860,9 @@ cudaError_t launch_hub_t(ising_graph* g, uint64_t t_begin, uint32_t sweeps, uint
   h.bit_words = bit_words;
   h.stage_bits = stage ? 1 : 0;
   h.par_end = g->parity;  // anneal_impl has already advanced it by this call's sweeps
+  h.pflips = g->d_hub_pflips;
+  h.pos = g->d_pos;
+  h.blk = g->d_hub_blk;
   isingx::PhiloxRounds rk = rk_in;
   BarrierState* bs = g->d_barrier;
   void* args[] = {&d, &h, &t_begin, &sweeps, &T, &T0, &replica, &rk, &bs};
@@ -869,8 +873,56 @@ cudaError_t launch_hub_t(ising_graph* g, uint64_t t_begin, uint32_t sweeps, uint
 
 cudaError_t launch_hub(ising_graph* g, uint64_t t_begin, uint32_t sweeps, uint64_t T, uint64_t T0,
                        uint32_t replica, const isingx::PhiloxRounds& rk) {
-  if (g->packed) return launch_hub_t<true>(g, t_begin, sweeps, T, T0, replica, rk);
-  return launch_hub_t<false>(g, t_begin, sweeps, T, T0, replica, rk);
+  // the worker blocks keep a copy of the spin map when it fits beside the
+  // chain block's tables in one block's shared memory
+  int optin = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, g->device);
+  if (e != cudaSuccess) return e;
+  const bool stage = isingx::hub_smem_bytes(g->num_hubs, g->hub_colours, g->n / 32 + 2, true) <= optin;
+  if (g->packed)
+    return stage ? launch_hub_t<true, true>(g, t_begin, sweeps, T, T0, replica, rk)
+                 : launch_hub_t<true, false>(g, t_begin, sweeps, T, T0, replica, rk);
+  return stage ? launch_hub_t<false, true>(g, t_begin, sweeps, T, T0, replica, rk)
+               : launch_hub_t<false, false>(g, t_begin, sweeps, T, T0, replica, rk);
+}
+
+// The non-hub classes' work split for G blocks (block 0 runs the hub
+// classes): per class, G item offsets; worker block b takes items
+// [blk[b], blk[b + 1]) of the class, a contiguous range of about equal
+// estimated work (entries streamed, plus a per-item and per-row cost).
+void build_hub_blocks(const WorkPlan& plan, int32_t hub_colours, int32_t num_colours, int32_t G,
+                      std::vector<int32_t>* blk) {
+  const int32_t workers = G - 1;
+  blk->clear();
+  std::vector<int64_t> cost;
+  for (int32_t c = hub_colours; c < num_colours; ++c) {
+    const int32_t ib = plan.class_item_begin[static_cast<size_t>(c)];
+    const int32_t ie = plan.class_item_begin[static_cast<size_t>(c) + 1];
+    cost.assign(static_cast<size_t>(ie - ib) + 1, 0);
+    for (int32_t i = ib; i < ie; ++i) {
+      const WorkItem& it = plan.items[static_cast<size_t>(i)];
+      int64_t w;
+      if (it.v_end < 0)  // slice
+        w = 64 + (it.e_end - it.e_begin);
+      else if (it.e_end < 0)  // light rows: nv x D words
+        w = 32 + static_cast<int64_t>(it.v_end - it.v_begin) * (-it.e_end - 1);
+      else  // group rows
+        w = 64 + (it.e_end - it.e_begin) + 8 * static_cast<int64_t>(it.v_end - it.v_begin);
+      cost[static_cast<size_t>(i - ib) + 1] = cost[static_cast<size_t>(i - ib)] + w;
+    }
+    const int64_t total = cost.back();
+    for (int32_t b = 0; b < workers; ++b) {
+      const int64_t goal = total * b / workers;
+      blk->push_back(ib + static_cast<int32_t>(std::lower_bound(cost.begin(), cost.end(), goal) - cost.begin()));
+    }
+    blk->push_back(ie);
+    // lower_bound can land on an item boundary past the goal: make the
+    // offsets non-decreasing and within the class
+    for (size_t k = blk->size() - static_cast<size_t>(G); k < blk->size(); ++k) {
+      (*blk)[k] = std::min<int32_t>(std::max<int32_t>((*blk)[k], ib), ie);
+      if (k > blk->size() - static_cast<size_t>(G)) (*blk)[k] = std::max((*blk)[k], (*blk)[k - 1]);
+    }
+  }
 }
 
 // Host plan of the hub engine. Rows are sorted by neighbour position and the
@@ -995,7 +1047,7 @@ int ising_create(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, c
   g->num_items = static_cast<int32_t>(plan.items.size());
   g->num_slots = static_cast<int32_t>(plan.split_parts.size());
   // the hub engine's plan (before the columns are packed)
-  std::vector<int32_t> hub_split, hub_end;
+  std::vector<int32_t> hub_split, hub_end, hub_blk;
   std::vector<int4> hub_items;
   g->num_hubs = hg.num_hubs;
   g->hub_colours = hg.hub_colours;
@@ -1007,6 +1059,12 @@ int ising_create(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, c
       return ISING_ENOMEM;
     }
     g->hub_num_items = static_cast<int32_t>(hub_items.size());
+    try {
+      build_hub_blocks(plan, hg.hub_colours, hg.num_colours, g->num_sms, &hub_blk);
+    } catch (const std::bad_alloc&) {
+      delete g;
+      return ISING_ENOMEM;
+    }
   }
   isingx::BlockPlan block;
   std::vector<int32_t> dep_ptr, deps;  // item dependencies (before the columns are packed)
@@ -1107,6 +1165,9 @@ int ising_create(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, c
       if ((e = alloc_copy<int32_t>(&g->d_hub_acc, nullptr, 3 * X, g->stream)) != cudaSuccess) break;
       if ((e = alloc_copy<uint32_t>(&g->d_hub_flips, nullptr, (X + 31) / 32, g->stream)) != cudaSuccess) break;
       if ((e = alloc_copy<uint32_t>(&g->d_hub_bits, nullptr, N / 32 + 2, g->stream)) != cudaSuccess) break;
+      if ((e = alloc_copy<uint32_t>(&g->d_hub_pflips, nullptr, N / 32 + 2, g->stream)) != cudaSuccess) break;
+      if ((e = alloc_copy(&g->d_hub_blk, hub_blk.data(), hub_blk.size(), g->stream)) != cudaSuccess) break;
+      g->hub_grid = g->num_sms;
       g->hub_ok = true;
     }
     if ((e = alloc_copy<unsigned>(&g->d_nflip_bits, nullptr, (N + 31) / 32, g->stream)) != cudaSuccess) break;

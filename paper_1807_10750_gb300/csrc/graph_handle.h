@@ -107,6 +107,9 @@ struct ising_graph {
   int32_t* d_hub_acc = nullptr;      // 3 * num_hubs sums (A by sweep parity, B)
   uint32_t* d_hub_flips = nullptr;   // flip bits of the chain's hubs
   uint32_t* d_hub_bits = nullptr;    // the spin map of a launch (n / 32 + 2 words)
+  uint32_t* d_hub_pflips = nullptr;  // a sweep's flips by position (n / 32 + 2 words)
+  int32_t* d_hub_blk = nullptr;      // non-hub classes' work split over the worker blocks
+  int32_t hub_grid = 0;              // blocks the split was made for
   uint8_t* d_bias = nullptr;         // per-position flip bias (null: none)
   int32_t* d_rowid = nullptr;        // row of every CSR entry (built on first use)
   isingx::BarrierState* d_barrier = nullptr;

@@ -84,6 +84,9 @@ struct HubArgs {
   int32_t bit_words;
   int32_t stage_bits;          // 1: worker blocks keep a copy of the map in shared memory
   int32_t par_end;             // update parity of every state byte after the launch
+  uint32_t* pflips;            // the sweep's flips by position (bit_words words)
+  const int32_t* pos;          // original id -> position
+  const int32_t* blk;          // per non-hub class: G first items of the worker blocks + end
 };
 
 // Shared memory. The chain block: the push tasks of one block-wide step
@@ -98,7 +101,7 @@ __host__ __device__ inline int hub_chain_smem(int X, int m) {
          ((X + 3) / 4) * 4 + 16;
 }
 __host__ __device__ inline int hub_worker_smem(int bit_words, bool stage) {
-  return 4 * kHubWarps * kHubGroupScratch + (stage ? 4 * bit_words : 0) + 16;
+  return 4 * kHubWarps * kHubGroupScratch + 16 + (stage ? 4 * bit_words : 0) + 16;
 }
 __host__ __device__ inline int hub_smem_bytes(int X, int m, int bit_words, bool stage) {
   const int c = hub_chain_smem(X, m), w = hub_worker_smem(bit_words, stage);
@@ -199,6 +202,33 @@ __device__ __forceinline__ void hub_push_range(const DevGraph& d, const HubSmem&
 #pragma unroll
   for (int i = 0; i < U; ++i)
     if (e0 + lane + 32 * i < e1) atomicAdd(s.F + x[i].col(), 2 * ns * x[i].weight());
+}
+
+// Up to four row ranges [e0[j], e1[j]) with new spins ns[j] pushed by one
+// warp together: 128 entries of each per round (4 per lane), all 16 loads
+// issued before any is applied, so a few short rows cost one L2 round trip.
+template <bool PACKED>
+__device__ __forceinline__ void hub_push4(const DevGraph& d, const HubSmem& s, int (&e0)[4],
+                                          const int (&e1)[4], const int (&ns)[4], int lane) {
+  for (;;) {
+    Edge<PACKED> x[4][4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) x[j][u].load(d, e0[j] + lane + 32 * u, e0[j] + lane + 32 * u < e1[j]);
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (e0[j] + lane + 32 * u < e1[j]) atomicAdd(s.F + x[j][u].col(), 2 * ns[j] * x[j][u].weight());
+    bool more = false;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      e0[j] += 128;
+      more |= e0[j] < e1[j];
+    }
+    if (!more) return;
+  }
 }
 
 // A whole row range pushed by one warp, kHubSlot entries per round.
@@ -346,13 +376,20 @@ __device__ __forceinline__ void hub_chain(const DevGraph& d, const HubArgs& h, c
         if (v < ce) ns = hub_decide(s, v, &sv);
         const bool changed = v < ce && ns != sv;
         map_publish(h.bits, cb, changed, lane);
-        // pushes into later classes now, one changed hub at a time
+        // pushes into later classes now, four changed hubs at a time
         unsigned ch = __ballot_sync(kFullMask, changed && he > sp);
         while (ch != 0u) {
-          const int src = __ffs(ch) - 1;
-          ch &= ch - 1;
-          hub_push_rows<PACKED>(d, s, __shfl_sync(kFullMask, sp, src), __shfl_sync(kFullMask, he, src),
-                                __shfl_sync(kFullMask, ns, src), lane);
+          int a[4], b[4], sg[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int src = ch != 0u ? __ffs(ch) - 1 : 0;
+            const bool have = ch != 0u;
+            ch &= ch - 1;
+            a[j] = __shfl_sync(kFullMask, sp, src);
+            b[j] = have ? __shfl_sync(kFullMask, he, src) : a[j];
+            sg[j] = __shfl_sync(kFullMask, ns, src);
+          }
+          hub_push4<PACKED>(d, s, a, b, sg, lane);
         }
         hub_defer<PACKED>(d, s, changed && sp > r0, v, ns, r0, sp, lane);
         __syncwarp();
@@ -421,28 +458,44 @@ __device__ __forceinline__ void hub_chain(const DevGraph& d, const HubArgs& h, c
 
 // ---------------------------------------------------------------------------
 // Worker items (the non-hub classes), on the spin map `sb` (the block's copy
-// or the global map). New spins go to the global map.
+// or the global map). New spins go to the global map; the flip of position p
+// is bit p of the sweep's flip map.
 // ---------------------------------------------------------------------------
 
-// Light rows (sliced ELL, staged by stage_item: words and flip draws).
+__device__ __forceinline__ bool pos_flip(const HubArgs& h, const SweepArgs& a, int p) {
+  return a.thr != 0u && ((h.pflips[p >> 5] >> (p & 31)) & 1u);
+}
+
+// Light rows (sliced ELL): every word of the item loaded before any is used.
 template <bool PACKED, int R>
-__device__ __forceinline__ void hub_light(const HubArgs& h, const uint32_t* sb,
-                                          const Staged<PACKED>& st, int lane) {
+__device__ __forceinline__ void hub_light(const DevGraph& d, const HubArgs& h, const uint32_t* sb,
+                                          const WorkItem& it, const SweepArgs& a, int lane) {
   constexpr int DM = light_slots(PACKED) / R;
-  const int nv = st.it.v_end - st.it.v_begin;
+  const int nv = it.v_end - it.v_begin;
+  const int D = -it.e_end - 1;
+  Edge<PACKED> x[R * DM];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int row = lane + 32 * r;
+#pragma unroll
+    for (int k = 0; k < DM; ++k) x[r * DM + k].load_ell(d, it.e_begin + k * nv + row, row < nv && k < D);
+  }
+  bool flip[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) flip[r] = lane + 32 * r < nv && pos_flip(h, a, it.v_begin + lane + 32 * r);
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     int f = 0;
 #pragma unroll
-    for (int k = 0; k < DM; ++k) f += st.x[r * DM + k].weight() * map_spin(sb, st.x[r * DM + k].col());
+    for (int k = 0; k < DM; ++k) f += x[r * DM + k].weight() * map_spin(sb, x[r * DM + k].col());
     const int row = lane + 32 * r;
-    const int p = st.it.v_begin + row;
+    const int p = it.v_begin + row;
     bool changed = false;
     if (row < nv) {
       const int old = map_bit(sb, p);
-      changed = decide_bit(f, old, (st.flips >> r) & 1u) != old;
+      changed = decide_bit(f, old, flip[r]) != old;
     }
-    map_publish(h.bits, st.it.v_begin + 32 * r, changed, lane);
+    map_publish(h.bits, it.v_begin + 32 * r, changed, lane);
   }
 }
 
@@ -454,7 +507,7 @@ __device__ __forceinline__ void hub_light(const HubArgs& h, const uint32_t* sb,
 template <bool PACKED>
 __device__ __forceinline__ void hub_group(const DevGraph& d, const HubArgs& h, const uint32_t* sb,
                                           int* scratch, const WorkItem& it, const SweepArgs& a,
-                                          const PhiloxRounds& rk, int lane) {
+                                          int lane) {
   int* rp = scratch;
   int* acc = scratch + 33;
   for (int base = it.v_begin; base < it.v_end; base += 32) {
@@ -462,7 +515,7 @@ __device__ __forceinline__ void hub_group(const DevGraph& d, const HubArgs& h, c
     const bool own = lane < rows;
     if (own) rp[lane] = __ldg(d.row_ptr + base + lane);
     if (lane == 0) rp[rows] = __ldg(d.row_ptr + base + rows);
-    const bool flip = own && flip_drawn(d, base + lane, static_cast<uint32_t>(__ldg(d.orig + base + lane)), a, rk);
+    const bool flip = own && pos_flip(h, a, base + lane);
     acc[lane] = 0;
     __syncwarp();
     const int e0 = rp[0], e1 = rp[rows];
@@ -513,8 +566,7 @@ __device__ __forceinline__ void hub_group(const DevGraph& d, const HubArgs& h, c
 // completes the row decides it.
 template <bool PACKED>
 __device__ __forceinline__ void hub_slice(const DevGraph& d, const HubArgs& h, const uint32_t* sb,
-                                          const WorkItem& it, const SweepArgs& a,
-                                          const PhiloxRounds& rk, int lane) {
+                                          const WorkItem& it, const SweepArgs& a, int lane) {
   int f = 0;
   for (int e = it.e_begin + lane; e < it.e_end; e += 32 * kHubGroupLoads) {
     Edge<PACKED> x[kHubGroupLoads];
@@ -537,34 +589,54 @@ __device__ __forceinline__ void hub_slice(const DevGraph& d, const HubArgs& h, c
       const int total = static_cast<int>(low - static_cast<long long>(parts) * kSliceBias);
       d.slice_acc[slot] = 0ull;
       const int ob = map_bit(sb, v);
-      if (decide_bit(total, ob, flip_drawn(d, v, static_cast<uint32_t>(__ldg(d.orig + v)), a, rk)) != ob)
-        atomicXor(h.bits + (v >> 5), 1u << (v & 31));
+      if (decide_bit(total, ob, pos_flip(h, a, v)) != ob) atomicXor(h.bits + (v >> 5), 1u << (v & 31));
     }
   }
 }
 
 template <bool PACKED>
 __device__ __forceinline__ void hub_item(const DevGraph& d, const HubArgs& h, const uint32_t* sb,
-                                         int* scratch, const WorkItem& it, const SweepArgs& a,
-                                         const PhiloxRounds& rk, int lane) {
+                                         int* scratch, const WorkItem& it, const SweepArgs& a, int lane) {
   const int kind = item_kind(it);
   if (kind == kStageGroup) {
-    hub_group<PACKED>(d, h, sb, scratch, it, a, rk, lane);
-    return;
+    hub_group<PACKED>(d, h, sb, scratch, it, a, lane);
+  } else if (kind == kStageSlice) {
+    hub_slice<PACKED>(d, h, sb, it, a, lane);
+  } else {
+    const int R = light_rows_per_lane(-it.e_end - 1, PACKED);
+    if (R == 4)
+      hub_light<PACKED, 4>(d, h, sb, it, a, lane);
+    else if (R == 2)
+      hub_light<PACKED, 2>(d, h, sb, it, a, lane);
+    else
+      hub_light<PACKED, 1>(d, h, sb, it, a, lane);
   }
-  if (kind == kStageSlice) {
-    hub_slice<PACKED>(d, h, sb, it, a, rk, lane);
-    return;
+}
+
+// The sweep's flips by position: Philox evaluation q gives the draws of
+// original ids 4q .. 4q + 3 (R5); each id below its threshold (with the flip
+// bias of its position, as in flip_drawn) sets its position's bit. Called by
+// the workers while the chain block runs, on a map cleared before.
+__device__ __forceinline__ void hub_flip_map(const DevGraph& d, const HubArgs& h, const SweepArgs& a,
+                                             const PhiloxRounds& rk, int gthread, int nthreads) {
+  if (a.thr == 0u) return;
+  const int n = d.pad_col;
+  for (int q = gthread; 4 * q < n; q += nthreads) {
+    const uint4 x = philox4x32_10(static_cast<uint32_t>(q), a.t, a.replica, 0u, rk);
+    const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int o = 4 * q + k;
+      if (o >= n) break;
+      uint64_t thr = a.thr;
+      const int p = __ldg(h.pos + o);
+      if (d.bias != nullptr) {
+        thr = (static_cast<uint64_t>(a.thr) * __ldg(d.bias + p)) >> 7;
+        if (thr > 0xffffffffull) thr = 0xffffffffull;
+      }
+      if (w[k] < thr) atomicOr(h.pflips + (p >> 5), 1u << (p & 31));
+    }
   }
-  Staged<PACKED> st;
-  stage_item<PACKED>(d, it, a, rk, lane, st);
-  const int R = light_rows_per_lane(-it.e_end - 1, PACKED);
-  if (R == 4)
-    hub_light<PACKED, 4>(h, sb, st, lane);
-  else if (R == 2)
-    hub_light<PACKED, 2>(h, sb, st, lane);
-  else
-    hub_light<PACKED, 1>(h, sb, st, lane);
 }
 
 // Copy map words [w0, w1) from global memory into the block's copy: every
@@ -590,28 +662,28 @@ __device__ __forceinline__ void map_refresh(uint32_t* sb, const uint32_t* g, int
 // workers, then the chain block) and each of the P non-hub classes G - 1
 // (workers only: the chain block meanwhile pushes its deferred hubs); the
 // epilogue barrier counts the workers again.
-template <bool PACKED>
+template <bool PACKED, bool STAGE>
 __global__ void __launch_bounds__(kHubBlock, 1)
     hub_kernel(DevGraph d, HubArgs h, uint64_t t_begin, uint32_t sweeps, uint64_t T, uint64_t T0,
                uint32_t replica, PhiloxRounds rk, BarrierState* bs) {
   extern __shared__ __align__(16) unsigned char hub_shared[];
   const int lane = threadIdx.x & 31;
   const bool chain = blockIdx.x == 0;
-  const int warp = (static_cast<int>(blockIdx.x) - 1) * kHubWarps + static_cast<int>(threadIdx.x >> 5);
+  const int wb = static_cast<int>(blockIdx.x) - 1;  // worker block index
+  const int warp = wb * kHubWarps + static_cast<int>(threadIdx.x >> 5);
   const int nwarps = (static_cast<int>(gridDim.x) - 1) * kHubWarps;
   const int W = (h.hubs + 31) / 32;
   const unsigned G = gridDim.x;
   const int P = h.classes - h.hub_classes;
   HubSmem s = hub_smem(hub_shared, h.hubs, h.hub_classes);
   int* scratch = reinterpret_cast<int*>(hub_shared) + (threadIdx.x >> 5) * kHubGroupScratch;
-  uint32_t* sb_copy = reinterpret_cast<uint32_t*>(hub_shared) + kHubWarps * kHubGroupScratch;
-  const uint32_t* sb = h.stage_bits ? sb_copy : h.bits;
+  int* queue = reinterpret_cast<int*>(hub_shared) + kHubWarps * kHubGroupScratch;
+  uint32_t* sb_copy = reinterpret_cast<uint32_t*>(queue + 4);
+  const uint32_t* sb = STAGE ? sb_copy : h.bits;
   if (chain && threadIdx.x < 4) s.cnt[threadIdx.x] = 0;
   bool skip = bs->skip_block == static_cast<int>(blockIdx.x) + 1;
   unsigned target = 0;
   int step = 0;
-  long long unused = 0;
-  (void)unused;
   // prologue: the workers build the global map from the state bytes, then
   // (after a workers-only barrier) their copies
   target += G - 1;
@@ -625,15 +697,14 @@ __global__ void __launch_bounds__(kHubBlock, 1)
     barrier_arrive(bs, skip);
     skip = false;
     if (!barrier_wait(bs, target)) return;
-    if (h.stage_bits) map_refresh(sb_copy, h.bits, 0, h.bit_words);
+    if (STAGE) map_refresh(sb_copy, h.bits, 0, h.bit_words);
   }
   for (uint32_t k = 0; k < sweeps; ++k) {
     const SweepArgs a = sweep_args(t_begin + k, T, T0, replica);
     target += G;
     if (!chain) {
       // 1. the hubs' field sums and flip bits of sweep t; the hub rows the
-      // chain pushes from into L2; then wait, polling sparsely, while the
-      // chain block runs the hub classes
+      // chain pushes from into L2; the flip map cleared
       for (int i = (k == 0 ? 0 : h.num_b_items) + warp; i < h.num_items; i += nwarps)
         hub_sum_item<PACKED>(d, h, sb, i, static_cast<int>(k & 1u), lane);
       for (int j = warp; j < W; j += nwarps) hub_flip_word(d, h, j, a, rk, lane);
@@ -642,19 +713,38 @@ __global__ void __launch_bounds__(kHubBlock, 1)
           const int4 it = __ldg(h.sums + i);
           hub_prefetch<PACKED>(d, it.y, it.z, lane);
         }
+      if (a.thr != 0u)
+        for (int j = warp * 32 + lane; j < h.bit_words; j += nwarps * 32) h.pflips[j] = 0u;
       barrier_arrive(bs, skip);
       skip = false;
+      // while the chain block runs the hub classes: once every worker has
+      // cleared its part, the flip map of the sweep; then wait, polling sparsely
+      if (!barrier_wait(bs, target - 1)) return;
+      hub_flip_map(d, h, a, rk, warp * 32 + lane, nwarps * 32);
       if (!barrier_wait_sleep(bs, target, 256)) return;
-      if (h.stage_bits) map_refresh(sb_copy, h.bits, 0, W);
-      // 3. the other classes, a workers-only grid barrier after each
+      if (STAGE) map_refresh(sb_copy, h.bits, 0, W);
+      // 3. the other classes, a workers-only grid barrier after each; the
+      // block's items of a class are a contiguous range of equal estimated
+      // work, taken by its warps from a shared counter
       for (int c = h.hub_classes; c < h.classes; ++c) {
-        const int ie = __ldg(h.class_items + c + 1);
-        for (int i = __ldg(h.class_items + c) + warp; i < ie; i += nwarps)
-          hub_item<PACKED>(d, h, sb, scratch, d.items[i], a, rk, lane);
+        const int* blk = h.blk + (c - h.hub_classes) * static_cast<int>(G);
+        const int i0 = __ldg(blk + wb), i1 = __ldg(blk + wb + 1);
+        if (threadIdx.x == 0) queue[0] = 0;
+        __syncthreads();
+        int i = 0;
+        if (lane == 0) i = atomicAdd(queue, 1);
+        i = __shfl_sync(kFullMask, i, 0) + i0;
+        while (i < i1) {
+          int nxt = 0;
+          if (lane == 0) nxt = atomicAdd(queue, 1);
+          nxt = __shfl_sync(kFullMask, nxt, 0) + i0;
+          hub_item<PACKED>(d, h, sb, scratch, d.items[i], a, lane);
+          i = nxt;
+        }
         barrier_arrive(bs, false);
         target += G - 1;
         if (!barrier_wait(bs, target)) return;
-        if (h.stage_bits)
+        if (STAGE)
           map_refresh(sb_copy, h.bits, __ldg(h.class_begin + c) >> 5, (__ldg(h.class_begin + c + 1) + 31) >> 5);
       }
     } else {
@@ -672,8 +762,8 @@ __global__ void __launch_bounds__(kHubBlock, 1)
   // epilogue: the state bytes from the map, every vertex's update parity
   // flipped once per sweep (the last class's barrier above orders the map)
   if (!chain)
-    for (int p = (static_cast<int>(blockIdx.x) - 1) * kHubBlock + static_cast<int>(threadIdx.x);
-         p < d.pad_col; p += (static_cast<int>(G) - 1) * kHubBlock)
+    for (int p = wb * kHubBlock + static_cast<int>(threadIdx.x); p < d.pad_col;
+         p += (static_cast<int>(G) - 1) * kHubBlock)
       d.spins[p] = static_cast<int8_t>(state_byte(1 - 2 * map_bit(h.bits, p), h.par_end));
 }
 

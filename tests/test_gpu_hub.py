@@ -140,3 +140,10 @@ def test_hub_engine_missing_arrival_reports_timeout(P):
     # the context stays usable
     g2 = synth.zipf_config_graph(20000, 2.0, 3, 3000, 17)
     check_hub(P, g2, seed=3, p0=0.1, T=10)
+
+
+def test_hub_engine_without_a_shared_memory_map(P):
+    # 2^21 vertices: the spin map (256 KiB) does not fit in a block's shared
+    # memory, so the workers read the global map
+    g = synth.zipf_config_graph(1 << 21, 2.5, 3, 3000, 18)  # ~2000 hubs
+    check_hub(P, g, seed=3, p0=0.1, T=2000, sweeps=4)
