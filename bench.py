@@ -298,6 +298,7 @@ def run_batched(args, world, rank, P, torch, dist):
     arrays = [(g.n, g.src, g.dst, g.w) for g in gs]
     b = P.ising_batch_create(arrays, replicas=R, stream=stream)
     block = P.ising_batch_autotune(b, probe_sweeps=20)
+    tuning = P.ising_batch_tuning(b)
     nvert = sum(g.n for g in gs)
     nnz = 2 * sum(g.m for g in gs)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
@@ -348,7 +349,7 @@ def run_batched(args, world, rank, P, torch, dist):
         for k in range(args.e2e_steps + 1):
             t0 = time.perf_counter()
             with P.ising_batch_create(arrays, replicas=R, stream=stream) as b2:
-                P.ising_batch_set_block(b2, block)
+                P.ising_batch_set_tuning(b2, tuning["block"], tuning["row_split"], tuning["tail"])
                 P.ising_batch_init_random(b2, seed + k)
                 P.ising_batch_anneal(b2, p0=p0, t_total=T, seed=seed + k, stream=stream)
                 P.ising_batch_cuts(b2)
@@ -369,6 +370,10 @@ def run_batched(args, world, rank, P, torch, dist):
         "data": "synthetic",
         "config": {"workload": "batched", "instances": len(gs), "vertices": nvert,
                    "edges": nnz // 2, "replicas": R, "sweeps": T, "p0": p0, "block": block,
+                   "tuning": {"block": tuning["block"], "row_split": tuning["row_split"],
+                              "tail": tuning["tail"],
+                              "probe_ms_20_sweeps": [round(x, 3) for x in tuning["probe_ms"]],
+                              "probe_order": "6 * block(128,256,512) + 2 * row_split(1,2,4) + tail(0,32)"},
                    "parallelism": f"replicas{world}",
                    "l2": "512 MiB buffer zeroed between timed steps (outside the events)"},
         "sweeps_per_s": T * args.steps * world / (total_ms / 1e3),

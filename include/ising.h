@@ -368,12 +368,28 @@ int ising_batch_cuts(ising_batch* b, int64_t* out_cuts);
  * ISING_EINVAL otherwise). Synchronise the stream. */
 int ising_batch_get_spins(ising_batch* b, int32_t graph, uint32_t replica, int8_t* out);
 int ising_batch_set_spins(ising_batch* b, int32_t graph, uint32_t replica, const int8_t* in);
-/* ising_batch_autotune -- times `probe_sweeps` sweeps of the batch for each
- * candidate block size (128, 256, 512 threads), keeps the fastest and restores
- * the spins. out_block (may be NULL) receives the choice. */
+/* ising_batch_autotune -- times `probe_sweeps` sweeps of the batch (from its
+ * current spins, which are restored afterwards) for each of 18 launch
+ * configurations and keeps the fastest: the block size (128, 256 or 512
+ * threads, one instance per block at a time), the threads that share a row's
+ * entries (1, 2 or 4; their partial sums are combined by warp shuffles) and
+ * the tail mode (0: every colour class with a block barrier after it; 32:
+ * classes of at most 32 vertices decided by one warp with warp barriers).
+ * Results do not depend on the configuration. out_block (may be NULL)
+ * receives the chosen block size; ising_batch_tuning reports the rest.
+ * Synchronises the batch's stream. */
 int ising_batch_autotune(ising_batch* b, uint32_t probe_sweeps, int32_t* out_block);
 /* ising_batch_set_block -- choose the block size directly (128, 256 or 512). */
 int ising_batch_set_block(ising_batch* b, int32_t block);
+/* ising_batch_set_tuning -- choose the whole configuration directly: block
+ * 128/256/512, row_split 1/2/4, tail 0..32 (ISING_EINVAL otherwise). */
+int ising_batch_set_tuning(ising_batch* b, int32_t block, int32_t row_split, int32_t tail);
+/* ising_batch_tuning -- the current configuration and, in out_probe_ms (18
+ * floats, may be NULL), the last autotune's probe time of configuration
+ * k = 6 * block_index + 2 * split_index + tail_index (block 128/256/512,
+ * split 1/2/4, tail 0/32; 0 before any autotune). Any pointer may be NULL. */
+int ising_batch_tuning(ising_batch* b, int32_t* out_block, int32_t* out_row_split, int32_t* out_tail,
+                       float* out_probe_ms);
 /* ising_batch_info -- instances, total vertices, block size, kernel launches. */
 int ising_batch_info(ising_batch* b, int32_t* out_num_graphs, int64_t* out_vertices,
                      int32_t* out_block, uint64_t* out_launches);

@@ -56,7 +56,7 @@ EXPORTS = (
     "ising_gnn_get_params", "ising_gnn_forward", "ising_gnn_gradients", "ising_gnn_train_step",
     "ising_gnn_warm_start", "ising_gnn_launch_count", "ising_gnn_destroy", "ising_debug_fault",
     "ising_engine_used", "ising_set_halo_sweeps", "ising_halo_info", "ising_plan_halo",
-    "ising_convergence_region",
+    "ising_convergence_region", "ising_batch_set_tuning", "ising_batch_tuning",
 )
 ISING_ENGINE_USED_BLOCK = 6
 ISING_FAULT_NONE = 0
@@ -125,6 +125,8 @@ def lib():
         L.ising_batch_set_spins.argtypes = [vp, ctypes.c_int32, ctypes.c_uint32, vp]
         L.ising_batch_autotune.argtypes = [vp, ctypes.c_uint32, ctypes.POINTER(ctypes.c_int32)]
         L.ising_batch_set_block.argtypes = [vp, ctypes.c_int32]
+        L.ising_batch_set_tuning.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
+        L.ising_batch_tuning.argtypes = [vp, vp, vp, vp, vp]
         L.ising_batch_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), i64p,
                                        ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_uint64)]
         L.ising_batch_destroy.argtypes = [vp]
@@ -526,6 +528,20 @@ def ising_batch_autotune(b: IsingBatch, probe_sweeps: int = 20) -> int:
 
 def ising_batch_set_block(b: IsingBatch, block: int) -> None:
     _check(lib().ising_batch_set_block(b.ptr, block), "ising_batch_set_block")
+
+
+def ising_batch_set_tuning(b: IsingBatch, block: int, row_split: int, tail: int) -> None:
+    _check(lib().ising_batch_set_tuning(b.ptr, block, row_split, tail), "ising_batch_set_tuning")
+
+
+def ising_batch_tuning(b: IsingBatch) -> dict:
+    """The configuration in use and the last autotune's 18 probe times (ms),
+    indexed 6 * block_index + 2 * split_index + tail_index."""
+    blk, split, tail = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    probe = np.zeros(18, dtype=np.float32)
+    _check(lib().ising_batch_tuning(b.ptr, ctypes.byref(blk), ctypes.byref(split), ctypes.byref(tail),
+                                    probe.ctypes.data), "ising_batch_tuning")
+    return {"block": blk.value, "row_split": split.value, "tail": tail.value, "probe_ms": probe.tolist()}
 
 
 def ising_batch_info(b: IsingBatch) -> dict:

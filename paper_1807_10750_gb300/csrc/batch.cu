@@ -76,14 +76,139 @@ __device__ __forceinline__ uint4 batch_philox(uint32_t x0, uint32_t x1, uint32_t
   return make_uint4(x0, x1, x2, x3);
 }
 
+// The field terms of one row's entries [e0, e1) taken with stride S (the
+// row is shared by S consecutive threads, this one starting at e0 + sub):
+// accumulator words for the byte-lane paths or per-replica sums, and the sum
+// of the weights.
+struct RowSums {
+  uint32_t a0, a1, a2, a3;  // byte lanes: lo / hi counts (+-1), or plo / phi / nlo / nhi
+  int acc[8];               // per-replica path
+  int wsum;
+};
+
+template <int S>
+__device__ __forceinline__ void row_sums(const BatchDev& d, const uint8_t* sp, int mode, int e0, int e1,
+                                         int sub, RowSums& r) {
+  r.a0 = r.a1 = r.a2 = r.a3 = 0u;
+  r.wsum = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) r.acc[k] = 0;
+  if (mode == 2) {
+    // +-1 weights: w_j s_j = -1 exactly when the neighbour's spin bit
+    // differs from the weight's sign bit, so with x = b ^ (0xff if w < 0)
+    // the byte lanes count the negative products and f_r = degree - 2 *
+    // count_r (each nibble of x spread into byte lanes as below)
+    for (int e = e0 + sub; e < e1; e += S) {
+      const uint32_t word = static_cast<uint32_t>(__ldg(d.adj + e));
+      // 0, or 0xffffffff for a negative weight byte
+      const uint32_t neg = static_cast<uint32_t>(static_cast<int32_t>(word << 24) >> 31);
+      const uint32_t b = sp[word >> 8];
+      r.a0 += (((b ^ neg) & 0xfu) * 0x00204081u) & 0x01010101u;
+      r.a1 += ((((b >> 4) ^ neg) & 0xfu) * 0x00204081u) & 0x01010101u;
+      r.wsum += 1;
+    }
+  } else if (mode == 1) {
+    // the 8 replica bits of a neighbour spread into 8 byte lanes (4 per
+    // word: x * 0x00204081 puts bit k of a nibble at bit 8k), weighted by
+    // |w| into a positive and a negative accumulator; no lane can exceed 255
+    // because the row's sum of |w| does not
+    for (int e = e0 + sub; e < e1; e += S) {
+      const int word = __ldg(d.adj + e);
+      const int wgt = (word << 24) >> 24;
+      const uint32_t b = sp[static_cast<unsigned>(word) >> 8];
+      r.wsum += wgt;
+      const uint32_t lo = ((b & 0xfu) * 0x00204081u) & 0x01010101u;
+      const uint32_t hi = ((b >> 4) * 0x00204081u) & 0x01010101u;
+      const uint32_t mag = static_cast<uint32_t>(wgt < 0 ? -wgt : wgt);
+      if (wgt > 0) {
+        r.a0 += lo * mag;
+        r.a1 += hi * mag;
+      } else {
+        r.a2 += lo * mag;
+        r.a3 += hi * mag;
+      }
+    }
+  } else {
+    for (int e = e0 + sub; e < e1; e += S) {
+      const int word = __ldg(d.adj + e);
+      const int wgt = (word << 24) >> 24;
+      const int b = sp[static_cast<unsigned>(word) >> 8];
+      r.wsum += wgt;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) r.acc[k] += (b >> k) & 1 ? wgt : 0;
+    }
+  }
+}
+
+// Combine the S partial sums of a row's threads (consecutive lanes of one
+// warp, group mask m): byte-lane words add without carries because no lane
+// of a row's total exceeds 255.
+template <int S>
+__device__ __forceinline__ void row_combine(RowSums& r, unsigned m) {
+#pragma unroll
+  for (int o = 1; o < S; o <<= 1) {
+    r.a0 += __shfl_xor_sync(m, r.a0, o);
+    r.a1 += __shfl_xor_sync(m, r.a1, o);
+    r.a2 += __shfl_xor_sync(m, r.a2, o);
+    r.a3 += __shfl_xor_sync(m, r.a3, o);
+    r.wsum += __shfl_xor_sync(m, r.wsum, o);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) r.acc[k] += __shfl_xor_sync(m, r.acc[k], o);
+  }
+}
+
+// The decision of one vertex for every replica (Eq. 2 under the max-cut sign,
+// then Algorithm 2's flip bits): the new replica byte.
+__device__ __forceinline__ int decide_replicas(const RowSums& r, int mode, int own, int fl, int replicas) {
+  int acc[8];
+  if (mode == 2) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      acc[k] = static_cast<int>((r.a0 >> (8 * k)) & 0xffu);
+      acc[k + 4] = static_cast<int>((r.a1 >> (8 * k)) & 0xffu);
+    }
+  } else if (mode == 1) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      acc[k] = static_cast<int>((r.a0 >> (8 * k)) & 0xffu) - static_cast<int>((r.a2 >> (8 * k)) & 0xffu);
+      acc[k + 4] = static_cast<int>((r.a1 >> (8 * k)) & 0xffu) - static_cast<int>((r.a3 >> (8 * k)) & 0xffu);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc[k] = r.acc[k];
+  }
+  // f_r = sum_j w_j s_j = wsum - 2 * sum over neighbours with spin -1
+  int nb = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    if (k >= replicas) break;
+    const int f = r.wsum - 2 * acc[k];
+    int bit = (own >> k) & 1;  // 1 = spin -1
+    if (f > 0)
+      bit = 1;
+    else if (f < 0)
+      bit = 0;
+    bit ^= (fl >> k) & 1;
+    nb |= bit << k;
+  }
+  return nb;
+}
+
 // One instance per block iteration; all sweeps t_begin .. t_begin + sweeps - 1.
-template <int BLOCK>
+// Tuning (ising_batch_autotune): BLOCK threads; S threads share each row
+// (the row's entries strided over them); classes of at most `tail` vertices
+// are decided by warp 0 alone with warp barriers (the other warps wait at
+// the next larger class's block barrier).
+template <int BLOCK, int S>
 __global__ void __launch_bounds__(BLOCK)
     batch_anneal_kernel(BatchDev d, int num_graphs, unsigned* work, uint64_t t_begin,
                         uint32_t sweeps, uint64_t T, uint64_t T0, uint32_t seed_lo,
-                        uint32_t seed_hi, int replicas) {
+                        uint32_t seed_hi, int replicas, int tail) {
   extern __shared__ uint8_t sp[];
   __shared__ int slot_shared;
+  const int lane = threadIdx.x & 31;
+  const int sub = lane % S;
+  const unsigned gmask = (S == 32 ? 0xffffffffu : ((1u << S) - 1u)) << (lane - sub);
   for (;;) {
     if (threadIdx.x == 0) slot_shared = static_cast<int>(atomicAdd(work, 1u));
     __syncthreads();
@@ -97,6 +222,7 @@ __global__ void __launch_bounds__(BLOCK)
     const uint32_t kb = seed_hi ^ (static_cast<uint32_t>(gi) * 0x9E3779B9u);
     const int32_t* rp = d.row_ptr + G.row_base;
     const int32_t* cls = d.class_pos + G.class_base;
+    const int mode = G.byte_lanes;
     for (uint32_t k = 0; k < sweeps; ++k) {
       const uint64_t t = t_begin + k;
       const uint32_t thr = (T <= 1) ? 0u : static_cast<uint32_t>((T0 * (T - 1 - t)) / (T - 1));
@@ -116,91 +242,41 @@ __global__ void __launch_bounds__(BLOCK)
         }
         __syncthreads();
       }
+      bool tail_run = false;  // warp 0 has decided tail classes since the last block barrier
       for (int c = 0; c < G.num_classes; ++c) {
-        const int ce = __ldg(cls + c + 1);
-        for (int v = __ldg(cls + c) + threadIdx.x; v < ce; v += BLOCK) {
-          const int e1 = __ldg(rp + v + 1);
-          int wsum = 0;
-          int acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-          if (G.byte_lanes == 2) {
-            // +-1 weights: w_j s_j = -1 exactly when the neighbour's spin bit
-            // differs from the weight's sign bit, so with x = b ^ (0xff if
-            // w < 0) the byte lanes count the negative products and
-            // f_r = degree - 2 * count_r (each nibble of x spread into byte
-            // lanes as below)
-            uint32_t lo = 0, hi = 0;
-            const int e0 = __ldg(rp + v);
-            for (int e = e0; e < e1; ++e) {
-              const uint32_t word = static_cast<uint32_t>(__ldg(d.adj + e));
-              // 0, or 0xffffffff for a negative weight byte
-              const uint32_t neg = static_cast<uint32_t>(static_cast<int32_t>(word << 24) >> 31);
-              const uint32_t b = sp[word >> 8];
-              lo += (((b ^ neg) & 0xfu) * 0x00204081u) & 0x01010101u;
-              hi += ((((b >> 4) ^ neg) & 0xfu) * 0x00204081u) & 0x01010101u;
+        const int cb = __ldg(cls + c), ce = __ldg(cls + c + 1);
+        const bool small = ce - cb <= tail;
+        if (small) {
+          // warp 0 alone: one vertex per lane
+          if (threadIdx.x < 32) {
+            const int v = cb + lane;
+            if (v < ce) {
+              RowSums r;
+              row_sums<1>(d, sp, mode, __ldg(rp + v), __ldg(rp + v + 1), 0, r);
+              const int fl = thr != 0u ? __ldcg(d.flips + G.vtx_base + __ldg(d.orig + G.vtx_base + v)) : 0;
+              sp[v] = static_cast<uint8_t>(decide_replicas(r, mode, sp[v], fl, replicas));
             }
-            wsum = e1 - e0;
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-              acc[r] = static_cast<int>((lo >> (8 * r)) & 0xffu);
-              acc[r + 4] = static_cast<int>((hi >> (8 * r)) & 0xffu);
-            }
-          } else if (G.byte_lanes) {
-            // the 8 replica bits of a neighbour spread into 8 byte lanes (4 per
-            // word: x * 0x00204081 puts bit k of a nibble at bit 8k), weighted
-            // by |w| into a positive and a negative accumulator; no lane can
-            // exceed 255 because the row's sum of |w| does not
-            uint32_t plo = 0, phi = 0, nlo = 0, nhi = 0;
-            for (int e = __ldg(rp + v); e < e1; ++e) {
-              const int word = __ldg(d.adj + e);
-              const int wgt = (word << 24) >> 24;
-              const uint32_t b = sp[static_cast<unsigned>(word) >> 8];
-              wsum += wgt;
-              const uint32_t lo = ((b & 0xfu) * 0x00204081u) & 0x01010101u;
-              const uint32_t hi = ((b >> 4) * 0x00204081u) & 0x01010101u;
-              const uint32_t mag = static_cast<uint32_t>(wgt < 0 ? -wgt : wgt);
-              if (wgt > 0) {
-                plo += lo * mag;
-                phi += hi * mag;
-              } else {
-                nlo += lo * mag;
-                nhi += hi * mag;
-              }
-            }
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-              acc[r] = static_cast<int>((plo >> (8 * r)) & 0xffu) - static_cast<int>((nlo >> (8 * r)) & 0xffu);
-              acc[r + 4] = static_cast<int>((phi >> (8 * r)) & 0xffu) - static_cast<int>((nhi >> (8 * r)) & 0xffu);
-            }
-          } else {
-            for (int e = __ldg(rp + v); e < e1; ++e) {
-              const int word = __ldg(d.adj + e);
-              const int wgt = (word << 24) >> 24;
-              const int b = sp[static_cast<unsigned>(word) >> 8];
-              wsum += wgt;
-#pragma unroll
-              for (int r = 0; r < 8; ++r) acc[r] += (b >> r) & 1 ? wgt : 0;
-            }
+            __syncwarp();
           }
-          // f_r = sum_j w_j s_j = wsum - 2 * sum over neighbours with spin -1
-          const int own = sp[v];
-          int nb = 0;
-          const int fl = thr != 0u ? __ldcg(d.flips + G.vtx_base + __ldg(d.orig + G.vtx_base + v)) : 0;
-#pragma unroll
-          for (int r = 0; r < 8; ++r) {
-            if (r >= replicas) break;
-            const int f = wsum - 2 * acc[r];
-            int bit = (own >> r) & 1;  // 1 = spin -1
-            if (f > 0)
-              bit = 1;
-            else if (f < 0)
-              bit = 0;
-            bit ^= (fl >> r) & 1;
-            nb |= bit << r;
+          tail_run = true;
+          continue;
+        }
+        if (tail_run) {  // warp 0's tail classes are complete and visible
+          __syncthreads();
+          tail_run = false;
+        }
+        for (int v = cb + static_cast<int>(threadIdx.x) / S; v < ce; v += BLOCK / S) {
+          RowSums r;
+          row_sums<S>(d, sp, mode, __ldg(rp + v), __ldg(rp + v + 1), sub, r);
+          if (S > 1) row_combine<S>(r, gmask);
+          if (sub == 0) {
+            const int fl = thr != 0u ? __ldcg(d.flips + G.vtx_base + __ldg(d.orig + G.vtx_base + v)) : 0;
+            sp[v] = static_cast<uint8_t>(decide_replicas(r, mode, sp[v], fl, replicas));
           }
-          sp[v] = static_cast<uint8_t>(nb);
         }
         __syncthreads();
       }
+      if (tail_run) __syncthreads();
     }
     for (int v = threadIdx.x; v < G.n; v += BLOCK) d.spins[G.vtx_base + v] = sp[v];
     __syncthreads();
@@ -262,6 +338,9 @@ uint64_t batch_t0(double p0) {
 }
 
 constexpr int kBlockChoices[3] = {128, 256, 512};
+constexpr int kSplitChoices[3] = {1, 2, 4};
+constexpr int kTailChoices[2] = {0, 32};
+constexpr int kTuneConfigs = 18;  // block x split x tail
 
 }  // namespace
 
@@ -273,7 +352,7 @@ struct ising_batch {
   int32_t num_graphs = 0;
   int replicas = 1;
   int32_t max_n = 0;
-  int block = 256;  // chosen by ising_batch_autotune
+  int block = 256;  // chosen by ising_batch_autotune (with split and tail below)
   uint64_t launches = 0;
   std::vector<int32_t> n;                  // per instance
   std::vector<int64_t> total_weight;       // per instance
@@ -293,7 +372,10 @@ struct ising_batch {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
   cudaGraphNode_t kernel_node = nullptr;
-  int graph_block = 0;
+  const void* graph_kernel = nullptr;  // the kernel the captured graph launches
+  int split = 1;  // threads per row (ising_batch_autotune)
+  int tail = 0;   // classes up to this size decided by one warp
+  float probe_ms[kTuneConfigs] = {};  // the autotuner's probe times
 
   BatchDev dev() const {
     BatchDev d;
@@ -350,17 +432,24 @@ cudaError_t upload(T** dst, const std::vector<T>& src, cudaStream_t s) {
   return cudaMemsetAsync(*dst, 0, bytes, s);
 }
 
-const void* batch_kernel_for(int block) {
-  if (block == 128) return reinterpret_cast<const void*>(batch_anneal_kernel<128>);
-  if (block == 512) return reinterpret_cast<const void*>(batch_anneal_kernel<512>);
-  return reinterpret_cast<const void*>(batch_anneal_kernel<256>);
+template <int BLOCK>
+const void* batch_kernel_split(int split) {
+  if (split == 2) return reinterpret_cast<const void*>(batch_anneal_kernel<BLOCK, 2>);
+  if (split == 4) return reinterpret_cast<const void*>(batch_anneal_kernel<BLOCK, 4>);
+  return reinterpret_cast<const void*>(batch_anneal_kernel<BLOCK, 1>);
+}
+
+const void* batch_kernel_for(int block, int split) {
+  if (block == 128) return batch_kernel_split<128>(split);
+  if (block == 512) return batch_kernel_split<512>(split);
+  return batch_kernel_split<256>(split);
 }
 
 // Blocks of the persistent batch kernel: every co-resident block (shared
 // memory holds the largest instance's spins).
-int batch_grid(ising_batch* b, int block, size_t smem) {
+int batch_grid(ising_batch* b, int block, int split, size_t smem) {
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel_for(block), block, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel_for(block, split), block, smem);
   cudaGetLastError();
   if (per_sm < 1) per_sm = 1;
   return std::min(per_sm * b->num_sms, std::max(1, b->num_graphs));
@@ -372,23 +461,24 @@ int batch_grid(ising_batch* b, int block, size_t smem) {
 int batch_launch(ising_batch* b, uint64_t t_begin, uint32_t sweeps, uint64_t T, uint64_t T0,
                  uint64_t seed) {
   const size_t smem = static_cast<size_t>(std::max(b->max_n, 1));
-  const void* kernel = batch_kernel_for(b->block);
+  const void* kernel = batch_kernel_for(b->block, b->split);
   BATCH_CUDA(b, cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      static_cast<int>(smem)));
-  const int grid = batch_grid(b, b->block, smem);
+  const int grid = batch_grid(b, b->block, b->split, smem);
   BatchDev d = b->dev();
   int num_graphs = b->num_graphs;
   unsigned* work = b->d_work;
   uint32_t seed_lo = static_cast<uint32_t>(seed), seed_hi = static_cast<uint32_t>(seed >> 32);
   int replicas = b->replicas;
-  void* args[] = {&d, &num_graphs, &work, &t_begin, &sweeps, &T, &T0, &seed_lo, &seed_hi, &replicas};
+  int tail = b->tail;
+  void* args[] = {&d, &num_graphs, &work, &t_begin, &sweeps, &T, &T0, &seed_lo, &seed_hi, &replicas, &tail};
   cudaKernelNodeParams kp = {};
   kp.func = const_cast<void*>(kernel);
   kp.gridDim = dim3(grid);
   kp.blockDim = dim3(b->block);
   kp.sharedMemBytes = static_cast<unsigned>(smem);
   kp.kernelParams = args;
-  if (b->graph_exec == nullptr || b->graph_block != b->block) {
+  if (b->graph_exec == nullptr || b->graph_kernel != kernel) {
     if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     b->graph_exec = nullptr;
@@ -404,7 +494,7 @@ int batch_launch(ising_batch* b, uint64_t t_begin, uint32_t sweeps, uint64_t T, 
     BATCH_CUDA(b, cudaGraphAddMemsetNode(&memset_node, b->graph, nullptr, 0, &mp));
     BATCH_CUDA(b, cudaGraphAddKernelNode(&b->kernel_node, b->graph, &memset_node, 1, &kp));
     BATCH_CUDA(b, cudaGraphInstantiate(&b->graph_exec, b->graph, 0));
-    b->graph_block = b->block;
+    b->graph_kernel = kernel;
   } else {
     BATCH_CUDA(b, cudaGraphExecKernelNodeSetParams(b->graph_exec, b->kernel_node, &kp));
   }
@@ -626,18 +716,21 @@ int ising_batch_autotune(ising_batch* b, uint32_t probe_sweeps, int32_t* out_blo
   int rc = batch_enter(b);
   if (rc != ISING_OK) return rc;
   if (probe_sweeps == 0) probe_sweeps = 1;
-  // time every block size on the batch itself, then restore the spins
+  // time every configuration (block size x threads per row x tail mode) on
+  // the batch itself, then restore the spins
   const int64_t total = b->vtx_base.empty() ? 0 : b->vtx_base.back() + b->n.back();
   uint8_t* saved = nullptr;
   BATCH_CUDA(b, cudaMalloc(reinterpret_cast<void**>(&saved), std::max<int64_t>(total, 16)));
   cudaError_t e = cudaMemcpyAsync(saved, b->d_spins, (size_t)total, cudaMemcpyDeviceToDevice, b->stream);
   cudaEvent_t t0 = nullptr, t1 = nullptr;
   float best_ms = 1e30f;
-  int best = b->block;
+  int best = 0;
   if (e == cudaSuccess) e = cudaEventCreate(&t0);
   if (e == cudaSuccess) e = cudaEventCreate(&t1);
-  for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
-    b->block = kBlockChoices[i];
+  for (int cfg = 0; cfg < kTuneConfigs && e == cudaSuccess; ++cfg) {
+    b->block = kBlockChoices[cfg / 6];
+    b->split = kSplitChoices[(cfg / 2) % 3];
+    b->tail = kTailChoices[cfg % 2];
     for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // first run warms the captured graph
       e = cudaEventRecord(t0, b->stream);
       if (e == cudaSuccess && batch_launch(b, 0, probe_sweeps, probe_sweeps + 1, batch_t0(0.1), 1) != ISING_OK)
@@ -647,9 +740,10 @@ int ising_batch_autotune(ising_batch* b, uint32_t probe_sweeps, int32_t* out_blo
     }
     float ms = 0.f;
     if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+    b->probe_ms[cfg] = ms;
     if (e == cudaSuccess && ms < best_ms) {
       best_ms = ms;
-      best = kBlockChoices[i];
+      best = cfg;
     }
   }
   if (e == cudaSuccess)
@@ -663,8 +757,10 @@ int ising_batch_autotune(ising_batch* b, uint32_t probe_sweeps, int32_t* out_blo
     b->status = ISING_ECUDA;
     return ISING_ECUDA;
   }
-  b->block = best;
-  if (out_block) *out_block = best;
+  b->block = kBlockChoices[best / 6];
+  b->split = kSplitChoices[(best / 2) % 3];
+  b->tail = kTailChoices[best % 2];
+  if (out_block) *out_block = b->block;
   return ISING_OK;
 }
 
@@ -672,6 +768,28 @@ int ising_batch_set_block(ising_batch* b, int32_t block) {
   if (b == nullptr) return ISING_EINVAL;
   if (block != 128 && block != 256 && block != 512) return ISING_EINVAL;
   b->block = block;
+  return ISING_OK;
+}
+
+int ising_batch_set_tuning(ising_batch* b, int32_t block, int32_t row_split, int32_t tail) {
+  if (b == nullptr) return ISING_EINVAL;
+  if (block != 128 && block != 256 && block != 512) return ISING_EINVAL;
+  if (row_split != 1 && row_split != 2 && row_split != 4) return ISING_EINVAL;
+  if (tail < 0 || tail > 32) return ISING_EINVAL;
+  b->block = block;
+  b->split = row_split;
+  b->tail = tail;
+  return ISING_OK;
+}
+
+int ising_batch_tuning(ising_batch* b, int32_t* out_block, int32_t* out_row_split, int32_t* out_tail,
+                       float* out_probe_ms) {
+  if (b == nullptr) return ISING_EINVAL;
+  if (out_block) *out_block = b->block;
+  if (out_row_split) *out_row_split = b->split;
+  if (out_tail) *out_tail = b->tail;
+  if (out_probe_ms)
+    for (int k = 0; k < kTuneConfigs; ++k) out_probe_ms[k] = b->probe_ms[k];
   return ISING_OK;
 }
 

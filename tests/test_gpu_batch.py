@@ -85,6 +85,22 @@ def test_batch_split_anneal_equals_whole_and_set_spins(P):
                 assert np.array_equal(P.ising_batch_get_spins(b, gi, r), want), (gi, r)
 
 
+@pytest.mark.parametrize("row_split", [1, 2, 4])
+@pytest.mark.parametrize("tail", [0, 32])
+def test_batch_every_tuning_is_bit_exact(P, row_split, tail):
+    # the autotuner's knobs change only the schedule of the work, never the
+    # result: threads sharing a row, one-warp tail classes
+    gs = small_batch()
+    with P.ising_batch_create([(g.n, g.src, g.dst, g.w) for g in gs], replicas=8) as b:
+        P.ising_batch_set_tuning(b, 256, row_split, tail)
+        P.ising_batch_init_random(b, 41)
+        P.ising_batch_anneal(b, p0=0.15, t_total=40, seed=6)
+        for gi, g in enumerate(gs):
+            for r in (0, 3, 7):
+                want = oracle_run(g, gi, r, init_seed=41, seed=6, p0=0.15, T=40)
+                assert np.array_equal(P.ising_batch_get_spins(b, gi, r), want), (gi, r)
+
+
 def test_batch_autotune_keeps_spins(P):
     gs = small_batch()
     with P.ising_batch_create([(g.n, g.src, g.dst, g.w) for g in gs], replicas=8) as b:
@@ -93,6 +109,9 @@ def test_batch_autotune_keeps_spins(P):
         block = P.ising_batch_autotune(b, probe_sweeps=5)
         assert block in (128, 256, 512)
         assert P.ising_batch_info(b)["block"] == block
+        tune = P.ising_batch_tuning(b)
+        assert tune["block"] == block and tune["row_split"] in (1, 2, 4) and tune["tail"] in (0, 32)
+        assert all(ms > 0 for ms in tune["probe_ms"])
         for gi in range(len(gs)):
             assert np.array_equal(P.ising_batch_get_spins(b, gi, 7), before[gi])
 

@@ -393,19 +393,36 @@ def test_itemflow_engine_matches_oracle_over_many_sweeps(P, name):
     assert np.array_equal(got, want)
 
 
+def _stars_without_hubs():
+    # a sparse random graph plus 20 vertices of about 210 neighbours each:
+    # rows long enough to be sliced across warps, but no vertex reaches the
+    # hub degree (256)
+    rng = np.random.default_rng(9)
+    base = synth.random_small_graph(20000, 4e-4, 2)
+    centres = np.repeat(np.arange(20, dtype=np.int32), 200)
+    leaves = np.concatenate([rng.choice(np.arange(20, 20000), 200, replace=False) for _ in range(20)])
+    src = np.concatenate([base.src, centres]).astype(np.int32)
+    dst = np.concatenate([base.dst, leaves]).astype(np.int32)
+    w = np.concatenate([base.w, synth.draw_weights("int8", centres.size, rng)]).astype(np.int32)
+    return synth.Graph(20000, src, dst, w)
+
+
 def test_auto_engine_choice(P):
     # small graph -> the one-block form; a lattice with about 1000 vertices
     # per SM -> halo; unsliced large graph without a halo plan (or with too
-    # much repeated work) -> item dataflow; a graph with sliced hub rows ->
-    # the grid engine; racy and N-flip anneals of an unsliced graph -> the
-    # grid engine
+    # much repeated work) -> item dataflow; a graph with hubs -> the hub
+    # engine; sliced rows without hubs -> the grid engine; racy and N-flip
+    # anneals of an unsliced graph -> the grid engine
     cases = [
         (synth.random_small_graph(400, 0.03, 1, weights="int8"), {}, P.ISING_ENGINE_USED_BLOCK),
         (synth.torus_graph(384, 2, weights="pm1"), {}, P.ISING_ENGINE_HALO),
         (synth.torus_graph(100, 2, weights="pm1"), {}, P.ISING_ENGINE_ITEMFLOW),
         (synth.torus_graph(96, 2, weights="pm1"), {}, P.ISING_ENGINE_ITEMFLOW),
         (synth.random_small_graph(20000, 4e-4, 2), {}, P.ISING_ENGINE_ITEMFLOW),
-        (synth.zipf_config_graph(20011, 2.1, 4, 3000, 5), {}, P.ISING_ENGINE_PERSISTENT_GRID),
+        (synth.zipf_config_graph(20011, 2.1, 4, 3000, 5), {}, P.ISING_ENGINE_HUB),
+        (_stars_without_hubs(), {}, P.ISING_ENGINE_PERSISTENT_GRID),
+        (synth.zipf_config_graph(20011, 2.1, 4, 3000, 5), {"mode": P.ISING_MODE_RACY},
+         P.ISING_ENGINE_PERSISTENT_GRID),
         (synth.torus_graph(96, 2, weights="pm1"), {"mode": P.ISING_MODE_RACY},
          P.ISING_ENGINE_PERSISTENT_GRID),
         (synth.torus_graph(96, 2, weights="pm1"), {"kind": P.ISING_SCHED_NFLIP, "n0": 50},
