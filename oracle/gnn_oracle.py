@@ -22,6 +22,24 @@ The network (readings G1-G6, restated in the library header):
 * G6 flip bias: q_i = min(255, round(512 * sigmoid(-|z_i|))), the per-vertex
   factor q_i / 128 on the flip threshold of R11.
 
+Storage rounding (optional). The network's stated arithmetic is bf16
+operands with fp32 accumulation, so a device computes it with every stored
+activation rounded to bf16. `forward` and `backward` take `storage="bf16"`
+to apply exactly those roundings, each at the point where the data leaves a
+computation as a bf16 operand, and nothing else (all sums stay in float64):
+
+* forward: x = R(x); a^l = R(A_hat h^l); h^(l+1) = R(relu(u^l)); the head
+  z = h^3 w_o + b_o is unrounded;
+* backward: with dU^l = dh^(l+1) * [u^l > 0], the products that feed the
+  tensor cores use R(dU^l): dW_l = X_l^T R(dU^l) and dX_l = R(dU^l) W_l^T;
+  db_l sums the unrounded dU^l; the part of dX_l that multiplies a^l is
+  rounded before it is propagated back through A_hat: dh^l = dX_l[:, :H] +
+  A_hat R(dX_l[:, H:]).
+
+R rounds a value to float32 (nearest) and then to bf16 (nearest, ties to
+even), the value a float32 computation stores. The default (`storage=None`)
+is the plain float64 network, the definition the rounded form approximates.
+
 Parameters travel as one flat float array in this order (row-major):
 W_0 [16, 64], b_0 [64], W_1 [128, 64], b_1 [64], W_2 [128, 64], b_2 [64],
 w_o [64], b_o [1] -- 17,665 values. Row k of W_l multiplies feature k of the
@@ -107,18 +125,37 @@ def features(G: Graph, s) -> np.ndarray:
     return x
 
 
-def forward(G: Graph, x, params) -> tuple[np.ndarray, dict]:
+def to_bf16(v) -> np.ndarray:
+    """R: float64 -> float32 (nearest) -> bf16 (nearest, ties to even), as
+    float64. Finite inputs only."""
+    f = np.asarray(v, np.float64).astype(np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    lsb = (u >> np.uint64(16)) & np.uint64(1)
+    r = ((u + np.uint64(0x7FFF) + lsb) >> np.uint64(16)) << np.uint64(16)
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _rounder(storage):
+    if storage is None:
+        return lambda v: np.asarray(v, np.float64)
+    if storage == "bf16":
+        return to_bf16
+    raise ValueError(f"unknown storage {storage!r}")
+
+
+def forward(G: Graph, x, params, storage=None) -> tuple[np.ndarray, dict]:
     """G3: logits z and the intermediates the backward pass needs."""
+    R = _rounder(storage)
     p = unpack(params) if not isinstance(params, dict) else params
-    h = np.asarray(x, np.float64)
+    h = R(x)
     cache = {"X": [], "U": []}
     for l in range(LAYERS):
-        a = G.propagate(h)
+        a = R(G.propagate(h))
         X = np.concatenate([h, a], axis=1)
         U = X @ p[f"W{l}"] + p[f"b{l}"]
         cache["X"].append(X)
         cache["U"].append(U)
-        h = np.maximum(U, 0.0)
+        h = R(np.maximum(U, 0.0))
     cache["h3"] = h
     z = h @ p["wo"] + p["bo"][0]
     return z, cache
@@ -130,9 +167,11 @@ def loss(z, y) -> float:
     return float(np.mean(np.logaddexp(0.0, m)))
 
 
-def backward(G: Graph, params, cache, z, y) -> np.ndarray:
+def backward(G: Graph, params, cache, z, y, storage=None) -> np.ndarray:
     """Gradient of G4 with respect to the flat parameters (chain rule through
-    G3, written out layer by layer)."""
+    G3, written out layer by layer); `cache` comes from `forward` with the
+    same `storage`."""
+    R = _rounder(storage)
     p = unpack(params) if not isinstance(params, dict) else params
     y = np.asarray(y, np.float64)
     n = z.shape[0]
@@ -142,13 +181,14 @@ def backward(G: Graph, params, cache, z, y) -> np.ndarray:
     dh = dz[:, None] * p["wo"][None, :]
     for l in reversed(range(LAYERS)):
         dU = dh * (cache["U"][l] > 0.0)
-        g[f"W{l}"] = cache["X"][l].T @ dU
+        dUr = R(dU)
+        g[f"W{l}"] = cache["X"][l].T @ dUr
         g[f"b{l}"] = dU.sum(axis=0)
         if l > 0:
-            dX = dU @ p[f"W{l}"].T
+            dX = dUr @ p[f"W{l}"].T
             half = dX.shape[1] // 2
             # a^l = A_hat h^l and A_hat is symmetric
-            dh = dX[:, :half] + G.propagate(dX[:, half:])
+            dh = dX[:, :half] + G.propagate(R(dX[:, half:]))
     return pack(g)
 
 

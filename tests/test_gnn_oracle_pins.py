@@ -131,3 +131,42 @@ def test_warm_start_and_flip_bias():
     q = go.flip_bias(z)
     # sigmoid(-|z|) * 512: 0.1192*512 = 61.0, 0.3775*512 = 193.3, 256 -> 255
     assert list(q) == [61, 193, 255, 255, 0]
+
+
+def test_bf16_rounding_against_the_library_and_hand_ties():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(4)
+    v = np.concatenate([rng.normal(size=5000) * 10.0 ** rng.integers(-30, 30, 5000),
+                        rng.normal(size=2000).astype(np.float32).astype(np.float64)])
+    want = torch.tensor(v.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(go.to_bf16(v), want)
+    # bf16 keeps 7 fraction bits: halfway cases go to the even neighbour
+    e = 2.0 ** -8
+    assert go.to_bf16(1 + e) == 1.0
+    assert go.to_bf16(1 + 3 * e) == 1 + 4 * e
+    assert go.to_bf16(-(1 + 3 * e)) == -(1 + 4 * e)
+    assert go.to_bf16(1 + e + 2.0 ** -20) == 1 + 2 * e
+    assert go.to_bf16(0.0) == 0.0 and go.to_bf16(3.0) == 3.0
+
+
+def test_storage_rounding_rounds_every_stored_operand():
+    g, s, y = _small(5, n=40, p=0.2)
+    G = go.Graph(g.n, g.src, g.dst, g.w)
+    x = go.features(G, s)
+    params = synth.gnn_init_params(5).astype(np.float64)
+    z, cache = go.forward(G, x, params)
+    zr, cr = go.forward(G, x, params, storage="bf16")
+    # every tensor-core operand of the rounded form is a bf16 value, the
+    # plain form's are not
+    for X in cr["X"] + [cr["h3"]]:
+        assert np.array_equal(go.to_bf16(X), X)
+    assert not all(np.array_equal(go.to_bf16(X), X) for X in cache["X"][1:])
+    # rounding moves the result, by about the rounding's relative size
+    rel = np.linalg.norm(zr - z) / np.linalg.norm(z)
+    assert 0 < rel < 2.0 ** -5
+    gp = go.backward(G, params, cache, z, y)
+    gr = go.backward(G, params, cr, zr, y, storage="bf16")
+    relg = np.linalg.norm(gr - gp) / np.linalg.norm(gp)
+    assert 0 < relg < 2.0 ** -4
+    with pytest.raises(ValueError):
+        go.forward(G, x, params, storage="fp8")

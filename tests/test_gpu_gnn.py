@@ -1,17 +1,40 @@
 """GPU parity of the flip bias (bit-exact against the oracle) and of the
 warm-start network (logits and gradients against the FP64 oracle).
 
-Tolerances of the network. The GPU uses bf16-rounded weights W_0..W_2 (the
-oracle is given the same rounded values) and stores every activation in
-bf16 between kernels (relative rounding 2^-9 per value). Emulating exactly
-those roundings in float64 on these graphs gives logits within 0.6 % of the
-exact network in norm and within 2 % element-wise (relative to |z| plus the
-rms logit), so the bars are 1e-2 in norm (the stated tolerance) and 5e-2
-element-wise. Gradients are compared per parameter block, also at 1e-2 in
-norm, with labels that agree with the input spins on 80 % of the vertices
-(as annealer labels do): emulated errors are 2e-3 there. With labels
-independent of the input the gradient is a sum that almost cancels and its
-relative error is not bounded by the arithmetic, so that case is not used.
+The network's arithmetic is bf16 operands with fp32 accumulation: the GPU
+uses bf16-rounded weights W_0..W_2 (the oracle is given the same rounded
+values) and keeps every activation in bf16 between kernels. Two oracle forms
+are compared:
+
+* the plain FP64 network (no activation rounding). Logits agree within the
+  stated 1e-2 relative tolerance in norm; element-wise the activation
+  rounding alone (relative 2^-9 per stored value) moves a logit by up to
+  2 % of |z| plus the rms logit, the bar used there.
+* the FP64 network with the same storage rounding (oracle `storage="bf16"`:
+  every value the GPU stores as bf16 is rounded at the same point, all sums
+  stay in float64). Against it every logit must agree to 1e-2 relative,
+  with a floor for logits that cancel their terms: |z - z_ref| <= 1e-2 *
+  max(|z_ref|, t / 2), t = sum_k |h3_k w_o,k| + |b_o| the size of the
+  logit's terms. At init a logit is a sum of 64 terms of either sign, so
+  |z| is often a tenth of t; there the error is set by the terms' rounding,
+  which fp32 and float64 resolve differently at about 1e-4 of the stored
+  values (a value whose fp32 and float64 results fall on either side of a
+  bf16 rounding boundary). An fp32 emulation of the network puts the
+  largest |dz| / t at 2.6e-3.
+
+Gradients are compared per parameter block at 1e-2 in norm against both
+forms, and element by element against the rounded form with the same
+floor rule (t the sum of the absolute terms of the element's sum, t / 4 as
+the floor). One relu whose pre-activation is within fp32 rounding of zero
+can switch sides between fp32 and float64 and move whole gradient entries,
+so the element-wise bar holds for all but 1 in 1000 entries and every entry
+stays within 1e-1. The labels agree with the input spins on 80 % of the
+vertices (as annealer labels do); with labels independent of the input the
+gradient is a sum that almost cancels and its relative error is not bounded
+by the arithmetic, so that case is not used. The 64 x 64 torus with +-1
+weights is left out of the element-wise gradient check: its vertices share
+a handful of feature vectors, so one pre-activation near zero is shared by
+thousands of vertices.
 """
 
 import numpy as np
@@ -69,10 +92,22 @@ def test_logits_match_fp64_oracle(name, pseed):
         P.ising_set_spins(h, s)
         z = P.ising_gnn_forward(net, h)
     G = go.Graph(g.n, g.src, g.dst, g.w)
-    z_or, _ = go.forward(G, go.features(G, s), effective_params(params))
+    pe = effective_params(params)
+    x = go.features(G, s)
+    # the plain FP64 network
+    z_or, _ = go.forward(G, x, pe)
     assert _norm_rel(z, z_or) <= 1e-2
     scale = np.abs(z_or) + np.sqrt(np.mean(z_or ** 2))
     assert np.all(np.abs(z - z_or) <= 5e-2 * scale)
+    # the FP64 network with the GPU's storage rounding: 1e-2 element-wise
+    z_rd, cache = go.forward(G, x, pe, storage="bf16")
+    d = go.unpack(pe)
+    t = np.abs(cache["h3"]) @ np.abs(d["wo"]) + abs(d["bo"][0])
+    err = np.abs(z.astype(np.float64) - z_rd)
+    ratio = err / np.maximum(np.abs(z_rd), t / 2)
+    print(f"{name} seed {pseed}: max |dz| / max(|z|, t/2) = {ratio.max():.2e}, max |dz| / t = "
+          f"{(err / t).max():.2e}, logits at the floor {np.mean(np.abs(z_rd) < t / 2):.2f}")
+    assert np.all(ratio <= 1e-2), (int(np.argmax(ratio)), float(ratio.max()))
 
 
 def test_logits_of_edgeless_and_single_vertex_graphs():
@@ -93,7 +128,27 @@ def test_logits_of_edgeless_and_single_vertex_graphs():
         assert np.all(np.abs(z - z_or) <= 1e-2 * terms)
 
 
-@pytest.mark.parametrize("name", ["er_int8", "zipf_hubs", "torus_pm1"])
+def _gradient_terms(G, params, cache, z, y):
+    """Per parameter, the sum of the absolute terms of its gradient sum in the
+    rounded oracle form (the same chain rule with every product taken in
+    absolute value at the last step)."""
+    p = go.unpack(params)
+    n = z.shape[0]
+    dz = -y / (1.0 + np.exp(y * z)) / n
+    T = {"wo": np.abs(cache["h3"]).T @ np.abs(dz), "bo": np.array([np.abs(dz).sum()])}
+    dh = dz[:, None] * p["wo"][None, :]
+    for l in reversed(range(3)):
+        dU = dh * (cache["U"][l] > 0.0)
+        dUr = go.to_bf16(dU)
+        T[f"W{l}"] = np.abs(cache["X"][l]).T @ np.abs(dUr)
+        T[f"b{l}"] = np.abs(dU).sum(axis=0)
+        if l > 0:
+            dX = dUr @ p[f"W{l}"].T
+            dh = dX[:, :64] + G.propagate(go.to_bf16(dX[:, 64:]))
+    return go.pack(T)
+
+
+@pytest.mark.parametrize("name", ["er_int8", "zipf_hubs", "torus_pm1", "int32_weights"])
 def test_gradients_match_fp64_oracle(name):
     g = GRAPHS[name]()
     s = _spins(g.n, 11)
@@ -105,14 +160,35 @@ def test_gradients_match_fp64_oracle(name):
         loss, grad = P.ising_gnn_gradients(net, h, y)
     G = go.Graph(g.n, g.src, g.dst, g.w)
     pe = effective_params(params)
-    z_or, cache = go.forward(G, go.features(G, s), pe)
-    assert loss == pytest.approx(go.loss(z_or, y.astype(np.float64)), rel=1e-3)
-    g_or = go.backward(G, pe, cache, z_or, y.astype(np.float64))
+    x = go.features(G, s)
+    yf = y.astype(np.float64)
+    z_or, cache = go.forward(G, x, pe)
+    assert loss == pytest.approx(go.loss(z_or, yf), rel=1e-3)
+    g_or = go.backward(G, pe, cache, z_or, yf)
+    z_rd, cache_rd = go.forward(G, x, pe, storage="bf16")
+    g_rd = go.backward(G, pe, cache_rd, z_rd, yf, storage="bf16")
+    t = _gradient_terms(G, pe, cache_rd, z_rd, yf)
     k = 0
+    elementwise = name != "torus_pm1"
+    report = []
     for blk, shape in go.SHAPES:
         size = int(np.prod(shape))
-        assert _norm_rel(grad[k:k + size], g_or[k:k + size]) <= 1e-2, blk
+        sl = slice(k, k + size)
+        assert _norm_rel(grad[sl], g_or[sl]) <= 1e-2, blk
+        assert _norm_rel(grad[sl], g_rd[sl]) <= 1e-2, blk
+        err = np.abs(grad[sl].astype(np.float64) - g_rd[sl])
+        tt = t[sl]
+        ratio = err / np.maximum(np.abs(g_rd[sl]), np.maximum(tt, 1e-300) / 4)
+        ratio[tt == 0] = 0.0
+        report.append(f"{blk} {ratio.max():.1e} ({int(np.sum(ratio > 1e-2))} > 1e-2)")
+        if elementwise:
+            # an entry whose terms are all zero (a unit that never fires) is
+            # an exact zero on both sides
+            assert np.all(err[tt == 0] == 0), blk
+            assert np.all(ratio <= 1e-1), (blk, int(np.argmax(ratio)), float(ratio.max()))
+            assert np.sum(ratio > 1e-2) <= size // 1000, (blk, int(np.sum(ratio > 1e-2)))
         k += size
+    print(name, "; ".join(report))
 
 
 def test_warm_start_and_bias_follow_the_logits():
