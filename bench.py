@@ -528,20 +528,19 @@ def run_warmstart(args, world, rank, P, torch, dist):
 
 
 def gnn_forward_bytes(n: int, nnz: int) -> int:
-    """Compulsory bytes of one forward pass of the warm-start network, by
-    kernel: row sums (CSR word, row id, neighbour spin per entry; an int4 per
-    row), features (sums, spin in; 8 bf16 features and c out), three
-    aggregations (CSR word, row id, c_j and the neighbour's feature row per
-    entry; one fp32 row out per vertex), three dense layers ([h, a] in, h'
-    out) and the head (h3 in, z out)."""
+    """Compulsory bytes of one forward pass of the warm-start network: row
+    sums (CSR word, row id, neighbour spin per entry; an int4 per row out),
+    features (sums, spin in; 8 bf16 features and c out), three layers (per
+    entry the CSR word, c_j and the neighbour's bf16 feature row; per row its
+    row bounds, c, its own row in and its 64-wide bf16 output) and the head
+    (h3 in, z out). The aggregate a never leaves the layer kernel, so it
+    moves no bytes."""
     rowsum = nnz * 9 + n * 16
     feats = n * (16 + 1 + 16 + 4)
-    agg8 = nnz * (12 + 16) + n * 32
-    agg64 = nnz * (12 + 128) + n * 256
-    mlp8 = n * (16 + 32 + 128)
-    mlp64 = n * (128 + 256 + 128)
+    layer8 = nnz * (8 + 16) + n * (12 + 16 + 128)
+    layer64 = nnz * (8 + 128) + n * (12 + 128 + 128)
     head = n * (128 + 4)
-    return rowsum + feats + agg8 + 2 * agg64 + mlp8 + 2 * mlp64 + head
+    return rowsum + feats + layer8 + 2 * layer64 + head
 
 
 def run_gnn(args, world, rank, P, torch, dist):

@@ -501,6 +501,19 @@ int ising_gnn_train_step(ising_gnn* net, ising_graph* g, const int8_t* labels, i
  * update parity, like ising_set_spins) and, if set_bias, G6 as g's flip bias.
  * Asynchronous on g's stream. */
 int ising_gnn_warm_start(ising_gnn* net, ising_graph* g, int set_bias);
+/* ising_gnn_batch_forward -- logits z (G3) of every vertex of every instance
+ * of batch b from replica `replica`'s spins, the instances taken together as
+ * one graph (no edge joins two instances, so each instance's logits are
+ * those of the instance alone): float[total vertices], instance by instance
+ * in batch order, each by vertex id; host (synchronises) or device.
+ * ISING_EINVAL for a replica the batch does not have. */
+int ising_gnn_batch_forward(ising_gnn* net, ising_batch* b, uint32_t replica, float* out_logits,
+                            int on_device);
+/* ising_gnn_batch_warm_start -- for replica `replica` (or every replica with
+ * ISING_ALL_REPLICAS): a forward pass from its spins, then G5 on its spins.
+ * Asynchronous on the batch's stream (the stream of its last anneal call). */
+#define ISING_ALL_REPLICAS 0xFFFFFFFFu
+int ising_gnn_batch_warm_start(ising_gnn* net, ising_batch* b, uint32_t replica);
 /* ising_gnn_launch_count -- kernels launched by this network handle. */
 int ising_gnn_launch_count(ising_gnn* net, uint64_t* out);
 /* ising_gnn_destroy -- free the network (NULL is ignored). */

@@ -57,12 +57,14 @@ EXPORTS = (
     "ising_gnn_warm_start", "ising_gnn_launch_count", "ising_gnn_destroy", "ising_debug_fault",
     "ising_engine_used", "ising_set_halo_sweeps", "ising_halo_info", "ising_plan_halo",
     "ising_convergence_region", "ising_batch_set_tuning", "ising_batch_tuning",
+    "ising_gnn_batch_forward", "ising_gnn_batch_warm_start",
 )
 ISING_ENGINE_USED_BLOCK = 6
 ISING_FAULT_NONE = 0
 ISING_FAULT_SKIP_ARRIVAL = 1
 ISING_FAULT_SHORT_COPY = 2
 ISING_GNN_NUM_PARAMS = 17665
+ISING_ALL_REPLICAS = 0xFFFFFFFF
 
 
 class IsingError(RuntimeError):
@@ -140,6 +142,8 @@ def lib():
         L.ising_gnn_gradients.argtypes = [vp, vp, vp, ctypes.c_int, vp, vp]
         L.ising_gnn_train_step.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_float, vp]
         L.ising_gnn_warm_start.argtypes = [vp, vp, ctypes.c_int]
+        L.ising_gnn_batch_forward.argtypes = [vp, vp, ctypes.c_uint32, vp, ctypes.c_int]
+        L.ising_gnn_batch_warm_start.argtypes = [vp, vp, ctypes.c_uint32]
         L.ising_gnn_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
         L.ising_gnn_destroy.argtypes = [vp]
         L.ising_gnn_destroy.restype = None
@@ -655,6 +659,22 @@ def ising_gnn_train_step(net: IsingGnn, g: IsingGraph, labels, lr: float, want_l
 
 def ising_gnn_warm_start(net: IsingGnn, g: IsingGraph, set_bias: bool = True) -> None:
     _check(lib().ising_gnn_warm_start(net.ptr, g.ptr, int(bool(set_bias))), "ising_gnn_warm_start")
+
+
+def ising_gnn_batch_forward(net: IsingGnn, b: IsingBatch, replica: int = 0, out=None):
+    """Logits of every instance of the batch from one replica's spins,
+    instance by instance in batch order, each by vertex id (numpy float32, or
+    into ``out``, a float32 numpy array or CUDA tensor)."""
+    total = ising_batch_info(b)["vertices"]
+    if out is None:
+        out = np.zeros(total, dtype=np.float32)
+    p, on_dev, _keep = _buffer(out, np.float32, total, True)
+    _check(lib().ising_gnn_batch_forward(net.ptr, b.ptr, replica, p, on_dev), "ising_gnn_batch_forward")
+    return out
+
+
+def ising_gnn_batch_warm_start(net: IsingGnn, b: IsingBatch, replica: int = ISING_ALL_REPLICAS) -> None:
+    _check(lib().ising_gnn_batch_warm_start(net.ptr, b.ptr, replica), "ising_gnn_batch_warm_start")
 
 
 def ising_gnn_launch_count(net: IsingGnn) -> int:

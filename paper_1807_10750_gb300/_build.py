@@ -22,6 +22,7 @@ BUILD_DIR = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["anneal.cu", "host_graph.cpp", "halo_plan.cpp", "energy_static.cu", "batch.cu", "gnn.cu"]
 HEADERS = ["host_graph.h", "philox.cuh", "sweep.cuh", "graph_handle.h", "block.cuh", "halo.cuh", "hub.cuh",
+           "batch_view.h",
            "host_parallel.h"]
 
 

@@ -442,7 +442,8 @@ void free_device(ising_graph* g) {
                   g->d_done, g->d_halo_hdr, g->d_halo_words, g->d_halo_slices, g->d_halo_gpos,
                   g->d_halo_imports, g->d_halo_nbrs, g->d_halo_exports, g->d_halo_quads, g->d_halo_flags,
                   g->d_spins2, g->d_hub_split, g->d_hub_end, g->d_hub_sums, g->d_hub_acc,
-                  g->d_hub_flips, g->d_hub_bits, g->d_hub_pflips, g->d_hub_blk};
+                  g->d_hub_flips, g->d_hub_bits, g->d_hub_pflips, g->d_hub_blk,
+                  g->d_gnn_hchunk, g->d_gnn_chunk_row};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }

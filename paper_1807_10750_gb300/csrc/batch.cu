@@ -27,6 +27,7 @@
 #include <vector>
 
 #include "../../include/ising.h"
+#include "batch_view.h"
 #include "host_graph.h"
 #include "philox.cuh"
 
@@ -376,6 +377,14 @@ struct ising_batch {
   int split = 1;  // threads per row (ising_batch_autotune)
   int tail = 0;   // classes up to this size decided by one warp
   float probe_ms[kTuneConfigs] = {};  // the autotuner's probe times
+  int64_t total_nnz = 0;
+  // the instances as one graph, for the warm-start network (batch_union)
+  int32_t* d_union_row_ptr = nullptr;
+  int32_t* d_union_vbase = nullptr;
+  int32_t* d_gnn_rowid = nullptr;
+  int32_t* d_gnn_hchunk = nullptr;
+  int32_t* d_gnn_chunk_row = nullptr;
+  int32_t gnn_num_chunks = -1;
 
   BatchDev dev() const {
     BatchDev d;
@@ -396,8 +405,10 @@ namespace {
 void batch_free(ising_batch* b) {
   if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
   if (b->graph) cudaGraphDestroy(b->graph);
-  void* ptrs[] = {b->d_graphs, b->d_order,  b->d_row_ptr, b->d_adj,    b->d_orig,
-                  b->d_class_pos, b->d_spins, b->d_flips, b->d_work, b->d_energy2};
+  void* ptrs[] = {b->d_graphs,       b->d_order,       b->d_row_ptr,    b->d_adj,
+                  b->d_orig,         b->d_class_pos,   b->d_spins,      b->d_flips,
+                  b->d_work,         b->d_energy2,     b->d_union_row_ptr, b->d_union_vbase,
+                  b->d_gnn_rowid,    b->d_gnn_hchunk,  b->d_gnn_chunk_row};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -422,6 +433,19 @@ int batch_enter(ising_batch* b) {
       return ISING_ECUDA;            \
     }                                \
   } while (0)
+
+// Row table of the disjoint union: every instance's rows by position, with
+// the instance's first position beside each row.
+__global__ void union_rows_kernel(const BatchGraph* graphs, const int32_t* row_ptr, int num_graphs,
+                                  int32_t* urow, int32_t* vbase) {
+  for (int gi = blockIdx.x; gi < num_graphs; gi += gridDim.x) {
+    const BatchGraph G = graphs[gi];
+    for (int v = threadIdx.x; v < G.n; v += blockDim.x) {
+      urow[G.vtx_base + v] = row_ptr[G.row_base + v];
+      vbase[G.vtx_base + v] = G.vtx_base;
+    }
+  }
+}
 
 template <typename T>
 cudaError_t upload(T** dst, const std::vector<T>& src, cudaStream_t s) {
@@ -579,6 +603,7 @@ int ising_batch_create(int32_t num_graphs, const int32_t* n, const int64_t* m, c
       edge_off += hg.nnz;
       vtx += hg.n;
     }
+    b->total_nnz = edge_off;
   } catch (const std::bad_alloc&) {
     rc = ISING_ENOMEM;
   }
@@ -623,6 +648,47 @@ int ising_batch_create(int32_t num_graphs, const int32_t* n, const int64_t* m, c
   *out = b;
   return ISING_OK;
 }
+
+}  // extern "C"
+
+namespace isingx {
+
+int batch_union(ising_batch* b, BatchUnion* out) {
+  const int rc = batch_enter(b);
+  if (rc != ISING_OK) return rc;
+  const int32_t n = b->vtx_base.back() + b->n.back();
+  if (b->d_union_row_ptr == nullptr) {
+    BATCH_CUDA(b, cudaMalloc(reinterpret_cast<void**>(&b->d_union_row_ptr), sizeof(int32_t) * (size_t(n) + 1)));
+    BATCH_CUDA(b, cudaMalloc(reinterpret_cast<void**>(&b->d_union_vbase), sizeof(int32_t) * std::max<size_t>(n, 1)));
+    union_rows_kernel<<<std::min(b->num_graphs, b->num_sms * 8), 256, 0, b->stream>>>(
+        b->d_graphs, b->d_row_ptr, b->num_graphs, b->d_union_row_ptr, b->d_union_vbase);
+    b->launches++;
+    BATCH_CUDA(b, cudaGetLastError());
+    const int32_t end = static_cast<int32_t>(b->total_nnz);
+    BATCH_CUDA(b, cudaMemcpyAsync(b->d_union_row_ptr + n, &end, sizeof(int32_t), cudaMemcpyHostToDevice, b->stream));
+    BATCH_CUDA(b, cudaStreamSynchronize(b->stream));
+  }
+  out->device = b->device;
+  out->stream = b->stream;
+  out->num_sms = b->num_sms;
+  out->n = n;
+  out->nnz = b->total_nnz;
+  out->replicas = b->replicas;
+  out->row_ptr = b->d_union_row_ptr;
+  out->adj = b->d_adj;
+  out->vbase = b->d_union_vbase;
+  out->orig = b->d_orig;
+  out->spins = b->d_spins;
+  out->rowid = &b->d_gnn_rowid;
+  out->hchunk = &b->d_gnn_hchunk;
+  out->chunk_row = &b->d_gnn_chunk_row;
+  out->num_chunks = &b->gnn_num_chunks;
+  return ISING_OK;
+}
+
+}  // namespace isingx
+
+extern "C" {
 
 void ising_batch_destroy(ising_batch* b) {
   if (b == nullptr) return;

@@ -6,26 +6,34 @@
 // in include/ising.h (G1-G6); this file holds its inference and training
 // kernels and their part of the C ABI.
 //
-// Data path, all by graph position (colour order) on the graph's stream:
-//   rowsum:    per-row sums of |w|, 1, w and w * s_j over the CSR entries,
-//              lanes over entries, segmented warp sums, int atomics at row
-//              ends (exact).
-//   features:  x (n x 8 bf16) and c = (d + 1)^-1/2 (G1, G2).
-//   aggregate: a = A_hat h, split by CSR entries (not rows), so a hub row of
-//              10k entries spreads over many warps: width 8 keeps one entry
-//              per lane with a segmented warp sum, width 64 one entry per
-//              warp step with two features per lane; fp32 atomics at row
-//              ends into a zeroed (forward) or pre-filled (backward) buffer.
-//   mlp:       u = [h, a] W + b, relu, on tensor cores (mma.sync m16n8k16,
-//              bf16 operands from padded shared-memory tiles via ldmatrix,
-//              fp32 accumulation); 64-row tiles, four warps per block.
-//   head:      z = h3 w_o + b_o per row (fp32), with the loss G4 and its
-//              gradient when labels are given.
-//   backward:  per layer one kernel forms dU = dh * (h' > 0), dX = dU W^T
-//              (tensor cores) and dW += X^T dU (tensor cores, partial sums
-//              in registers, fp32 atomics per block), db in fp32.
-//   adam:      fp32 master weights, moments, and the bf16 copies the mma
-//              kernels read.
+// A graph handle, or a batch's instances taken together as one graph (their
+// disjoint union), is seen through a GView; everything runs by graph
+// position (colour order) on the graph's stream:
+//   rowsum:   per-row sums of |w|, 1, w and w * s_j over the CSR entries,
+//             lanes over entries, segmented warp sums, int atomics at row
+//             ends (exact).
+//   features: x (n x 8 bf16) and c = (d + 1)^-1/2 (G1, G2).
+//   chunks:   rows with more than kHeavy entries (hubs) are summed in chunks
+//             of kChunk entries, one warp per chunk, into per-chunk partial
+//             sums of c_j w_rj h_j; the layer kernels add a heavy row's
+//             partials in order. Every aggregate is thus summed in a fixed
+//             order (no float atomics) and no tile waits on a hub.
+//   layer:    one kernel per layer fuses the aggregation into the dense
+//             layer: a 64-row tile gathers a = A_hat h for its rows (a
+//             sub-warp per row, lanes over features), rounds [h, a] to bf16
+//             into shared memory, and multiplies by W on tensor cores
+//             (mma.sync m16n8k16, ldmatrix, fp32 accumulation); bias and
+//             relu in the epilogue. a never goes to memory except, when
+//             training, as the bf16 operand the backward pass reuses.
+//   head:     z = h3 w_o + b_o per row (fp32), with the loss G4 and its
+//             gradient when labels are given.
+//   backward: one kernel per layer forms dL/dh' = (direct part) + A_hat da
+//             of the layer above (the same fused gather), dU = dL/dh' *
+//             (h' > 0), dX = dU W^T (tensor cores; direct part fp32, da
+//             bf16) and dW += X^T dU (tensor cores, partial sums in
+//             registers, fp32 atomics per block), db in fp32.
+//   adam:     fp32 master weights, moments, and the bf16 copies the mma
+//             kernels read.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -36,6 +44,7 @@
 #include <vector>
 
 #include "../../include/ising.h"
+#include "batch_view.h"
 #include "graph_handle.h"
 #include "sweep.cuh"
 
@@ -56,9 +65,10 @@ constexpr int kOffBo = kOffWo + kH;
 constexpr int kNumParams = kOffBo + 1;
 static_assert(kNumParams == ISING_GNN_NUM_PARAMS, "parameter layout");
 
-constexpr int kTileRows = 64;     // rows per mma tile
-constexpr int kMlpThreads = 128;  // four warps, 16 rows each
-constexpr int kAggChunk = 256;    // CSR entries per warp in the width-64 aggregation
+constexpr int kTile = 64;           // rows per tile of the layer kernels
+constexpr int kLayerThreads = 256;  // eight warps
+constexpr int kChunk = 64;          // CSR entries per chunk of a heavy row
+constexpr int kHeavy = 64;          // rows with more entries are summed by chunks
 
 using bf16 = __nv_bfloat16;
 using bf162 = __nv_bfloat162;
@@ -80,6 +90,26 @@ __device__ __forceinline__ void edge_at(const EdgeView& e, int k, int& col, int&
     w = __ldg(e.w + k);
   }
 }
+
+// The graph as the network sees it: a graph handle, or a batch's instances
+// as one graph (columns local to an instance, shifted by vbase).
+struct GView {
+  int n;
+  long long nnz;
+  const int32_t* row_ptr;
+  EdgeView ev;
+  const int32_t* vbase;  // per row: added to its entries' columns (null: none)
+  const int32_t* rowid;  // row of every entry
+  const uint8_t* spins;  // spin of position p is -1 when bit `shift` of spins[p] is set
+  int shift;
+  const int32_t* hchunk;     // per row: first chunk of a heavy row, else -1 (null: no heavy row)
+  const int32_t* chunk_row;  // row of every chunk
+  int num_chunks;
+};
+
+__device__ __forceinline__ int spin_of(const GView& v, int p) { return 1 - 2 * ((v.spins[p] >> v.shift) & 1); }
+
+__device__ __forceinline__ int col_base(const GView& v, int row) { return v.vbase ? __ldg(v.vbase + row) : 0; }
 
 __device__ __forceinline__ int spin_at(const int8_t* spins, int v) { return 1 - 2 * (spins[v] & 1); }
 
@@ -109,22 +139,21 @@ __global__ void rowid_kernel(const int32_t* row_ptr, int n, int32_t* rowid) {
 }
 
 // sums[v] = (sum |w|, degree, sum w, f = sum w s_j) of row v (zeroed first).
-__global__ void rowsum_kernel(EdgeView ev, const int32_t* rowid, const int8_t* spins, int nnz,
-                              int4* sums) {
+__global__ void rowsum_kernel(GView v, int4* sums) {
   const int lane = threadIdx.x & 31;
   const long long nw = (static_cast<long long>(gridDim.x) * blockDim.x) >> 5;
   for (long long base = ((static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5) * 32;
-       base < nnz; base += nw * 32) {
+       base < v.nnz; base += nw * 32) {
     const long long e = base + lane;
     int row = -1, a = 0, c = 0, ws = 0, f = 0;
-    if (e < nnz) {
+    if (e < v.nnz) {
       int col, w;
-      edge_at(ev, static_cast<int>(e), col, w);
-      row = __ldg(rowid + e);
+      edge_at(v.ev, static_cast<int>(e), col, w);
+      row = __ldg(v.rowid + e);
       a = w < 0 ? -w : w;
       c = 1;
       ws = w;
-      f = w * spin_at(spins, col);
+      f = w * spin_of(v, col + col_base(v, row));
     }
     a = seg_sum(a, row, lane);
     c = seg_sum(c, row, lane);
@@ -140,14 +169,14 @@ __global__ void rowsum_kernel(EdgeView ev, const int32_t* rowid, const int8_t* s
 }
 
 // G1/G2: x_v = [s, f c^2, s f c^2, log(1 + deg) / 8, (sum w) c^2, 1, 0, 0].
-__global__ void features_kernel(const int4* sums, const int8_t* spins, int n, uint4* x, float* cvec) {
-  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-    const int4 q = sums[v];
-    const float s = static_cast<float>(spin_at(spins, v));
+__global__ void features_kernel(GView v, const int4* sums, uint4* x, float* cvec) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < v.n; p += gridDim.x * blockDim.x) {
+    const int4 q = sums[p];
+    const float s = static_cast<float>(spin_of(v, p));
     const float d1 = static_cast<float>(q.x) + 1.0f;
     const float c2 = 1.0f / d1;
     const float f = static_cast<float>(q.w);
-    cvec[v] = 1.0f / sqrtf(d1);
+    cvec[p] = 1.0f / sqrtf(d1);
     bf162 p0 = __floats2bfloat162_rn(s, f * c2);
     bf162 p1 = __floats2bfloat162_rn(s * f * c2, log1pf(static_cast<float>(q.y)) * 0.125f);
     bf162 p2 = __floats2bfloat162_rn(static_cast<float>(q.z) * c2, 1.0f);
@@ -157,119 +186,216 @@ __global__ void features_kernel(const int4* sums, const int8_t* spins, int n, ui
     memcpy(&out.y, &p1, 4);
     memcpy(&out.z, &p2, 4);
     memcpy(&out.w, &p3, 4);
-    x[v] = out;
+    x[p] = out;
   }
 }
 
-// out[row] += c_row * sum_j w_rj c_j h_j for width-8 rows (one entry per lane).
-__global__ void aggregate8_kernel(EdgeView ev, const int32_t* rowid, const float* cvec,
-                                  const uint4* h, int nnz, float* out) {
-  const int lane = threadIdx.x & 31;
-  const long long nw = (static_cast<long long>(gridDim.x) * blockDim.x) >> 5;
-  for (long long base = ((static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5) * 32;
-       base < nnz; base += nw * 32) {
-    const long long e = base + lane;
-    int row = -1;
-    float v[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) v[k] = 0.0f;
-    if (e < nnz) {
-      int col, w;
-      edge_at(ev, static_cast<int>(e), col, w);
-      row = __ldg(rowid + e);
-      const float coef = static_cast<float>(w) * __ldg(cvec + col);
-      const uint4 raw = __ldg(h + col);
-      const uint32_t words[4] = {raw.x, raw.y, raw.z, raw.w};
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        bf162 p;
-        memcpy(&p, &words[k], 4);
-        const float2 f2 = __bfloat1622float2(p);
-        v[2 * k] = coef * f2.x;
-        v[2 * k + 1] = coef * f2.y;
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < 8; ++k) v[k] = seg_sum(v[k], row, lane);
-    if (seg_tail(row, lane)) {
-      const float cr = __ldg(cvec + row);
-#pragma unroll
-      for (int k = 0; k < 8; ++k) atomicAdd(out + static_cast<size_t>(row) * 8 + k, cr * v[k]);
-    }
+// ---------------------------------------------------------------------------
+// Gathers. A row of width D is read by a sub-warp of G lanes, F features per
+// lane: width 64 as 16 lanes x 4 (8-byte loads), width 8 as 4 lanes x 2.
+
+template <int D>
+struct RowIO;
+
+template <>
+struct RowIO<64> {
+  static constexpr int G = 16, F = 4;
+  using T = uint2;
+  static __device__ __forceinline__ T load(const bf16* p, long long row, int q) {
+    return __ldg(reinterpret_cast<const uint2*>(p) + row * 16 + q);
   }
-}
+  static __device__ __forceinline__ void store(bf16* p, long long row, int q, T val) {
+    reinterpret_cast<uint2*>(p)[row * 16 + q] = val;
+  }
+  static __device__ __forceinline__ void put(bf16* s, T val) { *reinterpret_cast<uint2*>(s) = val; }
+  static __device__ __forceinline__ void add(float (&acc)[F], float coef, T val) {
+    bf162 a, b;
+    memcpy(&a, &val.x, 4);
+    memcpy(&b, &val.y, 4);
+    const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+    acc[0] += coef * fa.x;
+    acc[1] += coef * fa.y;
+    acc[2] += coef * fb.x;
+    acc[3] += coef * fb.y;
+  }
+  static __device__ __forceinline__ T pack(const float (&acc)[F]) {
+    T out;
+    bf162 a = __floats2bfloat162_rn(acc[0], acc[1]), b = __floats2bfloat162_rn(acc[2], acc[3]);
+    memcpy(&out.x, &a, 4);
+    memcpy(&out.y, &b, 4);
+    return out;
+  }
+};
 
-// out[row] += c_row * sum_j w_rj c_j h_j for width-64 rows. A warp walks
-// kAggChunk consecutive CSR entries, 32 at a time: each lane decodes one
-// entry (row, column, w c_col) into a per-warp shared buffer, then the two
-// half-warps take alternate entries -- lane l of a half owns features
-// 4(l mod 16) .. +3 and loads them with one 8-byte read -- four entries in
-// flight per half. Rows are sorted, so each half flushes its running sum with
-// one vector atomic where its row changes.
-__device__ __forceinline__ void agg_flush(float* out, const float* cvec, int row, int hl,
-                                          float4 acc) {
-  if (row < 0) return;
-  const float cr = __ldg(cvec + row);
-  atomicAdd(reinterpret_cast<float4*>(out + static_cast<size_t>(row) * 64 + 4 * hl),
-            make_float4(cr * acc.x, cr * acc.y, cr * acc.z, cr * acc.w));
-}
+template <>
+struct RowIO<8> {
+  static constexpr int G = 4, F = 2;
+  using T = uint32_t;
+  static __device__ __forceinline__ T load(const bf16* p, long long row, int q) {
+    return __ldg(reinterpret_cast<const uint32_t*>(p) + row * 4 + q);
+  }
+  static __device__ __forceinline__ void store(bf16* p, long long row, int q, T val) {
+    reinterpret_cast<uint32_t*>(p)[row * 4 + q] = val;
+  }
+  static __device__ __forceinline__ void put(bf16* s, T val) { *reinterpret_cast<uint32_t*>(s) = val; }
+  static __device__ __forceinline__ void add(float (&acc)[F], float coef, T val) {
+    bf162 a;
+    memcpy(&a, &val, 4);
+    const float2 fa = __bfloat1622float2(a);
+    acc[0] += coef * fa.x;
+    acc[1] += coef * fa.y;
+  }
+  static __device__ __forceinline__ T pack(const float (&acc)[F]) {
+    bf162 a = __floats2bfloat162_rn(acc[0], acc[1]);
+    T out;
+    memcpy(&out, &a, 4);
+    return out;
+  }
+};
 
-__global__ void __launch_bounds__(256)
-    aggregate64_kernel(EdgeView ev, const int32_t* rowid, const float* cvec, const bf162* h,
-                       int nnz, float* out) {
-  __shared__ int4 meta[8][32];  // per warp of the 256-thread block
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int half = lane >> 4, hl = lane & 15;
-  const long long warp = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  const long long e_begin = warp * kAggChunk;
-  if (e_begin >= nnz) return;
-  const long long e_end = e_begin + kAggChunk < nnz ? e_begin + kAggChunk : nnz;
-  const uint2* hq = reinterpret_cast<const uint2*>(h);  // 4 bf16 per uint2, 16 per row
-  int cur = -1;
-  float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-  for (long long b = e_begin; b < e_end; b += 32) {
-    const long long e = b + lane;
-    int4 m = make_int4(-1, 0, 0, 0);
-    if (e < e_end) {
-      int col, w;
-      edge_at(ev, static_cast<int>(e), col, w);
-      m.x = __ldg(rowid + e);
-      m.y = col;
-      m.z = __float_as_int(static_cast<float>(w) * __ldg(cvec + col));
-    }
-    meta[wib][lane] = m;
-    __syncwarp();
-#pragma unroll
-    for (int j0 = 0; j0 < 32; j0 += 8) {
-      int4 mm[4];
-      uint2 hv[4];
+// acc += sum over entries [e0, e1) of w c_col src[col] (this lane's
+// features). Width 64: the 16 lanes of a sub-warp decode up to 64 entries
+// at once (column words and c_col, four per lane), then every lane reads its
+// 8 bytes of each of those rows, eight rows in flight -- two dependent memory
+// rounds per 64 entries. Width 8:
+// each of the 4 lanes takes every fourth entry and whole 16-byte rows, four
+// entries in flight, and the lanes' sums are combined at the end. Both fix
+// the order of every sum.
+template <int D>
+__device__ __forceinline__ void gather_entries(const GView& v, const float* __restrict__ c,
+                                               const bf16* __restrict__ src, int e0, int e1, int base,
+                                               int q, float (&acc)[RowIO<D>::F]) {
+  using IO = RowIO<D>;
+  constexpr int G = IO::G;
+  const unsigned lane = threadIdx.x & 31;
+  const unsigned mask = ((1u << G) - 1u) << (lane & ~(G - 1u));
+  if constexpr (D == 64) {
+    // up to 64 entries per round: lane q decodes entries q, q + 16, q + 32,
+    // q + 48 of the round (slots 0..3)
+    for (int b = e0; b < e1; b += 4 * G) {
+      const int cnt = min(4 * G, e1 - b);
+      int col[4];
+      float cf[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        mm[u] = meta[wib][j0 + 2 * u + half];
-        hv[u] = mm[u].x >= 0 ? hq[static_cast<size_t>(mm[u].y) * 16 + hl] : make_uint2(0u, 0u);
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        if (mm[u].x < 0) continue;  // past the chunk's end
-        if (mm[u].x != cur) {
-          agg_flush(out, cvec, cur, hl, acc);
-          acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-          cur = mm[u].x;
+        col[u] = 0;
+        cf[u] = 0.0f;
+        if (u * G + q < cnt) {
+          int w;
+          edge_at(v.ev, b + u * G + q, col[u], w);
+          col[u] += base;
+          cf[u] = static_cast<float>(w);
         }
-        const float coef = __int_as_float(mm[u].z);
-        bf162 p0, p1;
-        memcpy(&p0, &hv[u].x, 4);
-        memcpy(&p1, &hv[u].y, 4);
-        const float2 f0 = __bfloat1622float2(p0), f1 = __bfloat1622float2(p1);
-        acc.x += coef * f0.x;
-        acc.y += coef * f0.y;
-        acc.z += coef * f1.x;
-        acc.w += coef * f1.y;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (u * G + q < cnt) cf[u] *= __ldg(c + col[u]);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (u * G >= cnt) break;
+#pragma unroll
+        for (int j0 = 0; j0 < G; j0 += 8) {
+          if (u * G + j0 >= cnt) break;
+          typename IO::T hv[8];
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const int cj = __shfl_sync(mask, col[u], j0 + k, G);
+            hv[k] = u * G + j0 + k < cnt ? IO::load(src, cj, q) : typename IO::T{};
+          }
+#pragma unroll
+          for (int k = 0; k < 8; ++k) IO::add(acc, __shfl_sync(mask, cf[u], j0 + k, G), hv[k]);
+        }
       }
     }
-    __syncwarp();
+  } else {
+    float a8[8] = {};
+    for (int b = e0 + q; b < e1; b += 4 * G) {
+      int col[4];
+      float cf[4];
+      uint4 hv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        col[u] = 0;
+        cf[u] = 0.0f;
+        if (b + u * G < e1) {
+          int w;
+          edge_at(v.ev, b + u * G, col[u], w);
+          col[u] += base;
+          cf[u] = static_cast<float>(w);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const bool ok = b + u * G < e1;
+        cf[u] *= ok ? __ldg(c + col[u]) : 0.0f;
+        hv[u] = ok ? __ldg(reinterpret_cast<const uint4*>(src) + col[u]) : make_uint4(0, 0, 0, 0);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const uint32_t words[4] = {hv[u].x, hv[u].y, hv[u].z, hv[u].w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          bf162 p;
+          memcpy(&p, &words[k], 4);
+          const float2 f2 = __bfloat1622float2(p);
+          a8[2 * k] += cf[u] * f2.x;
+          a8[2 * k + 1] += cf[u] * f2.y;
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      a8[k] += __shfl_xor_sync(mask, a8[k], 1, G);
+      a8[k] += __shfl_xor_sync(mask, a8[k], 2, G);
+    }
+#pragma unroll
+    for (int f = 0; f < IO::F; ++f) acc[f] += a8[IO::F * q + f];
   }
-  agg_flush(out, cvec, cur, hl, acc);
+}
+
+// a_r = c_r * sum_j w_rj c_j src_j for one row (this lane's features): a
+// light row by its entries, a heavy row by its chunks' partial sums.
+template <int D>
+__device__ __forceinline__ void aggregate_row(const GView& v, const float* __restrict__ c,
+                                              const bf16* __restrict__ src, const float* __restrict__ partial,
+                                              int r, int q, float (&acc)[RowIO<D>::F]) {
+  constexpr int F = RowIO<D>::F;
+  const int e0 = __ldg(v.row_ptr + r), e1 = __ldg(v.row_ptr + r + 1);
+  const int hc = v.hchunk ? __ldg(v.hchunk + r) : -1;
+  if (hc >= 0) {
+    const int nc = (e1 - e0 + kChunk - 1) / kChunk;
+    for (int k = 0; k < nc; ++k) {
+      const float* pp = partial + static_cast<size_t>(hc + k) * D + q * F;
+#pragma unroll
+      for (int f = 0; f < F; ++f) acc[f] += pp[f];
+    }
+  } else {
+    gather_entries<D>(v, c, src, e0, e1, col_base(v, r), q, acc);
+  }
+  const float cr = __ldg(c + r);
+#pragma unroll
+  for (int f = 0; f < F; ++f) acc[f] *= cr;
+}
+
+// partial[k] = sum over chunk k's entries of w c_col src[col] (width D), one
+// sub-warp per chunk.
+template <int D>
+__global__ void __launch_bounds__(256)
+    chunk_partial_kernel(GView v, const float* __restrict__ c, const bf16* __restrict__ src,
+                         float* __restrict__ partial) {
+  using IO = RowIO<D>;
+  const int lane = threadIdx.x & 31, q = lane % IO::G;
+  const int subs = (gridDim.x * blockDim.x) / IO::G;
+  for (int k = (blockIdx.x * blockDim.x + threadIdx.x) / IO::G; k < v.num_chunks; k += subs) {
+    const int row = __ldg(v.chunk_row + k);
+    const int e0 = __ldg(v.row_ptr + row) + (k - __ldg(v.hchunk + row)) * kChunk;
+    const int e1 = min(e0 + kChunk, __ldg(v.row_ptr + row + 1));
+    float acc[IO::F] = {};
+    gather_entries<D>(v, c, src, e0, e1, col_base(v, row), q, acc);
+    float* out = partial + static_cast<size_t>(k) * D + q * IO::F;
+#pragma unroll
+    for (int f = 0; f < IO::F; ++f) out[f] = acc[f];
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -307,78 +433,75 @@ __device__ __forceinline__ uint32_t pack_bf162(float x, float y) {
   return u;
 }
 
-// Stage rows [r0, r0 + 64) of X = [h, a] (bf16 h, fp32 a rounded to bf16)
-// into sX (row stride KP elements); rows past n read as zero.
-template <int D, int KP>
-__device__ __forceinline__ void stage_x(bf16* sX, const bf16* h, const float* a, int r0, int n) {
-  constexpr int HC = D / 8;      // 16-byte chunks of an h row
-  constexpr int CH = 2 * HC;     // chunks of an X row
-  for (int idx = threadIdx.x; idx < kTileRows * CH; idx += blockDim.x) {
-    const int r = idx / CH, ch = idx % CH;
-    const int row = r0 + r;
-    uint4 val = make_uint4(0, 0, 0, 0);
-    if (row < n) {
-      if (ch < HC) {
-        val = *reinterpret_cast<const uint4*>(h + static_cast<size_t>(row) * D + ch * 8);
-      } else {
-        const float4* src = reinterpret_cast<const float4*>(a + static_cast<size_t>(row) * D + (ch - HC) * 8);
-        const float4 f0 = src[0], f1 = src[1];
-        val.x = pack_bf162(f0.x, f0.y);
-        val.y = pack_bf162(f0.z, f0.w);
-        val.z = pack_bf162(f1.x, f1.y);
-        val.w = pack_bf162(f1.z, f1.w);
-      }
-    }
-    *reinterpret_cast<uint4*>(sX + r * KP + ch * 8) = val;
-  }
-}
-
-// Forward layer: hout = relu([h, a] W + b), W [2D][64] bf16 row-major.
+// Forward layer: hout = relu([h, a] W + b) with a = A_hat h gathered by the
+// tile itself; W [2D][64] bf16 row-major. With a_store, a (bf16) is kept for
+// the backward pass. Eight warps: the gather takes two rows (D = 64) or
+// eight rows (D = 8) per warp at a time; the product gives each warp 16
+// rows x 32 columns.
 template <int D>
-__global__ void __launch_bounds__(kMlpThreads)
-    mlp_fwd_kernel(const bf16* __restrict__ h, const float* __restrict__ a,
-                   const bf16* __restrict__ W, const float* __restrict__ bias, int n,
-                   bf16* __restrict__ hout) {
+__global__ void __launch_bounds__(kLayerThreads)
+    layer_fwd_kernel(GView v, const float* __restrict__ c, const bf16* __restrict__ h,
+                     const float* __restrict__ partial, const bf16* __restrict__ W,
+                     const float* __restrict__ bias, bf16* __restrict__ a_store, bf16* __restrict__ hout) {
+  using IO = RowIO<D>;
   constexpr int K = 2 * D, KP = K + 8, NP = kH + 8;
+  constexpr int RPW = 32 / IO::G;  // rows a warp gathers at a time
   __shared__ __align__(16) bf16 sW[K * NP];
-  __shared__ __align__(16) bf16 sX[kTileRows * KP];
+  __shared__ __align__(16) bf16 sX[kTile * KP];
   __shared__ float sB[kH];
   for (int idx = threadIdx.x; idx < K * (kH / 8); idx += blockDim.x) {
-    const int k = idx / (kH / 8), c = idx % (kH / 8);
-    *reinterpret_cast<uint4*>(sW + k * NP + c * 8) = *reinterpret_cast<const uint4*>(W + k * kH + c * 8);
+    const int k = idx / (kH / 8), cc = idx % (kH / 8);
+    *reinterpret_cast<uint4*>(sW + k * NP + cc * 8) = *reinterpret_cast<const uint4*>(W + k * kH + cc * 8);
   }
   if (threadIdx.x < kH) sB[threadIdx.x] = bias[threadIdx.x];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int sub = lane / IO::G, q = lane % IO::G;
   const int g = lane >> 2, t = lane & 3;
-  for (int tile = blockIdx.x; tile * kTileRows < n; tile += gridDim.x) {
+  const int wm = wid & 3, wn = wid >> 2;
+  const int n = v.n;
+  for (int tile = blockIdx.x; tile * kTile < n; tile += gridDim.x) {
+    const int r0 = tile * kTile;
     __syncthreads();
-    stage_x<D, KP>(sX, h, a, tile * kTileRows, n);
+    for (int rl = wid * RPW + sub; rl < kTile; rl += 8 * RPW) {
+      const int r = r0 + rl;
+      typename IO::T own{}, ab{};
+      if (r < n) {
+        own = IO::load(h, r, q);
+        float acc[IO::F] = {};
+        aggregate_row<D>(v, c, h, partial, r, q, acc);
+        ab = IO::pack(acc);
+        if (a_store != nullptr) IO::store(a_store, r, q, ab);
+      }
+      IO::put(sX + rl * KP + q * IO::F, own);
+      IO::put(sX + rl * KP + D + q * IO::F, ab);
+    }
     __syncthreads();
-    float acc[8][4];
+    float acc[4][4];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.0f;
+    for (int i = 0; i < 4; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.0f;
 #pragma unroll
     for (int ks = 0; ks < K / 16; ++ks) {
       uint32_t af[4];
-      ldsm_x4(af, sX + (16 * wid + (lane & 7) + ((lane >> 3) & 1) * 8) * KP + ks * 16 + (lane >> 4) * 8);
+      ldsm_x4(af, sX + (16 * wm + (lane & 7) + ((lane >> 3) & 1) * 8) * KP + ks * 16 + (lane >> 4) * 8);
 #pragma unroll
-      for (int np = 0; np < 4; ++np) {
+      for (int np = 0; np < 2; ++np) {
         uint32_t bfr[4];
-        ldsm_x4_t(bfr, sW + (ks * 16 + (lane & 7) + ((lane >> 3) & 1) * 8) * NP + np * 16 + (lane >> 4) * 8);
+        ldsm_x4_t(bfr, sW + (ks * 16 + (lane & 7) + ((lane >> 3) & 1) * 8) * NP + 32 * wn + np * 16 +
+                           (lane >> 4) * 8);
         mma_bf16(acc[2 * np], af, bfr[0], bfr[1]);
         mma_bf16(acc[2 * np + 1], af, bfr[2], bfr[3]);
       }
     }
-    const int r0 = tile * kTileRows + 16 * wid + g;
+    const int rr = r0 + 16 * wm + g;
 #pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-      const int col = nt * 8 + 2 * t;
+    for (int nt = 0; nt < 4; ++nt) {
+      const int col = 32 * wn + nt * 8 + 2 * t;
       const float b0 = sB[col], b1 = sB[col + 1];
-      if (r0 < n)
-        *reinterpret_cast<uint32_t*>(hout + static_cast<size_t>(r0) * kH + col) =
+      if (rr < n)
+        *reinterpret_cast<uint32_t*>(hout + static_cast<size_t>(rr) * kH + col) =
             pack_bf162(fmaxf(acc[nt][0] + b0, 0.0f), fmaxf(acc[nt][1] + b1, 0.0f));
-      if (r0 + 8 < n)
-        *reinterpret_cast<uint32_t*>(hout + static_cast<size_t>(r0 + 8) * kH + col) =
+      if (rr + 8 < n)
+        *reinterpret_cast<uint32_t*>(hout + static_cast<size_t>(rr + 8) * kH + col) =
             pack_bf162(fmaxf(acc[nt][2] + b0, 0.0f), fmaxf(acc[nt][3] + b1, 0.0f));
     }
   }
@@ -435,106 +558,130 @@ __global__ void head_kernel(const bf162* h3, const float* params, const int8_t* 
   if (threadIdx.x == 0) atomicAdd(loss, sl);
 }
 
-// Backward of one layer (h' = relu([h, a] W + b)) given dh' = dL/dh':
-// dU = dh' * (h' > 0); gW += X^T dU; gb += colsum dU; with DX also
-// dX = dU W^T, split into dh (fp32, the direct part) and da (bf16, to be
-// propagated through A_hat by the caller).
-template <int D, bool DX>
-__global__ void __launch_bounds__(kMlpThreads)
-    mlp_bwd_kernel(const float* __restrict__ dhn, const bf16* __restrict__ hn,
-                   const bf16* __restrict__ h, const float* __restrict__ a,
-                   const bf16* __restrict__ W, int n, float* __restrict__ gW,
-                   float* __restrict__ gb, float* __restrict__ dh, bf16* __restrict__ da) {
+// Backward of one layer (h' = relu([h, a] W + b)). dL/dh' is `direct` plus,
+// with AGG, A_hat da_src (da_src = dL/da of the layer above, gathered by the
+// tile as in the forward pass). Then dU = dL/dh' * (h' > 0); gW += X^T dU;
+// gb += colsum dU; with DX also dX = dU W^T, split into dh_out (fp32, the
+// direct part for the layer below) and da_out (bf16, to be propagated).
+template <int D, bool DX, bool AGG>
+__global__ void __launch_bounds__(kLayerThreads, 2)
+    layer_bwd_kernel(GView v, const float* __restrict__ c, const float* __restrict__ direct,
+                     const bf16* __restrict__ da_src, const float* __restrict__ partial,
+                     const bf16* __restrict__ hn, const bf16* __restrict__ h, const bf16* __restrict__ a,
+                     const bf16* __restrict__ W, float* __restrict__ gW, float* __restrict__ gb,
+                     float* __restrict__ dh_out, bf16* __restrict__ da_out) {
   constexpr int K2 = 2 * D, KP = K2 + 8, NP = kH + 8;
-  constexpr int MT = K2 / 16;              // 16-row tiles of gW
-  constexpr int TPW = MT * 8 / 4;          // gW 16x8 tiles per warp
+  constexpr int MT = K2 / 16;  // 16-row tiles of gW; 8 x MT tiles of 16 x 8, MT per warp
   constexpr int WR = DX ? K2 : 1;
+  constexpr int XN = K2 / 16;  // dX: 8-column tiles per warp (half of K2 each)
   __shared__ __align__(16) bf16 sW[WR * NP];
-  __shared__ __align__(16) bf16 sX[kTileRows * KP];
-  __shared__ __align__(16) bf16 sU[kTileRows * NP];
+  __shared__ __align__(16) bf16 sX[kTile * KP];
+  __shared__ __align__(16) bf16 sU[kTile * NP];
   __shared__ float sdb[kH];
   if (DX) {
     for (int idx = threadIdx.x; idx < K2 * (kH / 8); idx += blockDim.x) {
-      const int k = idx / (kH / 8), c = idx % (kH / 8);
-      *reinterpret_cast<uint4*>(sW + k * NP + c * 8) = *reinterpret_cast<const uint4*>(W + k * kH + c * 8);
+      const int k = idx / (kH / 8), cc = idx % (kH / 8);
+      *reinterpret_cast<uint4*>(sW + k * NP + cc * 8) = *reinterpret_cast<const uint4*>(W + k * kH + cc * 8);
     }
   }
   if (threadIdx.x < kH) sdb[threadIdx.x] = 0.0f;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int g = lane >> 2, t = lane & 3;
-  float accW[TPW][4];
+  const int half = lane >> 4, hl = lane & 15;  // two rows per warp, four columns per lane
+  const int wm = wid & 3, wn = wid >> 2;
+  const int n = v.n;
+  float accW[MT][4];
 #pragma unroll
-  for (int i = 0; i < TPW; ++i) accW[i][0] = accW[i][1] = accW[i][2] = accW[i][3] = 0.0f;
+  for (int i = 0; i < MT; ++i) accW[i][0] = accW[i][1] = accW[i][2] = accW[i][3] = 0.0f;
   float dbp[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-  const int c4 = (threadIdx.x & 15) * 4;  // this thread's four columns of dU
-  for (int tile = blockIdx.x; tile * kTileRows < n; tile += gridDim.x) {
-    const int r0 = tile * kTileRows;
+  for (int tile = blockIdx.x; tile * kTile < n; tile += gridDim.x) {
+    const int r0 = tile * kTile;
     __syncthreads();
-    for (int r = threadIdx.x >> 4; r < kTileRows; r += kMlpThreads / 16) {
-      const int row = r0 + r;
+    for (int rl = wid * 2 + half; rl < kTile; rl += 16) {
+      const int r = r0 + rl;
       float u[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-      if (row < n) {
-        const float4 d4 = *reinterpret_cast<const float4*>(dhn + static_cast<size_t>(row) * kH + c4);
-        const uint2 hraw = *reinterpret_cast<const uint2*>(hn + static_cast<size_t>(row) * kH + c4);
+      if (r < n) {
+        const float4 d4 = *reinterpret_cast<const float4*>(direct + static_cast<size_t>(r) * kH + 4 * hl);
+        float dv[4] = {d4.x, d4.y, d4.z, d4.w};
+        if (AGG) {
+          float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+          aggregate_row<kH>(v, c, da_src, partial, r, hl, acc);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) dv[i] += acc[i];
+        }
+        const uint2 hraw = RowIO<kH>::load(hn, r, hl);
         bf162 p0, p1;
         memcpy(&p0, &hraw.x, 4);
         memcpy(&p1, &hraw.y, 4);
         const float2 h0 = __bfloat1622float2(p0), h1 = __bfloat1622float2(p1);
-        u[0] = h0.x > 0.0f ? d4.x : 0.0f;
-        u[1] = h0.y > 0.0f ? d4.y : 0.0f;
-        u[2] = h1.x > 0.0f ? d4.z : 0.0f;
-        u[3] = h1.y > 0.0f ? d4.w : 0.0f;
+        u[0] = h0.x > 0.0f ? dv[0] : 0.0f;
+        u[1] = h0.y > 0.0f ? dv[1] : 0.0f;
+        u[2] = h1.x > 0.0f ? dv[2] : 0.0f;
+        u[3] = h1.y > 0.0f ? dv[3] : 0.0f;
       }
 #pragma unroll
       for (int i = 0; i < 4; ++i) dbp[i] += u[i];
       uint2 packed;
       packed.x = pack_bf162(u[0], u[1]);
       packed.y = pack_bf162(u[2], u[3]);
-      *reinterpret_cast<uint2*>(sU + r * NP + c4) = packed;
+      *reinterpret_cast<uint2*>(sU + rl * NP + 4 * hl) = packed;
     }
-    stage_x<D, KP>(sX, h, a, r0, n);
+    // X = [h, a], both bf16, 16-byte chunks
+    constexpr int HC = D / 8, CH = 2 * HC;
+    for (int idx = threadIdx.x; idx < kTile * CH; idx += blockDim.x) {
+      const int rl = idx / CH, ch = idx % CH;
+      const int row = r0 + rl;
+      uint4 val = make_uint4(0, 0, 0, 0);
+      if (row < n) {
+        const bf16* srcp = ch < HC ? h + static_cast<size_t>(row) * D + ch * 8
+                                   : a + static_cast<size_t>(row) * D + (ch - HC) * 8;
+        val = __ldg(reinterpret_cast<const uint4*>(srcp));
+      }
+      *reinterpret_cast<uint4*>(sX + rl * KP + ch * 8) = val;
+    }
     __syncthreads();
     if (DX) {
-      float acc[K2 / 8][4];
+      float acc[XN][4];
 #pragma unroll
-      for (int i = 0; i < K2 / 8; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.0f;
+      for (int i = 0; i < XN; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.0f;
 #pragma unroll
       for (int ks = 0; ks < kH / 16; ++ks) {
         uint32_t af[4];
-        ldsm_x4(af, sU + (16 * wid + (lane & 7) + ((lane >> 3) & 1) * 8) * NP + ks * 16 + (lane >> 4) * 8);
+        ldsm_x4(af, sU + (16 * wm + (lane & 7) + ((lane >> 3) & 1) * 8) * NP + ks * 16 + (lane >> 4) * 8);
 #pragma unroll
-        for (int np = 0; np < K2 / 16; ++np) {
+        for (int np = 0; np < XN / 2; ++np) {
           uint32_t bfr[4];
           // B[k][m] = W[m][k]: W rows are B's columns, so no transpose
-          ldsm_x4(bfr, sW + (np * 16 + (lane & 7) + (lane >> 4) * 8) * NP + ks * 16 + ((lane >> 3) & 1) * 8);
+          ldsm_x4(bfr, sW + (D * wn + np * 16 + (lane & 7) + (lane >> 4) * 8) * NP + ks * 16 +
+                           ((lane >> 3) & 1) * 8);
           mma_bf16(acc[2 * np], af, bfr[0], bfr[1]);
           mma_bf16(acc[2 * np + 1], af, bfr[2], bfr[3]);
         }
       }
-      const int rr = r0 + 16 * wid + g;
+      const int rr = r0 + 16 * wm + g;
 #pragma unroll
-      for (int nt = 0; nt < K2 / 8; ++nt) {
-        const int col = nt * 8 + 2 * t;
-        if (col < D) {
+      for (int nt = 0; nt < XN; ++nt) {
+        const int col = nt * 8 + 2 * t;  // within this warp's half: wn 0 -> dh, wn 1 -> da
+        if (wn == 0) {
           if (rr < n)
-            *reinterpret_cast<float2*>(dh + static_cast<size_t>(rr) * D + col) = make_float2(acc[nt][0], acc[nt][1]);
+            *reinterpret_cast<float2*>(dh_out + static_cast<size_t>(rr) * D + col) = make_float2(acc[nt][0], acc[nt][1]);
           if (rr + 8 < n)
-            *reinterpret_cast<float2*>(dh + static_cast<size_t>(rr + 8) * D + col) = make_float2(acc[nt][2], acc[nt][3]);
+            *reinterpret_cast<float2*>(dh_out + static_cast<size_t>(rr + 8) * D + col) = make_float2(acc[nt][2], acc[nt][3]);
         } else {
           if (rr < n)
-            *reinterpret_cast<uint32_t*>(da + static_cast<size_t>(rr) * D + col - D) = pack_bf162(acc[nt][0], acc[nt][1]);
+            *reinterpret_cast<uint32_t*>(da_out + static_cast<size_t>(rr) * D + col) = pack_bf162(acc[nt][0], acc[nt][1]);
           if (rr + 8 < n)
-            *reinterpret_cast<uint32_t*>(da + static_cast<size_t>(rr + 8) * D + col - D) = pack_bf162(acc[nt][2], acc[nt][3]);
+            *reinterpret_cast<uint32_t*>(da_out + static_cast<size_t>(rr + 8) * D + col) = pack_bf162(acc[nt][2], acc[nt][3]);
         }
       }
     }
     // gW[m][j] += sum_rows X[row][m] dU[row][j]: A = X^T, B = dU (both via
     // transposing loads of the row-major tiles)
 #pragma unroll
-    for (int ks = 0; ks < kTileRows / 16; ++ks) {
+    for (int ks = 0; ks < kTile / 16; ++ks) {
 #pragma unroll
-      for (int i = 0; i < TPW; ++i) {
-        const int tile_id = wid * TPW + i;
+      for (int i = 0; i < MT; ++i) {
+        const int tile_id = wid * MT + i;
         const int mt = tile_id / 8, nt = tile_id % 8;
         uint32_t af[4], bfr[4];
         ldsm_x4_t(af, sX + (ks * 16 + (lane & 7) + (lane >> 4) * 8) * KP + mt * 16 + ((lane >> 3) & 1) * 8);
@@ -544,8 +691,8 @@ __global__ void __launch_bounds__(kMlpThreads)
     }
   }
 #pragma unroll
-  for (int i = 0; i < TPW; ++i) {
-    const int tile_id = wid * TPW + i;
+  for (int i = 0; i < MT; ++i) {
+    const int tile_id = wid * MT + i;
     const int mt = tile_id / 8, nt = tile_id % 8;
     const int m = mt * 16 + g, j = nt * 8 + 2 * t;
     atomicAdd(gW + m * kH + j, accW[i][0]);
@@ -555,7 +702,7 @@ __global__ void __launch_bounds__(kMlpThreads)
   }
   __syncthreads();
 #pragma unroll
-  for (int i = 0; i < 4; ++i) atomicAdd(&sdb[c4 + i], dbp[i]);
+  for (int i = 0; i < 4; ++i) atomicAdd(&sdb[4 * hl + i], dbp[i]);
   __syncthreads();
   if (threadIdx.x < kH) atomicAdd(gb + threadIdx.x, sdb[threadIdx.x]);
 }
@@ -587,9 +734,11 @@ __global__ void gather_labels_kernel(const int8_t* caller, const int32_t* orig, 
     pos_out[v] = caller[orig[v]];
 }
 
-__global__ void scatter_logits_kernel(const float* z, const int32_t* orig, int n, float* caller) {
+// caller[vbase[p] + orig[p]] = z[p] (vbase null: 0).
+__global__ void scatter_logits_kernel(const float* z, const int32_t* orig, const int32_t* vbase, int n,
+                                      float* caller) {
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
-    caller[orig[v]] = z[v];
+    caller[(vbase ? vbase[v] : 0) + orig[v]] = z[v];
 }
 
 __global__ void scatter_bias_kernel(const uint8_t* caller, const int32_t* pos, int n, uint8_t* bias) {
@@ -620,6 +769,18 @@ __global__ void warm_start_kernel(const float* z, int n, int8_t* spins, uint8_t*
   }
 }
 
+// G5 on one replica of a batch: bit `shift` of every position's spin byte.
+__global__ void batch_warm_start_kernel(const float* z, int n, uint8_t* spins, int shift) {
+  const uint8_t bit = static_cast<uint8_t>(1u << shift);
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    const float zv = z[v];
+    if (zv > 0.0f)
+      spins[v] = static_cast<uint8_t>(spins[v] & ~bit);
+    else if (zv < 0.0f)
+      spins[v] = static_cast<uint8_t>(spins[v] | bit);
+  }
+}
+
 int grid_of(long long work, int per_block, int cap) {
   long long b = (work + per_block - 1) / per_block;
   if (b < 1) b = 1;
@@ -647,37 +808,41 @@ struct ising_gnn {
   int4* d_sums = nullptr;
   float* d_c = nullptr;
   bf16* d_x = nullptr;
-  float* d_a0 = nullptr;
-  bf16* d_h[3] = {nullptr, nullptr, nullptr};  // h1, h2, h3
-  float* d_a[2] = {nullptr, nullptr};          // a1, a2
+  bf16* d_a0 = nullptr;                          // a^0 (bf16), kept for the backward pass
+  bf16* d_h[3] = {nullptr, nullptr, nullptr};    // h1, h2, h3
+  bf16* d_a[2] = {nullptr, nullptr};             // a^1, a^2 (bf16), kept for the backward pass
   float* d_z = nullptr;
   int8_t* d_y = nullptr;
-  float* d_dh[2] = {nullptr, nullptr};
-  bf16* d_da = nullptr;
+  float* d_dh[2] = {nullptr, nullptr};           // direct parts of dL/dh
+  bf16* d_da[2] = {nullptr, nullptr};            // dL/da of two consecutive layers
   float* d_out = nullptr;  // logits in caller order (host copies)
+  int64_t chunk_cap = 0;
+  float* d_partial = nullptr;  // per heavy-row chunk: its partial sum (width 64)
 };
 
 namespace {
 
 void free_work(ising_gnn* net) {
-  void* ptrs[] = {net->d_sums, net->d_c,     net->d_x,     net->d_a0,    net->d_h[0],
-                  net->d_h[1], net->d_h[2],  net->d_a[0],  net->d_a[1],  net->d_z,
-                  net->d_y,    net->d_dh[0], net->d_dh[1], net->d_da,    net->d_out};
+  void* ptrs[] = {net->d_sums,  net->d_c,     net->d_x,     net->d_a0,    net->d_h[0],
+                  net->d_h[1],  net->d_h[2],  net->d_a[0],  net->d_a[1],  net->d_z,
+                  net->d_y,     net->d_dh[0], net->d_dh[1], net->d_da[0], net->d_da[1],
+                  net->d_out};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   net->d_sums = nullptr;
-  net->d_c = net->d_a0 = net->d_z = net->d_out = nullptr;
-  net->d_x = net->d_da = nullptr;
+  net->d_c = net->d_z = net->d_out = nullptr;
+  net->d_x = net->d_a0 = nullptr;
   net->d_h[0] = net->d_h[1] = net->d_h[2] = nullptr;
-  net->d_a[0] = net->d_a[1] = net->d_dh[0] = net->d_dh[1] = nullptr;
+  net->d_a[0] = net->d_a[1] = net->d_da[0] = net->d_da[1] = nullptr;
+  net->d_dh[0] = net->d_dh[1] = nullptr;
   net->d_y = nullptr;
   net->n_cap = 0;
 }
 
 void free_net(ising_gnn* net) {
   free_work(net);
-  void* ptrs[] = {net->d_params, net->d_m, net->d_v, net->d_grad,
-                  net->d_w0,     net->d_w1, net->d_w2, net->d_loss};
+  void* ptrs[] = {net->d_params, net->d_m,  net->d_v,  net->d_grad, net->d_w0,
+                  net->d_w1,     net->d_w2, net->d_loss, net->d_partial};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -701,13 +866,23 @@ cudaError_t ensure_work(ising_gnn* net, int64_t n) {
   for (int l = 0; l < 2; ++l) {
     if ((e = dalloc(&net->d_a[l], N * kH)) != cudaSuccess) return e;
     if ((e = dalloc(&net->d_dh[l], N * kH)) != cudaSuccess) return e;
+    if ((e = dalloc(&net->d_da[l], N * kH)) != cudaSuccess) return e;
   }
   if ((e = dalloc(&net->d_z, N)) != cudaSuccess) return e;
   if ((e = dalloc(&net->d_y, N)) != cudaSuccess) return e;
-  if ((e = dalloc(&net->d_da, N * kH)) != cudaSuccess) return e;
   if ((e = dalloc(&net->d_out, N)) != cudaSuccess) return e;
   net->n_cap = n;
   return cudaSuccess;
+}
+
+cudaError_t ensure_partial(ising_gnn* net, int64_t chunks) {
+  if (chunks <= net->chunk_cap) return cudaSuccess;
+  if (net->d_partial) cudaFree(net->d_partial);
+  net->d_partial = nullptr;
+  net->chunk_cap = 0;
+  const cudaError_t e = dalloc(&net->d_partial, static_cast<size_t>(chunks) * kH);
+  if (e == cudaSuccess) net->chunk_cap = chunks;
+  return e;
 }
 
 int net_fail(ising_gnn* net) {
@@ -730,71 +905,165 @@ int net_enter(ising_gnn* net, ising_graph* g) {
   return ISING_OK;
 }
 
-EdgeView edges_of(const ising_graph* g) {
-  EdgeView ev;
-  ev.adj = g->d_adj;
-  ev.col = g->d_col;
-  ev.w = g->d_w;
-  ev.packed = g->packed ? 1 : 0;
-  return ev;
+// A graph and where the network runs it.
+struct Ctx {
+  GView v;
+  cudaStream_t st;
+  int sms;
+  const int32_t* orig;   // position -> vertex id (within the instance)
+  const int32_t* vbase;  // per position: the instance's first position (null: none)
+};
+
+// Row ids and heavy-row chunks of a row table, built once per graph and kept
+// by its owner: rowid[e] = row of entry e; hchunk[r] = index of row r's first
+// chunk if r has more than kHeavy entries, else -1; chunk_row[k] = row of
+// chunk k. A graph without heavy rows keeps no chunk arrays.
+cudaError_t build_row_tables(const int32_t* d_row_ptr, int n, long long nnz, cudaStream_t st, int sms,
+                             int32_t** rowid, int32_t** hchunk, int32_t** chunk_row, int32_t* num_chunks,
+                             uint64_t* launches) {
+  cudaError_t e = cudaSuccess;
+  if (*rowid == nullptr) {
+    if ((e = dalloc(rowid, static_cast<size_t>(nnz))) != cudaSuccess) {
+      *rowid = nullptr;
+      return e;
+    }
+    rowid_kernel<<<grid_of(n, 256, sms * 8), 256, 0, st>>>(d_row_ptr, n, *rowid);
+    (*launches)++;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (*num_chunks >= 0) return cudaSuccess;
+  std::vector<int32_t> rp(static_cast<size_t>(n) + 1);
+  if ((e = cudaMemcpyAsync(rp.data(), d_row_ptr, rp.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st)) !=
+          cudaSuccess ||
+      (e = cudaStreamSynchronize(st)) != cudaSuccess)
+    return e;
+  std::vector<int32_t> hc(static_cast<size_t>(n), -1), rows;
+  for (int r = 0; r < n; ++r) {
+    const int deg = rp[static_cast<size_t>(r) + 1] - rp[static_cast<size_t>(r)];
+    if (deg <= kHeavy) continue;
+    hc[static_cast<size_t>(r)] = static_cast<int32_t>(rows.size());
+    for (int k = 0; k < (deg + kChunk - 1) / kChunk; ++k) rows.push_back(r);
+  }
+  if (!rows.empty()) {
+    if ((e = dalloc(hchunk, hc.size())) != cudaSuccess) {
+      *hchunk = nullptr;
+      return e;
+    }
+    if ((e = dalloc(chunk_row, rows.size())) != cudaSuccess) {
+      *chunk_row = nullptr;
+      return e;
+    }
+    if ((e = cudaMemcpyAsync(*hchunk, hc.data(), hc.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st)) !=
+            cudaSuccess ||
+        (e = cudaMemcpyAsync(*chunk_row, rows.data(), rows.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                             st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+      return e;
+  }
+  *num_chunks = static_cast<int32_t>(rows.size());
+  return cudaSuccess;
 }
 
-// Forward pass over graph g from its current spins; with labels (by
-// position in net->d_y) also the loss and dL/dh3 into net->d_dh[0].
-int run_forward(ising_gnn* net, ising_graph* g, bool with_labels) {
-  const int n = g->n;
-  const long long nnz = g->nnz;
-  cudaStream_t st = g->stream;
-  const int sms = g->num_sms;
+int graph_ctx(ising_gnn* net, ising_graph* g, Ctx* ctx) {
+  GNN_CUDA(net, build_row_tables(g->d_row_ptr, g->n, g->nnz, g->stream, g->num_sms, &g->d_rowid,
+                                 &g->d_gnn_hchunk, &g->d_gnn_chunk_row, &g->gnn_num_chunks, &net->launches));
+  GView& v = ctx->v;
+  v.n = g->n;
+  v.nnz = g->nnz;
+  v.row_ptr = g->d_row_ptr;
+  v.ev.adj = g->d_adj;
+  v.ev.col = g->d_col;
+  v.ev.w = g->d_w;
+  v.ev.packed = g->packed ? 1 : 0;
+  v.vbase = nullptr;
+  v.rowid = g->d_rowid;
+  v.spins = reinterpret_cast<const uint8_t*>(g->d_spins);
+  v.shift = 0;
+  v.num_chunks = g->gnn_num_chunks;
+  v.hchunk = v.num_chunks > 0 ? g->d_gnn_hchunk : nullptr;
+  v.chunk_row = g->d_gnn_chunk_row;
+  ctx->st = g->stream;
+  ctx->sms = g->num_sms;
+  ctx->orig = g->d_orig;
+  ctx->vbase = nullptr;
+  return ISING_OK;
+}
+
+int batch_ctx(ising_gnn* net, ising_batch* b, uint32_t replica, Ctx* ctx, isingx::BatchUnion* u) {
+  if (net == nullptr) return ISING_EINVAL;
+  if (net->status != ISING_OK) return net->status;
+  int rc = isingx::batch_union(b, u);
+  if (rc != ISING_OK) return rc;
+  if (u->device != net->device || replica >= static_cast<uint32_t>(u->replicas)) return ISING_EINVAL;
+  GNN_CUDA(net, build_row_tables(u->row_ptr, u->n, u->nnz, u->stream, u->num_sms, u->rowid, u->hchunk,
+                                 u->chunk_row, u->num_chunks, &net->launches));
+  GView& v = ctx->v;
+  v.n = u->n;
+  v.nnz = u->nnz;
+  v.row_ptr = u->row_ptr;
+  v.ev.adj = u->adj;
+  v.ev.col = nullptr;
+  v.ev.w = nullptr;
+  v.ev.packed = 1;
+  v.vbase = u->vbase;
+  v.rowid = *u->rowid;
+  v.spins = u->spins;
+  v.shift = static_cast<int>(replica);
+  v.num_chunks = *u->num_chunks;
+  v.hchunk = v.num_chunks > 0 ? *u->hchunk : nullptr;
+  v.chunk_row = *u->chunk_row;
+  ctx->st = u->stream;
+  ctx->sms = u->num_sms;
+  ctx->orig = u->orig;
+  ctx->vbase = u->vbase;
+  return ISING_OK;
+}
+
+// Chunk partial sums of src (width D) when the graph has heavy rows.
+template <int D>
+int run_chunks(ising_gnn* net, const Ctx& x, const bf16* src) {
+  if (x.v.num_chunks <= 0) return ISING_OK;
+  chunk_partial_kernel<D><<<grid_of(static_cast<long long>(x.v.num_chunks) * RowIO<D>::G, 256, x.sms * 16), 256, 0,
+                            x.st>>>(x.v, net->d_c, src, net->d_partial);
+  net->launches++;
+  GNN_CUDA(net, cudaGetLastError());
+  return ISING_OK;
+}
+
+// Forward pass over the graph from its current spins; with labels (by
+// position in net->d_y) also the loss and dL/dh3 into net->d_dh[0], and the
+// aggregates a^l kept for the backward pass.
+int run_forward(ising_gnn* net, const Ctx& x, bool with_labels) {
+  const int n = x.v.n;
+  const long long nnz = x.v.nnz;
+  cudaStream_t st = x.st;
+  const int sms = x.sms;
   GNN_CUDA(net, ensure_work(net, n));
-  if (g->d_rowid == nullptr) {
-    if (cudaMalloc(&g->d_rowid, static_cast<size_t>(nnz > 0 ? nnz : 1) * sizeof(int32_t)) != cudaSuccess) {
-      g->d_rowid = nullptr;
-      return net_fail(net);
-    }
-    rowid_kernel<<<grid_of(n, 256, sms * 8), 256, 0, st>>>(g->d_row_ptr, n, g->d_rowid);
-    net->launches++;
-    GNN_CUDA(net, cudaGetLastError());
-  }
-  const EdgeView ev = edges_of(g);
+  GNN_CUDA(net, ensure_partial(net, x.v.num_chunks));
   const int ent_grid = grid_of((nnz + 31) / 32 * 32, 256, sms * 16);
   GNN_CUDA(net, cudaMemsetAsync(net->d_sums, 0, sizeof(int4) * static_cast<size_t>(n), st));
   if (nnz > 0) {
-    rowsum_kernel<<<ent_grid, 256, 0, st>>>(ev, g->d_rowid, g->d_spins, static_cast<int>(nnz), net->d_sums);
+    rowsum_kernel<<<ent_grid, 256, 0, st>>>(x.v, net->d_sums);
     net->launches++;
   }
-  features_kernel<<<grid_of(n, 256, sms * 8), 256, 0, st>>>(net->d_sums, g->d_spins, n,
-                                                             reinterpret_cast<uint4*>(net->d_x), net->d_c);
+  features_kernel<<<grid_of(n, 256, sms * 8), 256, 0, st>>>(x.v, net->d_sums, reinterpret_cast<uint4*>(net->d_x),
+                                                             net->d_c);
   net->launches++;
   GNN_CUDA(net, cudaGetLastError());
-  // about 36 KB of shared memory per block: six blocks fit on an SM
-  const int mlp_grid = grid_of((n + kTileRows - 1) / kTileRows, 1, sms * 6);
-  // layer 0
-  GNN_CUDA(net, cudaMemsetAsync(net->d_a0, 0, sizeof(float) * static_cast<size_t>(n) * kF, st));
-  if (nnz > 0) {
-    aggregate8_kernel<<<ent_grid, 256, 0, st>>>(ev, g->d_rowid, net->d_c,
-                                                reinterpret_cast<const uint4*>(net->d_x),
-                                                static_cast<int>(nnz), net->d_a0);
-    net->launches++;
-  }
-  mlp_fwd_kernel<kF><<<mlp_grid, kMlpThreads, 0, st>>>(net->d_x, net->d_a0, net->d_w0,
-                                                       net->d_params + kOffB0, n, net->d_h[0]);
+  const int tiles = (n + kTile - 1) / kTile;
+  int rc = run_chunks<kF>(net, x, net->d_x);
+  if (rc != ISING_OK) return rc;
+  layer_fwd_kernel<kF><<<tiles, kLayerThreads, 0, st>>>(x.v, net->d_c, net->d_x, net->d_partial, net->d_w0,
+                                                        net->d_params + kOffB0, with_labels ? net->d_a0 : nullptr,
+                                                        net->d_h[0]);
   net->launches++;
   GNN_CUDA(net, cudaGetLastError());
-  // layers 1 and 2
-  const long long agg_warps = (nnz + kAggChunk - 1) / kAggChunk;
-  const int agg_grid = static_cast<int>((agg_warps + 7) / 8);
   for (int l = 1; l <= 2; ++l) {
-    GNN_CUDA(net, cudaMemsetAsync(net->d_a[l - 1], 0, sizeof(float) * static_cast<size_t>(n) * kH, st));
-    if (nnz > 0) {
-      aggregate64_kernel<<<agg_grid, 256, 0, st>>>(ev, g->d_rowid, net->d_c,
-                                                   reinterpret_cast<const bf162*>(net->d_h[l - 1]),
-                                                   static_cast<int>(nnz), net->d_a[l - 1]);
-      net->launches++;
-    }
-    mlp_fwd_kernel<kH><<<mlp_grid, kMlpThreads, 0, st>>>(
-        net->d_h[l - 1], net->d_a[l - 1], l == 1 ? net->d_w1 : net->d_w2,
-        net->d_params + (l == 1 ? kOffB1 : kOffB2), n, net->d_h[l]);
+    rc = run_chunks<kH>(net, x, net->d_h[l - 1]);
+    if (rc != ISING_OK) return rc;
+    layer_fwd_kernel<kH><<<tiles, kLayerThreads, 0, st>>>(
+        x.v, net->d_c, net->d_h[l - 1], net->d_partial, l == 1 ? net->d_w1 : net->d_w2,
+        net->d_params + (l == 1 ? kOffB1 : kOffB2), with_labels ? net->d_a[l - 1] : nullptr, net->d_h[l]);
     net->launches++;
     GNN_CUDA(net, cudaGetLastError());
   }
@@ -809,39 +1078,31 @@ int run_forward(ising_gnn* net, ising_graph* g, bool with_labels) {
 
 // Backward pass after run_forward(with_labels): gradients into net->d_grad
 // (zeroed by the caller before the head kernel ran).
-int run_backward(ising_gnn* net, ising_graph* g) {
-  const int n = g->n;
-  const long long nnz = g->nnz;
-  cudaStream_t st = g->stream;
-  const int sms = g->num_sms;
-  const EdgeView ev = edges_of(g);
-  const int mlp_grid = grid_of((n + kTileRows - 1) / kTileRows, 1, sms * 2);
-  const long long agg_warps = (nnz + kAggChunk - 1) / kAggChunk;
-  const int agg_grid = static_cast<int>((agg_warps + 7) / 8);
-  // d_dh[0] holds dL/dh3; layers 2 and 1 produce dL/dh2, dL/dh1 alternately
-  int cur = 0;
-  for (int l = 2; l >= 1; --l) {
-    const int nxt = cur ^ 1;
-    const bf16* W = l == 2 ? net->d_w2 : net->d_w1;
-    float* gW = net->d_grad + (l == 2 ? kOffW2 : kOffW1);
-    float* gb = net->d_grad + (l == 2 ? kOffB2 : kOffB1);
-    mlp_bwd_kernel<kH, true><<<mlp_grid, kMlpThreads, 0, st>>>(
-        net->d_dh[cur], net->d_h[l], net->d_h[l - 1], net->d_a[l - 1], W, n, gW, gb, net->d_dh[nxt],
-        net->d_da);
-    net->launches++;
-    GNN_CUDA(net, cudaGetLastError());
-    if (nnz > 0) {
-      aggregate64_kernel<<<agg_grid, 256, 0, st>>>(ev, g->d_rowid, net->d_c,
-                                                   reinterpret_cast<const bf162*>(net->d_da),
-                                                   static_cast<int>(nnz), net->d_dh[nxt]);
-      net->launches++;
-      GNN_CUDA(net, cudaGetLastError());
-    }
-    cur = nxt;
-  }
-  mlp_bwd_kernel<kF, false><<<mlp_grid, kMlpThreads, 0, st>>>(
-      net->d_dh[cur], net->d_h[0], net->d_x, net->d_a0, net->d_w0, n, net->d_grad + kOffW0,
-      net->d_grad + kOffB0, nullptr, nullptr);
+int run_backward(ising_gnn* net, const Ctx& x) {
+  const int n = x.v.n;
+  cudaStream_t st = x.st;
+  // two blocks per SM (registers); each keeps its dW partial sums to the end
+  const int grid = grid_of((n + kTile - 1) / kTile, 1, x.sms * 2);
+  // layer 2: dL/dh3 (d_dh[0]) -> direct part of dL/dh2 (d_dh[1]), dL/da2 (d_da[0])
+  layer_bwd_kernel<kH, true, false><<<grid, kLayerThreads, 0, st>>>(
+      x.v, net->d_c, net->d_dh[0], nullptr, nullptr, net->d_h[2], net->d_h[1], net->d_a[1], net->d_w2,
+      net->d_grad + kOffW2, net->d_grad + kOffB2, net->d_dh[1], net->d_da[0]);
+  net->launches++;
+  GNN_CUDA(net, cudaGetLastError());
+  // layer 1: dL/dh2 = d_dh[1] + A_hat d_da[0] -> d_dh[0], d_da[1]
+  int rc = run_chunks<kH>(net, x, net->d_da[0]);
+  if (rc != ISING_OK) return rc;
+  layer_bwd_kernel<kH, true, true><<<grid, kLayerThreads, 0, st>>>(
+      x.v, net->d_c, net->d_dh[1], net->d_da[0], net->d_partial, net->d_h[1], net->d_h[0], net->d_a[0],
+      net->d_w1, net->d_grad + kOffW1, net->d_grad + kOffB1, net->d_dh[0], net->d_da[1]);
+  net->launches++;
+  GNN_CUDA(net, cudaGetLastError());
+  // layer 0: dL/dh1 = d_dh[0] + A_hat d_da[1]
+  rc = run_chunks<kH>(net, x, net->d_da[1]);
+  if (rc != ISING_OK) return rc;
+  layer_bwd_kernel<kF, false, true><<<grid, kLayerThreads, 0, st>>>(
+      x.v, net->d_c, net->d_dh[0], net->d_da[1], net->d_partial, net->d_h[0], net->d_x, net->d_a0, net->d_w0,
+      net->d_grad + kOffW0, net->d_grad + kOffB0, nullptr, nullptr);
   net->launches++;
   GNN_CUDA(net, cudaGetLastError());
   return ISING_OK;
@@ -866,12 +1127,31 @@ int load_labels(ising_gnn* net, ising_graph* g, const int8_t* labels, int on_dev
 int gradients_impl(ising_gnn* net, ising_graph* g, const int8_t* labels, int on_device) {
   if (labels == nullptr) return ISING_EINVAL;
   GNN_CUDA(net, ensure_work(net, g->n));
-  int rc = load_labels(net, g, labels, on_device);
+  Ctx x;
+  int rc = graph_ctx(net, g, &x);
+  if (rc != ISING_OK) return rc;
+  rc = load_labels(net, g, labels, on_device);
   if (rc != ISING_OK) return rc;
   GNN_CUDA(net, cudaMemsetAsync(net->d_grad, 0, sizeof(float) * kNumParams, g->stream));
-  rc = run_forward(net, g, true);
+  rc = run_forward(net, x, true);
   if (rc != ISING_OK) return rc;
-  return run_backward(net, g);
+  return run_backward(net, x);
+}
+
+// Logits of the context's graph into out (caller order), host or device.
+int forward_out(ising_gnn* net, const Ctx& x, float* out_logits, int on_device) {
+  int rc = run_forward(net, x, false);
+  if (rc != ISING_OK) return rc;
+  float* dst = on_device ? out_logits : net->d_out;
+  scatter_logits_kernel<<<grid_of(x.v.n, 256, x.sms * 8), 256, 0, x.st>>>(net->d_z, x.orig, x.vbase, x.v.n, dst);
+  net->launches++;
+  GNN_CUDA(net, cudaGetLastError());
+  if (!on_device) {
+    GNN_CUDA(net, cudaMemcpyAsync(out_logits, net->d_out, sizeof(float) * static_cast<size_t>(x.v.n),
+                                  cudaMemcpyDeviceToHost, x.st));
+    GNN_CUDA(net, cudaStreamSynchronize(x.st));
+  }
+  return ISING_OK;
 }
 
 int read_loss(ising_gnn* net, ising_graph* g, float* out_loss) {
@@ -959,16 +1239,42 @@ int ising_gnn_forward(ising_gnn* net, ising_graph* g, float* out_logits, int on_
   int rc = net_enter(net, g);
   if (rc != ISING_OK) return rc;
   if (out_logits == nullptr) return ISING_EINVAL;
-  rc = run_forward(net, g, false);
+  Ctx x;
+  rc = graph_ctx(net, g, &x);
   if (rc != ISING_OK) return rc;
-  float* dst = on_device ? out_logits : net->d_out;
-  scatter_logits_kernel<<<grid_of(g->n, 256, g->num_sms * 8), 256, 0, g->stream>>>(net->d_z, g->d_orig, g->n, dst);
-  net->launches++;
-  GNN_CUDA(net, cudaGetLastError());
-  if (!on_device) {
-    GNN_CUDA(net, cudaMemcpyAsync(out_logits, net->d_out, sizeof(float) * static_cast<size_t>(g->n),
-                                  cudaMemcpyDeviceToHost, g->stream));
-    GNN_CUDA(net, cudaStreamSynchronize(g->stream));
+  return forward_out(net, x, out_logits, on_device);
+}
+
+int ising_gnn_batch_forward(ising_gnn* net, ising_batch* b, uint32_t replica, float* out_logits,
+                            int on_device) {
+  if (out_logits == nullptr) return ISING_EINVAL;
+  Ctx x;
+  isingx::BatchUnion u;
+  const int rc = batch_ctx(net, b, replica, &x, &u);
+  if (rc != ISING_OK) return rc;
+  return forward_out(net, x, out_logits, on_device);
+}
+
+int ising_gnn_batch_warm_start(ising_gnn* net, ising_batch* b, uint32_t replica) {
+  isingx::BatchUnion u;
+  Ctx x;
+  int rc = batch_ctx(net, b, 0, &x, &u);
+  if (rc != ISING_OK) return rc;
+  uint32_t r0 = replica, r1 = replica + 1;
+  if (replica == ISING_ALL_REPLICAS) {
+    r0 = 0;
+    r1 = static_cast<uint32_t>(u.replicas);
+  } else if (replica >= static_cast<uint32_t>(u.replicas)) {
+    return ISING_EINVAL;
+  }
+  for (uint32_t r = r0; r < r1; ++r) {
+    x.v.shift = static_cast<int>(r);
+    rc = run_forward(net, x, false);
+    if (rc != ISING_OK) return rc;
+    batch_warm_start_kernel<<<grid_of(x.v.n, 256, x.sms * 8), 256, 0, x.st>>>(net->d_z, x.v.n, u.spins,
+                                                                               static_cast<int>(r));
+    net->launches++;
+    GNN_CUDA(net, cudaGetLastError());
   }
   return ISING_OK;
 }
@@ -1011,7 +1317,10 @@ int ising_gnn_train_step(ising_gnn* net, ising_graph* g, const int8_t* labels, i
 int ising_gnn_warm_start(ising_gnn* net, ising_graph* g, int set_bias) {
   int rc = net_enter(net, g);
   if (rc != ISING_OK) return rc;
-  rc = run_forward(net, g, false);
+  Ctx x;
+  rc = graph_ctx(net, g, &x);
+  if (rc != ISING_OK) return rc;
+  rc = run_forward(net, x, false);
   if (rc != ISING_OK) return rc;
   if (set_bias && g->d_bias == nullptr) {
     if (cudaMalloc(&g->d_bias, static_cast<size_t>(g->n)) != cudaSuccess) {

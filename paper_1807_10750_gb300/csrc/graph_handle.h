@@ -112,6 +112,9 @@ struct ising_graph {
   int32_t hub_grid = 0;              // blocks the split was made for
   uint8_t* d_bias = nullptr;         // per-position flip bias (null: none)
   int32_t* d_rowid = nullptr;        // row of every CSR entry (built on first use)
+  int32_t* d_gnn_hchunk = nullptr;   // warm-start network: per row, its first entry chunk or -1
+  int32_t* d_gnn_chunk_row = nullptr;  // warm-start network: the row of every entry chunk
+  int32_t gnn_num_chunks = -1;       // -1 until built
   isingx::BarrierState* d_barrier = nullptr;
   int persist_grid = 0;              // co-resident blocks of the persistent kernel
 
