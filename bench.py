@@ -58,6 +58,18 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweeps", type=int, default=None,
                     help="override the workload's schedule length (profiling runs only)")
+    ap.add_argument("--train-graphs", type=int, default=2048,
+                    help="warmstart: generated training graphs (1k-100k vertices)")
+    ap.add_argument("--train-batch", type=int, default=64,
+                    help="warmstart: training graphs per batch (one Adam step each)")
+    ap.add_argument("--train-steps", type=int, default=1500, help="warmstart: Adam steps")
+    ap.add_argument("--test-graphs", type=int, default=152,
+                    help="warmstart: held-out 100k-vertex power-law graphs")
+    ap.add_argument("--long-sweeps", type=int, default=20000,
+                    help="warmstart: sweeps of the long run that sets each graph's best cut")
+    ap.add_argument("--plain-sweeps", type=lambda t: [int(x) for x in t.split(",")],
+                    default=[100, 200, 400, 800, 1600, 3200, 6400],
+                    help="warmstart: the plain anneal lengths timed")
     return ap.parse_args()
 
 
@@ -387,142 +399,182 @@ def run_batched(args, world, rank, P, torch, dist):
     print(json.dumps(line), flush=True)
 
 
-def run_warmstart(args, world, rank, P, torch, dist):
-    """The learned warm start against the plain annealer on held-out graphs.
-
-    Untimed set-up: the network is trained on the GPU from annealer labels
-    (input: spins after a 100-sweep anneal; label: spins after a further
-    200-sweep anneal at p0 = 0.01), and the long-run best cut of every test
-    graph is the best of 4 replicas x 10000 sweeps. Timed (CUDA events on the
-    library's stream, from random spins): plain anneals of T sweeps, and the
-    learned form -- a short anneal, then rounds of network warm start
-    followed by 10 greedy sweeps. Reported: the least time at which each form
-    reaches 99 % of the best cut."""
+def _warmstart_graph(spec):
+    """Build one generated graph (a process-pool task)."""
     import synth
-    train, test, spec = synth.warmstart_workload()
+    g = synth.graph_from_spec(spec)
+    return (g.n, g.src, g.dst, g.w)
+
+
+def run_warmstart(args, world, rank, P, torch, dist):
+    """The learned warm start against the plain annealer, batched, on
+    held-out graphs.
+
+    Untimed set-up. Training data from the annealer itself: generated graphs
+    (power-law and Erdos-Renyi alternately, 1k-100k vertices) in batches of
+    `--train-batch` instances; per batch, input = the spins after a 100-sweep
+    anneal, label = the spins after a further 200-sweep anneal at p0 = 0.01.
+    The network trains on the GPU, one Adam step per batch of instances
+    (ising_gnn_batch_train_step). The held-out power-law graphs form one
+    batch of 8 replicas; the long-run best cut of each graph is the best of
+    its 8 replicas after `--long-sweeps` sweeps.
+
+    Timed (CUDA events on the batch's stream, from random spins): plain
+    batch anneals of T sweeps, and the learned form -- a short anneal, then
+    rounds of (network warm start of every replica + 10 greedy sweeps).
+    Reported: for each form the least time at which every held-out graph has
+    a replica at 99 % of its best cut."""
+    import multiprocessing as mp
+    import synth
+    train_specs, test_specs, spec = synth.warmstart_specs(
+        synth.WARMSTART_BATCHED, train_count=args.train_graphs, test_count=args.test_graphs)
+    per = max(1, args.train_batch)
     stream = torch.cuda.Stream()
     seed0 = 1000 + 7919 * rank
     t_setup = time.perf_counter()
-    # training data from the annealer itself
-    examples = []
-    for k, g in enumerate(train):
-        h = P.ising_create(g.n, g.src, g.dst, g.w, stream=stream)
-        P.ising_init_random(h, seed0 + k)
-        P.ising_anneal(h, p0=0.1, t_total=100, seed=seed0 + k, stream=stream)
-        snap = torch.empty(g.n, dtype=torch.int8, device="cuda")
-        P.ising_get_spins(h, snap)
-        P.ising_anneal(h, p0=0.01, t_total=200, seed=seed0 + 5000 + k, stream=stream)
-        lab = torch.empty(g.n, dtype=torch.int8, device="cuda")
-        P.ising_get_spins(h, lab)
-        examples.append((h, snap, lab))
+    pool = mp.get_context("spawn").Pool(processes=max(1, min(16, os.cpu_count() or 1)))
+    chunks = [train_specs[i:i + per] for i in range(0, len(train_specs), per)]
+    pending = pool.map_async(_warmstart_graph, chunks[0]) if chunks else None
+    gen_s = label_s = 0.0
+    train_vertices = 0
+    batches = []
+    for ci in range(len(chunks)):
+        tg = time.perf_counter()
+        graphs = pending.get()
+        pending = pool.map_async(_warmstart_graph, chunks[ci + 1]) if ci + 1 < len(chunks) else None
+        gen_s += time.perf_counter() - tg
+        tl = time.perf_counter()
+        b = P.ising_batch_create(graphs, replicas=1, stream=stream)
+        sd = seed0 + 17 * ci
+        P.ising_batch_init_random(b, sd)
+        P.ising_batch_anneal(b, p0=0.1, t_total=100, seed=sd, stream=stream)
+        snap = [P.ising_batch_get_spins(b, k, 0) for k in range(len(graphs))]
+        P.ising_batch_anneal(b, p0=0.01, t_total=200, seed=sd + 5000, stream=stream)
+        lab = np.concatenate([P.ising_batch_get_spins(b, k, 0) for k in range(len(graphs))])
+        for k, sp in enumerate(snap):
+            P.ising_batch_set_spins(b, k, 0, sp)
+        batches.append((b, torch.from_numpy(lab).to("cuda")))
+        train_vertices += lab.size
+        label_s += time.perf_counter() - tl
+        del graphs, snap
+    tg = time.perf_counter()
+    test_graphs = pool.map(_warmstart_graph, test_specs)
+    gen_s += time.perf_counter() - tg
+    pool.close()
+    pool.join()
+
     net = P.ising_gnn_create(synth.gnn_init_params(spec["gen_seed"]))
-    steps = 4000
+    steps = args.train_steps
+    rng = np.random.default_rng(spec["gen_seed"])
+    order = []
+    losses = []
     torch.cuda.synchronize()
     t_train = time.perf_counter()
-    losses = []
     for it in range(steps):
-        h, snap, lab = examples[it % len(examples)]
-        P.ising_set_spins(h, snap)
-        loss = P.ising_gnn_train_step(net, h, lab, lr=2e-3 if it < 3 * steps // 4 else 5e-4,
-                                      want_loss=(it % 500 == 0 or it == steps - 1))
+        if not order:
+            order = list(rng.permutation(len(batches)))
+        b, lab = batches[order.pop()]
+        lr = 2e-3 if it < 3 * steps // 4 else 5e-4
+        loss = P.ising_gnn_batch_train_step(net, b, lab, lr=lr,
+                                            want_loss=(it % 250 == 0 or it == steps - 1))
         if loss is not None:
             losses.append(round(loss, 4))
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t_train
-    for h, _, _ in examples:
-        h.close()
+    for b, _ in batches:
+        b.close()
+    batches = []
 
+    tb = P.ising_batch_create(test_graphs, replicas=8, stream=stream)
+    num = len(test_graphs)
+    test_vertices = sum(g[0] for g in test_graphs)
+    del test_graphs
+    P.ising_batch_init_random(tb, 1)
+    P.ising_batch_autotune(tb, 10)
+    tuning = P.ising_batch_tuning(tb)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
 
     def timed(fn):
+        torch.cuda.synchronize()
         ev[0].record(stream)
         fn()
         ev[1].record(stream)
         torch.cuda.synchronize()
         return ev[0].elapsed_time(ev[1]) / 1e3
 
-    results = []
-    for gi, g in enumerate(test):
-        h = P.ising_create(g.n, g.src, g.dst, g.w, stream=stream)
-        best = -(1 << 62)
-        for r in range(4):
-            P.ising_init_random(h, 90000 + r)
-            P.ising_anneal(h, p0=0.1, t_total=10000, seed=90000 + r, stream=stream)
-            best = max(best, P.ising_cut(h))
-        best_plain = best
-        # untimed: the network's workspace for this size and the graph's row table
-        P.ising_gnn_forward(net, h, torch.empty(g.n, dtype=torch.float32, device="cuda"))
-        torch.cuda.synchronize()
-        plain = []
-        for T in (100, 200, 400, 800, 1600, 3200, 6400, 12800):
-            P.ising_init_random(h, 7 + gi)
-            sec = timed(lambda: P.ising_anneal(h, p0=0.1, t_total=T, seed=7 + gi, stream=stream))
-            plain.append({"sweeps": T, "s": sec, "cut": P.ising_cut(h)})
-        learned = []
-        for Ta in (25, 50, 100):
-            for rounds in (1, 2, 4, 8):
-                P.ising_init_random(h, 7 + gi)
+    def graph_best():
+        return P.ising_batch_cuts(tb).reshape(num, 8).max(axis=1)
 
-                def run():
-                    P.ising_anneal(h, p0=0.1, t_total=Ta, seed=7 + gi, stream=stream)
-                    for r in range(rounds):
-                        P.ising_gnn_warm_start(net, h, set_bias=False)
-                        P.ising_anneal(h, p0=0.0, t_total=10, seed=11 + r, stream=stream)
-                sec = timed(run)
-                learned.append({"prefix": Ta, "rounds": rounds, "s": sec, "cut": P.ising_cut(h)})
-        # one forward pass alone
-        fwd = timed(lambda: P.ising_gnn_forward(net, h, torch.empty(g.n, dtype=torch.float32,
-                                                                     device="cuda")))
-        h.close()
-        # 99 % of the best cut any run found (the learned form can beat the
-        # plain annealer's long-run best)
-        best = max([best_plain] + [c["cut"] for c in plain + learned])
-        target = 0.99 * best
+    # long-run best of every held-out graph
+    P.ising_batch_init_random(tb, 90001)
+    long_s = timed(lambda: P.ising_batch_anneal(tb, p0=0.1, t_total=args.long_sweeps, seed=90001,
+                                                stream=stream))
+    long_best = graph_best()
+    # untimed: the network's workspace and the union's row tables
+    P.ising_gnn_batch_forward(net, tb, 0, torch.empty(test_vertices, dtype=torch.float32, device="cuda"))
+    fwd_s = timed(lambda: P.ising_gnn_batch_forward(
+        net, tb, 0, torch.empty(test_vertices, dtype=torch.float32, device="cuda")))
+    plain = []
+    for T in args.plain_sweeps:
+        P.ising_batch_init_random(tb, 7)
+        sec = timed(lambda: P.ising_batch_anneal(tb, p0=0.1, t_total=T, seed=7, stream=stream))
+        plain.append({"sweeps": T, "s": sec, "cuts": graph_best()})
+    learned = []
+    for Ta in (25, 50, 100):
+        for rounds in (1, 2, 4, 8):
+            P.ising_batch_init_random(tb, 7)
 
-        def first(curve, tgt):
-            ok = [c["s"] for c in curve if c["cut"] >= tgt]
-            return min(ok) if ok else None
-        target_plain = 0.99 * best_plain
-        results.append({"n": g.n, "m": g.m, "best": best, "best_plain_long_run": best_plain,
-                        "plain": plain, "learned": learned,
-                        "plain_s_to_99": first(plain, target), "learned_s_to_99": first(learned, target),
-                        "plain_s_to_99_of_plain_best": first(plain, target_plain),
-                        "learned_s_to_99_of_plain_best": first(learned, target_plain),
-                        "plain_longest_s": max(c["s"] for c in plain),
-                        "forward_ms": fwd * 1e3})
+            def run():
+                P.ising_batch_anneal(tb, p0=0.1, t_total=Ta, seed=7, stream=stream)
+                for r in range(rounds):
+                    P.ising_gnn_batch_warm_start(net, tb)
+                    P.ising_batch_anneal(tb, p0=0.0, t_total=10, seed=11 + r, stream=stream)
+            sec = timed(run)
+            learned.append({"prefix": Ta, "rounds": rounds, "s": sec, "cuts": graph_best()})
+    tb.close()
+    net.close()
+    best = np.maximum.reduce([long_best] + [c["cuts"] for c in plain + learned])
+
+    def summarise(curve, ref):
+        out = []
+        for c in curve:
+            ratio = c["cuts"] / np.maximum(ref, 1)
+            d = {k: v for k, v in c.items() if k != "cuts"}
+            d.update({"min_ratio": float(ratio.min()), "mean_ratio": float(ratio.mean()),
+                      "graphs_at_99": int(np.sum(ratio >= 0.99))})
+            out.append(d)
+        return out
+
+    def first(curve):
+        ok = [c["s"] for c in curve if c["graphs_at_99"] == num]
+        return min(ok) if ok else None
+    plain_c, learned_c = summarise(plain, best), summarise(learned, best)
+    plain_lr, learned_lr = summarise(plain, long_best), summarise(learned, long_best)
     if rank != 0:
         return
-    def mean_or_none(key):
-        xs = [r[key] for r in results]
-        return None if any(x is None for x in xs) else sum(xs) / len(xs)
-    value = mean_or_none("learned_s_to_99")
-    plain_value = mean_or_none("plain_s_to_99")
-    # where the plain annealer never got there, its longest timed run bounds
-    # its time from below
-    plain_bound = sum(r["plain_s_to_99"] if r["plain_s_to_99"] is not None else r["plain_longest_s"]
-                      for r in results) / len(results)
+    value, plain_value = first(learned_c), first(plain_c)
     line = {
         "metric": "time_to_cut_99pct_of_best", "value": value, "unit": "s", "n_gpus": world,
-        "steps": len(test), "warmup": 0, "ms_per_step": None if value is None else value * 1e3,
+        "steps": len(plain) + len(learned), "warmup": 0, "ms_per_step": None if value is None else value * 1e3,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "int8+bf16",
         "data": "synthetic",
-        "config": {"workload": "warmstart", "train_graphs": len(train),
-                   "train_vertices": sum(g.n for g in train), "train_steps": steps,
-                   "test_graphs": len(test), "test_n": spec["test_n"],
-                   "best_of": "max(best of 4 plain replicas x 10000 sweeps at p0 0.1, "
-                              "every timed run)",
-                   "learned_form": "anneal(prefix sweeps, p0 0.1) + rounds x (network warm start "
-                                   "+ 10 greedy sweeps)",
-                   "parallelism": f"replicas{world}"},
+        "config": {"workload": "warmstart", "form": "batched", "train_graphs": len(train_specs),
+                   "train_vertices": int(train_vertices), "train_n_range": [spec["nmin"], spec["nmax"]],
+                   "train_batch": per, "train_steps": steps, "test_graphs": num, "test_n": spec["test_n"],
+                   "replicas": 8, "best_of": f"max(best of 8 replicas x {args.long_sweeps} sweeps at p0 0.1, "
+                                             "every timed run), per graph",
+                   "reached": "every held-out graph has a replica at >= 99 % of its best cut",
+                   "learned_form": "anneal(prefix sweeps, p0 0.1) + rounds x (network warm start of every "
+                                   "replica + 10 greedy sweeps)",
+                   "batch_tuning": tuning, "parallelism": f"replicas{world}"},
         "plain_value": plain_value,
-        "plain_value_lower_bound": plain_bound,
-        "speedup_vs_plain": (None if value is None or plain_value is None else plain_value / value),
-        "speedup_vs_plain_lower_bound": None if value is None else plain_bound / value,
-        "of_plain_long_run_best": {"learned_s": mean_or_none("learned_s_to_99_of_plain_best"),
-                                   "plain_s": mean_or_none("plain_s_to_99_of_plain_best")},
-        "train_s": train_s, "setup_s": time.perf_counter() - t_setup, "train_loss": losses,
-        "results": results, "roofline": None, "cpu_baseline": None, "e2e": None,
-        "gpu_launches": None, "clocks": None,
+        "speedup_vs_plain": None if value is None or plain_value is None else plain_value / value,
+        "of_long_run_best": {"learned_s": first(learned_lr), "plain_s": first(plain_lr)},
+        "plain": plain_c, "learned": learned_c,
+        "long_run_s": long_s, "forward_one_replica_s": fwd_s,
+        "generate_s": gen_s, "label_s": label_s, "train_s": train_s,
+        "setup_s": time.perf_counter() - t_setup, "train_loss": losses,
+        "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": None,
     }
     print(json.dumps(line), flush=True)
 

@@ -514,6 +514,16 @@ int ising_gnn_batch_forward(ising_gnn* net, ising_batch* b, uint32_t replica, fl
  * Asynchronous on the batch's stream (the stream of its last anneal call). */
 #define ISING_ALL_REPLICAS 0xFFFFFFFFu
 int ising_gnn_batch_warm_start(ising_gnn* net, ising_batch* b, uint32_t replica);
+/* ising_gnn_batch_gradients / ising_gnn_batch_train_step -- as
+ * ising_gnn_gradients / ising_gnn_train_step on the batch's instances taken
+ * together as one graph, from replica `replica`'s spins: the loss G4 is the
+ * mean over every vertex of every instance (one minibatch of graphs).
+ * labels: int8[total vertices] (+1 / -1), laid out as the logits of
+ * ising_gnn_batch_forward; host values are checked. */
+int ising_gnn_batch_gradients(ising_gnn* net, ising_batch* b, uint32_t replica, const int8_t* labels,
+                              int labels_on_device, float* out_loss, float* out_grad);
+int ising_gnn_batch_train_step(ising_gnn* net, ising_batch* b, uint32_t replica, const int8_t* labels,
+                               int labels_on_device, float lr, float* out_loss);
 /* ising_gnn_launch_count -- kernels launched by this network handle. */
 int ising_gnn_launch_count(ising_gnn* net, uint64_t* out);
 /* ising_gnn_destroy -- free the network (NULL is ignored). */

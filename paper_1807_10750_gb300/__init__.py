@@ -57,7 +57,8 @@ EXPORTS = (
     "ising_gnn_warm_start", "ising_gnn_launch_count", "ising_gnn_destroy", "ising_debug_fault",
     "ising_engine_used", "ising_set_halo_sweeps", "ising_halo_info", "ising_plan_halo",
     "ising_convergence_region", "ising_batch_set_tuning", "ising_batch_tuning",
-    "ising_gnn_batch_forward", "ising_gnn_batch_warm_start",
+    "ising_gnn_batch_forward", "ising_gnn_batch_warm_start", "ising_gnn_batch_gradients",
+    "ising_gnn_batch_train_step",
 )
 ISING_ENGINE_USED_BLOCK = 6
 ISING_FAULT_NONE = 0
@@ -144,6 +145,8 @@ def lib():
         L.ising_gnn_warm_start.argtypes = [vp, vp, ctypes.c_int]
         L.ising_gnn_batch_forward.argtypes = [vp, vp, ctypes.c_uint32, vp, ctypes.c_int]
         L.ising_gnn_batch_warm_start.argtypes = [vp, vp, ctypes.c_uint32]
+        L.ising_gnn_batch_gradients.argtypes = [vp, vp, ctypes.c_uint32, vp, ctypes.c_int, vp, vp]
+        L.ising_gnn_batch_train_step.argtypes = [vp, vp, ctypes.c_uint32, vp, ctypes.c_int, ctypes.c_float, vp]
         L.ising_gnn_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
         L.ising_gnn_destroy.argtypes = [vp]
         L.ising_gnn_destroy.restype = None
@@ -675,6 +678,31 @@ def ising_gnn_batch_forward(net: IsingGnn, b: IsingBatch, replica: int = 0, out=
 
 def ising_gnn_batch_warm_start(net: IsingGnn, b: IsingBatch, replica: int = ISING_ALL_REPLICAS) -> None:
     _check(lib().ising_gnn_batch_warm_start(net.ptr, b.ptr, replica), "ising_gnn_batch_warm_start")
+
+
+def ising_gnn_batch_gradients(net: IsingGnn, b: IsingBatch, labels, replica: int = 0):
+    """(loss, gradient) over every instance of the batch; int8 +-1 labels laid
+    out as the logits of ising_gnn_batch_forward."""
+    total = ising_batch_info(b)["vertices"]
+    p, on_dev, _keep = _buffer(labels, np.int8, total, False)
+    loss = ctypes.c_float()
+    grad = np.zeros(ISING_GNN_NUM_PARAMS, dtype=np.float32)
+    _check(lib().ising_gnn_batch_gradients(net.ptr, b.ptr, replica, p, on_dev, ctypes.byref(loss),
+                                           grad.ctypes.data), "ising_gnn_batch_gradients")
+    return float(loss.value), grad
+
+
+def ising_gnn_batch_train_step(net: IsingGnn, b: IsingBatch, labels, lr: float, replica: int = 0,
+                               want_loss: bool = False):
+    """One Adam step on the batch's instances as one minibatch; returns the
+    loss (before the step) if ``want_loss``."""
+    total = ising_batch_info(b)["vertices"]
+    p, on_dev, _keep = _buffer(labels, np.int8, total, False)
+    loss = ctypes.c_float()
+    _check(lib().ising_gnn_batch_train_step(net.ptr, b.ptr, replica, p, on_dev, float(lr),
+                                            ctypes.byref(loss) if want_loss else None),
+           "ising_gnn_batch_train_step")
+    return float(loss.value) if want_loss else None
 
 
 def ising_gnn_launch_count(net: IsingGnn) -> int:

@@ -42,8 +42,10 @@ struct BatchGraph {
   int32_t vtx_base;    // first vertex in the concatenated vertex arrays
   int32_t row_base;    // first entry of this instance's row_ptr (n + 1 entries)
   int32_t class_base;  // first entry of this instance's class bounds (num_classes + 1)
-  int32_t byte_lanes;  // 1: every row's sum of |w| is at most 255 (byte-lane sums apply);
-                       // 2: moreover every weight is +1 or -1
+  int32_t byte_lanes;  // 2: every weight is +1 or -1; 1: every |w| is at most 31 (byte-lane
+                       // sums); 0: per-replica sums
+  int32_t flush;       // heavy rows, byte-lane modes: entries a lane adds before its byte
+                       // lanes could reach 255 (then they are moved to int sums)
 };
 
 struct BatchDev {
@@ -53,6 +55,9 @@ struct BatchDev {
   const int32_t* adj;        // packed (col << 8) | (w & 0xff), col local to the instance
   const int32_t* orig;       // position -> vertex id within the instance
   const int32_t* class_pos;  // per instance: first position of each class, then n
+  const int32_t* class_heavy;  // per instance and class: the end of the class's heavy rows
+                               // (positions class_pos[c] .. class_heavy[c] - 1; a class lists
+                               // its rows by decreasing degree)
   uint8_t* spins;            // replica bits per position
   uint8_t* flips;            // the sweep's flip bits per vertex id (bit r = replica r)
 };
@@ -195,6 +200,75 @@ __device__ __forceinline__ int decide_replicas(const RowSums& r, int mode, int o
   return nb;
 }
 
+// A heavy row (more entries than byte lanes can sum: degree * max|w| > 255)
+// decided by a whole warp: lanes stride the entries; in the byte-lane modes a
+// lane moves its byte lanes into int sums every `flush` entries, so no lane
+// overflows; the lanes' sums meet by warp shuffles and lane 0 decides.
+__device__ __forceinline__ void heavy_row(const BatchDev& d, uint8_t* sp, const BatchGraph& G, int mode,
+                                          const int32_t* rp, int v, int lane, uint32_t thr, int replicas) {
+  int acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int wsum = 0;
+  const int e1 = __ldg(rp + v + 1);
+  int e = __ldg(rp + v) + lane;
+  if (mode == 0) {
+    for (; e < e1; e += 32) {
+      const int word = __ldg(d.adj + e);
+      const int wgt = (word << 24) >> 24;
+      const int b = sp[static_cast<unsigned>(word) >> 8];
+      wsum += wgt;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) acc[k] += (b >> k) & 1 ? wgt : 0;
+    }
+  } else {
+    while (e < e1) {
+      uint32_t a0 = 0u, a1 = 0u, a2 = 0u, a3 = 0u;
+      for (int i = 0; i < G.flush && e < e1; ++i, e += 32) {
+        const uint32_t word = static_cast<uint32_t>(__ldg(d.adj + e));
+        const uint32_t b = sp[word >> 8];
+        if (mode == 2) {
+          const uint32_t neg = static_cast<uint32_t>(static_cast<int32_t>(word << 24) >> 31);
+          a0 += (((b ^ neg) & 0xfu) * 0x00204081u) & 0x01010101u;
+          a1 += ((((b >> 4) ^ neg) & 0xfu) * 0x00204081u) & 0x01010101u;
+          wsum += 1;
+        } else {
+          const int wgt = static_cast<int>(word << 24) >> 24;
+          const uint32_t lo = ((b & 0xfu) * 0x00204081u) & 0x01010101u;
+          const uint32_t hi = ((b >> 4) * 0x00204081u) & 0x01010101u;
+          const uint32_t mag = static_cast<uint32_t>(wgt < 0 ? -wgt : wgt);
+          wsum += wgt;
+          if (wgt > 0) {
+            a0 += lo * mag;
+            a1 += hi * mag;
+          } else {
+            a2 += lo * mag;
+            a3 += hi * mag;
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        acc[k] += static_cast<int>((a0 >> (8 * k)) & 0xffu) - static_cast<int>((a2 >> (8 * k)) & 0xffu);
+        acc[k + 4] += static_cast<int>((a1 >> (8 * k)) & 0xffu) - static_cast<int>((a3 >> (8 * k)) & 0xffu);
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+  }
+  if (lane == 0) {
+    RowSums r;
+    r.a0 = r.a1 = r.a2 = r.a3 = 0u;
+    r.wsum = wsum;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) r.acc[k] = acc[k];
+    const int fl = thr != 0u ? __ldcg(d.flips + G.vtx_base + __ldg(d.orig + G.vtx_base + v)) : 0;
+    sp[v] = static_cast<uint8_t>(decide_replicas(r, 0, sp[v], fl, replicas));
+  }
+}
+
 // One instance per block iteration; all sweeps t_begin .. t_begin + sweeps - 1.
 // Tuning (ising_batch_autotune): BLOCK threads; S threads share each row
 // (the row's entries strided over them); classes of at most `tail` vertices
@@ -223,6 +297,7 @@ __global__ void __launch_bounds__(BLOCK)
     const uint32_t kb = seed_hi ^ (static_cast<uint32_t>(gi) * 0x9E3779B9u);
     const int32_t* rp = d.row_ptr + G.row_base;
     const int32_t* cls = d.class_pos + G.class_base;
+    const int32_t* hcls = d.class_heavy + G.class_base;
     const int mode = G.byte_lanes;
     for (uint32_t k = 0; k < sweeps; ++k) {
       const uint64_t t = t_begin + k;
@@ -245,12 +320,13 @@ __global__ void __launch_bounds__(BLOCK)
       }
       bool tail_run = false;  // warp 0 has decided tail classes since the last block barrier
       for (int c = 0; c < G.num_classes; ++c) {
-        const int cb = __ldg(cls + c), ce = __ldg(cls + c + 1);
+        const int cb = __ldg(cls + c), ce = __ldg(cls + c + 1), hb = __ldg(hcls + c);
         const bool small = ce - cb <= tail;
         if (small) {
-          // warp 0 alone: one vertex per lane
+          // warp 0 alone: the heavy rows one at a time, then one light vertex per lane
           if (threadIdx.x < 32) {
-            const int v = cb + lane;
+            for (int v = cb; v < hb; ++v) heavy_row(d, sp, G, mode, rp, v, lane, thr, replicas);
+            const int v = hb + lane;
             if (v < ce) {
               RowSums r;
               row_sums<1>(d, sp, mode, __ldg(rp + v), __ldg(rp + v + 1), 0, r);
@@ -266,7 +342,9 @@ __global__ void __launch_bounds__(BLOCK)
           __syncthreads();
           tail_run = false;
         }
-        for (int v = cb + static_cast<int>(threadIdx.x) / S; v < ce; v += BLOCK / S) {
+        for (int v = cb + static_cast<int>(threadIdx.x) / 32; v < hb; v += BLOCK / 32)
+          heavy_row(d, sp, G, mode, rp, v, lane, thr, replicas);
+        for (int v = hb + static_cast<int>(threadIdx.x) / S; v < ce; v += BLOCK / S) {
           RowSums r;
           row_sums<S>(d, sp, mode, __ldg(rp + v), __ldg(rp + v + 1), sub, r);
           if (S > 1) row_combine<S>(r, gmask);
@@ -365,6 +443,7 @@ struct ising_batch {
   int32_t* d_adj = nullptr;
   int32_t* d_orig = nullptr;
   int32_t* d_class_pos = nullptr;
+  int32_t* d_class_heavy = nullptr;
   uint8_t* d_spins = nullptr;
   uint8_t* d_flips = nullptr;
   unsigned* d_work = nullptr;
@@ -394,6 +473,7 @@ struct ising_batch {
     d.adj = d_adj;
     d.orig = d_orig;
     d.class_pos = d_class_pos;
+    d.class_heavy = d_class_heavy;
     d.spins = d_spins;
     d.flips = d_flips;
     return d;
@@ -408,7 +488,7 @@ void batch_free(ising_batch* b) {
   void* ptrs[] = {b->d_graphs,       b->d_order,       b->d_row_ptr,    b->d_adj,
                   b->d_orig,         b->d_class_pos,   b->d_spins,      b->d_flips,
                   b->d_work,         b->d_energy2,     b->d_union_row_ptr, b->d_union_vbase,
-                  b->d_gnn_rowid,    b->d_gnn_hchunk,  b->d_gnn_chunk_row};
+                  b->d_gnn_rowid,    b->d_gnn_hchunk,  b->d_gnn_chunk_row, b->d_class_heavy};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -544,7 +624,7 @@ int ising_batch_create(int32_t num_graphs, const int32_t* n, const int64_t* m, c
   b->num_graphs = num_graphs;
   b->replicas = static_cast<int>(replicas);
   std::vector<BatchGraph> graphs((size_t)num_graphs);
-  std::vector<int32_t> row_ptr, adj, orig, class_pos;
+  std::vector<int32_t> row_ptr, adj, orig, class_pos, class_heavy;
   std::vector<int64_t> size_key((size_t)num_graphs);
   int64_t edge_off = 0, vtx = 0;
   int rc = ISING_OK;
@@ -578,16 +658,22 @@ int ising_batch_create(int32_t num_graphs, const int32_t* n, const int64_t* m, c
       G.vtx_base = static_cast<int32_t>(vtx);
       G.row_base = static_cast<int32_t>(row_ptr.size());
       G.class_base = static_cast<int32_t>(class_pos.size());
-      int64_t widest = 0;  // largest sum of |w| over a row
-      for (int32_t v = 0; v < hg.n; ++v) {
-        int64_t row = 0;
-        for (int32_t k = hg.row_ptr[(size_t)v]; k < hg.row_ptr[(size_t)v + 1]; ++k)
-          row += std::abs(static_cast<int64_t>(hg.w[(size_t)k]));
-        widest = std::max(widest, row);
+      int64_t wmax = 0;  // largest |w|
+      for (size_t k = 0; k < (size_t)hg.nnz; ++k)
+        wmax = std::max<int64_t>(wmax, std::abs(static_cast<int64_t>(hg.w[k])));
+      const bool unit = wmax <= 1;  // every weight +1 or -1 (merged weights are never 0)
+      // byte lanes hold sums up to 255: a light row has degree * max|w| <= 255
+      G.byte_lanes = unit ? 2 : (wmax <= 31 ? 1 : 0);
+      const int64_t heavy_deg = unit ? 255 : (wmax <= 31 ? 255 / std::max<int64_t>(wmax, 1) : 64);
+      G.flush = static_cast<int32_t>(G.byte_lanes ? heavy_deg : 0);
+      for (int32_t c = 0; c < hg.num_colours; ++c) {
+        const int32_t cb = hg.class_begin[(size_t)c], ce = hg.class_begin[(size_t)c + 1];
+        int32_t hb = cb;  // one past the class's last heavy row
+        for (int32_t p = cb; p < ce; ++p)
+          if (hg.row_ptr[(size_t)p + 1] - hg.row_ptr[(size_t)p] > heavy_deg) hb = p + 1;
+        class_heavy.push_back(hb);
       }
-      bool unit = true;  // every weight +1 or -1
-      for (size_t k = 0; k < (size_t)hg.nnz && unit; ++k) unit = hg.w[k] == 1 || hg.w[k] == -1;
-      G.byte_lanes = widest <= 255 ? (unit ? 2 : 1) : 0;
+      class_heavy.push_back(hg.n);  // same layout as the class bounds
       for (size_t v = 0; v <= (size_t)hg.n; ++v)
         row_ptr.push_back(static_cast<int32_t>(edge_off + hg.row_ptr[v]));
       for (size_t k = 0; k < (size_t)hg.nnz; ++k)
@@ -631,6 +717,7 @@ int ising_batch_create(int32_t num_graphs, const int32_t* n, const int64_t* m, c
     if ((e = upload(&b->d_adj, adj, b->stream)) != cudaSuccess) break;
     if ((e = upload(&b->d_orig, orig, b->stream)) != cudaSuccess) break;
     if ((e = upload(&b->d_class_pos, class_pos, b->stream)) != cudaSuccess) break;
+    if ((e = upload(&b->d_class_heavy, class_heavy, b->stream)) != cudaSuccess) break;
     if ((e = cudaMalloc(reinterpret_cast<void**>(&b->d_spins), std::max<int64_t>(vtx, 16))) != cudaSuccess) break;
     if ((e = cudaMemsetAsync(b->d_spins, 0, std::max<int64_t>(vtx, 16), b->stream)) != cudaSuccess) break;
     if ((e = cudaMalloc(reinterpret_cast<void**>(&b->d_flips), std::max<int64_t>(vtx, 16))) != cudaSuccess) break;

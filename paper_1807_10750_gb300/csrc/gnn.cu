@@ -729,9 +729,11 @@ __global__ void adam_kernel(float* p, float* m, float* v, const float* g, float 
   }
 }
 
-__global__ void gather_labels_kernel(const int8_t* caller, const int32_t* orig, int n, int8_t* pos_out) {
+// pos_out[p] = caller[vbase[p] + orig[p]] (vbase null: 0).
+__global__ void gather_labels_kernel(const int8_t* caller, const int32_t* orig, const int32_t* vbase, int n,
+                                     int8_t* pos_out) {
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
-    pos_out[v] = caller[orig[v]];
+    pos_out[v] = caller[(vbase ? vbase[v] : 0) + orig[v]];
 }
 
 // caller[vbase[p] + orig[p]] = z[p] (vbase null: 0).
@@ -1108,31 +1110,28 @@ int run_backward(ising_gnn* net, const Ctx& x) {
   return ISING_OK;
 }
 
-int load_labels(ising_gnn* net, ising_graph* g, const int8_t* labels, int on_device) {
-  const int n = g->n;
+int load_labels(ising_gnn* net, const Ctx& x, const int8_t* labels, int on_device) {
+  const int n = x.v.n;
   const int8_t* src = labels;
   if (!on_device) {
     for (int i = 0; i < n; ++i)
       if (labels[i] != 1 && labels[i] != -1) return ISING_EINVAL;
-    GNN_CUDA(net, cudaMemcpyAsync(net->d_out, labels, static_cast<size_t>(n), cudaMemcpyHostToDevice, g->stream));
+    GNN_CUDA(net, cudaMemcpyAsync(net->d_out, labels, static_cast<size_t>(n), cudaMemcpyHostToDevice, x.st));
     src = reinterpret_cast<const int8_t*>(net->d_out);
   }
-  gather_labels_kernel<<<grid_of(n, 256, g->num_sms * 8), 256, 0, g->stream>>>(src, g->d_orig, n, net->d_y);
+  gather_labels_kernel<<<grid_of(n, 256, x.sms * 8), 256, 0, x.st>>>(src, x.orig, x.vbase, n, net->d_y);
   net->launches++;
   GNN_CUDA(net, cudaGetLastError());
-  if (!on_device) GNN_CUDA(net, cudaStreamSynchronize(g->stream));
+  if (!on_device) GNN_CUDA(net, cudaStreamSynchronize(x.st));
   return ISING_OK;
 }
 
-int gradients_impl(ising_gnn* net, ising_graph* g, const int8_t* labels, int on_device) {
+int gradients_impl(ising_gnn* net, const Ctx& x, const int8_t* labels, int on_device) {
   if (labels == nullptr) return ISING_EINVAL;
-  GNN_CUDA(net, ensure_work(net, g->n));
-  Ctx x;
-  int rc = graph_ctx(net, g, &x);
+  GNN_CUDA(net, ensure_work(net, x.v.n));
+  int rc = load_labels(net, x, labels, on_device);
   if (rc != ISING_OK) return rc;
-  rc = load_labels(net, g, labels, on_device);
-  if (rc != ISING_OK) return rc;
-  GNN_CUDA(net, cudaMemsetAsync(net->d_grad, 0, sizeof(float) * kNumParams, g->stream));
+  GNN_CUDA(net, cudaMemsetAsync(net->d_grad, 0, sizeof(float) * kNumParams, x.st));
   rc = run_forward(net, x, true);
   if (rc != ISING_OK) return rc;
   return run_backward(net, x);
@@ -1154,11 +1153,36 @@ int forward_out(ising_gnn* net, const Ctx& x, float* out_logits, int on_device) 
   return ISING_OK;
 }
 
-int read_loss(ising_gnn* net, ising_graph* g, float* out_loss) {
+int read_loss(ising_gnn* net, const Ctx& x, float* out_loss) {
   double l = 0.0;
-  GNN_CUDA(net, cudaMemcpyAsync(&l, net->d_loss, sizeof(double), cudaMemcpyDeviceToHost, g->stream));
-  GNN_CUDA(net, cudaStreamSynchronize(g->stream));
-  *out_loss = static_cast<float>(l / static_cast<double>(g->n));
+  GNN_CUDA(net, cudaMemcpyAsync(&l, net->d_loss, sizeof(double), cudaMemcpyDeviceToHost, x.st));
+  GNN_CUDA(net, cudaStreamSynchronize(x.st));
+  *out_loss = static_cast<float>(l / static_cast<double>(x.v.n));
+  return ISING_OK;
+}
+
+// The gradient's public tail: copy it and the loss out when asked.
+int gradients_out(ising_gnn* net, const Ctx& x, float* out_loss, float* out_grad) {
+  if (out_grad != nullptr) {
+    GNN_CUDA(net, cudaMemcpyAsync(out_grad, net->d_grad, sizeof(float) * kNumParams, cudaMemcpyDeviceToHost, x.st));
+    GNN_CUDA(net, cudaStreamSynchronize(x.st));
+  }
+  if (out_loss != nullptr) return read_loss(net, x, out_loss);
+  return ISING_OK;
+}
+
+// One Adam step from net->d_grad, then fresh bf16 weight copies.
+int adam_step(ising_gnn* net, const Ctx& x, float lr) {
+  net->step++;
+  const double b1 = 0.9, b2 = 0.999;
+  const float bc1 = static_cast<float>(1.0 - std::pow(b1, static_cast<double>(net->step)));
+  const float bc2 = static_cast<float>(1.0 - std::pow(b2, static_cast<double>(net->step)));
+  adam_kernel<<<grid_of(kNumParams, 256, 128), 256, 0, x.st>>>(net->d_params, net->d_m, net->d_v, net->d_grad, lr,
+                                                               static_cast<float>(b1), static_cast<float>(b2), bc1,
+                                                               bc2, 1e-8f);
+  cast_weights_kernel<<<32, 256, 0, x.st>>>(net->d_params, net->d_w0, net->d_w1, net->d_w2);
+  net->launches += 2;
+  GNN_CUDA(net, cudaGetLastError());
   return ISING_OK;
 }
 
@@ -1283,14 +1307,12 @@ int ising_gnn_gradients(ising_gnn* net, ising_graph* g, const int8_t* labels, in
                         float* out_loss, float* out_grad) {
   int rc = net_enter(net, g);
   if (rc != ISING_OK) return rc;
-  rc = gradients_impl(net, g, labels, labels_on_device);
+  Ctx x;
+  rc = graph_ctx(net, g, &x);
   if (rc != ISING_OK) return rc;
-  if (out_grad != nullptr) {
-    GNN_CUDA(net, cudaMemcpyAsync(out_grad, net->d_grad, sizeof(float) * kNumParams, cudaMemcpyDeviceToHost, g->stream));
-    GNN_CUDA(net, cudaStreamSynchronize(g->stream));
-  }
-  if (out_loss != nullptr) return read_loss(net, g, out_loss);
-  return ISING_OK;
+  rc = gradients_impl(net, x, labels, labels_on_device);
+  if (rc != ISING_OK) return rc;
+  return gradients_out(net, x, out_loss, out_grad);
 }
 
 int ising_gnn_train_step(ising_gnn* net, ising_graph* g, const int8_t* labels, int labels_on_device,
@@ -1298,20 +1320,39 @@ int ising_gnn_train_step(ising_gnn* net, ising_graph* g, const int8_t* labels, i
   int rc = net_enter(net, g);
   if (rc != ISING_OK) return rc;
   if (!(lr >= 0.0f) || !std::isfinite(lr)) return ISING_EINVAL;
-  rc = gradients_impl(net, g, labels, labels_on_device);
+  Ctx x;
+  rc = graph_ctx(net, g, &x);
   if (rc != ISING_OK) return rc;
-  net->step++;
-  const double b1 = 0.9, b2 = 0.999;
-  const float bc1 = static_cast<float>(1.0 - std::pow(b1, static_cast<double>(net->step)));
-  const float bc2 = static_cast<float>(1.0 - std::pow(b2, static_cast<double>(net->step)));
-  adam_kernel<<<grid_of(kNumParams, 256, 128), 256, 0, g->stream>>>(
-      net->d_params, net->d_m, net->d_v, net->d_grad, lr, static_cast<float>(b1), static_cast<float>(b2), bc1, bc2,
-      1e-8f);
-  cast_weights_kernel<<<32, 256, 0, g->stream>>>(net->d_params, net->d_w0, net->d_w1, net->d_w2);
-  net->launches += 2;
-  GNN_CUDA(net, cudaGetLastError());
-  if (out_loss != nullptr) return read_loss(net, g, out_loss);
-  return ISING_OK;
+  rc = gradients_impl(net, x, labels, labels_on_device);
+  if (rc != ISING_OK) return rc;
+  rc = adam_step(net, x, lr);
+  if (rc != ISING_OK) return rc;
+  return gradients_out(net, x, out_loss, nullptr);
+}
+
+int ising_gnn_batch_gradients(ising_gnn* net, ising_batch* b, uint32_t replica, const int8_t* labels,
+                              int labels_on_device, float* out_loss, float* out_grad) {
+  Ctx x;
+  isingx::BatchUnion u;
+  int rc = batch_ctx(net, b, replica, &x, &u);
+  if (rc != ISING_OK) return rc;
+  rc = gradients_impl(net, x, labels, labels_on_device);
+  if (rc != ISING_OK) return rc;
+  return gradients_out(net, x, out_loss, out_grad);
+}
+
+int ising_gnn_batch_train_step(ising_gnn* net, ising_batch* b, uint32_t replica, const int8_t* labels,
+                               int labels_on_device, float lr, float* out_loss) {
+  if (!(lr >= 0.0f) || !std::isfinite(lr)) return ISING_EINVAL;
+  Ctx x;
+  isingx::BatchUnion u;
+  int rc = batch_ctx(net, b, replica, &x, &u);
+  if (rc != ISING_OK) return rc;
+  rc = gradients_impl(net, x, labels, labels_on_device);
+  if (rc != ISING_OK) return rc;
+  rc = adam_step(net, x, lr);
+  if (rc != ISING_OK) return rc;
+  return gradients_out(net, x, out_loss, nullptr);
 }
 
 int ising_gnn_warm_start(ising_gnn* net, ising_graph* g, int set_bias) {

@@ -16,6 +16,9 @@ from .graphs import (  # noqa: F401
     batched_workload,
     BATCHED,
     WARMSTART,
+    WARMSTART_BATCHED,
+    graph_from_spec,
+    warmstart_specs,
     warmstart_workload,
     complete_graph,
     cycle_graph,

@@ -47,6 +47,18 @@ def draw_weights(kind: str, m: int, rng: np.random.Generator) -> np.ndarray:
     raise ValueError(f"unknown weight kind {kind!r}")
 
 
+def _sorted_unique(a: np.ndarray) -> np.ndarray:
+    """np.unique(a) for an integer array, by sorting (the same result; much
+    faster than the hash-based path of recent numpy on large arrays)."""
+    a = np.sort(a, kind="stable")
+    if a.size == 0:
+        return a
+    keep = np.empty(a.size, dtype=bool)
+    keep[0] = True
+    np.not_equal(a[1:], a[:-1], out=keep[1:])
+    return a[keep]
+
+
 def _pairs_from_index(k: np.ndarray):
     """Map a linear index over {(i, j): 0 <= i < j} (ordered by j, then i) to
     the pair (i, j)."""
@@ -71,10 +83,10 @@ def er_graph(n: int, p: float, seed: int, weights: str = "one") -> Graph:
         # Same law as above without materialising all pairs: draw the edge
         # count, then that many distinct pair indices uniformly.
         m = int(rng.binomial(npairs, p))
-        idx = np.unique(rng.integers(0, npairs, size=m, dtype=np.int64))
+        idx = _sorted_unique(rng.integers(0, npairs, size=m, dtype=np.int64))
         while idx.size < m:
             more = rng.integers(0, npairs, size=m - idx.size, dtype=np.int64)
-            idx = np.unique(np.concatenate([idx, more]))
+            idx = _sorted_unique(np.concatenate([idx, more]))
         idx = idx[:m]
     i, j = _pairs_from_index(idx)
     w = draw_weights(weights, idx.size, rng)
@@ -174,7 +186,7 @@ def zipf_config_graph(n: int, alpha: float, dmin: int, dmax: int, seed: int,
     keep = a != b
     a, b = a[keep], b[keep]
     lo, hi = np.minimum(a, b), np.maximum(a, b)
-    key = np.unique(lo * n + hi)
+    key = _sorted_unique(lo * n + hi)
     src = (key // n).astype(np.int32)
     dst = (key % n).astype(np.int32)
     w = draw_weights(weights, src.size, rng)
@@ -245,13 +257,19 @@ def workload(name: str, **override) -> tuple[Graph, dict]:
 # The learned warm-start workload: training graphs (Erdos-Renyi with mean
 # degree 10 and power-law graphs, alternating; n log-uniform in
 # [nmin, nmax]; weights uniform in [-8, 8] without 0) and held-out
-# 100k-vertex power-law test graphs.
+# 100k-vertex power-law test graphs. WARMSTART is the small form the tests
+# and the single-graph measurements use; WARMSTART_BATCHED the batched form
+# (training graphs of 1k-100k vertices).
 WARMSTART = dict(train_count=64, nmin=1000, nmax=30000, gen_seed=5, test_count=2, test_n=100000,
                  test_seed=4242, alpha=2.1, dmin=4, dmax=10000)
+WARMSTART_BATCHED = dict(WARMSTART, train_count=2048, nmax=100000, test_count=152)
 
 
-def warmstart_workload(**override):
-    spec = dict(WARMSTART)
+def warmstart_specs(base=None, **override):
+    """(train, test, spec): graph specs (kind, n, seed, alpha, dmin, dmax) in
+    the order `warmstart_workload` generates them; `graph_from_spec` builds
+    one (so that a process pool can build them)."""
+    spec = dict(WARMSTART if base is None else base)
     spec.update(override)
     rng = np.random.default_rng(spec["gen_seed"])
     train = []
@@ -260,10 +278,21 @@ def warmstart_workload(**override):
                         spec["nmin"], spec["nmax"]))
         s = int(rng.integers(0, 2 ** 31 - 1))
         if k % 2 == 0:
-            train.append(zipf_config_graph(n, spec["alpha"], spec["dmin"], min(spec["dmax"], n // 4), s,
-                                           weights="int8"))
+            train.append(("zipf", n, s, spec["alpha"], spec["dmin"], min(spec["dmax"], n // 4)))
         else:
-            train.append(er_graph(n, min(1.0, 10.0 / (n - 1)), s, weights="int8"))
-    test = [zipf_config_graph(spec["test_n"], spec["alpha"], spec["dmin"], spec["dmax"],
-                              spec["test_seed"] + k, weights="int8") for k in range(spec["test_count"])]
+            train.append(("er", n, s, 0.0, 0, 0))
+    test = [("zipf", spec["test_n"], spec["test_seed"] + k, spec["alpha"], spec["dmin"], spec["dmax"])
+            for k in range(spec["test_count"])]
     return train, test, spec
+
+
+def graph_from_spec(t) -> Graph:
+    kind, n, s, alpha, dmin, dmax = t
+    if kind == "zipf":
+        return zipf_config_graph(n, alpha, dmin, dmax, s, weights="int8")
+    return er_graph(n, min(1.0, 10.0 / (n - 1)), s, weights="int8")
+
+
+def warmstart_workload(**override):
+    train, test, spec = warmstart_specs(**override)
+    return [graph_from_spec(t) for t in train], [graph_from_spec(t) for t in test], spec

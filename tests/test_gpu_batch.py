@@ -38,6 +38,13 @@ def small_batch():
     dst = np.concatenate([leaves, leaves[1:]])
     w = (rng.integers(5, 9, size=src.size) * rng.choice([-1, 1], size=src.size)).astype(np.int32)
     gs.append(synth.Graph(61, src, dst, w))
+    # power-law instances: rows longer than byte lanes can sum are decided by
+    # a whole warp (int8 weights: more than 31 entries; +-1 weights: more
+    # than 255), and weights up to |w| = 96 take the per-replica sums
+    gs.append(synth.zipf_config_graph(3000, 2.0, 3, 600, 31, weights="int8"))
+    gs.append(synth.zipf_config_graph(4000, 2.0, 3, 900, 32, weights="pm1"))
+    g = synth.random_small_graph(200, 0.05, 33, weights="int8")
+    gs.append(synth.Graph(g.n, g.src, g.dst, (g.w * 12).astype(np.int32)))
     return gs
 
 

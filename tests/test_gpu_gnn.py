@@ -279,6 +279,48 @@ def test_batch_warm_start_sets_each_replica_from_its_own_logits():
             off += g.n
 
 
+def _union(gs):
+    """The disjoint union of the instances, vertex ids offset instance by
+    instance (the layout of the batched logits and labels)."""
+    off = np.cumsum([0] + [g.n for g in gs])
+    src = np.concatenate([g.src.astype(np.int64) + o for g, o in zip(gs, off)])
+    dst = np.concatenate([g.dst.astype(np.int64) + o for g, o in zip(gs, off)])
+    w = np.concatenate([g.w for g in gs])
+    return go.Graph(int(off[-1]), src, dst, w)
+
+
+def test_batch_gradients_match_the_oracle_on_the_union():
+    gs = _batch_graphs()
+    params = synth.gnn_init_params(3)
+    pe = effective_params(params)
+    with P.ising_batch_create([(g.n, g.src, g.dst, g.w) for g in gs], replicas=2) as b, \
+            P.ising_gnn_create(params) as net:
+        P.ising_batch_init_random(b, 12)
+        s = np.concatenate([P.ising_batch_get_spins(b, k, 1) for k in range(len(gs))])
+        y = np.where(np.random.default_rng(13).random(s.size) < 0.8, s, -s).astype(np.int8)
+        loss, grad = P.ising_gnn_batch_gradients(net, b, y, replica=1)
+        # the train step's loss is the loss before its update
+        assert P.ising_gnn_batch_train_step(net, b, y, lr=1e-3, replica=1, want_loss=True) == pytest.approx(loss, rel=1e-6)
+    G = _union(gs)
+    x = go.features(G, s)
+    yf = y.astype(np.float64)
+    z_rd, cache = go.forward(G, x, pe, storage="bf16")
+    assert loss == pytest.approx(go.loss(z_rd, yf), rel=1e-3)
+    g_rd = go.backward(G, pe, cache, z_rd, yf, storage="bf16")
+    t = _gradient_terms(G, pe, cache, z_rd, yf)
+    k = 0
+    for blk, shape in go.SHAPES:
+        size = int(np.prod(shape))
+        sl = slice(k, k + size)
+        assert _norm_rel(grad[sl], g_rd[sl]) <= 1e-2, blk
+        err = np.abs(grad[sl].astype(np.float64) - g_rd[sl])
+        ratio = err / np.maximum(np.abs(g_rd[sl]), np.maximum(t[sl], 1e-300) / 4)
+        ratio[t[sl] == 0] = 0.0
+        assert np.all(ratio <= 1e-1), blk
+        assert np.sum(ratio > 1e-2) <= size // 1000, blk
+        k += size
+
+
 @pytest.mark.parametrize("engine", ["phase", "persistent", "dataflow"])
 @pytest.mark.parametrize("mode", ["det", "racy"])
 def test_flip_bias_anneal_matches_oracle(engine, mode):
