@@ -96,16 +96,21 @@ def algorithmic_bytes_per_sweep(n: int, nnz: int, entry_bytes: int) -> int:
 # the sweeps. The entry holds only while the kernel sources hash to `sources`:
 # once they change the counters are stale and traffic is reported as null.
 NCU_TRAFFIC = {
-    "torus1024": {"fixed": 31.81e6, "per_sweep": 3.1e3, "kernel": "halo_kernel",
+    "zipf1m": {"fixed": 98.16e6, "per_sweep": 11.90e6, "kernel": "hub_kernel", "engine": "hub",
+               "files": ('hub.cuh', 'sweep.cuh', 'philox.cuh', 'anneal.cu'),
+               "sources": "ffb04f714fb032d3",
+               "how": "ncu 4- and 12-sweep captures: 145.70 MB and 240.86 MB (read + write); the "
+                      "CSR is read from DRAM once and then mostly served from L2"},
+    "torus1024": {"fixed": 31.87e6, "per_sweep": 3.97e3, "kernel": "halo_kernel",
                   "engine": "halo",
                   "files": ('halo.cuh', 'halo_plan.cpp', 'host_graph.h', 'philox.cuh', 'sweep.cuh'),
-                  "sources": "aa2fbde569ce6aea",
-                  "how": "ncu 20- and 60-sweep captures: 31.871 MB and 31.996 MB, so the "
+                  "sources": "6b2b7998a08a8823",
+                  "how": "ncu 20- and 40-sweep captures: 31.870 MB and 31.950 MB, so the "
                          "working set is read once and then stays in shared memory and L2"},
-    "batched": {"fixed": 0.070e9, "per_sweep": 0.2287e9, "kernel": "batch_anneal_kernel",
+    "batched": {"fixed": 0.1266e9, "per_sweep": 0.2073e9, "kernel": "batch_anneal_kernel",
                 "files": ('batch.cu', 'philox.cuh'),
-                "sources": "1ac87464bf0332c2",
-                "how": "ncu 20- and 60-sweep captures: 4.643 GB and 13.789 GB"},
+                "sources": "4e515ffc2c5827dc",
+                "how": "ncu 20- and 60-sweep captures: 4.274 GB and 12.567 GB"},
 }
 
 
@@ -663,7 +668,13 @@ def run_gnn(args, world, rank, P, torch, dist):
 # Shared-memory traffic of the halo kernel per sweep: l1tex shared-memory
 # wavefronts (one wavefront moves up to 128 bytes) from ncu captures, slope
 # over the sweep count; valid while the kernel sources hash to `sources`.
-NCU_SMEM = {}
+NCU_SMEM = {
+    "torus1024": {"wavefronts_per_sweep": 575_453,
+                  "files": ('halo.cuh', 'halo_plan.cpp', 'host_graph.h', 'philox.cuh', 'sweep.cuh'),
+                  "sources": "6b2b7998a08a8823",
+                  "how": "l1tex__data_pipe_lsu_wavefronts_mem_shared.sum: 11,812,561 (20 sweeps) and "
+                         "23,321,622 (40 sweeps)"},
+}
 
 
 def roofline_entry(args, engine_name, T, B, B_lib, achieved, peak, peak_kind, sweep_s, clk):
