@@ -42,7 +42,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="zipf1m",
+    ap.add_argument("--workload", default=None,
                     choices=["torus1024", "zipf1m", "er800", "batched", "warmstart", "gnn", "region",
                              "all"])
     ap.add_argument("--engine", default="auto",
@@ -783,8 +783,41 @@ def run_region(args, world, rank, P, torch, dist):
     h.close()
 
 
+# The lines a default run (no --workload) adds under "secondary", each from
+# its own process after the headline zipf1m measurement: the batched workload
+# and a reduced batched warm-start run (the full-scale command and its result
+# are in profiles/warmstart_batched_config5.md).
+SECONDARY = [
+    ("batched", ["--workload", "batched", "--steps", "5", "--warmup", "3", "--e2e-steps", "1"], 900),
+    ("warmstart", ["--workload", "warmstart", "--train-graphs", "512", "--train-steps", "400",
+                   "--test-graphs", "32", "--long-sweeps", "4000",
+                   "--plain-sweeps", "100,200,400,800,1600,3200"], 1200),
+]
+
+
+def run_secondary():
+    """Run the SECONDARY workloads, one process each; their JSON lines (or
+    what went wrong)."""
+    out = []
+    for name, extra, limit in SECONDARY:
+        cmd = [sys.executable, os.path.abspath(__file__), "--no-cpu-baseline"] + extra
+        try:
+            r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, timeout=limit)
+            lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+            if r.returncode == 0 and lines:
+                out.append(json.loads(lines[-1]))
+            else:
+                out.append({"workload": name, "error": f"exit {r.returncode}: {r.stderr.strip()[-300:]}"})
+        except subprocess.TimeoutExpired:
+            out.append({"workload": name, "error": f"did not finish within {limit} s"})
+    return out
+
+
 def main():
     args = parse_args()
+    secondary = args.workload is None and args.impl == "ours" and args.sweeps is None
+    if args.workload is None:
+        args.workload = "zipf1m"
     if args.workload == "all":
         run_all(args)
     world, rank, local = dist_env()
@@ -997,6 +1030,8 @@ def main():
         "gpu_launches": int(launches),
         "clocks": clocks.summary(),
     }
+    if secondary and world == 1:
+        line["secondary"] = run_secondary()
     print(json.dumps(line), flush=True)
     P.ising_destroy(h)
     if world > 1:
