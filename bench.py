@@ -790,8 +790,9 @@ def run_region(args, world, rank, P, torch, dist):
 
 # The lines a default run (no --workload) adds under "secondary", each from
 # its own process after the headline zipf1m measurement: the batched workload
-# and a reduced batched warm-start run (the full-scale command and its result
-# are in profiles/warmstart_batched_config5.md).
+# and a reduced batched warm-start run (the full-scale run is
+# --workload warmstart --train-graphs 20000 --train-batch 256 --test-graphs 152
+# --long-sweeps 20000).
 SECONDARY = [
     ("batched", ["--workload", "batched", "--steps", "5", "--warmup", "3", "--e2e-steps", "1"], 900),
     ("warmstart", ["--workload", "warmstart", "--train-graphs", "512", "--train-steps", "400",
