@@ -685,7 +685,7 @@ NCU_SMEM = {
 def roofline_entry(args, engine_name, T, B, B_lib, achieved, peak, peak_kind, sweep_s, clk):
     """The roofline object of the dominant kernel. The grid and hub engines
     stream the CSR through L2 and HBM every sweep: bound "hbm", achieved =
-    algorithmic bytes (survey formula: 5 bytes per directed entry with int8
+    algorithmic bytes (5 bytes per directed entry with int8
     weights) over time. The halo engine reads its part of the graph from HBM
     once per launch and then works from shared memory, so its bound is the
     SMs' shared-memory bandwidth (152 SMs x 128 bytes per clock at the
