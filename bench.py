@@ -39,7 +39,8 @@ import numpy as np  # noqa: E402
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: per workload, a timed region of several seconds)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=None,
@@ -733,9 +734,13 @@ def run_all(args):
     # the CPU oracle arm covers the single-graph workloads
     names = WORKLOADS_ALL if args.impl == "ours" else ["er800", "torus1024", "zipf1m"]
     for wl in names:
-        cmd = [sys.executable, os.path.abspath(__file__), "--workload", wl, "--steps", str(args.steps),
+        cmd = [sys.executable, os.path.abspath(__file__), "--workload", wl,
                "--warmup", str(args.warmup), "--impl", args.impl, "--e2e-steps", str(args.e2e_steps),
                "--cpu-seconds", str(args.cpu_seconds)]
+        if args.steps is not None:
+            cmd += ["--steps", str(args.steps)]
+        if wl == "warmstart":  # the reduced form of the default run's secondary line
+            cmd += [x for x in dict((n, e) for n, e, _ in SECONDARY)["warmstart"] if x not in ("--workload", "warmstart")]
         if args.no_cpu_baseline:
             cmd.append("--no-cpu-baseline")
         r = subprocess.run(cmd, stdout=subprocess.PIPE, text=True)
@@ -794,7 +799,7 @@ def run_region(args, world, rank, P, torch, dist):
 # --workload warmstart --train-graphs 20000 --train-batch 256 --test-graphs 152
 # --long-sweeps 20000).
 SECONDARY = [
-    ("batched", ["--workload", "batched", "--steps", "5", "--warmup", "3", "--e2e-steps", "1"], 900),
+    ("batched", ["--workload", "batched", "--warmup", "3", "--e2e-steps", "1"], 900),
     ("warmstart", ["--workload", "warmstart", "--train-graphs", "512", "--train-steps", "400",
                    "--test-graphs", "32", "--long-sweeps", "4000",
                    "--plain-sweeps", "100,200,400,800,1600,3200"], 1200),
@@ -819,11 +824,19 @@ def run_secondary():
     return out
 
 
+# Default timed steps per workload: each timed region covers several seconds
+# (zipf1m 30 x 0.49 s, torus1024 300 x 11.6 ms, er800 200 x 17.8 ms, the
+# batched workload 25 x 140 ms, the region 20 x 0.18 s).
+DEFAULT_STEPS = {"zipf1m": 30, "torus1024": 300, "er800": 200, "batched": 25, "region": 20, "gnn": 20}
+
+
 def main():
     args = parse_args()
     secondary = args.workload is None and args.impl == "ours" and args.sweeps is None
     if args.workload is None:
         args.workload = "zipf1m"
+    if args.steps is None and args.workload != "all":
+        args.steps = DEFAULT_STEPS.get(args.workload, 30)
     if args.workload == "all":
         run_all(args)
     world, rank, local = dist_env()
