@@ -234,6 +234,111 @@ __global__ void __launch_bounds__(kPersistBlock, 2)
   }
 }
 
+// Small graphs whose whole packed CSR fits in one block's shared memory (the
+// 800-vertex workload: 38k entries, 160 KB): one block of 1024 threads holds
+// the row offsets, the entries, every state byte and the sweep's flips, for
+// the whole anneal call. A class is one pass in which 16 lanes share a row
+// (its entries strided over them, four in flight per lane, four shuffles to
+// combine) and the row's
+// first lane decides it at once, then one block barrier. The state bytes go
+// back to global memory at the end of the call. Deterministic linear
+// schedule (flip bias allowed); the spins equal one grid phase per class.
+constexpr int kCsrBlockThreads = 1024;
+constexpr int kCsrRowLanes = 16;
+
+struct CsrBlockLayout {
+  int rp, adj, cls, state, flip, total;
+};
+
+__host__ __device__ inline CsrBlockLayout csr_block_layout(int n, long long nnz, int ncls) {
+  CsrBlockLayout L{};
+  long long o = 0;
+  L.rp = 0;
+  o += 4LL * (n + 1);
+  L.adj = static_cast<int>((o + 15) & ~15LL);
+  o = L.adj + 4LL * nnz;
+  L.cls = static_cast<int>(o);
+  o += 4LL * (ncls + 1);
+  L.state = static_cast<int>(o);
+  o += n + 1;  // one spare state byte (spin +1) for a padding column
+  L.flip = static_cast<int>(o);
+  o += n;
+  o = (o + 15) & ~15LL;
+  L.total = o > 0x7fffffffLL ? 0x7fffffff : static_cast<int>(o);
+  return L;
+}
+
+__global__ void __launch_bounds__(kCsrBlockThreads, 1)
+    csr_block_kernel(DevGraph d, int n, int nnz, int ncls, const int32_t* __restrict__ class_pos,
+                     uint64_t t_begin, uint32_t sweeps, uint64_t T, uint64_t T0, uint32_t replica,
+                     isingx::PhiloxRounds rk) {
+  extern __shared__ __align__(16) unsigned char csr_mem[];
+  const CsrBlockLayout L = csr_block_layout(n, nnz, ncls);
+  int32_t* rp = reinterpret_cast<int32_t*>(csr_mem + L.rp);
+  int32_t* adj = reinterpret_cast<int32_t*>(csr_mem + L.adj);
+  int32_t* cls = reinterpret_cast<int32_t*>(csr_mem + L.cls);
+  uint8_t* state = csr_mem + L.state;
+  uint8_t* flip = csr_mem + L.flip;
+  const int tid = threadIdx.x;
+  for (int i = tid; i <= n; i += kCsrBlockThreads) rp[i] = __ldg(d.row_ptr + i);
+  for (int i = tid; i < nnz; i += kCsrBlockThreads) adj[i] = __ldg(d.adj + i);
+  for (int i = tid; i <= ncls; i += kCsrBlockThreads) cls[i] = __ldg(class_pos + i);
+  for (int i = tid; i < n; i += kCsrBlockThreads) state[i] = static_cast<uint8_t>(d.spins[i]);
+  if (tid == 0) state[n] = 0;
+  const int q = tid % kCsrRowLanes;                  // lane within the row's group
+  const int grp = tid / kCsrRowLanes;                // row group
+  const int ngrp = kCsrBlockThreads / kCsrRowLanes;
+  __syncthreads();
+  for (uint32_t k = 0; k < sweeps; ++k) {
+    const SweepArgs a = sweep_args(t_begin + k, T, T0, replica);
+    for (int i = tid; i < n; i += kCsrBlockThreads)
+      flip[i] = flip_drawn(d, i, static_cast<uint32_t>(__ldg(d.orig + i)), a, rk) ? 1 : 0;
+    __syncthreads();
+    for (int c = 0; c < ncls; ++c) {
+      const int ce = cls[c + 1];
+      for (int r0 = cls[c]; r0 < ce; r0 += ngrp) {
+        const int r = r0 + grp;
+        int f = 0;
+        if (r < ce) {
+          const int e1 = rp[r + 1];
+          int e = rp[r] + q;
+          for (; e + 3 * kCsrRowLanes < e1; e += 4 * kCsrRowLanes) {
+            uint32_t x[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) x[u] = static_cast<uint32_t>(adj[e + u * kCsrRowLanes]);
+            int sp[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) sp[u] = state[x[u] >> 8];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              f += static_cast<int>(static_cast<int8_t>(static_cast<uint8_t>(x[u] & 0xffu))) * isingx::spin_of(sp[u]);
+          }
+          for (; e < e1; e += kCsrRowLanes) {
+            const uint32_t x = static_cast<uint32_t>(adj[e]);
+            const int w = static_cast<int>(static_cast<int8_t>(static_cast<uint8_t>(x & 0xffu)));
+            f += w * isingx::spin_of(state[x >> 8]);
+          }
+        }
+        // every lane of the warp reaches the shuffles (r0 is uniform)
+#pragma unroll
+        for (int o = 1; o < kCsrRowLanes; o <<= 1) f += __shfl_xor_sync(isingx::kFullMask, f, o, kCsrRowLanes);
+        if (r < ce && q == 0) {
+          const int bt = state[r];
+          int sv = isingx::spin_of(bt);
+          if (f > 0)
+            sv = -1;
+          else if (f < 0)
+            sv = 1;
+          if (flip[r]) sv = -sv;
+          state[r] = static_cast<uint8_t>(isingx::state_byte(sv, ((bt >> 1) & 1) ^ 1));
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = tid; i < n; i += kCsrBlockThreads) d.spins[i] = static_cast<int8_t>(state[i]);
+}
+
 // Block engine (block.cuh): a graph of at most 4095 vertices, every sweep of
 // an anneal call in one block; deterministic pass, with Algorithm 1's flips
 // after each sweep when nflip0 > 0.
@@ -248,7 +353,10 @@ __global__ void __launch_bounds__(isingx::kBlockThreads)
   unsigned seq = 0;
   for (uint32_t k = 0; k < sweeps; ++k) {
     const SweepArgs a = sweep_args(t_begin + k, T, T0, replica);
-    if (!isingx::block_sweep(d, ba, a, rk, sh, seq)) return;
+    if (ba.resident_words > 0)
+      isingx::block_sweep_resident(d, ba, a, rk, sh);
+    else if (!isingx::block_sweep(d, ba, a, rk, sh, seq))
+      return;
     if (nflip0 != 0u) {
       // the sweep's updates are in global memory; warp 0 flips N_t spins
       const uint32_t N = isingx::nflip_count(nflip0, T, t_begin + k);
@@ -610,7 +718,31 @@ cudaError_t launch_block(ising_graph* g, uint64_t t_begin, uint32_t sweeps, uint
   ba.class_pos = g->d_class_begin;
   ba.wait_ns = static_cast<long long>(g->wait_budget_ns);
   ba.short_copy = g->fault_kind == ISING_FAULT_SHORT_COPY ? 1 : 0;
-  const int smem = isingx::block_layout(ba.n, ba.num_chunks, ba.num_classes).total;
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, g->device);
+  // the whole packed CSR in shared memory (linear schedule; not under the
+  // short-copy test, which needs the copies)
+  if (g->packed && nflip0 == 0u && !ba.short_copy && g->nnz < (1LL << 30)) {
+    const int csr_smem = csr_block_layout(g->n, g->nnz, g->num_colours).total;
+    if (csr_smem <= optin) {
+      cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void*>(csr_block_kernel),
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, csr_smem);
+      if (e != cudaSuccess) return e;
+      g->launches++;
+      csr_block_kernel<<<1, kCsrBlockThreads, csr_smem, g->stream>>>(
+          g->dev(), g->n, static_cast<int>(g->nnz), g->num_colours, g->d_class_begin, t_begin, sweeps, T, T0,
+          replica, rk);
+      return cudaGetLastError();
+    }
+  }
+  // every word resident in shared memory when it fits (not under the
+  // short-copy test, which needs the copies)
+  const int words = g->block_num_words;
+  ba.resident_words = 0;
+  if (!ba.short_copy && words > 0 &&
+      isingx::block_layout(ba.n, ba.num_chunks, ba.num_classes, words).total <= optin)
+    ba.resident_words = words;
+  const int smem = isingx::block_layout(ba.n, ba.num_chunks, ba.num_classes, ba.resident_words).total;
   cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void*>(block_kernel),
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
@@ -1157,6 +1289,7 @@ int ising_create(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, c
                           g->stream)) != cudaSuccess) break;
       g->block_ok = true;
       g->block_num_chunks = static_cast<int32_t>(block.chunk_off.size());
+      g->block_num_words = static_cast<int32_t>(block.words.size());
     }
     if (!hub_end.empty()) {
       const size_t X = hub_end.size();

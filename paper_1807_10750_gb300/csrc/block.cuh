@@ -11,6 +11,11 @@
 // changes, then a segmented scan across the warp), and each vertex of the
 // class applies Eq. 2 and Algorithm 2's flip exactly as the grid engines do.
 // The spins are identical to a sweep of one grid phase per class.
+//
+// When every packed word fits in shared memory with the tables (the
+// 800-vertex workload's 38k words take 154 KB), the block loads them once per
+// launch instead (resident form): no copies, no waits, and a class costs two
+// block barriers.
 #pragma once
 
 #include <cstdint>
@@ -32,6 +37,7 @@ struct BlockArgs {
   const int32_t* class_pos;     // per class + 1: first position
   long long wait_ns;            // bound of every wait (0: kBlockWaitNs)
   int short_copy;               // failure-detection tests: the first chunk expects 16 more bytes
+  int resident_words;           // > 0: every word is kept in shared memory (that many words)
 };
 
 constexpr int kBlockThreads = 512;
@@ -40,17 +46,17 @@ constexpr int kBlockChunkBytes = kBlockChunkWords * 4;
 constexpr int kBlockWordsPerThread = kBlockChunkWords / kBlockThreads;
 static_assert(kBlockWordsPerThread % 4 == 0, "whole 16-byte loads per thread");
 
-// Dynamic shared memory: kBlockRing mbarriers and chunk buffers, an int
-// accumulator per vertex (plus a spare slot for the padding words), the chunk
-// table, the class tables, then per vertex its state byte, its spin (+1/-1)
-// and its flip decision. Offsets in bytes.
+// Dynamic shared memory: kBlockRing mbarriers and chunk buffers (or, in the
+// resident form, every word), an int accumulator per vertex (plus a spare slot
+// for the padding words), the chunk table, the class tables, then per vertex
+// its state byte, its spin (+1/-1) and its flip decision. Offsets in bytes.
 struct BlockLayout {
   int acc, chunk, cls_chunk, cls_pos, state, spin, flip, total;
 };
 
-__host__ __device__ inline BlockLayout block_layout(int n, int nch, int ncls) {
+__host__ __device__ inline BlockLayout block_layout(int n, int nch, int ncls, int resident_words) {
   BlockLayout L{};
-  int o = 128 + kBlockRing * kBlockChunkBytes;
+  int o = 128 + (resident_words > 0 ? ((4 * resident_words + 15) & ~15) : kBlockRing * kBlockChunkBytes);
   L.acc = o;
   o += 4 * (n + 1);
   o = (o + 7) & ~7;
@@ -141,7 +147,7 @@ struct BlockShared {
 };
 
 __device__ __forceinline__ BlockShared block_shared(unsigned char* base, const BlockArgs& ba) {
-  const BlockLayout L = block_layout(ba.n, ba.num_chunks, ba.num_classes);
+  const BlockLayout L = block_layout(ba.n, ba.num_chunks, ba.num_classes, ba.resident_words);
   BlockShared s;
   s.bar = reinterpret_cast<unsigned long long*>(base);
   s.buf = reinterpret_cast<uint32_t*>(base + 128);
@@ -167,6 +173,9 @@ __device__ __forceinline__ void block_setup(const BlockArgs& ba, const BlockShar
     sh.cls_chunk[i] = ba.class_chunk[i];
     sh.cls_pos[i] = ba.class_pos[i];
   }
+  // resident form: every word, once (the word count is a multiple of 4)
+  for (int i = threadIdx.x; i < ba.resident_words / 4; i += blockDim.x)
+    reinterpret_cast<uint4*>(sh.buf)[i] = __ldg(reinterpret_cast<const uint4*>(ba.words) + i);
 }
 
 // Issue chunk q of this sweep, whose launch-wide sequence number is sq.
@@ -178,6 +187,108 @@ __device__ __forceinline__ void block_issue(const BlockArgs& ba, const BlockShar
   const int2 c = sh.chunk[q];
   bulk_load(sh.buf + b * kBlockChunkWords, ba.words + c.x, 4u * static_cast<unsigned>(c.y),
             sh.bar + b, (ba.short_copy && sq == 0u) ? 16u : 0u);
+}
+
+// The terms of one chunk's words (len of them at buf) added into the rows'
+// shared accumulators: each thread takes kBlockWordsPerThread consecutive
+// words (a chunk is one pass of the block).
+__device__ __forceinline__ void block_chunk(const BlockShared& sh, const uint32_t* buf, int len, int n,
+                                            int tid, int lane) {
+  // each thread takes kBlockWordsPerThread consecutive words (a chunk is
+  // one pass of the block): all terms first (independent shared loads),
+  // then a running sum per row, flushed where the row changes
+  const int w0 = tid * kBlockWordsPerThread;
+  if (__any_sync(kFullMask, w0 < len)) {
+    int row[kBlockWordsPerThread], val[kBlockWordsPerThread];
+    const uint32_t pad = static_cast<uint32_t>(n) << 20;
+#pragma unroll
+    for (int h = 0; h < kBlockWordsPerThread / 4; ++h) {
+      // chunk lengths are multiples of 4 words: past the end, pad words
+      // (spare row n, weight 0)
+      const uint4 x = w0 + 4 * h < len ? *reinterpret_cast<const uint4*>(buf + w0 + 4 * h)
+                                       : make_uint4(pad, pad, pad, pad);
+      const uint32_t wv[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const uint32_t w = wv[u];
+        const int col = static_cast<int>((w >> 8) & 0xfffu);
+        row[4 * h + u] = static_cast<int>(w >> 20);
+        val[4 * h + u] = static_cast<int>(static_cast<int8_t>(static_cast<uint8_t>(w & 0xffu))) *
+                         sh.spin[col < n ? col : 0];
+      }
+    }
+    int cur = row[0], sum = 0;
+#pragma unroll
+    for (int h = 0; h < kBlockWordsPerThread; ++h) {
+      if (row[h] != cur) {
+        atomicAdd(sh.acc + (cur <= n ? cur : n), sum);
+        cur = row[h];
+        sum = 0;
+      }
+      sum += val[h];
+    }
+    // the last run of each thread: lanes ending on the same row add up
+    // (segmented scan across the warp), the run's last lane adds to shared
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(kFullMask, sum, o);
+      const int r = __shfl_up_sync(kFullMask, cur, o);
+      if (lane >= o && r == cur) sum += u;
+    }
+    const int next = __shfl_down_sync(kFullMask, cur, 1);
+    if (lane == 31 || next != cur) atomicAdd(sh.acc + (cur <= n ? cur : n), sum);
+  }
+}
+
+// Eq. 2 and Algorithm 2 for the vertices of class k, from their accumulated
+// fields; the new state bytes go to shared and global memory.
+__device__ __forceinline__ void block_decide(const DevGraph& d, const BlockShared& sh, int k, int tid) {
+  for (int i = sh.cls_pos[k] + tid; i < sh.cls_pos[k + 1]; i += blockDim.x) {
+    const int f = sh.acc[i];
+    const int bt = sh.state[i];
+    int s = spin_of(bt);
+    if (f > 0)
+      s = -1;
+    else if (f < 0)
+      s = 1;
+    if (sh.flip[i]) s = -s;
+    const int nb = state_byte(s, ((bt >> 1) & 1) ^ 1);
+    sh.state[i] = static_cast<uint8_t>(nb);
+    sh.spin[i] = static_cast<int8_t>(s);
+    d.spins[i] = static_cast<int8_t>(nb);
+  }
+}
+
+// The sweep's start: state, spin and flip of every vertex into shared memory,
+// accumulators cleared.
+__device__ __forceinline__ void block_sweep_start(const DevGraph& d, const SweepArgs& a, const PhiloxRounds& rk,
+                                                  const BlockShared& sh, int n, int tid) {
+  for (int i = tid; i < n; i += blockDim.x) {
+    const int b = d.spins[i];
+    sh.state[i] = static_cast<uint8_t>(b);
+    sh.spin[i] = static_cast<int8_t>(spin_of(b));
+    sh.acc[i] = 0;
+    sh.flip[i] = flip_drawn(d, i, static_cast<uint32_t>(__ldg(d.orig + i)), a, rk) ? 1 : 0;
+  }
+  if (tid == 0) sh.acc[n] = 0;
+}
+
+// One sweep in the resident form: every class's words are in shared memory
+// already, so a class is its chunks, a block barrier, its decisions and a
+// block barrier.
+__device__ __forceinline__ void block_sweep_resident(const DevGraph& d, const BlockArgs& ba, const SweepArgs& a,
+                                                     const PhiloxRounds& rk, const BlockShared& sh) {
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  block_sweep_start(d, a, rk, sh, ba.n, tid);
+  __syncthreads();
+  for (int k = 0; k < ba.num_classes; ++k) {
+    for (int q = sh.cls_chunk[k]; q < sh.cls_chunk[k + 1]; ++q)
+      block_chunk(sh, sh.buf + sh.chunk[q].x, sh.chunk[q].y, ba.n, tid, lane);
+    __syncthreads();
+    block_decide(d, sh, k, tid);
+    __syncthreads();
+  }
 }
 
 // One sweep a.t of every class. seq numbers chunks over the whole launch:
@@ -200,14 +311,7 @@ __device__ __forceinline__ bool block_sweep(const DevGraph& d, const BlockArgs& 
     block_ok = 1;
     for (int q = 0; q < nch && q < kBlockRing - 1; ++q) block_issue(ba, sh, q, seq0 + q);
   }
-  for (int i = tid; i < n; i += blockDim.x) {
-    const int b = d.spins[i];
-    sh.state[i] = static_cast<uint8_t>(b);
-    sh.spin[i] = static_cast<int8_t>(spin_of(b));
-    sh.acc[i] = 0;
-    sh.flip[i] = flip_drawn(d, i, static_cast<uint32_t>(__ldg(d.orig + i)), a, rk) ? 1 : 0;
-  }
-  if (tid == 0) sh.acc[n] = 0;
+  block_sweep_start(d, a, rk, sh, n, tid);
   __syncthreads();
   int q = 0;  // chunk index within this sweep
   for (int k = 0; k < ba.num_classes; ++k) {
@@ -223,70 +327,11 @@ __device__ __forceinline__ bool block_sweep(const DevGraph& d, const BlockArgs& 
       }
       __syncthreads();
       if (!block_ok) break;
-      const int len = sh.chunk[q].y;
-      const uint32_t* buf = sh.buf + (sq % kBlockRing) * kBlockChunkWords;
-      // each thread takes kBlockWordsPerThread consecutive words (a chunk is
-      // one pass of the block): all terms first (independent shared loads),
-      // then a running sum per row, flushed where the row changes
-      const int w0 = tid * kBlockWordsPerThread;
-      if (__any_sync(kFullMask, w0 < len)) {
-        int row[kBlockWordsPerThread], val[kBlockWordsPerThread];
-        const uint32_t pad = static_cast<uint32_t>(n) << 20;
-#pragma unroll
-        for (int h = 0; h < kBlockWordsPerThread / 4; ++h) {
-          // chunk lengths are multiples of 4 words: past the end, pad words
-          // (spare row n, weight 0)
-          const uint4 x = w0 + 4 * h < len ? *reinterpret_cast<const uint4*>(buf + w0 + 4 * h)
-                                           : make_uint4(pad, pad, pad, pad);
-          const uint32_t wv[4] = {x.x, x.y, x.z, x.w};
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const uint32_t w = wv[u];
-            const int col = static_cast<int>((w >> 8) & 0xfffu);
-            row[4 * h + u] = static_cast<int>(w >> 20);
-            val[4 * h + u] = static_cast<int>(static_cast<int8_t>(static_cast<uint8_t>(w & 0xffu))) *
-                             sh.spin[col < n ? col : 0];
-          }
-        }
-        int cur = row[0], sum = 0;
-#pragma unroll
-        for (int h = 0; h < kBlockWordsPerThread; ++h) {
-          if (row[h] != cur) {
-            atomicAdd(sh.acc + (cur <= n ? cur : n), sum);
-            cur = row[h];
-            sum = 0;
-          }
-          sum += val[h];
-        }
-        // the last run of each thread: lanes ending on the same row add up
-        // (segmented scan across the warp), the run's last lane adds to shared
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int u = __shfl_up_sync(kFullMask, sum, o);
-          const int r = __shfl_up_sync(kFullMask, cur, o);
-          if (lane >= o && r == cur) sum += u;
-        }
-        const int next = __shfl_down_sync(kFullMask, cur, 1);
-        if (lane == 31 || next != cur) atomicAdd(sh.acc + (cur <= n ? cur : n), sum);
-      }
+      block_chunk(sh, sh.buf + (sq % kBlockRing) * kBlockChunkWords, sh.chunk[q].y, n, tid, lane);
       __syncthreads();
     }
     if (!block_ok) break;
-    // Eq. 2 and Algorithm 2 for the class's vertices
-    for (int i = sh.cls_pos[k] + tid; i < sh.cls_pos[k + 1]; i += blockDim.x) {
-      const int f = sh.acc[i];
-      const int bt = sh.state[i];
-      int s = spin_of(bt);
-      if (f > 0)
-        s = -1;
-      else if (f < 0)
-        s = 1;
-      if (sh.flip[i]) s = -s;
-      const int nb = state_byte(s, ((bt >> 1) & 1) ^ 1);
-      sh.state[i] = static_cast<uint8_t>(nb);
-      sh.spin[i] = static_cast<int8_t>(s);
-      d.spins[i] = static_cast<int8_t>(nb);
-    }
+    block_decide(d, sh, k, tid);
     __syncthreads();
   }
   seq = seq0 + static_cast<unsigned>(nch);

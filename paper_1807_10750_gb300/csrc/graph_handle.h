@@ -68,6 +68,7 @@ struct ising_graph {
   // block engine of small graphs (host_graph.h, block.cuh)
   bool block_ok = false;
   int32_t block_num_chunks = 0;
+  int32_t block_num_words = 0;
   int32_t* d_block_words = nullptr;
   int32_t* d_block_chunk_off = nullptr;
   int32_t* d_block_chunk_len = nullptr;

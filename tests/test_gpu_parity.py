@@ -332,9 +332,11 @@ def test_nflip_edge_cases(P):
 # Graphs the persistent engine anneals in one block (int8 weights, at most
 # 4095 vertices): dense with repeated edges (29 classes), K_40 (40 classes of
 # one vertex), a torus (2 classes), a 4095-vertex random graph (the size
-# limit) and a single vertex. Deterministic sweeps, with and without a flip
-# bias and Algorithm 1's schedule, must match the grid-barrier form and the
-# oracle bit for bit.
+# limit) and a single vertex. The first three keep every packed word in
+# shared memory (resident form); the 4095-vertex graph's 168k words stream
+# through the ring of bulk copies. Deterministic sweeps, with and without a
+# flip bias and Algorithm 1's schedule, must match the grid-barrier form and
+# the oracle bit for bit.
 BLOCK_GRAPHS = {
     "dense300": lambda: synth.random_small_graph(300, 0.3, 3, weights="int8", duplicates=100),
     "complete40": lambda: synth.complete_graph(40, 1, weights="pm1"),
