@@ -82,16 +82,16 @@ __device__ __forceinline__ uint4 batch_philox(uint32_t x0, uint32_t x1, uint32_t
   return make_uint4(x0, x1, x2, x3);
 }
 
-// The field terms of one row's entries [e0, e1) taken with stride S (the
-// row is shared by S consecutive threads, this one starting at e0 + sub):
-// accumulator words for the byte-lane paths or per-replica sums, and the sum
-// of the weights.
+// A row's field terms for every replica: accumulator words for the
+// byte-lane paths or per-replica sums, and the sum of the weights.
 struct RowSums {
   uint32_t a0, a1, a2, a3;  // byte lanes: lo / hi counts (+-1), or plo / phi / nlo / nhi
   int acc[8];               // per-replica path
   int wsum;
 };
 
+// The field terms of one row's entries [e0, e1) taken with stride S (the
+// row is shared by S consecutive threads, this one starting at e0 + sub).
 template <int S>
 __device__ __forceinline__ void row_sums(const BatchDev& d, const uint8_t* sp, int mode, int e0, int e1,
                                          int sub, RowSums& r) {
