@@ -27,6 +27,142 @@
 
 namespace isingx {
 
+namespace {
+
+// A reusable barrier for a fixed set of threads (spinning, then yielding:
+// the waits between colouring levels are short).
+class SpinBarrier {
+ public:
+  explicit SpinBarrier(int n) : n_(n) {}
+  void wait() {
+    const int gen = gen_.load(std::memory_order_acquire);
+    if (count_.fetch_add(1, std::memory_order_acq_rel) == n_ - 1) {
+      count_.store(0, std::memory_order_relaxed);
+      gen_.store(gen + 1, std::memory_order_release);
+      return;
+    }
+    for (int spin = 0; gen_.load(std::memory_order_acquire) == gen; ++spin)
+      if (spin > 4096) std::this_thread::yield();
+  }
+
+ private:
+  const int n_;
+  std::atomic<int> count_{0};
+  std::atomic<int> gen_{0};
+};
+
+// First-fit colours of the two tiers, relative to each tier (the hubs from 0,
+// the other vertices from 0: the caller adds the hubs' colour count), equal to
+// the sequential first fit in `order`. A vertex's colour depends only on the
+// colours of its same-tier neighbours earlier in the order, so the vertices
+// are coloured level by level: a vertex joins the next level when its last
+// earlier same-tier neighbour has been coloured (a per-vertex countdown), and
+// the threads split each level. Returns false (nothing written) when no helper
+// thread could be started; the caller then colours sequentially.
+bool colour_levels(size_t N, const int64_t* moff, const int32_t* mnb, const int32_t* deg,
+                   const std::vector<int32_t>& order, int32_t maxdeg, int32_t* rel) {
+  const int T = host_threads();
+  if (T <= 1) return false;
+  std::vector<int32_t> rank(N);
+  parallel_ranges((int64_t)N, 1 << 16, [&](int64_t lo, int64_t hi) {
+    for (int64_t i = lo; i < hi; ++i) rank[(size_t)order[(size_t)i]] = (int32_t)i;
+  });
+  auto hub = [&](size_t v) { return deg[v] >= kHubDegree; };
+  std::unique_ptr<std::atomic<int32_t>[]> pending(new std::atomic<int32_t>[N]);
+  parallel_ranges((int64_t)N, 1 << 14, [&](int64_t lo, int64_t hi) {
+    for (int64_t v = lo; v < hi; ++v) {
+      int32_t c = 0;
+      const bool hv = hub((size_t)v);
+      for (int64_t k = moff[v]; k < moff[v + 1]; ++k) {
+        const int32_t u = mnb[(size_t)k];
+        c += (hub((size_t)u) == hv && rank[(size_t)u] < rank[(size_t)v]) ? 1 : 0;
+      }
+      pending[(size_t)v].store(c, std::memory_order_relaxed);
+    }
+  });
+  std::vector<int32_t> frontier;
+  for (size_t v = 0; v < N; ++v)
+    if (pending[v].load(std::memory_order_relaxed) == 0) frontier.push_back((int32_t)v);
+  std::vector<std::vector<int32_t>> next((size_t)T);
+  std::vector<int64_t> cum;               // the frontier's degrees, running sum
+  auto rebuild_cum = [&] {
+    cum.resize(frontier.size() + 1);
+    cum[0] = 0;
+    for (size_t i = 0; i < frontier.size(); ++i) cum[i + 1] = cum[i] + deg[frontier[i]] + 1;
+  };
+  rebuild_cum();
+  int P = 1;                              // threads taking part (set before any starts work)
+  std::unique_ptr<SpinBarrier> barrier_p;
+  bool done = frontier.empty();
+  auto work = [&](int t) {
+    SpinBarrier& barrier = *barrier_p;
+    std::vector<int32_t> mark((size_t)maxdeg + 2, -1);
+    while (!done) {
+      // this level's vertices, split by their entry counts: each is coloured
+      // from its earlier same-tier neighbours (all final) and releases its
+      // later same-tier neighbours (coloured from the next level on)
+      const int64_t total = cum.back();
+      const size_t lo = (size_t)(std::lower_bound(cum.begin(), cum.end(), total * t / P) - cum.begin());
+      const size_t hi = (size_t)(std::lower_bound(cum.begin(), cum.end(), total * (t + 1) / P) - cum.begin());
+      std::vector<int32_t>& out = next[(size_t)t];
+      out.clear();
+      for (size_t i = lo; i < hi && i < frontier.size(); ++i) {
+        const int32_t v = frontier[i];
+        const bool hv = hub((size_t)v);
+        const int32_t d = deg[v];
+        const int32_t rv = rank[(size_t)v];
+        for (int64_t k = moff[v]; k < moff[(size_t)v + 1]; ++k) {
+          const int32_t u = mnb[(size_t)k];
+          if (hub((size_t)u) != hv) continue;
+          if (rank[(size_t)u] < rv) {
+            if (rel[u] <= d) mark[(size_t)rel[u]] = v;
+          } else if (pending[(size_t)u].fetch_sub(1, std::memory_order_relaxed) == 1) {
+            out.push_back(u);
+          }
+        }
+        int32_t c = 0;
+        while (mark[(size_t)c] == v) ++c;
+        rel[v] = c;
+      }
+      barrier.wait();  // this level's colours are final and its releases counted
+      if (t == 0) {
+        size_t F = 0;
+        for (int j = 0; j < P; ++j) F += next[(size_t)j].size();
+        frontier.resize(F);
+        F = 0;
+        for (int j = 0; j < P; ++j) {
+          std::copy(next[(size_t)j].begin(), next[(size_t)j].end(), frontier.begin() + (std::ptrdiff_t)F);
+          F += next[(size_t)j].size();
+        }
+        rebuild_cum();
+        done = frontier.empty();
+      }
+      barrier.wait();  // the next level is in place
+    }
+  };
+  // helpers wait for the gate; the barrier counts the threads that started
+  std::atomic<int> gate{0};
+  auto helper = [&](int t) {
+    while (gate.load(std::memory_order_acquire) == 0) std::this_thread::yield();
+    work(t);
+  };
+  std::vector<std::thread> pool;
+  try {
+    pool.reserve((size_t)T - 1);
+    for (int t = 1; t < T; ++t) pool.emplace_back(helper, t);
+  } catch (const std::system_error&) {
+  } catch (const std::bad_alloc&) {
+  }
+  P = 1 + (int)pool.size();
+  barrier_p.reset(new SpinBarrier(P));
+  gate.store(1, std::memory_order_release);
+  work(0);
+  for (std::thread& th : pool) th.join();
+  return true;
+}
+
+}  // namespace
+
 int build_host_graph(int32_t n, int64_t m, const int32_t* src, const int32_t* dst,
                      const int32_t* w, HostGraph* out) {
   if (out == nullptr || n <= 0 || m < 0) return ISING_EINVAL;
@@ -159,7 +295,25 @@ int build_host_graph(int32_t n, int64_t m, const int32_t* src, const int32_t* ds
   // the order reaches a non-hub, colours are counted from `base`, the hubs'
   // colour count, and the (smaller) colours of hub neighbours are ignored.
   g.colour.assign(N, -1);
-  {
+  // large graphs (8M entries and more; smaller ones colour in a few ms):
+  // level by level on several threads, the same colours
+  if (moff[N] >= (int64_t(1) << 23) &&
+      colour_levels(N, moff.data(), mnb.get(), mdeg.data(), order, maxdeg, g.colour.data())) {
+    int32_t hubs = 0, hub_c = 0, other_c = -1;
+    for (size_t v = 0; v < N; ++v) {
+      if (degree(v) >= kHubDegree) {
+        ++hubs;
+        hub_c = std::max(hub_c, g.colour[v] + 1);
+      } else {
+        other_c = std::max(other_c, g.colour[v]);
+      }
+    }
+    for (size_t v = 0; v < N; ++v)
+      if (degree(v) < kHubDegree) g.colour[v] += hub_c;
+    g.num_hubs = hubs;
+    g.hub_colours = hub_c;
+    g.num_colours = hub_c + other_c + 1;
+  } else {
     std::vector<int32_t> mark((size_t)maxdeg + 2, -1);
     int32_t C = 0, base = 0;
     bool hubs = true;

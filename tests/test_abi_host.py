@@ -116,6 +116,23 @@ def test_multithreaded_host_colouring_equals_oracle(P, make):
     assert P.ising_plan_colouring(g.n, g.src, g.dst, g.w)[1].tobytes() == col.tobytes()
 
 
+@pytest.mark.parametrize("make", [
+    # 8M and more merged entries: the colouring runs level by level on
+    # several threads and must still equal the sequential first fit
+    lambda: synth.zipf_config_graph(600_000, 2.1, 4, 10000, 3, weights="int8"),
+    lambda: synth.er_graph(400_000, 24.0 / 399_999, 5, weights="int8"),
+    # every vertex a hub (one tier only)
+    lambda: synth.zipf_config_graph(30_000, 1.5, 300, 2000, 7),
+])
+def test_level_parallel_colouring_equals_oracle(P, make):
+    g = make()
+    assert 2 * g.m >= 1 << 23
+    C, col = P.ising_plan_colouring(g.n, g.src, g.dst, g.w)
+    C2, col2 = oracle.colouring(g.n, g.src, g.dst, g.w)
+    assert C == C2
+    assert np.array_equal(col, col2)
+
+
 def test_host_colouring_edgeless_and_single_vertex(P):
     e = np.zeros(0, np.int32)
     C, col = P.ising_plan_colouring(5, e, e, e)
