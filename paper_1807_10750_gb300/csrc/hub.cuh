@@ -58,8 +58,8 @@ constexpr int kHubBlock = 1024;
 constexpr int kHubWarps = kHubBlock / 32;
 constexpr int kHubMaxHubs = 10240;  // shared memory of the chain block (hub_smem_bytes)
 constexpr int kHubSumChunk = 512;   // CSR entries per field-sum item
-constexpr int kHubSlot = 512;       // row entries per push task (16 per lane)
-constexpr int kHubListCap = 768;    // push tasks one block-wide decision step can list
+constexpr int kHubSlot = 128;       // row entries per push task (4 per lane)
+constexpr int kHubListCap = 3072;   // push tasks one block-wide decision step can list
 constexpr int kHubDeferCap = 2048;  // changed hubs whose earlier-class pushes wait
 constexpr int kHubSmallClass = 32;  // classes up to this size are decided by warp 0 alone
 constexpr int kHubGroupLoads = 8;   // CSR words in flight per lane in a group-row batch
@@ -190,7 +190,7 @@ __device__ __forceinline__ void hub_flip_word(const DevGraph& d, const HubArgs& 
 }
 
 // Push entries [e0, e1) of a changed hub's row (at most kHubSlot of them,
-// 16 per lane, all loaded before any is applied): each entry (v, w) adds
+// kHubSlot / 32 per lane, all loaded before any is applied): each entry (v, w) adds
 // 2 w ns to F_v, ns the hub's new spin.
 template <bool PACKED>
 __device__ __forceinline__ void hub_push_range(const DevGraph& d, const HubSmem& s, int e0, int e1,
