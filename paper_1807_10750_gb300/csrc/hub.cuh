@@ -62,6 +62,7 @@ constexpr int kHubSlot = 128;       // row entries per push task (4 per lane)
 constexpr int kHubListCap = 3072;   // push tasks one block-wide decision step can list
 constexpr int kHubDeferCap = 2048;  // changed hubs whose earlier-class pushes wait
 constexpr int kHubSmallClass = 32;  // classes up to this size are decided by warp 0 alone
+constexpr int kHubSmallWarps = 4;   // warps that push a small class's changes
 constexpr int kHubGroupLoads = 8;   // CSR words in flight per lane in a group-row batch
 constexpr int kHubGroupScratch = 65;  // per warp: 33 row offsets and 32 fields
 
@@ -91,13 +92,14 @@ struct HubArgs {
 
 // Shared memory. The chain block: the push tasks of one block-wide step
 // (kHubListCap int4: hub | sign << 31, first entry, end entry, unused), the
-// deferred hubs (kHubDeferCap int: hub | sign << 31), the fields F[X] = A + B
+// changed hubs of a small class (kHubSmallClass int4: first entry, end entry,
+// new spin, unused), the deferred hubs (kHubDeferCap int: hub | sign << 31), the fields F[X] = A + B
 // (int32), the flip bits fl[W], the class table cls[m + 1], four counters and
 // the state bytes S[X]. A worker block: the group-row scratch (kHubWarps x
 // kHubGroupScratch int) and, with stage_bits, the copy of the spin map.
 __host__ __device__ inline int hub_chain_smem(int X, int m) {
   const int W = (X + 31) / 32;
-  return 16 * kHubListCap + 4 * kHubDeferCap + 4 * X + 4 * W + 4 * (m + 1) + 16 +
+  return 16 * kHubListCap + 16 * kHubSmallClass + 4 * kHubDeferCap + 4 * X + 4 * W + 4 * (m + 1) + 16 +
          ((X + 3) / 4) * 4 + 16;
 }
 __host__ __device__ inline int hub_worker_smem(int bit_words, bool stage) {
@@ -110,11 +112,13 @@ __host__ __device__ inline int hub_smem_bytes(int X, int m, int bit_words, bool 
 
 struct HubSmem {
   int4* list;
+  int4* small;
   int32_t* defer;
   int32_t* F;
   uint32_t* fl;
   int32_t* cls;
-  int* cnt;  // [0], [1]: push tasks of a block-wide step, by step parity; [2]: deferred hubs
+  int* cnt;  // [0], [1]: push tasks of a block-wide step, by step parity; [2]: deferred hubs;
+             // [3]: changed hubs of a small class
   uint8_t* S;
 };
 
@@ -122,7 +126,8 @@ __device__ __forceinline__ HubSmem hub_smem(unsigned char* base, int X, int m) {
   HubSmem s;
   const int W = (X + 31) / 32;
   s.list = reinterpret_cast<int4*>(base);  // 16-byte aligned first
-  s.defer = reinterpret_cast<int32_t*>(s.list + kHubListCap);
+  s.small = s.list + kHubListCap;
+  s.defer = reinterpret_cast<int32_t*>(s.small + kHubSmallClass);
   s.F = s.defer + kHubDeferCap;
   s.fl = reinterpret_cast<uint32_t*>(s.F + X);
   s.cls = reinterpret_cast<int32_t*>(s.fl + W);
@@ -204,33 +209,6 @@ __device__ __forceinline__ void hub_push_range(const DevGraph& d, const HubSmem&
     if (e0 + lane + 32 * i < e1) atomicAdd(s.F + x[i].col(), 2 * ns * x[i].weight());
 }
 
-// Up to four row ranges [e0[j], e1[j]) with new spins ns[j] pushed by one
-// warp together: 128 entries of each per round (4 per lane), all 16 loads
-// issued before any is applied, so a few short rows cost one L2 round trip.
-template <bool PACKED>
-__device__ __forceinline__ void hub_push4(const DevGraph& d, const HubSmem& s, int (&e0)[4],
-                                          const int (&e1)[4], const int (&ns)[4], int lane) {
-  for (;;) {
-    Edge<PACKED> x[4][4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int u = 0; u < 4; ++u) x[j][u].load(d, e0[j] + lane + 32 * u, e0[j] + lane + 32 * u < e1[j]);
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (e0[j] + lane + 32 * u < e1[j]) atomicAdd(s.F + x[j][u].col(), 2 * ns[j] * x[j][u].weight());
-    bool more = false;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      e0[j] += 128;
-      more |= e0[j] < e1[j];
-    }
-    if (!more) return;
-  }
-}
-
 // A whole row range pushed by one warp, kHubSlot entries per round.
 template <bool PACKED>
 __device__ __forceinline__ void hub_push_rows(const DevGraph& d, const HubSmem& s, int e0, int e1,
@@ -307,13 +285,18 @@ __device__ __forceinline__ void hub_deferred(const DevGraph& d, const HubArgs& h
   }
 }
 
+// The barrier of the warps that run the small hub classes (named barrier 1).
+__device__ __forceinline__ void small_barrier() {
+  asm volatile("bar.sync 1, %0;" ::"r"(32 * kHubSmallWarps) : "memory");
+}
+
 // The m hub classes of one sweep, run by the chain block. `first`: the
 // launch's first sweep (B and the state bytes come from global memory).
 // `step` counts block-wide decision steps (it selects the step's counter).
 //
-// Classes of at most kHubSmallClass hubs are decided by warp 0 alone, which
-// also pushes their changes, with warp barriers only; larger classes use the
-// whole block: decide, list the push tasks, block barrier, push, block
+// Classes of at most kHubSmallClass hubs are decided by warp 0 alone and
+// their changes pushed by kHubSmallWarps warps, with a named barrier of those
+// warps only; larger classes use the whole block: decide, list the push tasks, block barrier, push, block
 // barrier. Only the pushes into later hub classes are made here; the rest
 // wait in the deferred queue (hub_deferred).
 template <bool PACKED>
@@ -371,28 +354,28 @@ __device__ __forceinline__ void hub_chain(const DevGraph& d, const HubArgs& h, c
     c = nc;
     base = nbase;
     if (small) {
-      if (warp == 0) {
-        int ns = 0, sv = 0;
-        if (v < ce) ns = hub_decide(s, v, &sv);
-        const bool changed = v < ce && ns != sv;
-        map_publish(h.bits, cb, changed, lane);
-        // pushes into later classes now, four changed hubs at a time
-        unsigned ch = __ballot_sync(kFullMask, changed && he > sp);
-        while (ch != 0u) {
-          int a[4], b[4], sg[4];
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const int src = ch != 0u ? __ffs(ch) - 1 : 0;
-            const bool have = ch != 0u;
-            ch &= ch - 1;
-            a[j] = __shfl_sync(kFullMask, sp, src);
-            b[j] = have ? __shfl_sync(kFullMask, he, src) : a[j];
-            sg[j] = __shfl_sync(kFullMask, ns, src);
-          }
-          hub_push4<PACKED>(d, s, a, b, sg, lane);
+      // warp 0 decides (one hub per lane); warps 0 .. kHubSmallWarps - 1 push
+      // the changed hubs' entries into later classes, one hub per warp at a
+      // time; a named barrier of those warps on either side of the pushes
+      if (warp < kHubSmallWarps) {
+        if (warp == 0) {
+          int ns = 0, sv = 0;
+          if (v < ce) ns = hub_decide(s, v, &sv);
+          const bool changed = v < ce && ns != sv;
+          map_publish(h.bits, cb, changed, lane);
+          const bool later = changed && he > sp;
+          const unsigned ch = __ballot_sync(kFullMask, later);
+          if (later) s.small[__popc(ch & ((1u << lane) - 1u))] = make_int4(sp, he, ns, 0);
+          if (lane == 0) s.cnt[3] = __popc(ch);
+          hub_defer<PACKED>(d, s, changed && sp > r0, v, ns, r0, sp, lane);
         }
-        hub_defer<PACKED>(d, s, changed && sp > r0, v, ns, r0, sp, lane);
-        __syncwarp();
+        small_barrier();
+        const int nch = s.cnt[3];
+        for (int k = warp; k < nch; k += kHubSmallWarps) {
+          const int4 t = s.small[k];
+          hub_push_rows<PACKED>(d, s, t.x, t.y, t.z, lane);
+        }
+        small_barrier();
       }
       small_run = true;
       continue;
