@@ -121,6 +121,15 @@ def test_hub_engine_with_flip_bias(P):
     check_hub(P, g, seed=2, p0=0.3, T=40, bias=q)
 
 
+def test_hub_engine_every_spin_flipping(P):
+    # p0 = 1: almost every hub changes in the first sweeps, so every class
+    # pushes along most of its hubs' rows (the small classes' shared pushes,
+    # the 128-entry push tasks and their list, the deferred queue at its
+    # fullest)
+    g = synth.zipf_config_graph(40000, 2.0, 3, 4000, 19)
+    check_hub(P, g, seed=11, p0=1.0, T=12)
+
+
 def test_hub_engine_long_run(P):
     # many chain steps with changes early and none late
     g = synth.zipf_config_graph(50000, 2.1, 4, 5000, 15)
