@@ -59,6 +59,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweeps", type=int, default=None,
                     help="override the workload's schedule length (profiling runs only)")
+    ap.add_argument("--gnn-dense", choices=["mma_sync", "tcgen05"], default="mma_sync",
+                    help="gnn: the forward layers' product (ising_gnn_set_dense_path)")
     ap.add_argument("--train-graphs", type=int, default=2048,
                     help="warmstart: generated training graphs (1k-100k vertices)")
     ap.add_argument("--train-batch", type=int, default=64,
@@ -617,6 +619,8 @@ def run_gnn(args, world, rank, P, torch, dist):
     h = P.ising_create(g.n, g.src, g.dst, g.w, stream=stream)
     P.ising_init_random(h, 1)
     net = P.ising_gnn_create(synth.gnn_init_params(1))
+    P.ising_gnn_set_dense_path(net, P.ISING_GNN_DENSE_TCGEN05 if args.gnn_dense == "tcgen05"
+                               else P.ISING_GNN_DENSE_MMA_SYNC)
     z = torch.empty(g.n, dtype=torch.float32, device="cuda")
     y = torch.from_numpy(np.where(np.random.default_rng(2).random(g.n) < 0.5, 1, -1).astype(np.int8)).cuda()
     nnz = 2 * P.ising_num_edges(h)
@@ -657,6 +661,7 @@ def run_gnn(args, world, rank, P, torch, dist):
         "ms_per_step": fwd_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "bf16", "data": "synthetic",
         "config": {"workload": "gnn", "n": g.n, "nnz": nnz, "layers": 3, "hidden": 64,
+                   "dense": args.gnn_dense.replace("_", "."),
                    "parallelism": f"replicas{world}",
                    "l2": "512 MiB buffer zeroed before every timed pass (outside the events)"},
         "train_step_ms": trn_ms, "train_vertices_per_s": g.n / (trn_ms / 1e3) * world,

@@ -524,6 +524,21 @@ int ising_gnn_batch_gradients(ising_gnn* net, ising_batch* b, uint32_t replica, 
                               int labels_on_device, float* out_loss, float* out_grad);
 int ising_gnn_batch_train_step(ising_gnn* net, ising_batch* b, uint32_t replica, const int8_t* labels,
                                int labels_on_device, float lr, float* out_loss);
+/* ising_gnn_set_dense_path -- the tensor-core path of the forward layers'
+ * products: ISING_GNN_DENSE_MMA_SYNC (the default; 64-row tiles, warp-level
+ * mma.sync, several blocks per SM) or ISING_GNN_DENSE_TCGEN05 (128-row
+ * tiles in a warp-specialised pipeline: gather warps fill a ring of shared
+ * memory tiles, one thread issues tcgen05.mma into fp32 accumulators in
+ * tensor memory, four warps read them back). The layer is bound by its
+ * neighbour gather, not by the product, and the default keeps more warps
+ * gathering per SM; it is the faster of the two on every graph measured.
+ * Both round the same bf16 operands and accumulate in fp32; results differ
+ * only in the order of the fp32 sums. A tcgen05 pipeline wait that does not
+ * end within 1 s latches ISING_ETIMEOUT in the network (reported by the next
+ * call that synchronises). ISING_EINVAL for any other value. */
+#define ISING_GNN_DENSE_TCGEN05 0
+#define ISING_GNN_DENSE_MMA_SYNC 1
+int ising_gnn_set_dense_path(ising_gnn* net, int path);
 /* ising_gnn_launch_count -- kernels launched by this network handle. */
 int ising_gnn_launch_count(ising_gnn* net, uint64_t* out);
 /* ising_gnn_destroy -- free the network (NULL is ignored). */

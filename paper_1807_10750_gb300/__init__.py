@@ -58,7 +58,7 @@ EXPORTS = (
     "ising_engine_used", "ising_set_halo_sweeps", "ising_halo_info", "ising_plan_halo",
     "ising_convergence_region", "ising_batch_set_tuning", "ising_batch_tuning",
     "ising_gnn_batch_forward", "ising_gnn_batch_warm_start", "ising_gnn_batch_gradients",
-    "ising_gnn_batch_train_step",
+    "ising_gnn_batch_train_step", "ising_gnn_set_dense_path",
 )
 ISING_ENGINE_USED_BLOCK = 6
 ISING_FAULT_NONE = 0
@@ -66,6 +66,8 @@ ISING_FAULT_SKIP_ARRIVAL = 1
 ISING_FAULT_SHORT_COPY = 2
 ISING_GNN_NUM_PARAMS = 17665
 ISING_ALL_REPLICAS = 0xFFFFFFFF
+ISING_GNN_DENSE_TCGEN05 = 0
+ISING_GNN_DENSE_MMA_SYNC = 1
 
 
 class IsingError(RuntimeError):
@@ -145,6 +147,7 @@ def lib():
         L.ising_gnn_warm_start.argtypes = [vp, vp, ctypes.c_int]
         L.ising_gnn_batch_forward.argtypes = [vp, vp, ctypes.c_uint32, vp, ctypes.c_int]
         L.ising_gnn_batch_warm_start.argtypes = [vp, vp, ctypes.c_uint32]
+        L.ising_gnn_set_dense_path.argtypes = [vp, ctypes.c_int]
         L.ising_gnn_batch_gradients.argtypes = [vp, vp, ctypes.c_uint32, vp, ctypes.c_int, vp, vp]
         L.ising_gnn_batch_train_step.argtypes = [vp, vp, ctypes.c_uint32, vp, ctypes.c_int, ctypes.c_float, vp]
         L.ising_gnn_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
@@ -703,6 +706,12 @@ def ising_gnn_batch_train_step(net: IsingGnn, b: IsingBatch, labels, lr: float, 
                                             ctypes.byref(loss) if want_loss else None),
            "ising_gnn_batch_train_step")
     return float(loss.value) if want_loss else None
+
+
+def ising_gnn_set_dense_path(net: IsingGnn, path: int) -> None:
+    """ISING_GNN_DENSE_MMA_SYNC (default) or ISING_GNN_DENSE_TCGEN05 for the
+    forward layers' products."""
+    _check(lib().ising_gnn_set_dense_path(net.ptr, int(path)), "ising_gnn_set_dense_path")
 
 
 def ising_gnn_launch_count(net: IsingGnn) -> int:

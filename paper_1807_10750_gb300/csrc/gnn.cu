@@ -507,6 +507,265 @@ __global__ void __launch_bounds__(kLayerThreads)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Fifth-generation tensor cores (tcgen05): the forward layer's product on
+// 128-row tiles with the accumulator in tensor memory, in a warp-specialised
+// pipeline. Operands sit in shared memory in the canonical no-swizzle K-major
+// layout: 8 x 8 bf16 core matrices of 128 contiguous bytes, K-adjacent ones
+// kTcLbo bytes apart and 8-row groups K / 8 * 128 bytes apart.
+//
+//   gather warps (kTcProducers)  rows of a tile -> stage s of a ring of
+//                                kTcStages tiles; each warp arrives on full[s]
+//   one issuing thread           waits full[s] and a free accumulator, issues
+//                                the K / 16 products 128 x 64 x 16, commits
+//                                them to empty[s] and acc_full[a]
+//   four epilogue warps          wait acc_full[a], read the 128 x 64 fp32
+//                                accumulator (tcgen05.ld, one lane quarter
+//                                each), arrive on acc_empty[a], add the bias,
+//                                apply ReLU and store bf16
+//
+// No block-wide barrier inside the loop: a gather warp held up by a long row
+// delays only its own tile, while the others fill the next stages.
+
+constexpr int kTcRows = 128;       // rows per tile (the product's M)
+constexpr int kTcProducers = 27;   // gather warps (with the five others, 1024 threads)
+constexpr int kTcStages = 4;       // tiles in the shared-memory ring
+constexpr int kTcAcc = 2;          // accumulators of 64 columns in tensor memory
+constexpr int kTcIssueWarp = kTcProducers;
+constexpr int kTcThreads = (kTcProducers + 1 + 4) * 32;
+constexpr int kTcMinBlocks = kTcProducers <= 16 ? 2 : 1;  // blocks per SM the registers are sized for
+constexpr int kTcLbo = 128;        // bytes between K-adjacent core matrices
+
+// Byte offset of element (r, k) of a K-major tile with K columns.
+__host__ __device__ constexpr int tc_canon(int r, int k, int K) {
+  return (r / 8) * (K / 8) * 128 + (k / 8) * kTcLbo + (r % 8) * 16 + (k % 8) * 2;
+}
+
+// Shared-memory matrix descriptor: start address, leading (K) and stride
+// (8-row) byte offsets, the fixed version bits 46-48 = 1, no swizzle.
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr, int K) {
+  const uint32_t sbo = static_cast<uint32_t>(K / 8) * 128u;
+  return static_cast<uint64_t>((addr >> 4) & 0x3FFFu) | (static_cast<uint64_t>((kTcLbo >> 4) & 0x3FFF) << 16) |
+         (static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: fp32 accumulator, bf16 A and B, both
+// K-major, N = 64, M = 128.
+constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(kH >> 3) << 17) |
+                              (static_cast<uint32_t>(kTcRows >> 4) << 24);
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// The tile's products D = A B^T (A: kTcRows x K at sa, B: 64 x K at sb),
+// issued by one thread.
+template <int K>
+__device__ __forceinline__ void tc_issue(uint32_t taddr, uint32_t sa, uint32_t sb) {
+#pragma unroll
+  for (int ks = 0; ks < K / 16; ++ks) {
+    const uint64_t da = tc_desc(sa + ks * 2 * kTcLbo, K), db = tc_desc(sb + ks * 2 * kTcLbo, K);
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(taddr),
+                 "l"(da), "l"(db), "r"(kTcIdesc), "r"(ks > 0 ? 1u : 0u)
+                 : "memory");
+  }
+}
+
+// bar's next phase completes once the products issued so far have.
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mb_arrive(uint32_t bar) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}" ::"r"(bar) : "memory");
+}
+
+// Waits for phase `parity` of bar, at most 1 s and only while no role of the
+// block has given up (*stop). A wait that runs out sets *stop and *err.
+__device__ __forceinline__ bool mb_wait(uint32_t bar, uint32_t parity, volatile int* stop, int* err) {
+  long long t0 = 0;
+  for (unsigned it = 0;; ++it) {
+    uint32_t done;
+    asm volatile("{\n .reg .pred q;\n mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n selp.u32 %0, 1, 0, q;\n}"
+                 : "=r"(done)
+                 : "r"(bar), "r"(parity)
+                 : "memory");
+    if (done) return true;
+    if (*stop) return false;
+    long long now;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+    if (it == 0) {
+      t0 = now;
+    } else if (now - t0 > 1000000000LL) {
+      *stop = 1;
+      atomicExch(err, 1);
+      return false;
+    }
+  }
+}
+
+// mb_wait by lane 0, its answer taken by the warp.
+__device__ __forceinline__ bool mb_wait_warp(uint32_t bar, uint32_t parity, volatile int* stop, int* err) {
+  int ok = 0;
+  if ((threadIdx.x & 31) == 0) ok = mb_wait(bar, parity, stop, err) ? 1 : 0;
+  return __shfl_sync(kFull, ok, 0) != 0;
+}
+
+// 16 consecutive fp32 columns of this warp's 32 accumulator lanes.
+__device__ __forceinline__ void tc_ld16(uint32_t addr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(addr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Shared memory of layer_fwd_tc_kernel<D>: the ring of A tiles (kTcRows x
+// 2D each), W transposed (64 x 2D), the bias, the mbarriers, the
+// tensor-memory address and the stop flag.
+__host__ __device__ constexpr int tc_layer_smem(int D) {
+  return kTcStages * kTcRows * 2 * D * 2 + kH * 2 * D * 2 + kH * 4 + (2 * kTcStages + 2 * kTcAcc) * 8 + 16;
+}
+
+// The forward layer of layer_fwd_kernel with the product on tcgen05, one
+// persistent block per SM walking tiles blockIdx.x, + gridDim.x, ... through
+// the pipeline above. Any wait that runs out (1 s) sets *err, stops every
+// role of the block and leaves the remaining outputs unwritten.
+template <int D>
+__global__ void __launch_bounds__(kTcThreads, kTcMinBlocks)
+    layer_fwd_tc_kernel(GView v, const float* __restrict__ c, const bf16* __restrict__ h,
+                        const float* __restrict__ partial, const bf16* __restrict__ W,
+                        const float* __restrict__ bias, bf16* __restrict__ a_store, bf16* __restrict__ hout,
+                        int* err) {
+  using IO = RowIO<D>;
+  constexpr int K = 2 * D;
+  constexpr int RPW = 32 / IO::G;
+  constexpr int kStage = kTcRows * K * 2;
+  extern __shared__ __align__(1024) unsigned char tc_mem[];
+  unsigned char* sX = tc_mem;                              // kTcStages tiles of kTcRows x K
+  unsigned char* sWt = tc_mem + kTcStages * kStage;        // 64 x K (W transposed)
+  float* sB = reinterpret_cast<float*>(sWt + kH * K * 2);  // 64
+  unsigned long long* full = reinterpret_cast<unsigned long long*>(sB + kH);
+  unsigned long long* empty = full + kTcStages;
+  unsigned long long* acc_full = empty + kTcStages;
+  unsigned long long* acc_empty = acc_full + kTcAcc;
+  uint32_t* slot = reinterpret_cast<uint32_t*>(acc_empty + kTcAcc);
+  volatile int* stop = reinterpret_cast<volatile int*>(slot + 1);
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (int idx = tid; idx < K * kH; idx += blockDim.x) {
+    const int k = idx / kH, o = idx % kH;
+    *reinterpret_cast<bf16*>(sWt + tc_canon(o, k, K)) = W[idx];
+  }
+  if (tid < kH) sB[tid] = bias[tid];
+  if (tid == 0) {
+    for (int s = 0; s < kTcStages; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(full + s)), "r"(kTcProducers)
+                   : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(empty + s)) : "memory");
+    }
+    for (int a = 0; a < kTcAcc; ++a) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(acc_full + a)) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_addr(acc_empty + a)) : "memory");
+    }
+    *stop = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (wid == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(slot)),
+                 "r"(kTcAcc * kH)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t taddr = *slot;
+  const int n = v.n;
+  const int tiles = static_cast<int>((static_cast<long long>(n) + kTcRows - 1) / kTcRows);
+  const int mine = tiles > static_cast<int>(blockIdx.x) ? (tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+
+  if (wid < kTcProducers) {
+    const int sub = lane / IO::G, q = lane % IO::G;
+    for (int i = 0; i < mine; ++i) {
+      const int s = i % kTcStages;
+      // stage s is free once the products of tile i - kTcStages completed
+      if (i >= kTcStages && !mb_wait_warp(smem_addr(empty + s), ((i / kTcStages) - 1) & 1, stop, err)) break;
+      unsigned char* X = sX + s * kStage;
+      const int r0 = (blockIdx.x + i * gridDim.x) * kTcRows;
+      for (int rl = wid * RPW + sub; rl < kTcRows; rl += kTcProducers * RPW) {
+        const int r = r0 + rl;
+        typename IO::T own{}, ab{};
+        if (r < n) {
+          own = IO::load(h, r, q);
+          float acc[IO::F] = {};
+          aggregate_row<D>(v, c, h, partial, r, q, acc);
+          ab = IO::pack(acc);
+          if (a_store != nullptr) IO::store(a_store, r, q, ab);
+        }
+        IO::put(reinterpret_cast<bf16*>(X + tc_canon(rl, q * IO::F, K)), own);
+        IO::put(reinterpret_cast<bf16*>(X + tc_canon(rl, D + q * IO::F, K)), ab);
+      }
+      // this warp's rows, visible to the tensor cores
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mb_arrive(smem_addr(full + s));
+    }
+  } else if (wid == kTcIssueWarp) {
+    if (lane == 0) {
+      for (int i = 0; i < mine; ++i) {
+        const int s = i % kTcStages, a = i % kTcAcc;
+        if (!mb_wait(smem_addr(full + s), (i / kTcStages) & 1, stop, err)) break;
+        // accumulator a is free once the epilogue read tile i - kTcAcc
+        if (i >= kTcAcc && !mb_wait(smem_addr(acc_empty + a), ((i / kTcAcc) - 1) & 1, stop, err)) break;
+        tc_fence_after();
+        tc_issue<K>(taddr + static_cast<uint32_t>(kH * a), smem_addr(sX + s * kStage), smem_addr(sWt));
+        tc_commit(smem_addr(empty + s));
+        tc_commit(smem_addr(acc_full + a));
+      }
+    }
+    __syncwarp();
+  } else {
+    const int quarter = wid & 3;  // the tensor-memory lanes this warp may read
+    for (int i = 0; i < mine; ++i) {
+      const int a = i % kTcAcc;
+      if (!mb_wait_warp(smem_addr(acc_full + a), (i / kTcAcc) & 1, stop, err)) break;
+      tc_fence_after();
+      const int row = (blockIdx.x + i * gridDim.x) * kTcRows + 32 * quarter + lane;
+      uint4* dst = reinterpret_cast<uint4*>(hout + static_cast<size_t>(row) * kH);
+#pragma unroll 1
+      for (int c0 = 0; c0 < kH; c0 += 16) {
+        uint32_t x[16];
+        tc_ld16(taddr + (static_cast<uint32_t>(32 * quarter) << 16) + static_cast<uint32_t>(kH * a + c0), x);
+        if (row < n) {
+#pragma unroll
+          for (int j = 0; j < 2; ++j) {
+            uint4 o;
+            o.x = pack_bf162(fmaxf(__uint_as_float(x[8 * j + 0]) + sB[c0 + 8 * j + 0], 0.0f),
+                             fmaxf(__uint_as_float(x[8 * j + 1]) + sB[c0 + 8 * j + 1], 0.0f));
+            o.y = pack_bf162(fmaxf(__uint_as_float(x[8 * j + 2]) + sB[c0 + 8 * j + 2], 0.0f),
+                             fmaxf(__uint_as_float(x[8 * j + 3]) + sB[c0 + 8 * j + 3], 0.0f));
+            o.z = pack_bf162(fmaxf(__uint_as_float(x[8 * j + 4]) + sB[c0 + 8 * j + 4], 0.0f),
+                             fmaxf(__uint_as_float(x[8 * j + 5]) + sB[c0 + 8 * j + 5], 0.0f));
+            o.w = pack_bf162(fmaxf(__uint_as_float(x[8 * j + 6]) + sB[c0 + 8 * j + 6], 0.0f),
+                             fmaxf(__uint_as_float(x[8 * j + 7]) + sB[c0 + 8 * j + 7], 0.0f));
+            dst[c0 / 8 + j] = o;
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mb_arrive(smem_addr(acc_empty + a));
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (wid == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kTcAcc * kH) : "memory");
+  }
+}
+
 // Head: z = h3 w_o + b_o. With labels y (+-1 by position): the loss G4 (sum
 // over rows, divided by n on the host), dz = -y sigmoid(-y z) / n, dh3 = dz w_o
 // and the head's gradients.
@@ -820,6 +1079,9 @@ struct ising_gnn {
   float* d_out = nullptr;  // logits in caller order (host copies)
   int64_t chunk_cap = 0;
   float* d_partial = nullptr;  // per heavy-row chunk: its partial sum (width 64)
+  int dense_path = ISING_GNN_DENSE_MMA_SYNC;  // forward layers' product
+  int* d_err = nullptr;                      // a tensor-core product that timed out
+  int tc_blocks[2] = {0, 0};                 // resident tcgen05 layer blocks per SM (D = 8, 64)
 };
 
 namespace {
@@ -843,8 +1105,8 @@ void free_work(ising_gnn* net) {
 
 void free_net(ising_gnn* net) {
   free_work(net);
-  void* ptrs[] = {net->d_params, net->d_m,  net->d_v,  net->d_grad, net->d_w0,
-                  net->d_w1,     net->d_w2, net->d_loss, net->d_partial};
+  void* ptrs[] = {net->d_params, net->d_m,  net->d_v,    net->d_grad,    net->d_w0,
+                  net->d_w1,     net->d_w2, net->d_loss, net->d_partial, net->d_err};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -1032,6 +1294,47 @@ int run_chunks(ising_gnn* net, const Ctx& x, const bf16* src) {
   return ISING_OK;
 }
 
+// One forward layer (aggregation fused with the product) on the chosen
+// dense path: tcgen05 with 128-row tiles, or mma.sync with 64-row tiles.
+template <int D>
+int run_layer(ising_gnn* net, const Ctx& x, const bf16* h, const bf16* W, const float* bias, bf16* a_store,
+              bf16* hout) {
+  const int n = x.v.n;
+  if (net->dense_path == ISING_GNN_DENSE_TCGEN05) {
+    const int smem = tc_layer_smem(D);
+    int& per_sm = net->tc_blocks[D == kH ? 1 : 0];
+    if (per_sm == 0) {
+      const void* fn = reinterpret_cast<const void*>(layer_fwd_tc_kernel<D>);
+      GNN_CUDA(net, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+      GNN_CUDA(net, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kTcThreads, smem));
+      // each block holds 128 of the SM's 512 tensor-memory columns
+      per_sm = std::max(1, std::min(per_sm, 4));
+    }
+    const long long tiles = (static_cast<long long>(n) + kTcRows - 1) / kTcRows;
+    const int grid = static_cast<int>(std::min<long long>(tiles, static_cast<long long>(x.sms) * per_sm));
+    if (grid > 0)
+      layer_fwd_tc_kernel<D><<<grid, kTcThreads, smem, x.st>>>(x.v, net->d_c, h, net->d_partial, W, bias, a_store,
+                                                               hout, net->d_err);
+  } else {
+    layer_fwd_kernel<D><<<(n + kTile - 1) / kTile, kLayerThreads, 0, x.st>>>(x.v, net->d_c, h, net->d_partial, W,
+                                                                            bias, a_store, hout);
+  }
+  net->launches++;
+  GNN_CUDA(net, cudaGetLastError());
+  return ISING_OK;
+}
+
+// A tensor-core product that timed out (read after the stream has synchronised).
+int check_err(ising_gnn* net) {
+  int e = 0;
+  GNN_CUDA(net, cudaMemcpy(&e, net->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e != 0) {
+    net->status = ISING_ETIMEOUT;
+    return ISING_ETIMEOUT;
+  }
+  return ISING_OK;
+}
+
 // Forward pass over the graph from its current spins; with labels (by
 // position in net->d_y) also the loss and dL/dh3 into net->d_dh[0], and the
 // aggregates a^l kept for the backward pass.
@@ -1052,22 +1355,18 @@ int run_forward(ising_gnn* net, const Ctx& x, bool with_labels) {
                                                              net->d_c);
   net->launches++;
   GNN_CUDA(net, cudaGetLastError());
-  const int tiles = (n + kTile - 1) / kTile;
   int rc = run_chunks<kF>(net, x, net->d_x);
   if (rc != ISING_OK) return rc;
-  layer_fwd_kernel<kF><<<tiles, kLayerThreads, 0, st>>>(x.v, net->d_c, net->d_x, net->d_partial, net->d_w0,
-                                                        net->d_params + kOffB0, with_labels ? net->d_a0 : nullptr,
-                                                        net->d_h[0]);
-  net->launches++;
-  GNN_CUDA(net, cudaGetLastError());
+  rc = run_layer<kF>(net, x, net->d_x, net->d_w0, net->d_params + kOffB0, with_labels ? net->d_a0 : nullptr,
+                     net->d_h[0]);
+  if (rc != ISING_OK) return rc;
   for (int l = 1; l <= 2; ++l) {
     rc = run_chunks<kH>(net, x, net->d_h[l - 1]);
     if (rc != ISING_OK) return rc;
-    layer_fwd_kernel<kH><<<tiles, kLayerThreads, 0, st>>>(
-        x.v, net->d_c, net->d_h[l - 1], net->d_partial, l == 1 ? net->d_w1 : net->d_w2,
-        net->d_params + (l == 1 ? kOffB1 : kOffB2), with_labels ? net->d_a[l - 1] : nullptr, net->d_h[l]);
-    net->launches++;
-    GNN_CUDA(net, cudaGetLastError());
+    rc = run_layer<kH>(net, x, net->d_h[l - 1], l == 1 ? net->d_w1 : net->d_w2,
+                       net->d_params + (l == 1 ? kOffB1 : kOffB2), with_labels ? net->d_a[l - 1] : nullptr,
+                       net->d_h[l]);
+    if (rc != ISING_OK) return rc;
   }
   if (with_labels) GNN_CUDA(net, cudaMemsetAsync(net->d_loss, 0, sizeof(double), st));
   head_kernel<<<grid_of(static_cast<long long>(n) * 32, 256, sms * 8), 256, 0, st>>>(
@@ -1149,6 +1448,7 @@ int forward_out(ising_gnn* net, const Ctx& x, float* out_logits, int on_device) 
     GNN_CUDA(net, cudaMemcpyAsync(out_logits, net->d_out, sizeof(float) * static_cast<size_t>(x.v.n),
                                   cudaMemcpyDeviceToHost, x.st));
     GNN_CUDA(net, cudaStreamSynchronize(x.st));
+    return check_err(net);
   }
   return ISING_OK;
 }
@@ -1158,7 +1458,7 @@ int read_loss(ising_gnn* net, const Ctx& x, float* out_loss) {
   GNN_CUDA(net, cudaMemcpyAsync(&l, net->d_loss, sizeof(double), cudaMemcpyDeviceToHost, x.st));
   GNN_CUDA(net, cudaStreamSynchronize(x.st));
   *out_loss = static_cast<float>(l / static_cast<double>(x.v.n));
-  return ISING_OK;
+  return check_err(net);
 }
 
 // The gradient's public tail: copy it and the loss out when asked.
@@ -1166,6 +1466,8 @@ int gradients_out(ising_gnn* net, const Ctx& x, float* out_loss, float* out_grad
   if (out_grad != nullptr) {
     GNN_CUDA(net, cudaMemcpyAsync(out_grad, net->d_grad, sizeof(float) * kNumParams, cudaMemcpyDeviceToHost, x.st));
     GNN_CUDA(net, cudaStreamSynchronize(x.st));
+    const int rc = check_err(net);
+    if (rc != ISING_OK) return rc;
   }
   if (out_loss != nullptr) return read_loss(net, x, out_loss);
   return ISING_OK;
@@ -1221,6 +1523,8 @@ int ising_gnn_create(const float* params, ising_gnn** out) {
     if ((e = dalloc(&net->d_w1, 2 * kH * kH)) != cudaSuccess) break;
     if ((e = dalloc(&net->d_w2, 2 * kH * kH)) != cudaSuccess) break;
     if ((e = dalloc(&net->d_loss, 1)) != cudaSuccess) break;
+    if ((e = dalloc(&net->d_err, 1)) != cudaSuccess) break;
+    if ((e = cudaMemset(net->d_err, 0, sizeof(int))) != cudaSuccess) break;
     if ((e = cudaMemset(net->d_m, 0, sizeof(float) * kNumParams)) != cudaSuccess) break;
     if ((e = cudaMemset(net->d_v, 0, sizeof(float) * kNumParams)) != cudaSuccess) break;
   } while (0);
@@ -1374,6 +1678,13 @@ int ising_gnn_warm_start(ising_gnn* net, ising_graph* g, int set_bias) {
   net->launches++;
   GNN_CUDA(net, cudaGetLastError());
   g->parity = 0;
+  return ISING_OK;
+}
+
+int ising_gnn_set_dense_path(ising_gnn* net, int path) {
+  if (net == nullptr) return ISING_EINVAL;
+  if (path != ISING_GNN_DENSE_TCGEN05 && path != ISING_GNN_DENSE_MMA_SYNC) return ISING_EINVAL;
+  net->dense_path = path;
   return ISING_OK;
 }
 

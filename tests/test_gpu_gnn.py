@@ -110,6 +110,60 @@ def test_logits_match_fp64_oracle(name, pseed):
     assert np.all(ratio <= 1e-2), (int(np.argmax(ratio)), float(ratio.max()))
 
 
+@pytest.mark.parametrize("name", sorted(GRAPHS))
+def test_tcgen05_and_mma_sync_layers_agree_and_match_the_oracle(name):
+    # the forward layers' products on the fifth-generation tensor cores
+    # (tcgen05, accumulator in tensor memory) and on mma.sync: the same bf16
+    # operands, fp32 sums in a different order
+    g = GRAPHS[name]()
+    s = _spins(g.n, 5)
+    params = synth.gnn_init_params(2)
+    out = {}
+    with P.ising_create(g.n, g.src, g.dst, g.w) as h, P.ising_gnn_create(params) as net:
+        P.ising_set_spins(h, s)
+        for path in (P.ISING_GNN_DENSE_TCGEN05, P.ISING_GNN_DENSE_MMA_SYNC):
+            P.ising_gnn_set_dense_path(net, path)
+            out[path] = P.ising_gnn_forward(net, h).astype(np.float64)
+        with pytest.raises(P.IsingError):
+            P.ising_gnn_set_dense_path(net, 7)
+    G = go.Graph(g.n, g.src, g.dst, g.w)
+    pe = effective_params(params)
+    d = go.unpack(pe)
+    z_rd, cache = go.forward(G, go.features(G, s), pe, storage="bf16")
+    t = np.abs(cache["h3"]) @ np.abs(d["wo"]) + abs(d["bo"][0])
+    for path, z in out.items():
+        ratio = np.abs(z - z_rd) / np.maximum(np.abs(z_rd), t / 2)
+        assert np.all(ratio <= 1e-2), (path, float(ratio.max()))
+    a, b = out[P.ISING_GNN_DENSE_TCGEN05], out[P.ISING_GNN_DENSE_MMA_SYNC]
+    assert np.all(np.abs(a - b) <= 1e-2 * np.maximum(np.abs(b), t / 2))
+    assert _norm_rel(a, b) <= 1e-3
+
+
+def test_tcgen05_pipeline_wraps_its_ring_on_a_large_graph():
+    # 150,001 vertices: 1,172 tiles of 128 rows (the last one 113 rows) over
+    # one persistent block per SM, so every block passes through its ring of
+    # shared-memory stages and its two accumulators several times
+    g = synth.er_graph(150_001, 10.0 / 150_000, 12, weights="int8")
+    s = _spins(g.n, 6)
+    params = synth.gnn_init_params(3)
+    out = {}
+    with P.ising_create(g.n, g.src, g.dst, g.w) as h, P.ising_gnn_create(params) as net:
+        P.ising_set_spins(h, s)
+        for path in (P.ISING_GNN_DENSE_TCGEN05, P.ISING_GNN_DENSE_MMA_SYNC):
+            P.ising_gnn_set_dense_path(net, path)
+            out[path] = P.ising_gnn_forward(net, h).astype(np.float64)
+    G = go.Graph(g.n, g.src, g.dst, g.w)
+    pe = effective_params(params)
+    d = go.unpack(pe)
+    z_rd, cache = go.forward(G, go.features(G, s), pe, storage="bf16")
+    t = np.abs(cache["h3"]) @ np.abs(d["wo"]) + abs(d["bo"][0])
+    for path, z in out.items():
+        ratio = np.abs(z - z_rd) / np.maximum(np.abs(z_rd), t / 2)
+        assert np.all(ratio <= 1e-2), (path, int(np.argmax(ratio)), float(ratio.max()))
+    a, b = out[P.ISING_GNN_DENSE_TCGEN05], out[P.ISING_GNN_DENSE_MMA_SYNC]
+    assert _norm_rel(a, b) <= 1e-3
+
+
 def test_logits_of_edgeless_and_single_vertex_graphs():
     params = synth.gnn_init_params(4)
     e = np.zeros(0, np.int32)
