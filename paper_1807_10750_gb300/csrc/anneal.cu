@@ -1244,15 +1244,19 @@ int ising_create(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, c
     }
     const size_t NELL = plan.ell_col.size();
     if (g->packed) {
-      for (size_t k = 0; k < NELL; ++k)
-        plan.ell_col[k] = plan.ell_col[k] < 0
-                              ? static_cast<int32_t>(static_cast<uint32_t>(hg.n) << 8)
-                              : static_cast<int32_t>((static_cast<uint32_t>(plan.ell_col[k]) << 8) |
-                                                     (static_cast<uint32_t>(plan.ell_w[k]) & 0xffu));
+      isingx::parallel_ranges(static_cast<int64_t>(NELL), int64_t(1) << 18, [&](int64_t lo, int64_t hi) {
+        for (int64_t k = lo; k < hi; ++k)
+          plan.ell_col[k] = plan.ell_col[k] < 0
+                                ? static_cast<int32_t>(static_cast<uint32_t>(hg.n) << 8)
+                                : static_cast<int32_t>((static_cast<uint32_t>(plan.ell_col[k]) << 8) |
+                                                       (static_cast<uint32_t>(plan.ell_w[k]) & 0xffu));
+      });
       if ((e = alloc_copy(&g->d_ell, plan.ell_col.data(), NELL, g->stream)) != cudaSuccess) break;
     } else {
-      for (size_t k = 0; k < NELL; ++k)
-        if (plan.ell_col[k] < 0) plan.ell_col[k] = hg.n;  // pad entry, weight 0
+      isingx::parallel_ranges(static_cast<int64_t>(NELL), int64_t(1) << 18, [&](int64_t lo, int64_t hi) {
+        for (int64_t k = lo; k < hi; ++k)
+          if (plan.ell_col[k] < 0) plan.ell_col[k] = hg.n;  // pad entry, weight 0
+      });
       if ((e = alloc_copy(&g->d_ell_col, plan.ell_col.data(), NELL, g->stream)) != cudaSuccess) break;
       if ((e = alloc_copy(&g->d_ell_w, plan.ell_w.data(), NELL, g->stream)) != cudaSuccess) break;
     }

@@ -54,11 +54,19 @@ class SpinBarrier {
 // First-fit colours of the two tiers, relative to each tier (the hubs from 0,
 // the other vertices from 0: the caller adds the hubs' colour count), equal to
 // the sequential first fit in `order`. A vertex's colour depends only on the
-// colours of its same-tier neighbours earlier in the order, so the vertices
-// are coloured level by level: a vertex joins the next level when its last
-// earlier same-tier neighbour has been coloured (a per-vertex countdown), and
-// the threads split each level. Returns false (nothing written) when no helper
-// thread could be started; the caller then colours sequentially.
+// colours of its same-tier neighbours earlier in the order.
+//
+// The hubs, the order's first vertices, are close to a clique on a power-law
+// graph: their dependencies form a chain hundreds of levels deep with one or
+// two hubs per level. So every hub's earlier hub neighbours are listed first
+// (all threads, by rank), and one thread then colours the hubs in order from
+// those lists.
+//
+// The other vertices are coloured level by level: a vertex joins the next
+// level when its last earlier same-tier neighbour has been coloured (a
+// per-vertex countdown), and the threads split each level. Returns false
+// (nothing written) when no helper thread could be started; the caller then
+// colours sequentially.
 bool colour_levels(size_t N, const int64_t* moff, const int32_t* mnb, const int32_t* deg,
                    const std::vector<int32_t>& order, int32_t maxdeg, int32_t* rel) {
   const int T = host_threads();
@@ -68,14 +76,49 @@ bool colour_levels(size_t N, const int64_t* moff, const int32_t* mnb, const int3
     for (int64_t i = lo; i < hi; ++i) rank[(size_t)order[(size_t)i]] = (int32_t)i;
   });
   auto hub = [&](size_t v) { return deg[v] >= kHubDegree; };
+  // the hub tier: the hubs hold ranks [0, X)
+  size_t X = 0;
+  while (X < N && hub((size_t)order[X])) ++X;
+  if (X > 0) {
+    std::vector<int64_t> hoff(X + 1, 0);  // the hubs' row lengths in rank order, for the split
+    for (size_t i = 0; i < X; ++i) {
+      const size_t v = (size_t)order[i];
+      hoff[i + 1] = hoff[i] + (moff[v + 1] - moff[v]);
+    }
+    std::vector<std::vector<int32_t>> earlier(X);
+    parallel_rows((int64_t)X, hoff.data(), [&](int64_t lo, int64_t hi) {
+      for (int64_t i = lo; i < hi; ++i) {
+        const size_t v = (size_t)order[(size_t)i];
+        std::vector<int32_t>& e = earlier[(size_t)i];
+        for (int64_t k = moff[v]; k < moff[v + 1]; ++k) {
+          const int32_t r = rank[(size_t)mnb[(size_t)k]];
+          if (r < i) e.push_back(r);  // a rank below i < X is a hub's
+        }
+      }
+    });
+    std::vector<int32_t> hc(X), mark((size_t)maxdeg + 2, -1);
+    for (size_t i = 0; i < X; ++i) {
+      const int32_t d = deg[(size_t)order[i]];
+      for (const int32_t r : earlier[i])
+        if (hc[(size_t)r] <= d) mark[(size_t)hc[(size_t)r]] = (int32_t)i;
+      int32_t c = 0;
+      while (mark[(size_t)c] == (int32_t)i) ++c;
+      hc[i] = c;
+      rel[(size_t)order[i]] = c;
+    }
+  }
+  // the other tier: countdowns of earlier same-tier neighbours
   std::unique_ptr<std::atomic<int32_t>[]> pending(new std::atomic<int32_t>[N]);
   parallel_ranges((int64_t)N, 1 << 14, [&](int64_t lo, int64_t hi) {
     for (int64_t v = lo; v < hi; ++v) {
       int32_t c = 0;
-      const bool hv = hub((size_t)v);
-      for (int64_t k = moff[v]; k < moff[v + 1]; ++k) {
-        const int32_t u = mnb[(size_t)k];
-        c += (hub((size_t)u) == hv && rank[(size_t)u] < rank[(size_t)v]) ? 1 : 0;
+      if (hub((size_t)v)) {
+        c = -1;  // coloured above
+      } else {
+        for (int64_t k = moff[v]; k < moff[v + 1]; ++k) {
+          const int32_t u = mnb[(size_t)k];
+          c += (!hub((size_t)u) && rank[(size_t)u] < rank[(size_t)v]) ? 1 : 0;
+        }
       }
       pending[(size_t)v].store(c, std::memory_order_relaxed);
     }
@@ -361,8 +404,8 @@ int build_host_graph(int32_t n, int64_t m, const int32_t* src, const int32_t* ds
   // sorted (positions in a row are distinct), in the key buffer's front.
   g.row_ptr.assign(N + 1, 0);
   for (size_t p = 0; p < N; ++p) g.row_ptr[p + 1] = g.row_ptr[p] + degree((size_t)g.perm[p]);
-  g.col.assign((size_t)g.nnz, 0);
-  g.w.assign((size_t)g.nnz, 0);
+  g.col.resize((size_t)g.nnz);  // every entry is written below
+  g.w.resize((size_t)g.nnz);
   parallel_rows((int64_t)N, g.row_ptr.data(), [&](int64_t lo, int64_t hi) {
     for (int64_t p = lo; p < hi; ++p) {
       const size_t x = (size_t)g.perm[(size_t)p];

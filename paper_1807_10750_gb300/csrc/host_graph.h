@@ -5,6 +5,9 @@
 
 #include <atomic>
 #include <cstdint>
+#include <memory>
+#include <new>
+#include <utility>
 #include <vector>
 
 #include "../../include/ising.h"
@@ -21,6 +24,27 @@ namespace isingx {
 //    and v_end = -(slot + 1) names the partial-sum slot that combines slices.
 struct WorkItem {
   int32_t v_begin, v_end, e_begin, e_end;
+};
+
+// An allocator whose resize leaves new elements uninitialised, for the large
+// arrays the build writes in full right after sizing them.
+template <typename T>
+struct NoInitAllocator : std::allocator<T> {
+  template <typename U>
+  struct rebind {
+    using other = NoInitAllocator<U>;
+  };
+  NoInitAllocator() = default;
+  template <typename U>
+  NoInitAllocator(const NoInitAllocator<U>&) noexcept {}
+  template <typename U>
+  void construct(U* p) noexcept {
+    ::new (static_cast<void*>(p)) U;
+  }
+  template <typename U, typename... Args>
+  void construct(U* p, Args&&... args) {
+    ::new (static_cast<void*>(p)) U(std::forward<Args>(args)...);
+  }
 };
 
 // Vertices with at least this many distinct neighbours are hubs (ising.h).
@@ -42,8 +66,8 @@ struct HostGraph {
   std::vector<int32_t> pos;          // original id -> position
   std::vector<int32_t> class_begin;  // num_colours + 1 positions
   std::vector<int32_t> row_ptr;      // n + 1, by position
-  std::vector<int32_t> col;          // nnz, neighbour positions
-  std::vector<int32_t> w;            // nnz
+  std::vector<int32_t, NoInitAllocator<int32_t>> col;  // nnz, neighbour positions
+  std::vector<int32_t, NoInitAllocator<int32_t>> w;    // nnz
 };
 
 struct WorkPlan {
