@@ -483,10 +483,10 @@ __device__ __forceinline__ void hub_light(const DevGraph& d, const HubArgs& h, c
 }
 
 // Rows between the light and the sliced sizes, 32 at a time: their CSR
-// entries are contiguous, streamed lane-strided kHubGroupLoads per lane at a
-// time; each lane finds its entries' rows among the 33 row offsets and adds
-// runs of one row's terms into that row's shared accumulator; lane l then
-// decides row l.
+// entries are contiguous, streamed 32 x kHubGroupLoads at a time, each lane
+// taking a block of consecutive entries; each lane finds its entries' rows
+// among the 33 row offsets and adds runs of one row's terms into that row's
+// shared accumulator; lane l then decides row l.
 template <bool PACKED>
 __device__ __forceinline__ void hub_group(const DevGraph& d, const HubArgs& h, const uint32_t* sb,
                                           int* scratch, const WorkItem& it, const SweepArgs& a,
@@ -503,16 +503,18 @@ __device__ __forceinline__ void hub_group(const DevGraph& d, const HubArgs& h, c
     __syncwarp();
     const int e0 = rp[0], e1 = rp[rows];
     for (int eb = e0; eb < e1; eb += 32 * kHubGroupLoads) {
+      // lane l takes the kHubGroupLoads consecutive entries from el: they
+      // fall in one or two rows, so few lanes add into the same row
+      const int el = eb + lane * kHubGroupLoads;
       Edge<PACKED> x[kHubGroupLoads];
 #pragma unroll
-      for (int u = 0; u < kHubGroupLoads; ++u) x[u].load(d, eb + lane + 32 * u, eb + lane + 32 * u < e1);
-      int e = eb + lane;
-      if (e < e1) {
-        // the row holding entry e: the largest r with rp[r] <= e
+      for (int u = 0; u < kHubGroupLoads; ++u) x[u].load(d, el + u, el + u < e1);
+      if (el < e1) {
+        // the row holding entry el: the largest r with rp[r] <= el
         int lo = 0, hi = rows - 1;
         while (lo < hi) {
           const int mid = (lo + hi + 1) >> 1;
-          if (rp[mid] <= e)
+          if (rp[mid] <= el)
             lo = mid;
           else
             hi = mid - 1;
@@ -520,7 +522,7 @@ __device__ __forceinline__ void hub_group(const DevGraph& d, const HubArgs& h, c
         int r = lo, run = 0;
 #pragma unroll
         for (int u = 0; u < kHubGroupLoads; ++u) {
-          e = eb + lane + 32 * u;
+          const int e = el + u;
           if (e < e1) {
             while (rp[r + 1] <= e) {
               if (run != 0) atomicAdd(acc + r, run);
@@ -575,6 +577,12 @@ __device__ __forceinline__ void hub_slice(const DevGraph& d, const HubArgs& h, c
       if (decide_bit(total, ob, pos_flip(h, a, v)) != ob) atomicXor(h.bits + (v >> 5), 1u << (v & 31));
     }
   }
+}
+
+static_assert(sizeof(WorkItem) == sizeof(int4), "a work item is one 16-byte load");
+__device__ __forceinline__ WorkItem load_item(const DevGraph& d, int i) {
+  const int4 x = __ldg(reinterpret_cast<const int4*>(d.items) + i);
+  return WorkItem{x.x, x.y, x.z, x.w};
 }
 
 template <bool PACKED>
@@ -717,12 +725,16 @@ __global__ void __launch_bounds__(kHubBlock, 1)
         int i = 0;
         if (lane == 0) i = atomicAdd(queue, 1);
         i = __shfl_sync(kFullMask, i, 0) + i0;
+        // the next item's descriptor is loaded before the current item runs
+        WorkItem cur = i < i1 ? load_item(d, i) : WorkItem{};
         while (i < i1) {
           int nxt = 0;
           if (lane == 0) nxt = atomicAdd(queue, 1);
           nxt = __shfl_sync(kFullMask, nxt, 0) + i0;
-          hub_item<PACKED>(d, h, sb, scratch, d.items[i], a, lane);
+          const WorkItem nx = nxt < i1 ? load_item(d, nxt) : WorkItem{};
+          hub_item<PACKED>(d, h, sb, scratch, cur, a, lane);
           i = nxt;
+          cur = nx;
         }
         barrier_arrive(bs, false);
         target += G - 1;
