@@ -99,21 +99,21 @@ def algorithmic_bytes_per_sweep(n: int, nnz: int, entry_bytes: int) -> int:
 # the sweeps. The entry holds only while the kernel sources hash to `sources`:
 # once they change the counters are stale and traffic is reported as null.
 NCU_TRAFFIC = {
-    "zipf1m": {"fixed": 96.6e6, "per_sweep": 12.16e6, "kernel": "hub_kernel", "engine": "hub",
+    "zipf1m": {"fixed": 97.8e6, "per_sweep": 11.99e6, "kernel": "hub_kernel", "engine": "hub",
                "files": ('hub.cuh', 'sweep.cuh', 'philox.cuh', 'anneal.cu'),
-               "sources": "1f88ea8dd020d858",
-               "how": "ncu 4- and 12-sweep captures: 145.31 MB and 242.61 MB (read + write); the "
+               "sources": "670f0ca302ce93b3",
+               "how": "ncu 4- and 12-sweep captures: 145.77 MB and 241.70 MB (read + write); the "
                       "CSR is read from DRAM once and then mostly served from L2"},
-    "torus1024": {"fixed": 31.87e6, "per_sweep": 3.97e3, "kernel": "halo_kernel",
+    "torus1024": {"fixed": 31.79e6, "per_sweep": 4.03e3, "kernel": "halo_kernel",
                   "engine": "halo",
                   "files": ('halo.cuh', 'halo_plan.cpp', 'host_graph.h', 'philox.cuh', 'sweep.cuh'),
-                  "sources": "6b2b7998a08a8823",
-                  "how": "ncu 20- and 40-sweep captures: 31.870 MB and 31.950 MB, so the "
+                  "sources": "6bf5d71760ec383b",
+                  "how": "ncu 20- and 40-sweep captures: 31.870 MB and 31.951 MB, so the "
                          "working set is read once and then stays in shared memory and L2"},
-    "batched": {"fixed": 0.1266e9, "per_sweep": 0.2073e9, "kernel": "batch_anneal_kernel",
+    "batched": {"fixed": 0.2126e9, "per_sweep": 0.2083e9, "kernel": "batch_anneal_kernel",
                 "files": ('batch.cu', 'philox.cuh'),
-                "sources": "4e515ffc2c5827dc",
-                "how": "ncu 20- and 60-sweep captures: 4.274 GB and 12.567 GB"},
+                "sources": "cb30dcc0eb10999b",
+                "how": "ncu 20- and 60-sweep captures: 4.379 GB and 12.710 GB"},
 }
 
 
@@ -680,11 +680,11 @@ def run_gnn(args, world, rank, P, torch, dist):
 # wavefronts (one wavefront moves up to 128 bytes) from ncu captures, slope
 # over the sweep count; valid while the kernel sources hash to `sources`.
 NCU_SMEM = {
-    "torus1024": {"wavefronts_per_sweep": 575_453,
+    "torus1024": {"wavefronts_per_sweep": 575_506,
                   "files": ('halo.cuh', 'halo_plan.cpp', 'host_graph.h', 'philox.cuh', 'sweep.cuh'),
-                  "sources": "6b2b7998a08a8823",
-                  "how": "l1tex__data_pipe_lsu_wavefronts_mem_shared.sum: 11,812,561 (20 sweeps) and "
-                         "23,321,622 (40 sweeps)"},
+                  "sources": "6bf5d71760ec383b",
+                  "how": "l1tex__data_pipe_lsu_wavefronts_mem_shared.sum: 11,810,305 (20 sweeps) and "
+                         "23,320,433 (40 sweeps)"},
 }
 
 
