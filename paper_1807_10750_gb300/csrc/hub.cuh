@@ -482,58 +482,42 @@ __device__ __forceinline__ void hub_light(const DevGraph& d, const HubArgs& h, c
   }
 }
 
-// Rows between the light and the sliced sizes, 32 at a time: their CSR
-// entries are contiguous, streamed 32 x kHubGroupLoads at a time, each lane
-// taking a block of consecutive entries; each lane finds its entries' rows
-// among the 33 row offsets and adds runs of one row's terms into that row's
-// shared accumulator; lane l then decides row l.
+// Rows between the light and the sliced sizes, 32 at a time: eight lanes per
+// row, four rows at a time. Lane q of a row's eight sums the row's entries
+// q, q + 8, q + 16, ... (kHubGroupLoads loads in flight), shuffles combine the
+// eight partial sums, and the row's field goes to the warp's shared scratch;
+// lane l then decides row l.
 template <bool PACKED>
 __device__ __forceinline__ void hub_group(const DevGraph& d, const HubArgs& h, const uint32_t* sb,
                                           int* scratch, const WorkItem& it, const SweepArgs& a,
                                           int lane) {
   int* rp = scratch;
   int* acc = scratch + 33;
+  const int sub = lane >> 3, q = lane & 7;
   for (int base = it.v_begin; base < it.v_end; base += 32) {
     const int rows = min(32, it.v_end - base);
     const bool own = lane < rows;
     if (own) rp[lane] = __ldg(d.row_ptr + base + lane);
     if (lane == 0) rp[rows] = __ldg(d.row_ptr + base + rows);
     const bool flip = own && pos_flip(h, a, base + lane);
-    acc[lane] = 0;
     __syncwarp();
-    const int e0 = rp[0], e1 = rp[rows];
-    for (int eb = e0; eb < e1; eb += 32 * kHubGroupLoads) {
-      // lane l takes the kHubGroupLoads consecutive entries from el: they
-      // fall in one or two rows, so few lanes add into the same row
-      const int el = eb + lane * kHubGroupLoads;
-      Edge<PACKED> x[kHubGroupLoads];
+    for (int r0 = 0; r0 < rows; r0 += 4) {
+      const int r = r0 + sub;
+      int f = 0;
+      if (r < rows) {
+        const int e1 = rp[r + 1];
+        for (int eb = rp[r] + q; eb < e1; eb += 8 * kHubGroupLoads) {
+          Edge<PACKED> x[kHubGroupLoads];
 #pragma unroll
-      for (int u = 0; u < kHubGroupLoads; ++u) x[u].load(d, el + u, el + u < e1);
-      if (el < e1) {
-        // the row holding entry el: the largest r with rp[r] <= el
-        int lo = 0, hi = rows - 1;
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (rp[mid] <= el)
-            lo = mid;
-          else
-            hi = mid - 1;
-        }
-        int r = lo, run = 0;
+          for (int u = 0; u < kHubGroupLoads; ++u) x[u].load(d, eb + 8 * u, eb + 8 * u < e1);
 #pragma unroll
-        for (int u = 0; u < kHubGroupLoads; ++u) {
-          const int e = el + u;
-          if (e < e1) {
-            while (rp[r + 1] <= e) {
-              if (run != 0) atomicAdd(acc + r, run);
-              run = 0;
-              ++r;
-            }
-            run += x[u].weight() * map_spin(sb, x[u].col());
-          }
+          for (int u = 0; u < kHubGroupLoads; ++u) f += x[u].weight() * map_spin(sb, x[u].col());
         }
-        if (run != 0) atomicAdd(acc + r, run);
       }
+      f += __shfl_xor_sync(kFullMask, f, 1);
+      f += __shfl_xor_sync(kFullMask, f, 2);
+      f += __shfl_xor_sync(kFullMask, f, 4);
+      if (q == 0 && r < rows) acc[r] = f;
     }
     __syncwarp();
     bool changed = false;
