@@ -99,10 +99,10 @@ def algorithmic_bytes_per_sweep(n: int, nnz: int, entry_bytes: int) -> int:
 # the sweeps. The entry holds only while the kernel sources hash to `sources`:
 # once they change the counters are stale and traffic is reported as null.
 NCU_TRAFFIC = {
-    "zipf1m": {"fixed": 97.8e6, "per_sweep": 11.99e6, "kernel": "hub_kernel", "engine": "hub",
+    "zipf1m": {"fixed": 99.3e6, "per_sweep": 11.61e6, "kernel": "hub_kernel", "engine": "hub",
                "files": ('hub.cuh', 'sweep.cuh', 'philox.cuh', 'anneal.cu'),
-               "sources": "670f0ca302ce93b3",
-               "how": "ncu 4- and 12-sweep captures: 145.77 MB and 241.70 MB (read + write); the "
+               "sources": "263febaf28510827",
+               "how": "ncu 4- and 12-sweep captures: 145.73 MB and 238.62 MB (read + write); the "
                       "CSR is read from DRAM once and then mostly served from L2"},
     "torus1024": {"fixed": 31.79e6, "per_sweep": 4.03e3, "kernel": "halo_kernel",
                   "engine": "halo",
