@@ -231,27 +231,74 @@ int build_host_graph(int32_t n, int64_t m, const int32_t* src, const int32_t* ds
   // Directed rows: every edge (u, v, w) becomes the entries v of row u and u
   // of row v, each held as the key (neighbour << 32) | (uint32) w; sorting
   // each row's keys then orders it by neighbour (then weight), so repeated
-  // neighbours are adjacent. On several threads each thread owns a
-  // contiguous range of rows, scans every edge and fills only its own rows,
-  // so no counter is shared and a row's entries arrive in edge order.
+  // neighbours are adjacent. A row's entries arrive in edge order.
+  //
+  // On several threads, when a counter per part and vertex fits in 2^26
+  // words: part t takes the edges [m t / P, m (t + 1) / P), counts its
+  // entries per row, the counts become each part's first slot in every row,
+  // and every part fills its own slots (each edge read twice in all).
+  // Otherwise each thread owns a contiguous range of rows, scans every edge
+  // and fills only its own rows.
   const int64_t parts = m >= 2 * kGrain ? host_threads() : 1;
-  auto part_lo = [&](int64_t t) { return (int64_t)N * t / parts; };
   std::vector<int64_t> off(N + 1, 0);
-  parallel_ranges(parts, 1, [&](int64_t t0, int64_t t1) {
-    for (int64_t t = t0; t < t1; ++t) {
-      const uint32_t lo = (uint32_t)part_lo(t), span = (uint32_t)(part_lo(t + 1) - part_lo(t));
-      for (int64_t e = 0; e < m; ++e) {
-        const uint32_t u = (uint32_t)src[e], v = (uint32_t)dst[e];
-        if (u - lo < span) ++off[(size_t)u + 1];
-        if (v - lo < span) ++off[(size_t)v + 1];
+  std::unique_ptr<uint64_t[]> key;  // scratch, left uninitialised (every slot is written before it is read)
+  if (parts > 1 && (uint64_t)parts * N <= (uint64_t(1) << 26)) {
+    auto edge_lo = [&](int64_t t) { return m * t / parts; };
+    std::unique_ptr<int32_t[]> cur(new int32_t[(size_t)parts * N]);
+    parallel_ranges(parts, 1, [&](int64_t t0, int64_t t1) {
+      for (int64_t t = t0; t < t1; ++t) {
+        int32_t* c = cur.get() + (size_t)t * N;
+        std::fill(c, c + N, 0);
+        for (int64_t e = edge_lo(t); e < edge_lo(t + 1); ++e) {
+          ++c[(size_t)src[e]];
+          ++c[(size_t)dst[e]];
+        }
       }
-    }
-  });
-  for (size_t i = 0; i < N; ++i) off[i + 1] += off[i];
-  const size_t D = (size_t)off[N];
-  // scratch, left uninitialised (every slot is written before it is read)
-  std::unique_ptr<uint64_t[]> key(new uint64_t[std::max<size_t>(D, 1)]);
-  {
+    });
+    parallel_ranges((int64_t)N, 1 << 14, [&](int64_t lo, int64_t hi) {
+      for (int64_t v = lo; v < hi; ++v) {
+        int64_t len = 0;
+        for (int64_t t = 0; t < parts; ++t) len += cur[(size_t)t * N + (size_t)v];
+        off[(size_t)v + 1] = len;
+      }
+    });
+    for (size_t i = 0; i < N; ++i) off[i + 1] += off[i];
+    // each part's first slot in every row (below 2m < 2^31)
+    parallel_ranges((int64_t)N, 1 << 14, [&](int64_t lo, int64_t hi) {
+      for (int64_t v = lo; v < hi; ++v) {
+        int64_t run = off[(size_t)v];
+        for (int64_t t = 0; t < parts; ++t) {
+          const int32_t c = cur[(size_t)t * N + (size_t)v];
+          cur[(size_t)t * N + (size_t)v] = (int32_t)run;
+          run += c;
+        }
+      }
+    });
+    key.reset(new uint64_t[std::max<size_t>((size_t)off[N], 1)]);
+    parallel_ranges(parts, 1, [&](int64_t t0, int64_t t1) {
+      for (int64_t t = t0; t < t1; ++t) {
+        int32_t* c = cur.get() + (size_t)t * N;
+        for (int64_t e = edge_lo(t); e < edge_lo(t + 1); ++e) {
+          const uint32_t u = (uint32_t)src[e], v = (uint32_t)dst[e], wt = (uint32_t)w[e];
+          key[(size_t)c[u]++] = ((uint64_t)v << 32) | wt;
+          key[(size_t)c[v]++] = ((uint64_t)u << 32) | wt;
+        }
+      }
+    });
+  } else {
+    auto part_lo = [&](int64_t t) { return (int64_t)N * t / parts; };
+    parallel_ranges(parts, 1, [&](int64_t t0, int64_t t1) {
+      for (int64_t t = t0; t < t1; ++t) {
+        const uint32_t lo = (uint32_t)part_lo(t), span = (uint32_t)(part_lo(t + 1) - part_lo(t));
+        for (int64_t e = 0; e < m; ++e) {
+          const uint32_t u = (uint32_t)src[e], v = (uint32_t)dst[e];
+          if (u - lo < span) ++off[(size_t)u + 1];
+          if (v - lo < span) ++off[(size_t)v + 1];
+        }
+      }
+    });
+    for (size_t i = 0; i < N; ++i) off[i + 1] += off[i];
+    key.reset(new uint64_t[std::max<size_t>((size_t)off[N], 1)]);
     std::vector<int64_t> fill(off.begin(), off.end() - 1);
     parallel_ranges(parts, 1, [&](int64_t t0, int64_t t1) {
       for (int64_t t = t0; t < t1; ++t) {
