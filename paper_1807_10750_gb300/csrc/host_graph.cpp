@@ -64,10 +64,13 @@ class SpinBarrier {
 //
 // The other vertices are coloured level by level: a vertex joins the next
 // level when its last earlier same-tier neighbour has been coloured (a
-// per-vertex countdown), and the threads split each level. Returns false
-// (nothing written) when no helper thread could be started; the caller then
-// colours sequentially.
-bool colour_levels(size_t N, const int64_t* moff, const int32_t* mnb, const int32_t* deg,
+// per-vertex countdown), and the threads split each level. Each such row is
+// first partitioned in place (neighbours with their weights): earlier
+// same-tier neighbours, then later same-tier ones, then the hubs, so a level
+// reads only the entries it needs. The rows' order is otherwise free: the
+// colour-ordered CSR sorts them again. Returns false (nothing written) when
+// no helper thread could be started; the caller then colours sequentially.
+bool colour_levels(size_t N, const int64_t* moff, int32_t* mnb, int32_t* mwt, const int32_t* deg,
                    const std::vector<int32_t>& order, int32_t maxdeg, int32_t* rel) {
   const int T = host_threads();
   if (T <= 1) return false;
@@ -107,18 +110,34 @@ bool colour_levels(size_t N, const int64_t* moff, const int32_t* mnb, const int3
       rel[(size_t)order[i]] = c;
     }
   }
-  // the other tier: countdowns of earlier same-tier neighbours
+  // the other tier: rows partitioned (earlier | later same-tier | hubs) and
+  // countdowns of earlier same-tier neighbours
   std::unique_ptr<std::atomic<int32_t>[]> pending(new std::atomic<int32_t>[N]);
+  std::vector<int32_t> n_earlier(N, 0), n_later(N, 0);  // per row: the first two parts' lengths
   parallel_ranges((int64_t)N, 1 << 14, [&](int64_t lo, int64_t hi) {
     for (int64_t v = lo; v < hi; ++v) {
-      int32_t c = 0;
-      if (hub((size_t)v)) {
-        c = -1;  // coloured above
-      } else {
-        for (int64_t k = moff[v]; k < moff[v + 1]; ++k) {
-          const int32_t u = mnb[(size_t)k];
-          c += (!hub((size_t)u) && rank[(size_t)u] < rank[(size_t)v]) ? 1 : 0;
+      int32_t c = -1;  // a hub: coloured above
+      if (!hub((size_t)v)) {
+        const int32_t rv = rank[(size_t)v];
+        int64_t i = moff[v], lt = moff[v], gt = moff[v + 1];
+        while (i < gt) {
+          const int32_t u = mnb[(size_t)i];
+          if (hub((size_t)u)) {
+            --gt;
+            std::swap(mnb[(size_t)i], mnb[(size_t)gt]);
+            std::swap(mwt[(size_t)i], mwt[(size_t)gt]);
+          } else if (rank[(size_t)u] < rv) {
+            std::swap(mnb[(size_t)i], mnb[(size_t)lt]);
+            std::swap(mwt[(size_t)i], mwt[(size_t)lt]);
+            ++lt;
+            ++i;
+          } else {
+            ++i;
+          }
         }
+        c = (int32_t)(lt - moff[v]);
+        n_earlier[(size_t)v] = c;
+        n_later[(size_t)v] = (int32_t)(gt - lt);
       }
       pending[(size_t)v].store(c, std::memory_order_relaxed);
     }
@@ -151,17 +170,17 @@ bool colour_levels(size_t N, const int64_t* moff, const int32_t* mnb, const int3
       out.clear();
       for (size_t i = lo; i < hi && i < frontier.size(); ++i) {
         const int32_t v = frontier[i];
-        const bool hv = hub((size_t)v);
         const int32_t d = deg[v];
-        const int32_t rv = rank[(size_t)v];
-        for (int64_t k = moff[v]; k < moff[(size_t)v + 1]; ++k) {
+        const int64_t k0 = moff[v];
+        const int64_t ke = k0 + n_earlier[(size_t)v];
+        for (int64_t k = k0; k < ke; ++k) {
           const int32_t u = mnb[(size_t)k];
-          if (hub((size_t)u) != hv) continue;
-          if (rank[(size_t)u] < rv) {
-            if (rel[u] <= d) mark[(size_t)rel[u]] = v;
-          } else if (pending[(size_t)u].fetch_sub(1, std::memory_order_relaxed) == 1) {
-            out.push_back(u);
-          }
+          if (rel[u] <= d) mark[(size_t)rel[u]] = v;
+        }
+        const int64_t kl = ke + n_later[(size_t)v];
+        for (int64_t k = ke; k < kl; ++k) {
+          const int32_t u = mnb[(size_t)k];
+          if (pending[(size_t)u].fetch_sub(1, std::memory_order_relaxed) == 1) out.push_back(u);
         }
         int32_t c = 0;
         while (mark[(size_t)c] == v) ++c;
@@ -388,7 +407,7 @@ int build_host_graph(int32_t n, int64_t m, const int32_t* src, const int32_t* ds
   // large graphs (8M entries and more; smaller ones colour in a few ms):
   // level by level on several threads, the same colours
   if (moff[N] >= (int64_t(1) << 23) &&
-      colour_levels(N, moff.data(), mnb.get(), mdeg.data(), order, maxdeg, g.colour.data())) {
+      colour_levels(N, moff.data(), mnb.get(), mwt.get(), mdeg.data(), order, maxdeg, g.colour.data())) {
     int32_t hubs = 0, hub_c = 0, other_c = -1;
     for (size_t v = 0; v < N; ++v) {
       if (degree(v) >= kHubDegree) {
