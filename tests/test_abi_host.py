@@ -133,6 +133,26 @@ def test_level_parallel_colouring_equals_oracle(P, make):
     assert np.array_equal(col, col2)
 
 
+def test_large_build_merges_repeated_and_cancelling_edges(P):
+    # more than 2^19 edges, so the directed rows are built by several threads
+    # from per-thread edge ranges; edges listed again in either orientation
+    # and exact cancellations (an edge plus its negation) must merge as the
+    # oracle merges them, which the colouring shows
+    g = synth.random_small_graph(300_000, 4.0 / 299_999, 31, weights="int8", duplicates=60_000)
+    k = 20_000
+    src = np.concatenate([g.src, g.dst[:k]]).astype(np.int32)
+    dst = np.concatenate([g.dst, g.src[:k]]).astype(np.int32)
+    w = np.concatenate([g.w, -g.w[:k]]).astype(np.int32)
+    assert src.size >= 1 << 19
+    C, col = P.ising_plan_colouring(g.n, src, dst, w)
+    C2, col2 = oracle.colouring(g.n, src, dst, w)
+    assert C == C2
+    assert np.array_equal(col, col2)
+    # the cancellations changed the graph: without them the colouring differs
+    C3, col3 = P.ising_plan_colouring(g.n, g.src, g.dst, g.w)
+    assert not np.array_equal(col, col3)
+
+
 def test_host_colouring_edgeless_and_single_vertex(P):
     e = np.zeros(0, np.int32)
     C, col = P.ising_plan_colouring(5, e, e, e)
